@@ -1,0 +1,211 @@
+"""Seeded synthetic workloads: model node lists and the random inputs drawn
+outside the method.
+
+This module holds data only -- node lists, constants and numpy draws of the
+quantities the method takes as inputs (per-toy mean sizes, per-toy generating
+parameters, seeds).  It holds none of the method's arithmetic (no pdf, no
+normalisation, no likelihood), so both the CUDA path and the CPU oracle may
+consume it.
+
+A model is a list of ``Node`` plus the index of its top pdf.  This mirrors the
+paper's computation graph (Sec. 1, Fig. 1): observables and parameters are
+leaves; functions/PDFs take them as inputs.  Input conventions per kind:
+
+=========  ==========================================================
+obs        no inputs; ``lo``/``hi`` = observable range; column = order of obs nodes
+param      no inputs; ``value`` = default start, ``lo``/``hi`` = fit bounds
+gauss      [obs, mu, sigma]
+exp        [obs, c]                       (exp(c x))
+gaussexp   [obs, tau, mu, sigma]          (decay (x) Gaussian resolution)
+cheb       [obs, c1, ..., cn]             (1 + sum c_k T_k, implicit c0 = 1)
+poly       [obs, a1, ..., an]             (1 + sum a_k x^k, implicit a0 = 1)
+sum        [pdf_1..pdf_n, f_1..f_{n-1}]   (last fraction = 1 - sum f)
+prod       [pdf_1..pdf_n]                 (disjoint observables)
+=========  ==========================================================
+
+The five workloads (sizes, true values and ranges) are the ones the
+benchmark configurations name; constants the configurations leave open
+(fit bounds, default starts, the product model's mass and angle shapes) are
+fixed here once.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+from typing import List, Sequence
+
+import numpy as np
+
+KINDS = ("obs", "param", "gauss", "exp", "gaussexp", "cheb", "poly", "sum", "prod")
+
+
+@dataclass(frozen=True)
+class Node:
+    kind: str
+    inputs: Sequence[int] = ()
+    value: float = 0.0
+    lo: float = 0.0
+    hi: float = 0.0
+    free: bool = False
+
+
+@dataclass
+class ModelSpec:
+    nodes: List[Node]
+    root: int
+    names: List[str] = field(default_factory=list)  # free-parameter names, theta order
+
+    @property
+    def n_free(self) -> int:
+        return sum(1 for n in self.nodes if n.kind == "param" and n.free)
+
+    @property
+    def n_obs(self) -> int:
+        return sum(1 for n in self.nodes if n.kind == "obs")
+
+    def defaults(self) -> np.ndarray:
+        return np.array([n.value for n in self.nodes if n.kind == "param" and n.free], dtype=np.float64)
+
+    def bounds(self) -> np.ndarray:
+        return np.array([[n.lo, n.hi] for n in self.nodes if n.kind == "param" and n.free], dtype=np.float64)
+
+
+class _Builder:
+    def __init__(self):
+        self.nodes: List[Node] = []
+        self.names: List[str] = []
+
+    def add(self, node: Node, name: str | None = None) -> int:
+        self.nodes.append(node)
+        if node.kind == "param" and node.free:
+            self.names.append(name or f"p{len(self.names)}")
+        return len(self.nodes) - 1
+
+    def obs(self, lo, hi):
+        return self.add(Node("obs", (), 0.0, lo, hi))
+
+    def param(self, name, value, lo, hi, free=True):
+        return self.add(Node("param", (), value, lo, hi, free), name)
+
+    def pdf(self, kind, *inputs):
+        return self.add(Node(kind, tuple(inputs)))
+
+    def spec(self, root):
+        return ModelSpec(self.nodes, root, self.names)
+
+
+# ------------------------------------------------------------------ models
+
+def gauss_poly1_model() -> ModelSpec:
+    """1-D f*Gauss(x; mu, sigma) + (1-f)*Poly1(x; a1) on x in [0, 10].
+    Parameter defaults are the fit start (mu=4.5, sigma=1, f=0.5, a1=0)."""
+    b = _Builder()
+    x = b.obs(0.0, 10.0)
+    mu = b.param("mu", 4.5, 0.0, 10.0)
+    sg = b.param("sigma", 1.0, 0.01, 10.0)
+    f = b.param("f", 0.5, 0.0, 1.0)
+    a1 = b.param("a1", 0.0, -0.1, 1.0)
+    g = b.pdf("gauss", x, mu, sg)
+    p = b.pdf("poly", x, a1)
+    return b.spec(b.pdf("sum", g, p, f))
+
+
+GAUSS_POLY1_TRUE = np.array([5.0, 0.5, 0.3, -0.05])
+
+
+def _decay_part(b: _Builder, t: int, start: Sequence[float]):
+    tau = b.param("tau", start[0], 0.1, 10.0)
+    mur = b.param("mu_r", start[1], -0.5, 0.5)
+    sgr = b.param("sigma_r", start[2], 0.005, 1.0)
+    c1 = b.param("c1", start[3], -1.0, 1.0)
+    c2 = b.param("c2", start[4], -1.0, 1.0)
+    fs = b.param("f_sig", start[5], 0.0, 1.0)
+    sig = b.pdf("gaussexp", t, tau, mur, sgr)
+    bkg = b.pdf("cheb", t, c1, c2)
+    return b.pdf("sum", sig, bkg, fs)
+
+
+DECAY_TRUE = np.array([1.5, 0.0, 0.05, -0.2, 0.05, 0.2])
+DECAY_START = np.array([1.0, 0.0, 0.1, 0.0, 0.0, 0.5])
+
+
+def decay_model() -> ModelSpec:
+    """Decay-time model on t in [0, 10]: f_sig * [exp(-t/tau) (x) Gauss(mu_r, sigma_r)]
+    + (1 - f_sig) * Chebychev2(c1, c2).  Defaults are the plain fit start."""
+    b = _Builder()
+    t = b.obs(0.0, 10.0)
+    return b.spec(_decay_part(b, t, DECAY_START))
+
+
+PROD3_TRUE = np.array([5.28, 0.015, 0.4, -0.3, *DECAY_TRUE, 0.1, 0.3])
+
+
+def prod3_model() -> ModelSpec:
+    """3-observable product: [mass m in [5.2,5.4]: f_m Gauss + (1-f_m) Chebychev1]
+    x [decay time t in [0,10]: the decay model] x [cos(theta) in [-1,1]: Poly2].
+    12 free parameters; defaults are the generating values."""
+    b = _Builder()
+    m = b.obs(5.2, 5.4)
+    t = b.obs(0.0, 10.0)
+    c = b.obs(-1.0, 1.0)
+    mum = b.param("mu_m", 5.28, 5.2, 5.4)
+    sgm = b.param("sigma_m", 0.015, 0.001, 0.1)
+    fm = b.param("f_m", 0.4, 0.0, 1.0)
+    cm = b.param("c_m", -0.3, -1.0, 1.0)
+    gm = b.pdf("gauss", m, mum, sgm)
+    bm = b.pdf("cheb", m, cm)
+    mass = b.pdf("sum", gm, bm, fm)
+    decay = _decay_part(b, t, DECAY_TRUE)
+    a1 = b.param("a1", 0.1, -1.0, 1.0)
+    a2 = b.param("a2", 0.3, -1.0, 1.0)
+    ang = b.pdf("poly", c, a1, a2)
+    return b.spec(b.pdf("prod", mass, decay, ang))
+
+
+# ------------------------------------------------------------------ configs
+
+SEED_BASE = 20031286
+
+
+@dataclass(frozen=True)
+class Workload:
+    name: str
+    model: str            # constructor name above
+    n_events: int         # per set (single-set workloads) or 0 for toy batches
+    n_sets: int
+    seed: int
+    f32_columns: bool = False
+
+
+WORKLOADS = {
+    "gauss_poly1_1e4": Workload("gauss_poly1_1e4", "gauss_poly1_model", 10_000, 1, SEED_BASE + 0),
+    "decay_1e7": Workload("decay_1e7", "decay_model", 10_000_000, 1, SEED_BASE + 1),
+    "decay_toys_4096": Workload("decay_toys_4096", "decay_model", 0, 4096, SEED_BASE + 2),
+    "prod3_1e8_f32": Workload("prod3_1e8_f32", "prod3_model", 100_000_000, 1, SEED_BASE + 3, True),
+    "learned_start": Workload("learned_start", "decay_model", 0, 10_000, SEED_BASE + 4),
+}
+
+
+def model_for(name: str) -> ModelSpec:
+    return globals()[name]()
+
+
+def toy_mean_sizes(n_sets: int, seed: int, lo: float = 1e3, hi: float = 1e5) -> np.ndarray:
+    """Per-toy mean event counts, log-uniform in [lo, hi] (numpy PCG64 stream)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    u = rng.random(n_sets)
+    return np.exp(np.log(lo) + u * (np.log(hi) - np.log(lo)))
+
+
+def toy_thetas(n_sets: int, seed: int, center: np.ndarray = DECAY_TRUE, rel: float = 0.3,
+               abs_width: np.ndarray | None = None) -> np.ndarray:
+    """Per-toy generating parameters drawn uniformly within +-rel of `center`.
+    Where a centre is 0 the half-width is taken from `abs_width` instead
+    (for the decay model mu_r = 0 uses +-0.3 sigma_r = +-0.015)."""
+    rng = np.random.Generator(np.random.PCG64(seed + 7919))
+    center = np.asarray(center, dtype=np.float64)
+    half = np.abs(center) * rel
+    if abs_width is None:
+        abs_width = np.where(center == 0.0, 0.015, 0.0)
+    half = np.where(center == 0.0, abs_width, half)
+    u = rng.random((n_sets, center.size))
+    return center + (2.0 * u - 1.0) * half
