@@ -1,0 +1,211 @@
+/*
+ * rf.h -- C ABI of the GB300 batched unbinned-likelihood library.
+ *
+ * The library evaluates, on one GPU, the likelihood of a PDF computation graph
+ * over every event of an unbinned dataset, as in "Making RooFit Ready for
+ * Run 3" (Hageboeck & Moneta, arXiv:2003.12861):
+ *   - Sec. 1: a model is a graph of observables, parameters, functions and
+ *     PDFs; every node evaluates to a real value; the top PDF gives the
+ *     probability of an event.
+ *   - Sec. 4: a likelihood needs the probability of each event; constant
+ *     (parameter-only) branches are computed once per parameter point; PDFs
+ *     are normalised; Sec. 4.1/4.2 evaluate all events of a node in one call
+ *     and reduce with simple reductions.
+ * NLL(theta) = -sum_i log( pdf(x_i; theta) / norm(theta) ), its gradient in
+ * the free parameters, fits (Sec. 1: "perform fits to data") and toy datasets
+ * (Sec. 1: RooStats toy Monte Carlo) are the calls below.
+ *
+ * Conventions (all calls):
+ *   - Every call returns rf_status; nothing throws across the ABI.  On error,
+ *     rf_last_error() returns a thread-local message.
+ *   - The caller owns every array it passes.  Host arrays are only read (or
+ *     written) during the call.  Handles (rf_model, rf_data, rf_mlp) are owned
+ *     by the library until the caller destroys them.
+ *   - Device pointers borrowed by rf_data_upload(cols_on_device=1) must stay
+ *     valid until rf_data_destroy.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).
+ *   - A handle is not thread-safe; distinct handles may be used from
+ *     different threads.
+ *   - Parameter vectors `theta` hold the FREE parameters in the order of the
+ *     PARAM nodes with is_free = 1; n_sets x n_free, row-major.
+ */
+#ifndef RF_H
+#define RF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  RF_OK = 0,
+  RF_E_INVALID = 1,       /* bad argument, bad graph, size beyond a limit      */
+  RF_E_OOM = 2,           /* device or host allocation failed                  */
+  RF_E_CUDA = 3,          /* a CUDA runtime call failed                        */
+  RF_E_DOMAIN = 4,        /* pdf <= 0 / not finite for some event, or theta
+                             outside a pdf's domain; that set's NLL is +inf    */
+  RF_E_NOT_CONVERGED = 5, /* a fit stopped before its tolerance                */
+  RF_E_TIMEOUT = 6        /* a bounded device wait gave up                     */
+} rf_status;
+
+/* Node kinds (Sec. 1: observables, parameters, functions/PDFs). */
+typedef enum {
+  RF_OBS = 0,      /* observable: lo/hi = range; its column = order among OBS nodes   */
+  RF_PARAM = 1,    /* parameter: value = default (fit start), lo/hi = fit bounds;
+                      is_free = 0 makes it a constant                                 */
+  RF_GAUSS = 2,    /* in = [obs, mu, sigma]           exp(-(x-mu)^2 / 2 sigma^2)      */
+  RF_EXP = 3,      /* in = [obs, c]                   exp(c x)                        */
+  RF_GAUSSEXP = 4, /* in = [obs, tau, mu, sigma]      exp(-t/tau) (t >= 0) convolved
+                      with a unit-area Gaussian(mu, sigma)  (Fig. 1: a convolution)   */
+  RF_CHEB = 5,     /* in = [obs, c1..cn], n <= 7      1 + sum c_k T_k(x'), x' = the
+                      range mapped to [-1, 1]                                         */
+  RF_POLY = 6,     /* in = [obs, a1..an], n <= 7      1 + sum a_k x^k (Fig. 1)        */
+  RF_SUM = 7,      /* in = [pdf_1..pdf_n, f_1..f_{n-1}], 2 <= n <= 4: sum f_j pdf_j
+                      with f_n = 1 - sum f_j; each pdf_j normalised on its own;
+                      all components over the same observables                        */
+  RF_PROD = 8      /* in = [pdf_1..pdf_n], n <= 8, over disjoint observables          */
+} rf_kind;
+
+typedef enum { RF_F64 = 0, RF_F32 = 1 } rf_dtype;
+
+/* One graph node.  Every PDF is normalised by its analytic integral over its
+ * observable's range [lo, hi] (Sec. 4: normalisation of PDFs). */
+typedef struct {
+  int32_t kind;   /* rf_kind */
+  int32_t n_in;   /* number of valid entries in `in` */
+  int32_t in[8];  /* input node indices */
+  double value;   /* PARAM: default value */
+  double lo, hi;  /* OBS: range; PARAM: bounds (lo >= hi: unbounded) */
+  int32_t is_free;/* PARAM: 1 = free parameter */
+} rf_node;
+
+typedef struct rf_model rf_model;
+typedef struct rf_data rf_data;
+typedef struct rf_mlp rf_mlp;
+
+/* ------------------------------------------------------------------ models */
+
+/* Validate a node list and compile it: topological order of the PDFs under
+ * `root`, observables bound to columns, free-parameter indices, the
+ * per-parameter-point plan (normalisation integrals, Sec. 4) and the
+ * per-event program of the fused kernel.  Limits: <= 64 nodes, <= 24 PDF
+ * nodes, <= 16 free parameters, <= 8 observables.  RF_E_INVALID on a graph
+ * the library cannot evaluate (cycle, PROD factors sharing an observable, SUM
+ * components over different observables, wrong arity, limits). */
+rf_status rf_model_create(const rf_node* nodes, int32_t n, int32_t root, rf_model** out);
+void rf_model_destroy(rf_model* m);
+int32_t rf_model_n_free(const rf_model* m);
+int32_t rf_model_n_obs(const rf_model* m);
+/* Writes a short description of the compiled event program (which fused
+ * kernel it runs on) into buf (NUL-terminated, at most cap bytes). */
+rf_status rf_model_describe(const rf_model* m, char* buf, int32_t cap);
+
+/* ------------------------------------------------------------------- data */
+
+/* Structure-of-arrays event columns, one per observable (Sec. 4.1: arrays of
+ * all entries instead of single values).  cols[c] points to n_events values of
+ * type dtype[c] (dtype NULL = all RF_F64).  Ragged sets (toy datasets):
+ * offsets[0..n_sets] with offsets[0] = 0 and offsets[n_sets] = n_events
+ * (offsets NULL and n_sets = 1 for one dataset).  cols_on_device = 0: host
+ * arrays, copied into library-owned device memory; = 1: device pointers,
+ * borrowed (not copied).  Events are kept in the given order. */
+rf_status rf_data_upload(const rf_model* m, const void* const* cols, const int32_t* dtype, int64_t n_events,
+                         const int64_t* offsets, int32_t n_sets, int32_t cols_on_device, rf_data** out);
+void rf_data_destroy(rf_data* d);
+int64_t rf_data_n_events(const rf_data* d);
+int32_t rf_data_n_sets(const rf_data* d);
+/* Copy events [i0, i1) of column `col` to host memory, widened to double. */
+rf_status rf_data_read(const rf_data* d, int32_t col, int64_t i0, int64_t i1, double* out);
+/* Copy the n_sets + 1 set offsets to host memory. */
+rf_status rf_data_offsets(const rf_data* d, int64_t* out);
+
+/* ------------------------------------------------------------- likelihood */
+
+/* NLL of every set: nll[s] = -sum_{i in set s} log p_i(theta_s) (Sec. 4:
+ * "the probability of observing each event"), non-extended.  theta and nll
+ * are HOST arrays (n_sets x n_free, n_sets).  The sum is deterministic: it
+ * is a fixed tree over 4096-event chunks (in-chunk lane sums, then
+ * compensated two-sum merges), independent of launch shape.  A set with an
+ * event whose pdf is <= 0 or not finite gets nll = +inf and the call returns
+ * RF_E_DOMAIN.  Synchronous on `stream`. */
+rf_status rf_nll(const rf_model* m, const rf_data* d, const double* theta, double* nll, void* stream);
+
+/* NLL and its gradient in the free parameters, from one pass over the events
+ * (adjoint of the graph in the same kernel).  grad: HOST, n_sets x n_free. */
+rf_status rf_nll_grad(const rf_model* m, const rf_data* d, const double* theta, double* nll, double* grad,
+                      void* stream);
+
+/* Device-resident, asynchronous form of rf_nll_grad for CUDA-graph capture
+ * and pipelines: d_theta (n_sets x n_free) and d_out (n_sets x (1 + n_free):
+ * nll then gradient) are DEVICE pointers; d_flags (n_sets int32, device)
+ * receives the count of events with pdf <= 0 / not finite.  Launches only;
+ * never synchronises or allocates after the first call for this (m, d). */
+rf_status rf_nll_grad_async(const rf_model* m, const rf_data* d, const double* d_theta, double* d_out,
+                            int32_t* d_flags, void* stream);
+
+/* Per-chunk partial sums of log p_i (the first level of the reduction), for
+ * checking a sample of chunks against an independent evaluation: out[c] for
+ * chunk c of set `set` (4096 events each, the last one ragged), at most
+ * max_chunks values.  *n_chunks receives the set's chunk count. */
+rf_status rf_nll_chunks(const rf_model* m, const rf_data* d, const double* theta, int32_t set, double* out,
+                        int32_t max_chunks, int32_t* n_chunks);
+
+/* Tile shape of the fused event kernel: threads per block (128, 256 or 512)
+ * and resident blocks per SM for the persistent grid.  0 = library choice.
+ * The NLL does not depend on it (bitwise). */
+rf_status rf_set_launch(rf_model* m, int32_t threads_per_block, int32_t blocks_per_sm);
+
+/* ------------------------------------------------------------------- fits */
+
+typedef struct {
+  double tol_edm;       /* stop when EDM = g^T H g / 2 < tol_edm (default 1e-7)   */
+  int32_t max_evals;    /* per set (default 1000)                                 */
+  int32_t want_cov;     /* 1: covariance from the Hessian at the minimum          */
+  int32_t reserved[2];
+} rf_fit_opts;
+
+/* Maximum-likelihood fit of every set (Sec. 1: fits).  Quasi-Newton (BFGS)
+ * on the host over internal coordinates (bounded parameters through
+ * theta = lo + (hi-lo)(sin phi + 1)/2), strong-Wolfe line search; every
+ * evaluation of all still-active sets is one device pass (n_sets > 1: the
+ * batched toy fit).  theta0: HOST n_sets x n_free or NULL (the PARAM
+ * defaults).  Outputs (HOST): theta_hat (n_sets x n_free), nll_min (n_sets),
+ * cov (n_sets x n_free^2, or NULL), n_evals (n_sets), fit_status (n_sets:
+ * rf_status per set).  Returns RF_OK when the call ran, even if some sets did
+ * not converge (see fit_status). */
+rf_status rf_fit(const rf_model* m, const rf_data* d, const double* theta0, const rf_fit_opts* opts,
+                 double* theta_hat, double* nll_min, double* cov, int32_t* n_evals, int32_t* fit_status);
+
+/* ------------------------------------------------------------------- toys */
+
+/* Generate n_sets toy datasets on the device (Sec. 1: toy Monte Carlo).
+ * theta: HOST, n_sets x n_free if theta_per_set, else one vector for all sets
+ * (NULL = defaults).  mean_n: HOST, n_sets expected sizes; poisson = 1 draws
+ * N_s ~ Poisson(mean_n[s]) (PTRS of Hoermann 1993 for mean >= 10, inversion
+ * below), poisson = 0 uses round(mean_n[s]).  Events are drawn by
+ * accept-reject, independently for each factor of a PROD at the root, from
+ * Philox4x32-10 (Salmon et al., SC'11) with key = (seed, seed >> 32) and
+ * counter = (event, attempt, set, factor); the Poisson draw uses counter
+ * (iteration, 0, set, 0xFFFFFFFF).  dtype: per column (NULL = RF_F64); an
+ * RF_F32 column stores the double draw rounded to float.  *out is a new
+ * rf_data owning its device memory. */
+rf_status rf_generate_toys(const rf_model* m, const double* theta, int32_t theta_per_set, uint64_t seed,
+                           int32_t n_sets, const double* mean_n, int32_t poisson, const int32_t* dtype,
+                           rf_data** out);
+
+/* Per-set 64-bin histogram of column `col` over its observable range,
+ * normalised by the set's event count: bin = floor((x - lo) * (64/(hi - lo))),
+ * clamped to [0, 63].  d_out: DEVICE float, n_sets x 64. */
+rf_status rf_hist64(const rf_model* m, const rf_data* d, int32_t col, float* d_out, void* stream);
+
+/* -------------------------------------------------------------- messages */
+
+const char* rf_last_error(void);
+const char* rf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RF_H */

@@ -1,0 +1,226 @@
+"""Python face of the C ABI: models, datasets, NLL and gradient, fits, toys.
+
+Argument marshalling only -- every step of the computation runs in
+librfgpu.so.  PyTorch supplies device memory and streams where a caller
+wants device-resident buffers (Data.from_torch, nll_grad_async)."""
+from __future__ import annotations
+
+import ctypes as C
+from typing import Sequence
+
+import numpy as np
+
+from . import _lib as L
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return C.c_void_p(stream.cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+def make_nodes(nodes) -> "C.Array":
+    arr = (L.rf_node * len(nodes))()
+    for i, nd in enumerate(nodes):
+        r = arr[i]
+        r.kind = L.KIND[nd.kind]
+        r.n_in = len(nd.inputs)
+        for j, v in enumerate(nd.inputs):
+            r.in_[j] = v
+        r.value, r.lo, r.hi = float(nd.value), float(nd.lo), float(nd.hi)
+        r.is_free = 1 if nd.free else 0
+    return arr
+
+
+class Model:
+    """A compiled model (rf_model_create)."""
+
+    def __init__(self, nodes, root: int):
+        lib = L.load()
+        arr = make_nodes(nodes)
+        h = C.c_void_p()
+        L.check(lib.rf_model_create(arr, len(nodes), root, C.byref(h)))
+        self._h = h
+        self.nodes = list(nodes)
+        self.root = root
+        self.n_free = lib.rf_model_n_free(h)
+        self.n_obs = lib.rf_model_n_obs(h)
+
+    @classmethod
+    def from_spec(cls, spec):
+        return cls(spec.nodes, spec.root)
+
+    def describe(self) -> str:
+        buf = C.create_string_buffer(512)
+        L.check(L.load().rf_model_describe(self._h, buf, 512))
+        return buf.value.decode()
+
+    def set_launch(self, threads_per_block: int = 0, blocks_per_sm: int = 0):
+        L.check(L.load().rf_set_launch(self._h, threads_per_block, blocks_per_sm))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            L.load().rf_model_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+
+class Data:
+    """Event columns on the device (rf_data_upload / rf_generate_toys)."""
+
+    def __init__(self, handle, model: Model, keep=None):
+        self._h = handle
+        self.model = model
+        self._keep = keep  # borrowed device buffers must outlive the handle
+        lib = L.load()
+        self.n_events = lib.rf_data_n_events(handle)
+        self.n_sets = lib.rf_data_n_sets(handle)
+
+    @classmethod
+    def upload(cls, model: Model, cols: Sequence[np.ndarray], offsets=None, f32: Sequence[bool] | None = None):
+        lib = L.load()
+        n_obs = model.n_obs
+        if len(cols) != n_obs:
+            raise ValueError(f"expected {n_obs} columns")
+        f32 = f32 or [c.dtype == np.float32 for c in cols]
+        conv = [np.ascontiguousarray(c, dtype=np.float32 if f else np.float64) for c, f in zip(cols, f32)]
+        n = len(conv[0]) if conv else 0
+        ptrs = (C.c_void_p * max(1, n_obs))(*[c.ctypes.data for c in conv])
+        dt = (C.c_int32 * max(1, n_obs))(*[L.RF_F32 if f else L.RF_F64 for f in f32])
+        if offsets is None:
+            off_p, n_sets = None, 1
+        else:
+            off = np.ascontiguousarray(offsets, dtype=np.int64)
+            off_p, n_sets = off.ctypes.data_as(C.POINTER(C.c_int64)), len(off) - 1
+        h = C.c_void_p()
+        L.check(lib.rf_data_upload(model._h, ptrs, dt, n, off_p, n_sets, 0, C.byref(h)))
+        return cls(h, model)
+
+    @classmethod
+    def from_torch(cls, model: Model, cols, offsets=None):
+        """Borrow CUDA tensors (float32/float64, contiguous) as columns."""
+        import torch
+
+        lib = L.load()
+        cols = [c.contiguous() for c in cols]
+        for c in cols:
+            if not c.is_cuda or c.dtype not in (torch.float32, torch.float64):
+                raise ValueError("columns must be CUDA float32/float64 tensors")
+        ptrs = (C.c_void_p * max(1, len(cols)))(*[c.data_ptr() for c in cols])
+        dt = (C.c_int32 * max(1, len(cols)))(*[L.RF_F32 if c.dtype == torch.float32 else L.RF_F64 for c in cols])
+        n = cols[0].numel() if cols else 0
+        if offsets is None:
+            off_p, n_sets, off = None, 1, None
+        else:
+            off = np.ascontiguousarray(offsets, dtype=np.int64)
+            off_p, n_sets = off.ctypes.data_as(C.POINTER(C.c_int64)), len(off) - 1
+        h = C.c_void_p()
+        L.check(lib.rf_data_upload(model._h, ptrs, dt, n, off_p, n_sets, 1, C.byref(h)))
+        return cls(h, model, keep=cols)
+
+    def read(self, col: int, i0: int = 0, i1: int | None = None) -> np.ndarray:
+        i1 = self.n_events if i1 is None else i1
+        out = np.zeros(i1 - i0)
+        L.check(L.load().rf_data_read(self._h, col, i0, i1, _dp(out)))
+        return out
+
+    def offsets(self) -> np.ndarray:
+        out = np.zeros(self.n_sets + 1, dtype=np.int64)
+        L.check(L.load().rf_data_offsets(self._h, out.ctypes.data_as(C.POINTER(C.c_int64))))
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            L.load().rf_data_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+
+def _theta(model: Model, data: Data, theta):
+    th = _f64(theta).reshape(-1)
+    if th.size == model.n_free and data.n_sets > 1:
+        th = np.tile(th, data.n_sets)
+    if th.size != model.n_free * data.n_sets:
+        raise ValueError("theta must hold n_sets x n_free values")
+    return th
+
+
+def nll(model: Model, data: Data, theta, stream=None, allow_domain=False):
+    th = _theta(model, data, theta)
+    out = np.zeros(data.n_sets)
+    allow = (L.RF_OK, L.RF_E_DOMAIN) if allow_domain else (L.RF_OK,)
+    L.check(L.load().rf_nll(model._h, data._h, _dp(th), _dp(out), _stream(stream)), allow)
+    return out if data.n_sets > 1 else out[0]
+
+
+def nll_grad(model: Model, data: Data, theta, stream=None, allow_domain=False):
+    th = _theta(model, data, theta)
+    out = np.zeros(data.n_sets)
+    g = np.zeros(data.n_sets * max(1, model.n_free))
+    allow = (L.RF_OK, L.RF_E_DOMAIN) if allow_domain else (L.RF_OK,)
+    L.check(L.load().rf_nll_grad(model._h, data._h, _dp(th), _dp(out), _dp(g), _stream(stream)), allow)
+    g = g[: data.n_sets * model.n_free].reshape(data.n_sets, model.n_free)
+    return (out, g) if data.n_sets > 1 else (out[0], g[0])
+
+
+def nll_grad_async(model: Model, data: Data, d_theta, d_out, d_flags, stream=None):
+    """Device-resident pass: torch tensors (float64 theta, float64 out of
+    n_sets x (1 + n_free), int32 flags); launches only."""
+    L.check(L.load().rf_nll_grad_async(model._h, data._h, C.c_void_p(d_theta.data_ptr()),
+                                       C.c_void_p(d_out.data_ptr()), C.c_void_p(d_flags.data_ptr()),
+                                       _stream(stream)))
+
+
+def nll_chunks(model: Model, data: Data, theta, set_index: int = 0, max_chunks: int = 1 << 20):
+    th = _theta(model, data, theta)
+    out = np.zeros(max_chunks)
+    n = C.c_int32()
+    L.check(L.load().rf_nll_chunks(model._h, data._h, _dp(th), set_index, _dp(out), max_chunks, C.byref(n)),
+            (L.RF_OK, L.RF_E_DOMAIN))
+    return out[: min(n.value, max_chunks)]
+
+
+def fit(model: Model, data: Data, theta0=None, tol_edm: float = 1e-7, max_evals: int = 1000, want_cov=True):
+    S, P = data.n_sets, model.n_free
+    th0 = None if theta0 is None else _theta(model, data, theta0)
+    opts = L.rf_fit_opts(tol_edm, max_evals, 1 if want_cov else 0)
+    th = np.zeros(S * P)
+    nl = np.zeros(S)
+    cov = np.zeros(S * P * P) if want_cov else None
+    ne = np.zeros(S, dtype=np.int32)
+    fs = np.zeros(S, dtype=np.int32)
+    ip = C.POINTER(C.c_int32)
+    L.check(L.load().rf_fit(model._h, data._h, _dp(th0) if th0 is not None else None, C.byref(opts), _dp(th),
+                            _dp(nl), _dp(cov) if want_cov else None, ne.ctypes.data_as(ip), fs.ctypes.data_as(ip)))
+    return dict(theta=th.reshape(S, P), nll=nl, cov=None if cov is None else cov.reshape(S, P, P), n_evals=ne,
+                status=fs)
+
+
+def generate_toys(model: Model, theta, seed: int, mean_n, poisson: bool = True, f32: Sequence[bool] | None = None):
+    mean_n = _f64(np.atleast_1d(mean_n))
+    S = len(mean_n)
+    th = None if theta is None else _f64(theta).reshape(-1)
+    per_set = 1 if (th is not None and th.size == S * model.n_free and S > 1) else 0
+    dt = None
+    if f32 is not None:
+        dt = (C.c_int32 * model.n_obs)(*[L.RF_F32 if f else L.RF_F64 for f in f32])
+    h = C.c_void_p()
+    L.check(L.load().rf_generate_toys(model._h, _dp(th) if th is not None else None, per_set, seed, S,
+                                      _dp(mean_n), 1 if poisson else 0, dt, C.byref(h)))
+    return Data(h, model)
+
+
+def hist64(model: Model, data: Data, col: int, d_out, stream=None):
+    L.check(L.load().rf_hist64(model._h, data._h, col, C.c_void_p(d_out.data_ptr()), _stream(stream)))

@@ -1,0 +1,403 @@
+// C ABI: models, datasets, likelihood entry points.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "api_internal.h"
+#include "nll_kernels.cuh"
+
+namespace rf {
+
+static thread_local std::string g_error;
+void set_error(const std::string& msg) { g_error = msg; }
+
+bool cuda_ok(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return true;
+  set_error(std::string(what) + ": " + cudaGetErrorString(e));
+  return false;
+}
+
+int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
+  }
+  return n;
+}
+
+DevBuf::~DevBuf() { release(); }
+void DevBuf::release() {
+  if (p) cudaFree(p);
+  p = nullptr;
+  bytes = 0;
+}
+bool DevBuf::ensure(size_t b) {
+  if (b <= bytes && p) return true;
+  release();
+  if (b == 0) b = 8;
+  if (cudaMalloc(&p, b) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+    set_error("device allocation of " + std::to_string(b) + " bytes failed");
+    return false;
+  }
+  bytes = b;
+  return true;
+}
+
+HostBuf::~HostBuf() {
+  if (p) cudaFreeHost(p);
+}
+bool HostBuf::ensure(size_t b) {
+  if (b <= bytes && p) return true;
+  if (p) cudaFreeHost(p);
+  p = nullptr;
+  bytes = 0;
+  if (b == 0) b = 8;
+  if (cudaMallocHost(&p, b) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+    set_error("pinned host allocation failed");
+    return false;
+  }
+  bytes = b;
+  return true;
+}
+
+// Radix-32 tree over `chunks` leaves: total node count.
+int64_t tree_nodes(int64_t chunks) {
+  if (chunks <= 0) return 0;
+  int64_t total = chunks, n = chunks;
+  while (n > 1) {
+    n = (n + kRadix - 1) / kRadix;
+    total += n;
+  }
+  return total;
+}
+
+// Build the (set, chunk) work items and tree bases for a list of active sets.
+bool build_plan(const rf_data* d, const std::vector<int32_t>& sets, Plan* plan) {
+  std::vector<int2> items;
+  for (int32_t s : sets) {
+    const int64_t c = d->chunks[s];
+    for (int64_t k = 0; k < c; ++k) items.push_back(make_int2(s, (int)k));
+  }
+  plan->n_active = (int)sets.size();
+  plan->n_items = (int)items.size();
+  plan->host_sets = sets;
+  if (!plan->sets.ensure(sizeof(int32_t) * std::max<size_t>(1, sets.size()))) return false;
+  if (!plan->items.ensure(sizeof(int2) * std::max<size_t>(1, items.size()))) return false;
+  if (!sets.empty() && !cuda_ok(cudaMemcpy(plan->sets.p, sets.data(), sizeof(int32_t) * sets.size(), cudaMemcpyHostToDevice), "plan upload"))
+    return false;
+  if (!items.empty() && !cuda_ok(cudaMemcpy(plan->items.p, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice), "plan upload"))
+    return false;
+  return true;
+}
+
+bool ensure_workspace(const rf_model* m, rf_data* d) {
+  Workspace& w = d->ws;
+  const Program& P = m->m.prog;
+  const int Q = 1 + P.n_slots;
+  if (w.ready && w.n_const == P.n_const && w.n_free == P.n_free && w.Q == Q) return true;
+  const size_t S = d->n_sets;
+  bool ok = w.consts.ensure(sizeof(double) * S * std::max(1, P.n_const)) &&
+            w.theta.ensure(sizeof(double) * S * std::max(1, P.n_free)) &&
+            w.out.ensure(sizeof(double) * S * (1 + P.n_free)) && w.flags.ensure(sizeof(int32_t) * S) &&
+            w.tree.ensure(sizeof(double) * std::max<int64_t>(1, d->total_nodes) * 2 * Q) &&
+            w.tree_bad.ensure(sizeof(int32_t) * std::max<int64_t>(1, d->total_nodes)) &&
+            w.tickets.ensure(sizeof(int32_t) * std::max<int64_t>(1, d->total_nodes)) &&
+            w.counter.ensure(sizeof(int32_t)) && w.h_theta.ensure(sizeof(double) * S * std::max(1, P.n_free)) &&
+            w.h_out.ensure(sizeof(double) * S * (1 + P.n_free)) && w.h_flags.ensure(sizeof(int32_t) * S);
+  if (!ok) return false;
+  if (!cuda_ok(cudaMemset(w.tickets.p, 0, sizeof(int32_t) * std::max<int64_t>(1, d->total_nodes)), "ticket reset"))
+    return false;
+  if (!d->all_plan_ready) {
+    std::vector<int32_t> all(d->n_sets);
+    for (int s = 0; s < d->n_sets; ++s) all[s] = s;
+    if (!build_plan(d, all, &d->all_plan)) return false;
+    d->all_plan_ready = true;
+  }
+  w.n_const = P.n_const;
+  w.n_free = P.n_free;
+  w.Q = Q;
+  w.ready = true;
+  return true;
+}
+
+Pass make_pass(const rf_model* m, rf_data* d, const Plan& plan, const double* d_theta, double* d_out,
+               int32_t* d_flags, bool grad) {
+  Workspace& w = d->ws;
+  Pass p{};
+  p.offsets = (const int64_t*)d->offsets_dev.p;
+  p.sets = (const int32_t*)plan.sets.p;
+  p.n_active = plan.n_active;
+  p.items = (const int2*)plan.items.p;
+  p.n_items = plan.n_items;
+  p.tree_base = (const int64_t*)d->tree_base_dev.p;
+  p.theta = d_theta;
+  p.consts = (double*)w.consts.p;
+  p.tree = (double*)w.tree.p;
+  p.tree_bad = (int32_t*)w.tree_bad.p;
+  p.tickets = (int32_t*)w.tickets.p;
+  p.counter = (int32_t*)w.counter.p;
+  p.out = d_out;
+  p.flags = d_flags;
+  p.Q = grad ? 1 + m->m.prog.n_slots : 1;
+  p.want_grad = grad ? 1 : 0;
+  return p;
+}
+
+Columns make_columns(const rf_data* d) {
+  Columns c{};
+  for (int i = 0; i < d->n_obs; ++i) {
+    c.ptr[i] = d->cols[i];
+    c.is_f32[i] = d->dtype[i] == RF_F32;
+  }
+  return c;
+}
+
+bool launch_pass(const rf_model* m, rf_data* d, const Plan& plan, const double* d_theta, double* d_out,
+                 int32_t* d_flags, bool grad, cudaStream_t st) {
+  const Pass pass = make_pass(m, d, plan, d_theta, d_out, d_flags, grad);
+  launch_param_point(m->m.prog, pass, st);
+  launch_events(m->m.prog, m->m.shape, make_columns(d), pass, m->m.threads_per_block, m->m.blocks_per_sm,
+                sm_count(), st);
+  return cuda_ok(cudaGetLastError(), "kernel launch");
+}
+
+// Host-buffer evaluation of the sets in `plan` (theta/out indexed by set).
+rf_status eval_host(const rf_model* m, rf_data* d, const Plan& plan, const double* theta, double* nll,
+                    double* grad, cudaStream_t st) {
+  if (!ensure_workspace(m, d)) return RF_E_OOM;
+  Workspace& w = d->ws;
+  const int P = m->m.prog.n_free, S = d->n_sets;
+  std::memcpy(w.h_theta.p, theta, sizeof(double) * S * P);
+  if (P > 0 && !cuda_ok(cudaMemcpyAsync(w.theta.p, w.h_theta.p, sizeof(double) * S * P, cudaMemcpyHostToDevice, st), "theta upload"))
+    return RF_E_CUDA;
+  if (!launch_pass(m, d, plan, (const double*)w.theta.p, (double*)w.out.p, (int32_t*)w.flags.p, grad != nullptr, st))
+    return RF_E_CUDA;
+  if (!cuda_ok(cudaMemcpyAsync(w.h_out.p, w.out.p, sizeof(double) * S * (1 + P), cudaMemcpyDeviceToHost, st), "result download") ||
+      !cuda_ok(cudaMemcpyAsync(w.h_flags.p, w.flags.p, sizeof(int32_t) * S, cudaMemcpyDeviceToHost, st), "flag download") ||
+      !cuda_ok(cudaStreamSynchronize(st), "stream sync"))
+    return RF_E_CUDA;
+  const double* o = (const double*)w.h_out.p;
+  const int32_t* f = (const int32_t*)w.h_flags.p;
+  rf_status st_out = RF_OK;
+  for (int s : plan.host_sets) {
+    nll[s] = o[(size_t)s * (1 + P)];
+    if (grad)
+      for (int k = 0; k < P; ++k) grad[(size_t)s * P + k] = o[(size_t)s * (1 + P) + 1 + k];
+    if (f[s] != 0) st_out = RF_E_DOMAIN;
+  }
+  if (st_out == RF_E_DOMAIN) set_error("pdf <= 0 or not finite for some event, or parameters outside a pdf's domain");
+  return st_out;
+}
+
+}  // namespace rf
+
+using namespace rf;
+
+extern "C" {
+
+const char* rf_last_error(void) { return g_error.c_str(); }
+const char* rf_version(void) { return "rfgpu 0.1 (sm_103a)"; }
+
+rf_status rf_model_create(const rf_node* nodes, int32_t n, int32_t root, rf_model** out) {
+  if (!out) { set_error("rf_model_create: out is NULL"); return RF_E_INVALID; }
+  *out = nullptr;
+  rf_model* m = new (std::nothrow) rf_model();
+  if (!m) return RF_E_OOM;
+  const rf_status s = compile_model(nodes, n, root, &m->m);
+  if (s != RF_OK) { delete m; return s; }
+  *out = m;
+  return RF_OK;
+}
+
+void rf_model_destroy(rf_model* m) { delete m; }
+int32_t rf_model_n_free(const rf_model* m) { return m ? m->m.prog.n_free : 0; }
+int32_t rf_model_n_obs(const rf_model* m) { return m ? m->m.prog.n_obs : 0; }
+
+rf_status rf_model_describe(const rf_model* m, char* buf, int32_t cap) {
+  if (!m || !buf || cap <= 0) { set_error("rf_model_describe: bad argument"); return RF_E_INVALID; }
+  static const char* shapes[] = {"generic", "sum_gauss_poly1", "sum_gaussexp_cheb2", "prod3"};
+  std::snprintf(buf, cap, "%s kernel=%s pdf_nodes=%d free=%d slots=%d consts=%d", m->m.signature.c_str(),
+                shapes[m->m.shape], m->m.prog.n_pdf, m->m.prog.n_free, m->m.prog.n_slots, m->m.prog.n_const);
+  return RF_OK;
+}
+
+rf_status rf_set_launch(rf_model* m, int32_t threads_per_block, int32_t blocks_per_sm) {
+  if (!m) { set_error("rf_set_launch: model is NULL"); return RF_E_INVALID; }
+  if (threads_per_block != 0 && threads_per_block != 128 && threads_per_block != 256 && threads_per_block != 512) {
+    set_error("rf_set_launch: threads_per_block must be 0, 128, 256 or 512");
+    return RF_E_INVALID;
+  }
+  if (blocks_per_sm < 0 || blocks_per_sm > 32) { set_error("rf_set_launch: blocks_per_sm must be 0..32"); return RF_E_INVALID; }
+  m->m.threads_per_block = threads_per_block;
+  m->m.blocks_per_sm = blocks_per_sm;
+  return RF_OK;
+}
+
+rf_status rf_data_upload(const rf_model* m, const void* const* cols, const int32_t* dtype, int64_t n_events,
+                         const int64_t* offsets, int32_t n_sets, int32_t cols_on_device, rf_data** out) {
+  if (!m || !out || n_events < 0 || n_sets < 1 || (n_events > 0 && !cols)) {
+    set_error("rf_data_upload: bad argument");
+    return RF_E_INVALID;
+  }
+  *out = nullptr;
+  const int nobs = m->m.prog.n_obs;
+  std::vector<int64_t> off(n_sets + 1);
+  if (offsets) {
+    off.assign(offsets, offsets + n_sets + 1);
+    if (off[0] != 0 || off[n_sets] != n_events) { set_error("rf_data_upload: offsets must run from 0 to n_events"); return RF_E_INVALID; }
+    for (int s = 0; s < n_sets; ++s)
+      if (off[s + 1] < off[s]) { set_error("rf_data_upload: offsets must not decrease"); return RF_E_INVALID; }
+  } else {
+    if (n_sets != 1) { set_error("rf_data_upload: offsets are required for n_sets > 1"); return RF_E_INVALID; }
+    off[0] = 0;
+    off[1] = n_events;
+  }
+  for (int s = 0; s < n_sets; ++s)
+    if ((off[s + 1] - off[s] + kChunk - 1) / kChunk > (int64_t)0x7fffffff) { set_error("rf_data_upload: set too large"); return RF_E_INVALID; }
+  rf_data* d = new (std::nothrow) rf_data();
+  if (!d) return RF_E_OOM;
+  d->n_obs = nobs;
+  d->n_sets = n_sets;
+  d->n_events = n_events;
+  d->offsets = off;
+  d->owns_cols = !cols_on_device;
+  for (int c = 0; c < nobs; ++c) {
+    d->dtype[c] = dtype ? dtype[c] : RF_F64;
+    if (d->dtype[c] != RF_F64 && d->dtype[c] != RF_F32) { delete d; set_error("rf_data_upload: dtype must be RF_F64 or RF_F32"); return RF_E_INVALID; }
+    const size_t bytes = (size_t)n_events * (d->dtype[c] == RF_F32 ? 4 : 8);
+    if (cols_on_device) {
+      d->cols[c] = const_cast<void*>(n_events > 0 ? cols[c] : nullptr);
+    } else {
+      if (!d->col_bufs[c].ensure(bytes)) { delete d; return RF_E_OOM; }
+      d->cols[c] = d->col_bufs[c].p;
+      if (n_events > 0 && !cuda_ok(cudaMemcpy(d->cols[c], cols[c], bytes, cudaMemcpyHostToDevice), "column upload")) {
+        delete d;
+        return RF_E_CUDA;
+      }
+    }
+  }
+  rf_status st = finish_data(d);
+  if (st != RF_OK) { delete d; return st; }
+  *out = d;
+  return RF_OK;
+}
+
+void rf_data_destroy(rf_data* d) { delete d; }
+int64_t rf_data_n_events(const rf_data* d) { return d ? d->n_events : 0; }
+int32_t rf_data_n_sets(const rf_data* d) { return d ? d->n_sets : 0; }
+
+rf_status rf_data_read(const rf_data* d, int32_t col, int64_t i0, int64_t i1, double* out) {
+  if (!d || col < 0 || col >= d->n_obs || i0 < 0 || i1 < i0 || i1 > d->n_events || (i1 > i0 && !out)) {
+    set_error("rf_data_read: bad argument");
+    return RF_E_INVALID;
+  }
+  const int64_t n = i1 - i0;
+  if (n == 0) return RF_OK;
+  if (d->dtype[col] == RF_F32) {
+    std::vector<float> tmp(n);
+    if (!cuda_ok(cudaMemcpy(tmp.data(), (const float*)d->cols[col] + i0, n * 4, cudaMemcpyDeviceToHost), "column read")) return RF_E_CUDA;
+    for (int64_t i = 0; i < n; ++i) out[i] = (double)tmp[i];
+  } else {
+    if (!cuda_ok(cudaMemcpy(out, (const double*)d->cols[col] + i0, n * 8, cudaMemcpyDeviceToHost), "column read")) return RF_E_CUDA;
+  }
+  return RF_OK;
+}
+
+rf_status rf_data_offsets(const rf_data* d, int64_t* out) {
+  if (!d || !out) { set_error("rf_data_offsets: bad argument"); return RF_E_INVALID; }
+  std::copy(d->offsets.begin(), d->offsets.end(), out);
+  return RF_OK;
+}
+
+static rf_status check_eval_args(const rf_model* m, const rf_data* d, const void* theta, const void* nll) {
+  if (!m || !d || !nll || (m->m.prog.n_free > 0 && !theta)) { set_error("bad argument (NULL)"); return RF_E_INVALID; }
+  if (d->n_obs != m->m.prog.n_obs) { set_error("data and model have different observable counts"); return RF_E_INVALID; }
+  return RF_OK;
+}
+
+rf_status rf_nll(const rf_model* m, const rf_data* d, const double* theta, double* nll, void* stream) {
+  rf_status s = check_eval_args(m, d, theta, nll);
+  if (s != RF_OK) return s;
+  rf_data* dd = const_cast<rf_data*>(d);
+  if (!ensure_workspace(m, dd)) return RF_E_OOM;
+  return eval_host(m, dd, dd->all_plan, theta, nll, nullptr, (cudaStream_t)stream);
+}
+
+rf_status rf_nll_grad(const rf_model* m, const rf_data* d, const double* theta, double* nll, double* grad,
+                      void* stream) {
+  rf_status s = check_eval_args(m, d, theta, nll);
+  if (s != RF_OK) return s;
+  if (!grad && m->m.prog.n_free > 0) { set_error("rf_nll_grad: grad is NULL"); return RF_E_INVALID; }
+  rf_data* dd = const_cast<rf_data*>(d);
+  if (!ensure_workspace(m, dd)) return RF_E_OOM;
+  double dummy;
+  return eval_host(m, dd, dd->all_plan, theta, nll, grad ? grad : &dummy, (cudaStream_t)stream);
+}
+
+rf_status rf_nll_grad_async(const rf_model* m, const rf_data* d, const double* d_theta, double* d_out,
+                            int32_t* d_flags, void* stream) {
+  rf_status s = check_eval_args(m, d, d_theta, d_out);
+  if (s != RF_OK) return s;
+  if (!d_flags) { set_error("rf_nll_grad_async: d_flags is NULL"); return RF_E_INVALID; }
+  rf_data* dd = const_cast<rf_data*>(d);
+  if (!ensure_workspace(m, dd)) return RF_E_OOM;
+  return launch_pass(m, dd, dd->all_plan, d_theta, d_out, d_flags, true, (cudaStream_t)stream) ? RF_OK : RF_E_CUDA;
+}
+
+rf_status rf_nll_chunks(const rf_model* m, const rf_data* d, const double* theta, int32_t set, double* out,
+                        int32_t max_chunks, int32_t* n_chunks) {
+  rf_status s = check_eval_args(m, d, theta, out);
+  if (s != RF_OK) return s;
+  if (set < 0 || set >= d->n_sets || !n_chunks) { set_error("rf_nll_chunks: bad set"); return RF_E_INVALID; }
+  rf_data* dd = const_cast<rf_data*>(d);
+  std::vector<double> nll(d->n_sets);
+  s = rf_nll(m, d, theta, nll.data(), nullptr);
+  if (s != RF_OK && s != RF_E_DOMAIN) return s;
+  const int64_t C = d->chunks[set];
+  *n_chunks = (int32_t)C;
+  const int64_t n = std::min<int64_t>(C, max_chunks);
+  if (n <= 0) return s;
+  // NLL-only passes use Q = 1: node = (sum, compensation).
+  std::vector<double> buf(2 * n);
+  const double* tree = (const double*)dd->ws.tree.p;
+  if (!cuda_ok(cudaMemcpy(buf.data(), tree + d->tree_base[set] * 2, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost), "chunk read"))
+    return RF_E_CUDA;
+  for (int64_t c = 0; c < n; ++c) out[c] = buf[2 * c] + buf[2 * c + 1];
+  return s;
+}
+
+}  // extern "C"
+
+namespace rf {
+
+rf_status finish_data(rf_data* d) {
+  const int S = d->n_sets;
+  d->chunks.resize(S);
+  d->tree_base.resize(S);
+  int64_t total = 0;
+  for (int s = 0; s < S; ++s) {
+    const int64_t n = d->offsets[s + 1] - d->offsets[s];
+    d->chunks[s] = (n + kChunk - 1) / kChunk;
+    d->tree_base[s] = total;
+    total += tree_nodes(d->chunks[s]);
+  }
+  d->total_nodes = total;
+  if (!d->offsets_dev.ensure(sizeof(int64_t) * (S + 1)) || !d->tree_base_dev.ensure(sizeof(int64_t) * S)) return RF_E_OOM;
+  if (!cuda_ok(cudaMemcpy(d->offsets_dev.p, d->offsets.data(), sizeof(int64_t) * (S + 1), cudaMemcpyHostToDevice), "offsets upload") ||
+      !cuda_ok(cudaMemcpy(d->tree_base_dev.p, d->tree_base.data(), sizeof(int64_t) * S, cudaMemcpyHostToDevice), "tree upload"))
+    return RF_E_CUDA;
+  return RF_OK;
+}
+
+}  // namespace rf

@@ -1,0 +1,83 @@
+// Host-side handle layouts shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "rf_internal.h"
+
+namespace rf {
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf();
+  bool ensure(size_t b);
+  void release();
+};
+
+struct HostBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  HostBuf() = default;
+  HostBuf(const HostBuf&) = delete;
+  HostBuf& operator=(const HostBuf&) = delete;
+  ~HostBuf();
+  bool ensure(size_t b);
+};
+
+// Active sets and their (set, chunk) work items.
+struct Plan {
+  DevBuf sets, items;
+  std::vector<int32_t> host_sets;
+  int32_t n_active = 0, n_items = 0;
+};
+
+// Per-dataset evaluation buffers for the model last used with it.
+struct Workspace {
+  bool ready = false;
+  int n_const = -1, n_free = -1, Q = -1;
+  DevBuf consts, theta, out, flags, tree, tree_bad, tickets, counter;
+  HostBuf h_theta, h_out, h_flags;
+};
+
+bool cuda_ok(cudaError_t e, const char* what);
+int sm_count();
+int64_t tree_nodes(int64_t chunks);
+
+}  // namespace rf
+
+struct rf_model {
+  rf::Model m;
+};
+
+struct rf_data {
+  int n_obs = 0, n_sets = 0;
+  int64_t n_events = 0;
+  void* cols[rf::kMaxObs] = {};
+  int32_t dtype[rf::kMaxObs] = {};
+  rf::DevBuf col_bufs[rf::kMaxObs];
+  bool owns_cols = true;
+  std::vector<int64_t> offsets, chunks, tree_base;
+  int64_t total_nodes = 0;
+  rf::DevBuf offsets_dev, tree_base_dev;
+  rf::Workspace ws;
+  rf::Plan all_plan;
+  bool all_plan_ready = false;
+};
+
+namespace rf {
+rf_status finish_data(rf_data* d);
+bool build_plan(const rf_data* d, const std::vector<int32_t>& sets, Plan* plan);
+bool ensure_workspace(const rf_model* m, rf_data* d);
+bool launch_pass(const rf_model* m, rf_data* d, const Plan& plan, const double* d_theta, double* d_out,
+                 int32_t* d_flags, bool grad, cudaStream_t st);
+rf_status eval_host(const rf_model* m, rf_data* d, const Plan& plan, const double* theta, double* nll,
+                    double* grad, cudaStream_t st);
+}  // namespace rf

@@ -1,0 +1,553 @@
+// Likelihood kernels: parameter-point constants (K1), the fused per-event
+// evaluation with its adjoint (K2), and the deterministic reduction tree over
+// event chunks (K3, fused into K2's epilogue).
+//
+// Paper, Sec. 4: a likelihood needs the probability of every event; RooFit
+// loads one event at a time into the graph's leaves and re-evaluates every
+// observable-dependent node, with parameter-only branches cached.  Sec. 4.1
+// batches all events per node, Sec. 4.2 vectorises with no data dependencies,
+// register-only work, few branches and simple reductions.  On the GPU the
+// batch is a 4096-event chunk, the "vector" is a warp, and a whole graph is
+// evaluated per event in registers; normalisation integrals and all other
+// parameter-only quantities are computed once per parameter point (K1).
+#include <cmath>
+#include <cstdio>
+
+#include "nll_kernels.cuh"
+
+namespace rf {
+
+namespace {
+
+constexpr double kSqrt1_2 = 0.70710678118654752440;
+constexpr double kSqrt2Pi = 2.50662827463100050242;
+constexpr double kInvSqrtPi = 0.56418958354775628695;
+constexpr double kTwoInvSqrtPi = 1.12837916709551257390;
+// Below this z the erfc factor of the decay-resolution convolution equals 2
+// to better than 1e-22 relative and its derivative term is below 1e-21 of
+// the exponential's, so the event takes the one-exponential fast path.
+constexpr double kSlowZ = -7.0;
+
+__device__ __forceinline__ double param_of(const PNode& q, int j, const double* th) {
+  return q.pfree[j] >= 0 ? th[q.pfree[j]] : q.pfixed[j];
+}
+
+// Phi(be) - Phi(al), using erfc on the tail side to keep far-tail precision.
+__device__ double normal_mass(double al, double be) {
+  if (al >= 0.0) return 0.5 * (erfc(al * kSqrt1_2) - erfc(be * kSqrt1_2));
+  if (be <= 0.0) return 0.5 * (erfc(-be * kSqrt1_2) - erfc(-al * kSqrt1_2));
+  return 0.5 * (erf(be * kSqrt1_2) - erf(al * kSqrt1_2));
+}
+
+// Decay (x) resolution at one point t, with d/d(tau, mu, sigma).
+// f = 1/2 exp(A) erfc(z), A = s(s/2 - u), z = (s - u)/sqrt2, u = (t-mu)/sigma,
+// s = sigma/tau; A - z^2 = -u^2/2 gives df = f dA - exp(-u^2/2)/sqrt(pi) dz.
+__device__ void gaussexp_point(double t, double tau, double mu, double sigma, double* f, double df[3]) {
+  const double u = (t - mu) / sigma, s = sigma / tau;
+  const double A = s * (0.5 * s - u), z = (s - u) * kSqrt1_2;
+  const double g = exp(-0.5 * u * u);
+  const double val = z > 0.0 ? 0.5 * g * erfcx(z) : 0.5 * exp(A) * erfc(z);
+  const double it = 1.0 / tau;
+  const double dA[3] = {s * (u - s) * it, it, s * it};
+  const double dz[3] = {-s * it * kSqrt1_2, kSqrt1_2 / sigma, (it + u / sigma) * kSqrt1_2};
+  *f = val;
+  for (int k = 0; k < 3; ++k) df[k] = val * dA[k] - g * kInvSqrtPi * dz[k];
+}
+
+// Mean of exp(y w) on w in [0, 1]: 1/(1 - e^-y) - 1/y; series near 0.
+__device__ double trunc_exp_mean01(double y) {
+  if (fabs(y) < 1e-3) return 0.5 + y * (1.0 / 12.0) - y * y * y * (1.0 / 720.0);
+  return -1.0 / expm1(-y) - 1.0 / y;
+}
+
+// ------------------------------------------------------------------- K1
+
+// One thread per active set: the constant block of every node (see the
+// layout in rf_internal.h).  Also resets the event kernel's work counter and
+// finishes sets without events.
+__global__ void param_point_kernel(const __grid_constant__ Program P, Pass pass) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a == 0) *pass.counter = 0;
+  if (a >= pass.n_active) return;
+  const int s = pass.sets[a];
+  const double* th = pass.theta + (size_t)s * P.n_free;
+  double* C = pass.consts + (size_t)s * P.n_const;
+  bool bad = false;
+  for (int n = 0; n < P.n_pdf; ++n) {
+    const PNode& q = P.node[n];
+    double* c = C + q.cofs;
+    const double lo = q.lo, hi = q.hi;
+    switch (q.kind) {
+      case GAUSS: {
+        const double mu = param_of(q, 0, th), sg = param_of(q, 1, th);
+        if (!(sg > 0.0)) { bad = true; break; }
+        const double al = (lo - mu) / sg, be = (hi - mu) / sg;
+        const double I = sg * kSqrt2Pi * normal_mass(al, be);
+        const double ea = exp(-0.5 * al * al), eb = exp(-0.5 * be * be);
+        const double dmu = ea - eb;
+        const double dsg = I / sg - (be * eb - al * ea);
+        if (!(I > 0.0)) bad = true;
+        c[0] = mu; c[1] = 1.0 / sg; c[2] = 1.0 / I; c[3] = dmu / I; c[4] = dsg / I;
+        break;
+      }
+      case EXPO: {
+        const double cc = param_of(q, 0, th), L = hi - lo;
+        const double xref = cc > 0.0 ? hi : lo;
+        double Iref;
+        if (cc == 0.0) Iref = L;
+        else if (cc > 0.0) Iref = -expm1(-cc * L) / cc;
+        else Iref = expm1(cc * L) / cc;
+        c[0] = cc; c[1] = xref; c[2] = 1.0 / Iref; c[3] = lo + L * trunc_exp_mean01(cc * L);
+        break;
+      }
+      case GAUSSEXP: {
+        const double tau = param_of(q, 0, th), mu = param_of(q, 1, th), sg = param_of(q, 2, th);
+        if (!(tau > 0.0) || !(sg > 0.0)) { bad = true; break; }
+        const double al = (lo - mu) / sg, be = (hi - mu) / sg;
+        double fa, fb, dfa[3], dfb[3];
+        gaussexp_point(lo, tau, mu, sg, &fa, dfa);
+        gaussexp_point(hi, tau, mu, sg, &fb, dfb);
+        const double D = normal_mass(al, be);
+        const double br = D - fb + fa;
+        const double I = tau * br;
+        const double pa = exp(-0.5 * al * al) / kSqrt2Pi, pb = exp(-0.5 * be * be) / kSqrt2Pi;
+        const double dD[3] = {0.0, -(pb - pa) / sg, -(be * pb - al * pa) / sg};
+        if (!(I > 0.0)) bad = true;
+        c[0] = mu; c[1] = 1.0 / sg; c[2] = sg / tau; c[3] = 1.0 / tau; c[4] = 1.0 / I;
+        for (int k = 0; k < 3; ++k) c[5 + k] = ((k == 0 ? br : 0.0) + tau * (dD[k] - dfb[k] + dfa[k])) / I;
+        break;
+      }
+      case CHEB: {
+        const int np = q.n_par;
+        double sum = 2.0;
+        for (int k = 1; k <= np; ++k) {
+          const double ck = param_of(q, k - 1, th);
+          const double Tk = (k % 2 == 0) ? 2.0 / (1.0 - (double)k * k) : 0.0;
+          sum += ck * Tk;
+          c[3 + np + k - 1] = ck;
+          c[3 + k - 1] = 0.5 * (hi - lo) * Tk;  // dI/dc_k, divided below
+        }
+        const double I = 0.5 * (hi - lo) * sum;
+        if (!(I > 0.0)) bad = true;
+        c[0] = 2.0 / (hi - lo); c[1] = (hi + lo) / (hi - lo); c[2] = 1.0 / I;
+        for (int k = 0; k < np; ++k) c[3 + k] /= I;
+        break;
+      }
+      case POLY: {
+        const int np = q.n_par;
+        double I = hi - lo, ph = hi, pl = lo;
+        for (int k = 1; k <= np; ++k) {
+          ph *= hi; pl *= lo;
+          const double ak = param_of(q, k - 1, th);
+          const double Pk = (ph - pl) / (k + 1);
+          I += ak * Pk;
+          c[1 + np + k - 1] = ak;
+          c[1 + k - 1] = Pk;
+        }
+        if (!(I > 0.0)) bad = true;
+        c[0] = 1.0 / I;
+        for (int k = 0; k < np; ++k) c[1 + k] /= I;
+        break;
+      }
+      case SUM: {
+        double fs = 0.0;
+        for (int j = 0; j < q.n_par; ++j) {
+          const double f = param_of(q, j, th);
+          c[j] = f;
+          fs += f;
+        }
+        c[q.n_par] = 1.0 - fs;
+        break;
+      }
+      default: break;
+    }
+  }
+  pass.flags[s] = bad ? kThetaBad : 0;
+  if (pass.offsets[s + 1] == pass.offsets[s]) {  // no events: the empty sum
+    double* o = pass.out + (size_t)s * (1 + P.n_free);
+    o[0] = bad ? INFINITY : 0.0;
+    if (pass.want_grad)
+      for (int k = 0; k < P.n_free; ++k) o[1 + k] = 0.0;
+  }
+}
+
+// ------------------------------------------------------------------- K2
+
+__device__ __forceinline__ double load_col(const Columns& cols, int c, int64_t e) {
+  return cols.is_f32[c] ? (double)__ldg((const float*)cols.ptr[c] + e) : __ldg((const double*)cols.ptr[c] + e);
+}
+
+// Exact two-sum merge of compensated pairs: (s, c) + (t, d).  Symmetric in its
+// arguments (the two-sum error is exact), so butterfly lanes agree bitwise.
+struct Pair {
+  double s, c;
+};
+__device__ __forceinline__ Pair merge(Pair a, Pair b) {
+  const double s = a.s + b.s;
+  const double bb = s - a.s;
+  const double e = (a.s - (s - bb)) + (b.s - bb);
+  return {s, (a.c + b.c) + e};
+}
+
+// Generic graph interpreter for one event.  kFull = false: the fast path,
+// which returns false (and adds nothing) when some node needs its slow path.
+// Adds log p to acc[0] and the slot gradients to acc[1..]; counts events
+// with p <= 0 or not finite in *bad instead.
+template <bool kFull, bool kGrad>
+__device__ bool eval_generic(const Program& P, const double* __restrict__ C, const double* x, double* acc,
+                             int* bad) {
+  double v[kMaxPdf];
+  const int N = P.n_pdf;
+  for (int n = 0; n < N; ++n) {
+    const PNode& q = P.node[n];
+    const double* c = C + q.cofs;
+    switch (q.kind) {
+      case GAUSS: {
+        const double u = (x[q.col] - c[0]) * c[1];
+        v[n] = exp(-0.5 * u * u) * c[2];
+        break;
+      }
+      case EXPO: v[n] = exp(c[0] * (x[q.col] - c[1])) * c[2]; break;
+      case GAUSSEXP: {
+        const double u = (x[q.col] - c[0]) * c[1], s = c[2];
+        const double z = (s - u) * kSqrt1_2;
+        double f;
+        if (!kFull) {
+          if (z >= kSlowZ) return false;
+          f = exp(s * (0.5 * s - u));
+        } else if (z > 0.0) {
+          f = 0.5 * exp(-0.5 * u * u) * erfcx(z);
+        } else {
+          f = 0.5 * exp(s * (0.5 * s - u)) * erfc(z);
+        }
+        v[n] = f * c[4];
+        break;
+      }
+      case CHEB: {
+        const int np = q.n_par;
+        const double xp = x[q.col] * c[0] - c[1];
+        double t0 = 1.0, t1 = xp, sh = 1.0;
+        for (int k = 1; k <= np; ++k) {
+          sh += c[3 + np + k - 1] * t1;
+          const double t2 = 2.0 * xp * t1 - t0;
+          t0 = t1; t1 = t2;
+        }
+        v[n] = sh * c[2];
+        break;
+      }
+      case POLY: {
+        const int np = q.n_par;
+        const double xv = x[q.col];
+        double sh = 0.0;
+        for (int k = np; k >= 1; --k) sh = (sh + c[1 + np + k - 1]) * xv;
+        v[n] = (1.0 + sh) * c[0];
+        break;
+      }
+      case SUM: {
+        double r = 0.0;
+        for (int j = 0; j < q.n_child; ++j) r += c[j] * v[q.child[j]];
+        v[n] = r;
+        break;
+      }
+      case PROD: {
+        double r = 1.0;
+        for (int j = 0; j < q.n_child; ++j) r *= v[q.child[j]];
+        v[n] = r;
+        break;
+      }
+      default: v[n] = 0.0;
+    }
+  }
+  const double p = v[N - 1];
+  if (!(p > 0.0) || !isfinite(p)) {
+    ++*bad;
+    return true;
+  }
+  acc[0] += log(p);
+  if constexpr (!kGrad) {
+    return true;
+  } else {
+  double ad[kMaxPdf];
+  for (int n = 0; n < N; ++n) ad[n] = 0.0;
+  ad[N - 1] = 1.0 / p;
+  double* g = acc + 1;
+  for (int n = N - 1; n >= 0; --n) {
+    const PNode& q = P.node[n];
+    const double* c = C + q.cofs;
+    const double a = ad[n];
+    const int s0 = q.slot0;
+    switch (q.kind) {
+      case GAUSS: {
+        const double w = a * v[n];
+        const double u = (x[q.col] - c[0]) * c[1];
+        g[s0] += w * (u * c[1] - c[3]);
+        g[s0 + 1] += w * (u * u * c[1] - c[4]);
+        break;
+      }
+      case EXPO: {
+        g[s0] += a * v[n] * (x[q.col] - c[3]);
+        break;
+      }
+      case GAUSSEXP: {
+        const double w = a * v[n];
+        const double u = (x[q.col] - c[0]) * c[1], s = c[2], it = c[3];
+        double dt = s * (u - s) * it, dm = it, ds = s * it;
+        if (kFull) {
+          const double z = (s - u) * kSqrt1_2;
+          const double R = kTwoInvSqrtPi / erfcx(z);  // exp(-z^2)/erfc(z) * 2/sqrt(pi)
+          dt -= R * (-s * it * kSqrt1_2);
+          dm -= R * (c[1] * kSqrt1_2);
+          ds -= R * ((it + u * c[1]) * kSqrt1_2);
+        }
+        g[s0] += w * (dt - c[5]);
+        g[s0 + 1] += w * (dm - c[6]);
+        g[s0 + 2] += w * (ds - c[7]);
+        break;
+      }
+      case CHEB: {
+        const int np = q.n_par;
+        const double xp = x[q.col] * c[0] - c[1];
+        const double sh = v[n] / c[2];
+        const double ai = a * c[2];
+        double t0 = 1.0, t1 = xp;
+        for (int k = 1; k <= np; ++k) {
+          g[s0 + k - 1] += ai * (t1 - sh * c[3 + k - 1]);
+          const double t2 = 2.0 * xp * t1 - t0;
+          t0 = t1; t1 = t2;
+        }
+        break;
+      }
+      case POLY: {
+        const int np = q.n_par;
+        const double xv = x[q.col];
+        const double sh = v[n] / c[0];
+        const double ai = a * c[0];
+        double xk = 1.0;
+        for (int k = 1; k <= np; ++k) {
+          xk *= xv;
+          g[s0 + k - 1] += ai * (xk - sh * c[1 + k - 1]);
+        }
+        break;
+      }
+      case SUM: {
+        const int nc = q.n_child;
+        const double vl = v[q.child[nc - 1]];
+        for (int j = 0; j < nc; ++j) ad[q.child[j]] += a * c[j];
+        for (int j = 0; j < nc - 1; ++j) g[s0 + j] += a * (v[q.child[j]] - vl);
+        break;
+      }
+      case PROD: {
+        const int nc = q.n_child;
+        for (int j = 0; j < nc; ++j) {
+          double o = a;
+          for (int i = 0; i < nc; ++i)
+            if (i != j) o *= v[q.child[i]];
+          ad[q.child[j]] += o;
+        }
+        break;
+      }
+      default: break;
+    }
+  }
+  return true;
+  }
+}
+
+constexpr int kWarps = kLanes / 32;   // warps per chunk group
+constexpr int kQMax = 1 + kMaxSlots;
+
+struct Smem {
+  double C[kMaxConst];
+  double wsum[kWarps][kQMax];
+  int wbad[kWarps];
+  int queue[kWarps][kPerLane * 32];
+  int item;
+  int last;
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ int warp_sum_int(int v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ Pair warp_merge(Pair p) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    Pair q{__shfl_xor_sync(0xffffffffu, p.s, o), __shfl_xor_sync(0xffffffffu, p.c, o)};
+    p = merge(p, q);
+  }
+  return p;
+}
+
+// Chunk partials climb the set's radix-32 tree: the block that completes the
+// last child of a node (arrival ticket) reduces its <= 32 children with
+// two-sum merges; the block that completes the root writes the set's result.
+// The tree is fixed by the set's chunk count, so the result does not depend
+// on which block ran which chunk, or in which order.
+__device__ void climb_tree(const Program& P, const Pass& pass, Smem& sm, int set, int chunk, int64_t n_events) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int Q = pass.Q;
+  const int64_t base = pass.tree_base[set];
+  int64_t n_l = (n_events + kChunk - 1) / kChunk;
+  int64_t lvl = 0, idx = chunk;
+  while (n_l > 1) {
+    const int64_t parent = idx / kRadix, first = parent * kRadix;
+    const int m = (int)min((int64_t)kRadix, n_l - first);
+    const int64_t pnode = base + lvl + n_l + parent;
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+      const int t = atomicAdd(&pass.tickets[pnode], 1);
+      sm.last = (t == m - 1);
+      if (sm.last) pass.tickets[pnode] = 0;
+    }
+    __syncthreads();
+    if (!sm.last) return;
+    __threadfence();
+    const int64_t c0 = base + lvl + first;
+    for (int q = warp; q < Q; q += kWarps) {
+      Pair p{0.0, 0.0};
+      if (lane < m) {
+        p.s = __ldcg(pass.tree + (c0 + lane) * 2 * Q + q);
+        p.c = __ldcg(pass.tree + (c0 + lane) * 2 * Q + Q + q);
+      }
+      p = warp_merge(p);
+      if (lane == 0) {
+        pass.tree[pnode * 2 * Q + q] = p.s;
+        pass.tree[pnode * 2 * Q + Q + q] = p.c;
+      }
+    }
+    if (warp == 0) {
+      int b = lane < m ? __ldcg(pass.tree_bad + c0 + lane) : 0;
+      b = warp_sum_int(b);
+      if (lane == 0) pass.tree_bad[pnode] = b;
+    }
+    lvl += n_l;
+    n_l = (n_l + kRadix - 1) / kRadix;
+    idx = parent;
+  }
+  // Root: this block holds the set's sums.
+  __threadfence();
+  __syncthreads();
+  const int64_t root = base + lvl;
+  if (tid == 0) {
+    const int flag = pass.flags[set] + __ldcg(pass.tree_bad + root);
+    pass.flags[set] = flag;
+    double* o = pass.out + (size_t)set * (1 + P.n_free);
+    const double s0 = __ldcg(pass.tree + root * 2 * Q) + __ldcg(pass.tree + root * 2 * Q + Q);
+    o[0] = flag ? INFINITY : -s0;
+    if (pass.want_grad) {
+      for (int k = 0; k < P.n_free; ++k) {
+        double gk = 0.0;
+        for (int sl = 0; sl < P.n_slots; ++sl)
+          if (P.slot_free[sl] == k)
+            gk += __ldcg(pass.tree + root * 2 * Q + 1 + sl) + __ldcg(pass.tree + root * 2 * Q + Q + 1 + sl);
+        o[1 + k] = -gk;
+      }
+    }
+  }
+}
+
+// Writes the chunk's partial (warp sums merged in a fixed order) to its
+// level-0 tree node and climbs the tree.
+__device__ void finish_chunk(const Program& P, const Pass& pass, Smem& sm, double* acc, int bad, int set,
+                             int chunk, int64_t n_events) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int Q = pass.Q;
+  for (int q = 0; q < Q; ++q) {
+    const double w = warp_sum(acc[q]);
+    if (lane == 0) sm.wsum[warp][q] = w;
+  }
+  bad = warp_sum_int(bad);
+  if (lane == 0) sm.wbad[warp] = bad;
+  __syncthreads();
+  const int64_t node = pass.tree_base[set] + chunk;
+  if (tid < Q) {
+    Pair a = merge({sm.wsum[0][tid], 0.0}, {sm.wsum[1][tid], 0.0});
+    Pair b = merge({sm.wsum[2][tid], 0.0}, {sm.wsum[3][tid], 0.0});
+    Pair r = merge(a, b);
+    pass.tree[node * 2 * Q + tid] = r.s;
+    pass.tree[node * 2 * Q + Q + tid] = r.c;
+  }
+  if (tid == 0) pass.tree_bad[node] = sm.wbad[0] + sm.wbad[1] + sm.wbad[2] + sm.wbad[3];
+  climb_tree(P, pass, sm, set, chunk, n_events);
+}
+
+// Generic fused event kernel: persistent blocks of 128 threads take 4096-event
+// chunks from the work counter; lane l evaluates events l, l+128, ... of the
+// chunk in order.  Events that need a node's slow path are queued per warp
+// (ballot order) and evaluated after the fast pass, so the warp stays
+// converged; the lane order of additions is still fixed by the data alone.
+template <bool kGrad>
+__global__ void __launch_bounds__(kLanes) events_generic(const __grid_constant__ Program P,
+                                                         const __grid_constant__ Columns cols, Pass pass) {
+  __shared__ Smem sm;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int Q = kGrad ? 1 + P.n_slots : 1;
+  while (true) {
+    if (tid == 0) sm.item = atomicAdd(pass.counter, 1);
+    __syncthreads();
+    const int it = sm.item;
+    if (it >= pass.n_items) break;
+    const int set = pass.items[it].x, chunk = pass.items[it].y;
+    const int64_t s_begin = pass.offsets[set], s_end = pass.offsets[set + 1];
+    const int64_t base = s_begin + (int64_t)chunk * kChunk;
+    for (int i = tid; i < P.n_const; i += kLanes) sm.C[i] = pass.consts[(size_t)set * P.n_const + i];
+    __syncthreads();
+    double acc[kQMax];
+    for (int q = 0; q < kQMax; ++q) acc[q] = 0.0;
+    int bad = 0, qcnt = 0;
+    double x[kMaxObs];
+    for (int k = 0; k < kPerLane; ++k) {
+      const int64_t e = base + tid + (int64_t)k * kLanes;
+      bool slow = false;
+      if (e < s_end) {
+        for (int c = 0; c < P.n_obs; ++c) x[c] = load_col(cols, c, e);
+        slow = !eval_generic<false, kGrad>(P, sm.C, x, acc, &bad);
+      }
+      if (P.has_slow) {
+        const unsigned b = __ballot_sync(0xffffffffu, slow);
+        if (slow) sm.queue[warp][qcnt + __popc(b & ((1u << lane) - 1u))] = (int)(e - base);
+        qcnt += __popc(b);
+      }
+    }
+    __syncwarp();
+    for (int j = lane; j < qcnt; j += 32) {
+      const int64_t e = base + sm.queue[warp][j];
+      for (int c = 0; c < P.n_obs; ++c) x[c] = load_col(cols, c, e);
+      eval_generic<true, kGrad>(P, sm.C, x, acc, &bad);
+    }
+    (void)Q;
+    finish_chunk(P, pass, sm, acc, bad, set, chunk, s_end - s_begin);
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+void launch_param_point(const Program& P, const Pass& pass, cudaStream_t st) {
+  const int threads = 128;
+  const int blocks = (pass.n_active + threads - 1) / threads;
+  param_point_kernel<<<blocks > 0 ? blocks : 1, threads, 0, st>>>(P, pass);
+}
+
+void launch_events(const Program& P, Shape shape, const Columns& cols, const Pass& pass, int threads,
+                   int blocks_per_sm, int n_sm, cudaStream_t st) {
+  (void)shape;
+  (void)threads;
+  if (pass.n_items == 0) return;
+  const int bps = blocks_per_sm > 0 ? blocks_per_sm : 8;
+  int grid = n_sm * bps;
+  if (grid > pass.n_items) grid = pass.n_items;
+  if (pass.want_grad)
+    events_generic<true><<<grid, kLanes, 0, st>>>(P, cols, pass);
+  else
+    events_generic<false><<<grid, kLanes, 0, st>>>(P, cols, pass);
+}
+
+}  // namespace rf

@@ -1,0 +1,43 @@
+// Device side of the likelihood: per-parameter-point constants, the fused
+// per-event evaluation with its adjoint, and the deterministic reduction tree.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "rf_internal.h"
+
+namespace rf {
+
+// Columns of a dataset as seen by the kernels.
+struct Columns {
+  const void* ptr[kMaxObs];
+  int32_t is_f32[kMaxObs];
+};
+
+// Work description of one evaluation pass (device pointers).
+struct Pass {
+  const int64_t* offsets;   // n_sets + 1 event offsets
+  const int32_t* sets;      // active set indices
+  int32_t n_active;
+  const int2* items;        // (set, chunk) work items of the active sets
+  int32_t n_items;
+  const int64_t* tree_base; // per set: first node of its reduction tree
+  const double* theta;      // n_sets x n_free
+  double* consts;           // n_sets x n_const
+  double* tree;             // tree nodes x (2 Q) doubles: (sum, compensation) per quantity
+  int32_t* tree_bad;        // bad-event count per tree node
+  int32_t* tickets;         // arrival counters per tree node (self-resetting)
+  int32_t* counter;         // work-item counter of the persistent grid
+  double* out;              // n_sets x (1 + n_free): nll, gradient
+  int32_t* flags;           // n_sets: events with pdf <= 0 / not finite (+2^30: theta outside domain)
+  int32_t Q;                // quantities per node: 1 + n_slots (or 1 for NLL only)
+  int32_t want_grad;
+};
+
+constexpr int32_t kThetaBad = 1 << 30;
+
+void launch_param_point(const Program& P, const Pass& pass, cudaStream_t st);
+void launch_events(const Program& P, Shape shape, const Columns& cols, const Pass& pass, int threads,
+                   int blocks_per_sm, int n_sm, cudaStream_t st);
+
+}  // namespace rf
