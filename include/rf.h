@@ -199,6 +199,38 @@ rf_status rf_generate_toys(const rf_model* m, const double* theta, int32_t theta
  * clamped to [0, 63].  d_out: DEVICE float, n_sets x 64. */
 rf_status rf_hist64(const rf_model* m, const rf_data* d, int32_t col, float* d_out, void* stream);
 
+/* ------------------------------------------------------------ measurement */
+
+/* Re-copy host columns (same count and dtypes as the dataset was created
+ * with) into a dataset's library-owned device columns, asynchronously on
+ * `stream`: the next batch of events in the same layout.  Pinned host memory
+ * gives full copy bandwidth.  RF_E_INVALID for a dataset that borrows its
+ * columns. */
+rf_status rf_data_refill(rf_data* d, const void* const* cols, void* stream);
+
+/* Kernel timing: while enabled (enable = 1), the library brackets every
+ * launch of its fused event kernel with CUDA events on the launching stream.
+ * rf_kernel_time reads (and with reset = 1 clears) the summed duration in ms
+ * and the number of launches since the last reset; it synchronises on the
+ * recorded events. */
+rf_status rf_kernel_timing(int32_t enable);
+rf_status rf_kernel_time(double* total_ms, int64_t* launches, int32_t reset);
+
+/* Events that took the slow path (the decay-resolution convolution near the
+ * resolution region) in the last pass over `d`, summed over sets. */
+rf_status rf_slow_events(const rf_data* d, int64_t* count);
+
+/* Throughput probes for the roofline, run on the current device:
+ *   kind 0: FP64 fused multiply-add rate            -> *rate in FLOP/s
+ *   kind 1: FP32 fused multiply-add rate            -> *rate in FLOP/s
+ *   kind 2: per-event transcendental set on register data, with the
+ *           library's own implementations: n_exp exponentials, n_erfc
+ *           complementary error functions, n_log logarithms and n_rcp
+ *           reciprocals per event                   -> *rate in events/s
+ *   kind 3: streaming read of a device buffer       -> *rate in bytes/s
+ * Each probe allocates and frees its own scratch. */
+rf_status rf_probe(int32_t kind, int32_t n_exp, int32_t n_erfc, int32_t n_log, int32_t n_rcp, double* rate);
+
 /* -------------------------------------------------------------- messages */
 
 const char* rf_last_error(void);

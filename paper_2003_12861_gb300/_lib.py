@@ -49,6 +49,11 @@ SIGNATURES = {
     "rf_fit": (C.c_int, [_vp, _vp, _dp, C.POINTER(rf_fit_opts), _dp, _dp, _dp, _ip, _ip]),
     "rf_generate_toys": (C.c_int, [_vp, _dp, C.c_int32, C.c_uint64, C.c_int32, _dp, C.c_int32, _ip, C.POINTER(_vp)]),
     "rf_hist64": (C.c_int, [_vp, _vp, C.c_int32, _vp, _vp]),
+    "rf_data_refill": (C.c_int, [_vp, C.POINTER(_vp), _vp]),
+    "rf_kernel_timing": (C.c_int, [C.c_int32]),
+    "rf_kernel_time": (C.c_int, [_dp, _i64p, C.c_int32]),
+    "rf_slow_events": (C.c_int, [_vp, _i64p]),
+    "rf_probe": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, _dp]),
     "rf_last_error": (C.c_char_p, []),
     "rf_version": (C.c_char_p, []),
 }

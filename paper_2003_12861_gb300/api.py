@@ -224,3 +224,36 @@ def generate_toys(model: Model, theta, seed: int, mean_n, poisson: bool = True, 
 
 def hist64(model: Model, data: Data, col: int, d_out, stream=None):
     L.check(L.load().rf_hist64(model._h, data._h, col, C.c_void_p(d_out.data_ptr()), _stream(stream)))
+
+
+# ------------------------------------------------------------- measurement
+
+def refill(data: Data, cols, stream=None):
+    """Copy the next batch of host columns (same layout) into `data`.
+    Columns may be numpy arrays or pinned CPU torch tensors."""
+    ptrs = (C.c_void_p * max(1, len(cols)))(*[c.data_ptr() if hasattr(c, "data_ptr") else c.ctypes.data
+                                              for c in cols])
+    L.check(L.load().rf_data_refill(data._h, ptrs, _stream(stream)))
+
+
+def kernel_timing(enable: bool):
+    L.check(L.load().rf_kernel_timing(1 if enable else 0))
+
+
+def kernel_time(reset: bool = True):
+    ms = C.c_double()
+    n = C.c_int64()
+    L.check(L.load().rf_kernel_time(C.byref(ms), C.byref(n), 1 if reset else 0))
+    return ms.value, n.value
+
+
+def slow_events(data: Data) -> int:
+    n = C.c_int64()
+    L.check(L.load().rf_slow_events(data._h, C.byref(n)))
+    return n.value
+
+
+def probe(kind: int, n_exp: int = 0, n_erfc: int = 0, n_log: int = 0, n_rcp: int = 0) -> float:
+    r = C.c_double()
+    L.check(L.load().rf_probe(kind, n_exp, n_erfc, n_log, n_rcp, C.byref(r)))
+    return r.value

@@ -113,7 +113,7 @@ bool ensure_workspace(const rf_model* m, rf_data* d) {
             w.tree.ensure(sizeof(double) * std::max<int64_t>(1, d->total_nodes) * 2 * Q) &&
             w.tree_bad.ensure(sizeof(int32_t) * std::max<int64_t>(1, d->total_nodes)) &&
             w.tickets.ensure(sizeof(int32_t) * std::max<int64_t>(1, d->total_nodes)) &&
-            w.counter.ensure(sizeof(int32_t)) && w.h_theta.ensure(sizeof(double) * S * std::max(1, P.n_free)) &&
+            w.counter.ensure(sizeof(int32_t)) && w.slow.ensure(sizeof(unsigned long long)) && w.h_theta.ensure(sizeof(double) * S * std::max(1, P.n_free)) &&
             w.h_out.ensure(sizeof(double) * S * (1 + P.n_free)) && w.h_flags.ensure(sizeof(int32_t) * S);
   if (!ok) return false;
   if (!cuda_ok(cudaMemset(w.tickets.p, 0, sizeof(int32_t) * std::max<int64_t>(1, d->total_nodes)), "ticket reset"))
@@ -147,6 +147,7 @@ Pass make_pass(const rf_model* m, rf_data* d, const Plan& plan, const double* d_
   p.tree_bad = (int32_t*)w.tree_bad.p;
   p.tickets = (int32_t*)w.tickets.p;
   p.counter = (int32_t*)w.counter.p;
+  p.slow = (unsigned long long*)w.slow.p;
   p.out = d_out;
   p.flags = d_flags;
   p.Q = grad ? 1 + m->m.prog.n_slots : 1;

@@ -67,7 +67,10 @@ __device__ double trunc_exp_mean01(double y) {
 // finishes sets without events.
 __global__ void param_point_kernel(const __grid_constant__ Program P, Pass pass) {
   const int a = blockIdx.x * blockDim.x + threadIdx.x;
-  if (a == 0) *pass.counter = 0;
+  if (a == 0) {
+    *pass.counter = 0;
+    if (pass.slow) *pass.slow = 0ull;
+  }
   if (a >= pass.n_active) return;
   const int s = pass.sets[a];
   const double* th = pass.theta + (size_t)s * P.n_free;
@@ -517,6 +520,7 @@ __global__ void __launch_bounds__(kLanes) events_generic(const __grid_constant__
       }
     }
     __syncwarp();
+    if (P.has_slow && lane == 0 && qcnt > 0 && pass.slow) atomicAdd(pass.slow, (unsigned long long)qcnt);
     for (int j = lane; j < qcnt; j += 32) {
       const int64_t e = base + sm.queue[warp][j];
       for (int c = 0; c < P.n_obs; ++c) x[c] = load_col(cols, c, e);
@@ -544,10 +548,12 @@ void launch_events(const Program& P, Shape shape, const Columns& cols, const Pas
   const int bps = blocks_per_sm > 0 ? blocks_per_sm : 8;
   int grid = n_sm * bps;
   if (grid > pass.n_items) grid = pass.n_items;
+  timing_begin(st);
   if (pass.want_grad)
     events_generic<true><<<grid, kLanes, 0, st>>>(P, cols, pass);
   else
     events_generic<false><<<grid, kLanes, 0, st>>>(P, cols, pass);
+  timing_end(st);
 }
 
 }  // namespace rf

@@ -30,6 +30,7 @@ struct Pass {
   int32_t* counter;         // work-item counter of the persistent grid
   double* out;              // n_sets x (1 + n_free): nll, gradient
   int32_t* flags;           // n_sets: events with pdf <= 0 / not finite (+2^30: theta outside domain)
+  unsigned long long* slow; // events that took a slow path in this pass (reset by K1)
   int32_t Q;                // quantities per node: 1 + n_slots (or 1 for NLL only)
   int32_t want_grad;
 };
@@ -37,6 +38,10 @@ struct Pass {
 constexpr int32_t kThetaBad = 1 << 30;
 
 void launch_param_point(const Program& P, const Pass& pass, cudaStream_t st);
+// Kernel timing hooks (measure.cu): bracket a launch with CUDA events.
+void timing_begin(cudaStream_t st);
+void timing_end(cudaStream_t st);
+
 void launch_events(const Program& P, Shape shape, const Columns& cols, const Pass& pass, int threads,
                    int blocks_per_sm, int n_sm, cudaStream_t st);
 
