@@ -231,6 +231,29 @@ rf_status rf_slow_events(const rf_data* d, int64_t* count);
  * Each probe allocates and frees its own scratch. */
 rf_status rf_probe(int32_t kind, int32_t n_exp, int32_t n_erfc, int32_t n_log, int32_t n_rcp, double* rate);
 
+/* --------------------------------------------------- allocation-free pass */
+
+/* rf_nll_grad_async for one dataset whose columns are caller-owned device
+ * arrays, allocating no device memory at all.  The paper has no counterpart:
+ * this serves callers that cannot call cudaMalloc while they run (an online
+ * filter or service that reserves all GPU memory at start-up, where an
+ * allocation mid-run has unbounded latency and may fail).  Its scratch lives
+ * in a static 2 MiB device array inside the library (held by every GPU that
+ * loads it, until exit); a dataset whose scratch would not fit -- beyond
+ * about 6.5e7 events for a model with 6 free parameters, 3.7e7 with 12 --
+ * is rejected with RF_E_INVALID and a message giving the limit.
+ *   d_cols : n_obs DEVICE column pointers (host array of pointers), dtype per
+ *            column (NULL = all RF_F64), n_events events each.
+ *   d_theta: DEVICE n_free parameters; d_out: DEVICE 1 + n_free doubles (NLL,
+ *            gradient); d_flags: DEVICE int32, events with pdf <= 0 / not
+ *            finite (+2^30 when theta is outside a pdf's domain).
+ * Asynchronous on `stream`.  All calls on a device share the array, so calls
+ * that overlap on the GPU race and must be serialised by the caller.  The
+ * first call on each device looks the array up (cudaGetSymbolAddress) with
+ * that device current; make it before any stream capture. */
+rf_status rf_nll_grad_noalloc(const rf_model* m, const void* const* d_cols, const int32_t* dtype, int64_t n_events,
+                              const double* d_theta, double* d_out, int32_t* d_flags, void* stream);
+
 /* -------------------------------------------------------------- messages */
 
 const char* rf_last_error(void);

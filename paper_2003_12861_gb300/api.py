@@ -257,3 +257,18 @@ def probe(kind: int, n_exp: int = 0, n_erfc: int = 0, n_log: int = 0, n_rcp: int
     r = C.c_double()
     L.check(L.load().rf_probe(kind, n_exp, n_erfc, n_log, n_rcp, C.byref(r)))
     return r.value
+
+
+def nll_grad_noalloc(model: Model, cols, d_theta, d_out, d_flags, stream=None):
+    """NLL + gradient of one dataset held in caller-owned CUDA tensors, with no
+    device allocation by the library (its scratch is a static device array).
+    For callers that cannot allocate device memory while they run.  Launches
+    only; overlapping calls on one GPU must be serialised by the caller."""
+    import torch
+
+    ptrs = (C.c_void_p * max(1, len(cols)))(*[c.data_ptr() for c in cols])
+    dt = (C.c_int32 * max(1, len(cols)))(*[L.RF_F32 if c.dtype == torch.float32 else L.RF_F64 for c in cols])
+    n = cols[0].numel() if cols else 0
+    L.check(L.load().rf_nll_grad_noalloc(model._h, ptrs, dt, n, C.c_void_p(d_theta.data_ptr()),
+                                         C.c_void_p(d_out.data_ptr()), C.c_void_p(d_flags.data_ptr()),
+                                         _stream(stream)))
