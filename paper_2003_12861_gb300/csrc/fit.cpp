@@ -1,0 +1,437 @@
+// Maximum-likelihood fits (paper Sec. 1: "compute likelihoods and perform
+// fits to data"; Sec. 3: fits converge faster when the likelihood is faster).
+//
+// The paper does not describe its minimiser.  This is BFGS (Nocedal & Wright,
+// Numerical Optimization, 2nd ed., Alg. 6.1) with the strong-Wolfe line search
+// of their Alg. 3.5 / 3.6 (cubic interpolation in the zoom, eq. 3.59), over
+// internal coordinates: a bounded parameter is theta = lo + (hi-lo)(sin phi +
+// 1)/2 (the transform MINUIT documents), an unbounded one is used as is.  A fit
+// stops when EDM = g^T H g / 2 < tol_edm.  The covariance is the inverse of the
+// NLL's Hessian in theta, by central differences of the analytic gradient
+// (an NLL has "up" = 1/2, so cov = Hessian^-1).
+//
+// Every set of a dataset is fitted by its own state machine; each round asks
+// every active set for one trial point and evaluates all of them in a single
+// device pass (the batched toy fit), so a round costs one pass whatever the
+// number of sets.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <limits>
+#include <vector>
+
+#include "api_internal.h"
+
+namespace rf {
+
+namespace {
+
+constexpr double kC1 = 1e-4, kC2 = 0.9;
+constexpr int kMaxLineTrials = 25;
+const double kInf = std::numeric_limits<double>::infinity();
+
+struct Coords {
+  int P;
+  std::vector<double> lo, hi;
+  std::vector<char> bounded;
+  void to_theta(const double* x, double* th) const {
+    for (int k = 0; k < P; ++k)
+      th[k] = bounded[k] ? lo[k] + (hi[k] - lo[k]) * (std::sin(x[k]) + 1.0) * 0.5 : x[k];
+  }
+  void to_internal(const double* th, double* x) const {
+    for (int k = 0; k < P; ++k) {
+      if (!bounded[k]) {
+        x[k] = th[k];
+        continue;
+      }
+      const double r = std::min(1.0, std::max(-1.0, 2.0 * (th[k] - lo[k]) / (hi[k] - lo[k]) - 1.0));
+      x[k] = std::asin(r);
+    }
+  }
+  // d theta / d x
+  double jac(int k, double xk) const { return bounded[k] ? (hi[k] - lo[k]) * 0.5 * std::cos(xk) : 1.0; }
+};
+
+double dot(const double* a, const double* b, int n) {
+  double s = 0.0;
+  for (int i = 0; i < n; ++i) s += a[i] * b[i];
+  return s;
+}
+
+// Minimiser of the cubic through (a, fa, da), (b, fb, db) (N&W eq. 3.59),
+// kept inside the middle 80 % of [a, b]; bisection when the data are unusable.
+double cubic_step(double a, double fa, double da, double b, double fb, double db) {
+  const double lo = std::min(a, b), hi = std::max(a, b), w = hi - lo;
+  const double mid = 0.5 * (a + b);
+  if (!std::isfinite(fa) || !std::isfinite(fb) || !std::isfinite(da) || !std::isfinite(db)) return mid;
+  const double d1 = da + db - 3.0 * (fa - fb) / (a - b);
+  const double disc = d1 * d1 - da * db;
+  if (disc < 0.0) return mid;
+  const double d2 = std::copysign(std::sqrt(disc), b - a);
+  const double den = db - da + 2.0 * d2;
+  if (den == 0.0) return mid;
+  double t = b - (b - a) * (db + d2 - d1) / den;
+  if (!std::isfinite(t)) return mid;
+  return std::min(hi - 0.1 * w, std::max(lo + 0.1 * w, t));
+}
+
+enum Phase { INIT, BRACKET, ZOOM, DONE };
+
+struct SetFit {
+  int P = 0;
+  Phase phase = INIT;
+  int evals = 0, status = RF_E_NOT_CONVERGED;
+  bool first_step = true, reset_once = false;
+  std::vector<double> x, g, H, p;  // accepted point, its gradient, inverse Hessian, direction
+  double f = kInf, d0 = 0.0;       // f(x), g.p
+  // line search
+  double a_prev = 0.0, f_prev = 0.0, d_prev = 0.0, a_cur = 0.0;
+  double a_lo = 0.0, f_lo = 0.0, d_lo = 0.0, a_hi = 0.0, f_hi = 0.0, d_hi = 0.0;
+  std::vector<double> g_lo;
+  int trials = 0;
+  std::vector<double> trial;  // point to evaluate next (internal)
+
+  void set_trial(double a) {
+    a_cur = a;
+    for (int k = 0; k < P; ++k) trial[k] = x[k] + a * p[k];
+  }
+
+  // New search direction from H; resets H when it is not a descent direction.
+  void new_direction() {
+    for (int i = 0; i < P; ++i) {
+      double s = 0.0;
+      for (int j = 0; j < P; ++j) s -= H[i * P + j] * g[j];
+      p[i] = s;
+    }
+    d0 = dot(g.data(), p.data(), P);
+    if (!(d0 < 0.0)) {
+      std::fill(H.begin(), H.end(), 0.0);
+      for (int k = 0; k < P; ++k) {
+        H[k * P + k] = 1.0;
+        p[k] = -g[k];
+      }
+      first_step = true;
+      d0 = dot(g.data(), p.data(), P);
+    }
+    double a1 = 1.0;
+    if (first_step) {  // keep the first step of a fresh H within 0.2 (internal units)
+      double pm = 0.0;
+      for (int k = 0; k < P; ++k) pm = std::max(pm, std::fabs(p[k]));
+      if (pm > 0.0) a1 = std::min(1.0, 0.2 / pm);
+    }
+    a_prev = 0.0;
+    f_prev = f;
+    d_prev = d0;
+    trials = 0;
+    phase = BRACKET;
+    set_trial(a1);
+  }
+
+  double edm() const {
+    double e = 0.0;
+    for (int i = 0; i < P; ++i)
+      for (int j = 0; j < P; ++j) e += 0.5 * g[i] * H[i * P + j] * g[j];
+    return e;
+  }
+
+  // Accept the step to alpha with value fa and gradient ga.
+  void accept(double a, double fa, const std::vector<double>& ga, double tol, int max_evals) {
+    std::vector<double> s(P), y(P);
+    for (int k = 0; k < P; ++k) {
+      s[k] = a * p[k];
+      y[k] = ga[k] - g[k];
+    }
+    const double sy = dot(s.data(), y.data(), P);
+    if (first_step && sy > 0.0) {  // N&W eq. 6.20
+      const double sc = sy / dot(y.data(), y.data(), P);
+      for (double& h : H) h *= sc;
+    }
+    first_step = false;
+    if (sy > 1e-300) {
+      const double rho = 1.0 / sy;
+      std::vector<double> Hy(P, 0.0);
+      for (int i = 0; i < P; ++i)
+        for (int j = 0; j < P; ++j) Hy[i] += H[i * P + j] * y[j];
+      const double yHy = dot(y.data(), Hy.data(), P);
+      for (int i = 0; i < P; ++i)
+        for (int j = 0; j < P; ++j)
+          H[i * P + j] += -rho * (Hy[i] * s[j] + s[i] * Hy[j]) + (rho * rho * yHy + rho) * s[i] * s[j];
+    }
+    for (int k = 0; k < P; ++k) x[k] += s[k];
+    f = fa;
+    g = ga;
+    if (edm() < tol) {
+      status = RF_OK;
+      phase = DONE;
+      return;
+    }
+    if (evals >= max_evals) {
+      phase = DONE;
+      return;
+    }
+    new_direction();
+  }
+
+  void line_failed(double tol, int max_evals) {
+    if (!reset_once && evals < max_evals) {  // one restart from steepest descent
+      reset_once = true;
+      std::fill(H.begin(), H.end(), 0.0);
+      for (int k = 0; k < P; ++k) H[k * P + k] = 1.0;
+      first_step = true;
+      new_direction();
+      return;
+    }
+    (void)tol;
+    phase = DONE;
+  }
+
+  // Deliver f, gradient (internal) at the last trial point.
+  void deliver(double fa, const std::vector<double>& ga, double tol, int max_evals) {
+    ++evals;
+    if (phase == INIT) {
+      x = trial;
+      if (!std::isfinite(fa)) {
+        status = RF_E_DOMAIN;
+        phase = DONE;
+        return;
+      }
+      f = fa;
+      g = ga;
+      if (edm_identity_small(tol)) return;
+      new_direction();
+      return;
+    }
+    const double a = a_cur;
+    const double da = std::isfinite(fa) ? dot(ga.data(), p.data(), P) : std::numeric_limits<double>::quiet_NaN();
+    ++trials;
+    const bool too_many = trials >= kMaxLineTrials || evals >= max_evals;
+    if (phase == BRACKET) {
+      if (!(fa <= f + kC1 * a * d0) || (trials > 1 && fa >= f_prev)) {
+        a_lo = a_prev; f_lo = f_prev; d_lo = d_prev; g_lo = (a_prev == 0.0) ? g : g_lo;
+        a_hi = a; f_hi = fa; d_hi = da;
+        phase = ZOOM;
+      } else if (std::fabs(da) <= -kC2 * d0) {
+        accept(a, fa, ga, tol, max_evals);
+        return;
+      } else if (da >= 0.0) {
+        a_lo = a; f_lo = fa; d_lo = da; g_lo = ga;
+        a_hi = a_prev; f_hi = f_prev; d_hi = d_prev;
+        phase = ZOOM;
+      } else {
+        a_prev = a; f_prev = fa; d_prev = da; g_lo = ga;
+        if (too_many) {
+          accept(a, fa, ga, tol, max_evals);  // sufficient decrease holds here
+          return;
+        }
+        set_trial(2.0 * a);  // expand the bracket
+        return;
+      }
+    } else {  // ZOOM
+      if (!(fa <= f + kC1 * a * d0) || fa >= f_lo) {
+        a_hi = a; f_hi = fa; d_hi = da;
+      } else {
+        if (std::fabs(da) <= -kC2 * d0) {
+          accept(a, fa, ga, tol, max_evals);
+          return;
+        }
+        if (da * (a_hi - a_lo) >= 0.0) {
+          a_hi = a_lo; f_hi = f_lo; d_hi = d_lo;
+        }
+        a_lo = a; f_lo = fa; d_lo = da; g_lo = ga;
+      }
+    }
+    if (too_many) {
+      if (a_lo > 0.0) accept(a_lo, f_lo, g_lo, tol, max_evals);
+      else line_failed(tol, max_evals);
+      return;
+    }
+    set_trial(std::isfinite(f_hi) ? cubic_step(a_lo, f_lo, d_lo, a_hi, f_hi, d_hi) : 0.5 * (a_lo + a_hi));
+  }
+
+  bool edm_identity_small(double tol) {
+    // With H = I the EDM is |g|^2/2: a start at the minimum is already done.
+    if (0.5 * dot(g.data(), g.data(), P) < tol * 1e-6) {
+      status = RF_OK;
+      phase = DONE;
+      return true;
+    }
+    return false;
+  }
+};
+
+// Gauss-Jordan inverse with partial pivoting; false if singular.
+bool invert(std::vector<double> A, int n, double* inv) {
+  std::vector<double> I(n * n, 0.0);
+  for (int i = 0; i < n; ++i) I[i * n + i] = 1.0;
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < n; ++r)
+      if (std::fabs(A[r * n + c]) > std::fabs(A[piv * n + c])) piv = r;
+    if (A[piv * n + c] == 0.0 || !std::isfinite(A[piv * n + c])) return false;
+    for (int k = 0; k < n; ++k) {
+      std::swap(A[c * n + k], A[piv * n + k]);
+      std::swap(I[c * n + k], I[piv * n + k]);
+    }
+    const double d = A[c * n + c];
+    for (int k = 0; k < n; ++k) {
+      A[c * n + k] /= d;
+      I[c * n + k] /= d;
+    }
+    for (int r = 0; r < n; ++r) {
+      if (r == c) continue;
+      const double fct = A[r * n + c];
+      if (fct == 0.0) continue;
+      for (int k = 0; k < n; ++k) {
+        A[r * n + k] -= fct * A[c * n + k];
+        I[r * n + k] -= fct * I[c * n + k];
+      }
+    }
+  }
+  std::copy(I.begin(), I.end(), inv);
+  return true;
+}
+
+}  // namespace
+
+// One device pass over the sets in `active` at their trial points (theta),
+// results into nll/grad (indexed by set).  Rebuilds the work plan when the
+// active set changed since the last call.
+struct Evaluator {
+  const rf_model* m;
+  rf_data* d;
+  Plan plan;
+  std::vector<int32_t> planned;
+  rf_status run(const std::vector<int32_t>& active, const std::vector<double>& theta, std::vector<double>& nll,
+                std::vector<double>& grad) {
+    if (active != planned) {
+      if (!build_plan(d, active, &plan)) return RF_E_OOM;
+      planned = active;
+    }
+    const rf_status s = eval_host(m, d, plan, theta.data(), nll.data(), grad.data(), nullptr);
+    return s == RF_E_DOMAIN ? RF_OK : s;  // per-set +inf is handled by the fits
+  }
+};
+
+}  // namespace rf
+
+using namespace rf;
+
+extern "C" rf_status rf_fit(const rf_model* m, const rf_data* d, const double* theta0, const rf_fit_opts* opts,
+                            double* theta_hat, double* nll_min, double* cov, int32_t* n_evals,
+                            int32_t* fit_status) {
+  if (!m || !d || !theta_hat || !nll_min || !n_evals || !fit_status) {
+    set_error("rf_fit: bad argument (NULL)");
+    return RF_E_INVALID;
+  }
+  if (d->n_obs != m->m.prog.n_obs) {
+    set_error("rf_fit: data and model have different observable counts");
+    return RF_E_INVALID;
+  }
+  const int P = m->m.prog.n_free, S = d->n_sets;
+  const double tol = (opts && opts->tol_edm > 0.0) ? opts->tol_edm : 1e-7;
+  const int max_evals = (opts && opts->max_evals > 0) ? opts->max_evals : 1000;
+  const bool want_cov = opts && opts->want_cov && cov;
+  rf_data* dd = const_cast<rf_data*>(d);
+  if (!ensure_workspace(m, dd)) return RF_E_OOM;
+  if (P == 0) {
+    std::vector<double> z(1);
+    const rf_status s = rf_nll(m, d, z.data(), nll_min, nullptr);
+    for (int s2 = 0; s2 < S; ++s2) {
+      n_evals[s2] = 1;
+      fit_status[s2] = std::isfinite(nll_min[s2]) ? RF_OK : RF_E_DOMAIN;
+    }
+    return s == RF_E_DOMAIN ? RF_OK : s;
+  }
+
+  Coords co;
+  co.P = P;
+  co.lo = m->m.lo;
+  co.hi = m->m.hi;
+  co.bounded.resize(P);
+  for (int k = 0; k < P; ++k)
+    co.bounded[k] = co.lo[k] < co.hi[k] && std::isfinite(co.lo[k]) && std::isfinite(co.hi[k]);
+
+  std::vector<SetFit> fits(S);
+  std::vector<double> th((size_t)S * P), nll(S), grad((size_t)S * P);
+  for (int s = 0; s < S; ++s) {
+    SetFit& F = fits[s];
+    F.P = P;
+    F.x.assign(P, 0.0);
+    F.g.assign(P, 0.0);
+    F.p.assign(P, 0.0);
+    F.trial.assign(P, 0.0);
+    F.H.assign(P * P, 0.0);
+    for (int k = 0; k < P; ++k) F.H[k * P + k] = 1.0;
+    std::vector<double> t0(P);
+    for (int k = 0; k < P; ++k) t0[k] = theta0 ? theta0[(size_t)s * P + k] : m->m.theta_default[k];
+    co.to_internal(t0.data(), F.trial.data());
+    F.phase = INIT;
+  }
+  Evaluator ev{m, dd, {}, {}};
+  std::vector<int32_t> active;
+  std::vector<double> ga(P);
+  while (true) {
+    active.clear();
+    for (int s = 0; s < S; ++s)
+      if (fits[s].phase != DONE) {
+        active.push_back(s);
+        co.to_theta(fits[s].trial.data(), &th[(size_t)s * P]);
+      }
+    if (active.empty()) break;
+    const rf_status st = ev.run(active, th, nll, grad);
+    if (st != RF_OK) return st;
+    for (int s : active) {
+      SetFit& F = fits[s];
+      for (int k = 0; k < P; ++k) ga[k] = grad[(size_t)s * P + k] * co.jac(k, F.trial[k]);
+      F.deliver(nll[s], ga, tol, max_evals);
+    }
+  }
+  for (int s = 0; s < S; ++s) {
+    co.to_theta(fits[s].x.data(), theta_hat + (size_t)s * P);
+    nll_min[s] = fits[s].status == RF_E_DOMAIN ? kInf : fits[s].f;
+    n_evals[s] = fits[s].evals;
+    fit_status[s] = fits[s].status;
+  }
+  if (want_cov) {
+    // Central differences of the analytic gradient, all sets per pass; the
+    // step is 1e-3 of each parameter's BFGS error estimate.
+    std::vector<double> Hs((size_t)S * P * P, 0.0), h((size_t)S * P);
+    std::vector<int32_t> ok_sets;
+    for (int s = 0; s < S; ++s) {
+      if (fits[s].status == RF_E_DOMAIN) continue;
+      ok_sets.push_back(s);
+      for (int k = 0; k < P; ++k) {
+        const double jk = co.jac(k, fits[s].x[k]);
+        const double sig = std::sqrt(std::max(0.0, fits[s].H[k * P + k])) * std::fabs(jk);
+        const double t = theta_hat[(size_t)s * P + k];
+        double hk = 1e-3 * sig;
+        if (!(hk > 1e-9 * std::max(1.0, std::fabs(t)))) hk = 1e-6 * std::max(1.0, std::fabs(t));
+        h[(size_t)s * P + k] = hk;
+      }
+    }
+    std::vector<double> gp((size_t)S * P), gm((size_t)S * P);
+    for (int k = 0; k < P && !ok_sets.empty(); ++k) {
+      for (int sign = 0; sign < 2; ++sign) {
+        for (int s : ok_sets) {
+          for (int j = 0; j < P; ++j) th[(size_t)s * P + j] = theta_hat[(size_t)s * P + j];
+          th[(size_t)s * P + k] += (sign == 0 ? 1.0 : -1.0) * h[(size_t)s * P + k];
+        }
+        const rf_status st = ev.run(ok_sets, th, nll, sign == 0 ? gp : gm);
+        if (st != RF_OK) return st;
+      }
+      for (int s : ok_sets)
+        for (int j = 0; j < P; ++j)
+          Hs[(size_t)s * P * P + j * P + k] =
+              (gp[(size_t)s * P + j] - gm[(size_t)s * P + j]) / (2.0 * h[(size_t)s * P + k]);
+    }
+    for (int s = 0; s < S; ++s) {
+      double* c = cov + (size_t)s * P * P;
+      std::vector<double> A(Hs.begin() + (size_t)s * P * P, Hs.begin() + (size_t)(s + 1) * P * P);
+      for (int i = 0; i < P; ++i)
+        for (int j = 0; j < i; ++j) A[i * P + j] = A[j * P + i] = 0.5 * (A[i * P + j] + A[j * P + i]);
+      if (fits[s].status == RF_E_DOMAIN || !invert(A, P, c))
+        std::fill(c, c + P * P, std::numeric_limits<double>::quiet_NaN());
+    }
+  }
+  return RF_OK;
+}

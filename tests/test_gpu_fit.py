@@ -1,0 +1,115 @@
+"""rf_fit against the oracle's own fitter: fitted parameters within 1e-3 of
+the oracle's standard deviation, covariance and minimum NLL consistent, for
+one dataset and for a batch of ragged toy datasets fitted together."""
+import numpy as np
+import pytest
+
+from paper_2003_12861_gb300 import _lib as L
+from paper_2003_12861_gb300 import api
+from paper_2003_12861_gb300 import workloads as W
+
+from helpers import TRUE
+
+pytestmark = pytest.mark.gpu
+
+TOL_EDM = 1e-10
+
+
+def compare_fit(gpu, ora, what=""):
+    sig = np.sqrt(np.diag(ora["cov"]))
+    assert ora["status"] == 0, what
+    assert np.all(np.abs(gpu["theta"] - ora["theta"]) <= 1e-3 * sig), (what, gpu["theta"], ora["theta"], sig)
+    assert abs(gpu["nll"] - ora["nll"]) <= 1e-7 * max(1.0, abs(ora["nll"])), (what, gpu["nll"], ora["nll"])
+    if gpu.get("cov") is not None:
+        # Both covariances are inverses of finite-difference Hessians with
+        # different steps; near-singular minima amplify the difference.
+        corr = ora["cov"] / np.outer(sig, sig)
+        ev = np.linalg.eigvalsh(corr)
+        tol = 2e-3 if ev[-1] / ev[0] < 100 else 0.15
+        gs = np.sqrt(np.diag(gpu["cov"]))
+        assert np.all(np.abs(gs / sig - 1) < tol), (what, gs, sig, ev[-1] / ev[0])
+
+
+def test_fit_gauss_poly1_1e4(oracle_mod):
+    spec = W.gauss_poly1_model()
+    om = oracle_mod.Model(spec.nodes, spec.root)
+    cols = om.generate(TRUE["gauss_poly1_model"], W.SEED_BASE, 0, 0, 10_000)
+    m = api.Model.from_spec(spec)
+    d = api.Data.upload(m, cols)
+    r = api.fit(m, d, tol_edm=TOL_EDM)
+    assert r["status"][0] == L.RF_OK
+    o = om.fit(cols, tol_edm=TOL_EDM)
+    compare_fit({"theta": r["theta"][0], "nll": r["nll"][0], "cov": r["cov"][0]}, o, "gauss_poly1")
+    # the gradient vanishes at the fitted point
+    _, g, _, ag, _ = om.nll(r["theta"][0], cols)
+    assert np.all(np.abs(g) <= 1e-4 * ag)
+
+
+def test_fit_decay_1e5(oracle_mod):
+    spec = W.decay_model()
+    om = oracle_mod.Model(spec.nodes, spec.root)
+    cols = om.generate(TRUE["decay_model"], W.SEED_BASE + 1, 0, 0, 100_000)
+    m = api.Model.from_spec(spec)
+    d = api.Data.upload(m, cols)
+    r = api.fit(m, d, tol_edm=TOL_EDM)
+    assert r["status"][0] == L.RF_OK
+    o = om.fit(cols, tol_edm=TOL_EDM)
+    compare_fit({"theta": r["theta"][0], "nll": r["nll"][0], "cov": r["cov"][0]}, o, "decay")
+
+
+def test_batched_ragged_toy_fits(oracle_mod):
+    spec = W.decay_model()
+    om = oracle_mod.Model(spec.nodes, spec.root)
+    S = 48
+    mean = W.toy_mean_sizes(S, 4, 1e3, 1.5e4)
+    th = W.toy_thetas(S, 4)
+    seed = W.SEED_BASE + 2
+    cols, off = [], [0]
+    for s in range(S):
+        n = oracle_mod.poisson(seed, s, mean[s])
+        cols.append(om.generate(th[s], seed, s, 0, n)[0])
+        off.append(off[-1] + n)
+    m = api.Model.from_spec(spec)
+    d = api.Data.upload(m, [np.concatenate(cols)], offsets=off)
+    r = api.fit(m, d, tol_edm=TOL_EDM)
+    assert (r["status"] == L.RF_OK).mean() >= 0.9, r["status"]
+    # Parity is defined at one minimum, where it is interior: a toy whose
+    # minimum sits on a parameter bound (where the sin transform flattens the
+    # NLL) or whose covariance is not positive definite has no 1e-3 sigma.
+    # Small toys of this model have several local minima, and two correct
+    # fitters may stop in different ones from the same start; then the oracle
+    # is restarted at the GPU's point, which must be a minimum of its NLL.
+    lo, hi = spec.bounds().T
+    compared = 0
+    for s in np.argsort(-np.diff(off))[:16]:
+        if r["status"][s] != L.RF_OK:
+            continue
+        o = om.fit([cols[s]], tol_edm=TOL_EDM)
+        if abs(o["nll"] - r["nll"][s]) > 1e-6:
+            o = om.fit([cols[s]], theta0=r["theta"][s], tol_edm=TOL_EDM)
+        interior = np.all(np.minimum(o["theta"] - lo, hi - o["theta"]) > 1e-3 * (hi - lo))
+        if o["status"] != 0 or not interior or not np.all(np.isfinite(o["cov"])) \
+                or not np.all(np.linalg.eigvalsh(o["cov"]) > 0):
+            continue
+        compare_fit({"theta": r["theta"][s], "nll": r["nll"][s], "cov": r["cov"][s]}, o, f"toy {s}")
+        compared += 1
+    assert compared >= 4
+    # a batch of one set reproduces the batched result for that set
+    d0 = api.Data.upload(m, [cols[7]])
+    r0 = api.fit(m, d0, tol_edm=TOL_EDM)
+    assert np.array_equal(r0["theta"][0], r["theta"][7])
+
+
+def test_fit_limits_and_domain(oracle_mod):
+    spec = W.decay_model()
+    om = oracle_mod.Model(spec.nodes, spec.root)
+    cols = om.generate(TRUE["decay_model"], 9, 0, 0, 20_000)
+    m = api.Model.from_spec(spec)
+    d = api.Data.upload(m, cols)
+    r = api.fit(m, d, max_evals=5, want_cov=False)
+    assert r["status"][0] == L.RF_E_NOT_CONVERGED and r["n_evals"][0] <= 6
+    # background only, with a Chebychev that is negative near t = 0: NLL = +inf
+    bad = W.DECAY_START.copy()
+    bad[3], bad[4], bad[5] = 1.0, -1.0, 0.0
+    r = api.fit(m, d, theta0=bad, want_cov=False)
+    assert r["status"][0] == L.RF_E_DOMAIN and r["nll"][0] == np.inf
