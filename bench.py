@@ -1,21 +1,28 @@
-"""Benchmark: events/s of one NLL + gradient pass over the decay-time model
-(1e7 events, t in [0, 10], f*[exp(-t/tau) (x) Gauss] + (1-f)*Chebychev2,
-6 free parameters, FP64 columns), the configuration the headline metric is
-quoted on.
+"""Benchmark of the batched unbinned-likelihood hot path on GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload decay_1e7|prod3_1e8_f32|decay_toys_4096|gauss_poly1_1e4]
 
-One step = one pass of the whole hot path over the dataset: the
+Default workload (the configuration the headline metric is quoted on):
+events/s of one NLL + gradient pass over the decay-time model, 1e7 events,
+t in [0, 10], f*[exp(-t/tau) (x) Gauss] + (1-f)*Chebychev2, 6 free parameters,
+FP64 column.  One step = one pass of the whole path over the dataset: the
 parameter-point kernel and the fused event/adjoint/reduction kernel.  The
 device-resident value times K steps with CUDA events (inputs already in HBM,
 L2 flushed between steps).  The end-to-end number runs the same step through
 the C ABI with host buffers: host->device copy of the event columns from
-pinned memory, rf_nll_grad with host parameters, device->host read of the NLL
-and gradient.  Multi-GPU (torchrun): every rank evaluates its own dataset
-(weak scaling, no collective on the data path); rank 0 prints one JSON line.
+pinned memory, rf_nll_grad with host parameters, device->host read of the
+NLL and gradient.
 
---impl reference times the CPU oracle (single thread, the machine's host cores)
-on a bounded sample of the same workload, with the same metric.
+Other workloads: prod3_1e8_f32 (3-observable product, 1e8 events, FP32
+columns, 12 parameters); decay_toys_4096 (toy fits/s of 4096 ragged toys of
+the decay model fitted together, graph-replayed evaluation step, autotuned
+tile shape); gauss_poly1_1e4 (1e4 events, latency-bound).
+
+Multi-GPU (torchrun): every rank evaluates its own dataset (weak scaling, no
+collective on the data path); rank 0 prints one JSON line.  --impl reference
+times the CPU oracle (single thread, the machine's host cores) on a bounded sample
+of the same workload, with the same metric.
 """
 from __future__ import annotations
 
@@ -35,16 +42,19 @@ sys.path.insert(0, ROOT)
 from paper_2003_12861_gb300 import workloads as W  # noqa: E402
 
 METRIC = "events/s of NLL+grad eval; toy fits/s learned-start vs plain at |ΔNLL|<1e-6"
-WORKLOAD = "decay_1e7"
-N_EVENTS = 10_000_000
-BYTES_PER_EVENT = 8  # one FP64 column
+
+WORKLOADS = {
+    # name: model constructor, generating theta, events per dataset, FP32 columns, bytes/event
+    "decay_1e7": ("decay_model", W.DECAY_TRUE, 10_000_000, False, 8),
+    "prod3_1e8_f32": ("prod3_model", W.PROD3_TRUE, 100_000_000, True, 12),
+    "gauss_poly1_1e4": ("gauss_poly1_model", W.GAUSS_POLY1_TRUE, 10_000, False, 8),
+    "decay_toys_4096": ("decay_model", W.DECAY_TRUE, 0, False, 8),
+}
+DEFAULT_STEPS = {"decay_1e7": 400, "prod3_1e8_f32": 40, "gauss_poly1_1e4": 2000, "decay_toys_4096": 3}
 
 
 def dist_env():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
 
 
 def measured_peaks():
@@ -63,9 +73,7 @@ class ClockSampler:
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, gpu_index: int):
-        self.gpu = gpu_index
-        self.proc = None
-        self.out = None
+        self.gpu, self.proc, self.out = gpu_index, None, None
 
     def __enter__(self):
         try:
@@ -104,79 +112,147 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
-def cpu_baseline(seconds: float = 12.0, n_sample: int = 400_000):
-    """The oracle as it stands, single-threaded, on a bounded sample."""
+# ------------------------------------------------------------- CPU oracle
+
+def oracle_events_per_s(wl: str, seconds: float, n_sample: int):
+    """The oracle as it stands, single-threaded, on a bounded sample of the
+    workload's model (oracle-generated events, fewer of them)."""
     import oracle
 
-    spec = W.decay_model()
+    ctor, theta, _, f32, _ = WORKLOADS[wl]
+    spec = W.model_for(ctor)
     om = oracle.Model(spec.nodes, spec.root)
-    cols = om.generate(W.DECAY_TRUE, W.SEED_BASE + 1, 0, 0, n_sample)
-    th = W.DECAY_TRUE
+    cols = om.generate(theta, W.SEED_BASE + 1, 0, 0, n_sample)
+    if f32:
+        cols = [c.astype(np.float32).astype(np.float64) for c in cols]
     reps, t0 = 0, time.perf_counter()
     while True:
-        om.nll(th, cols)
+        om.nll(theta, cols)
         reps += 1
         if time.perf_counter() - t0 >= seconds:
             break
     dt = time.perf_counter() - t0
-    return {"value": reps * n_sample / dt, "unit": "events/s", "cores": 1, "kind": "oracle",
-            "sample": f"{reps} NLL+gradient passes of the oracle over {n_sample} decay-model events "
-                      f"(the workload's model and parameters, fewer events), {dt:.1f} s, 1 thread"}
+    return reps * n_sample / dt, f"{reps} oracle NLL+gradient passes over {n_sample} events of the {ctor}, {dt:.1f} s"
 
 
-def run_reference(args):
-    rank, world, _ = dist_env()
-    if rank != 0:
-        return 0
+def oracle_toy_fits_per_s(seconds: float):
+    """The oracle's own fitter on the toy workload's first toys (same seeds,
+    sizes and generating parameters), one at a time, single-threaded."""
     import oracle
 
     spec = W.decay_model()
     om = oracle.Model(spec.nodes, spec.root)
-    n_sample = 200_000
-    cols = om.generate(W.DECAY_TRUE, W.SEED_BASE + 1, 0, 0, n_sample)
-    for _ in range(args.warmup):
-        om.nll(W.DECAY_TRUE, cols)
+    seed = W.SEED_BASE + 2
+    mean = W.toy_mean_sizes(4096, seed)
+    th = W.toy_thetas(4096, seed)
+    fits, dt = 0, 0.0
+    while dt < seconds and fits < 4096:
+        n = oracle.poisson(seed, fits, mean[fits])
+        cols = om.generate(th[fits], seed, fits, 0, n)
+        t1 = time.perf_counter()
+        om.fit(cols, tol_edm=1e-7, cov=False)
+        dt += time.perf_counter() - t1
+        fits += 1
+    return fits / dt, f"oracle BFGS fits (plain start) of the first {fits} toys of the 4096-toy batch, {dt:.1f} s"
+
+
+def cpu_baseline(wl: str):
+    if wl == "decay_toys_4096":
+        v, s = oracle_toy_fits_per_s(15.0)
+        return {"value": v, "unit": "toy fits/s", "cores": 1, "kind": "oracle", "sample": s}
+    v, s = oracle_events_per_s(wl, 12.0, 400_000 if wl != "gauss_poly1_1e4" else 10_000)
+    return {"value": v, "unit": "events/s", "cores": 1, "kind": "oracle", "sample": s}
+
+
+def run_reference(args):
+    rank, _, _ = dist_env()
+    if rank != 0:
+        return 0
+    wl = args.workload
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        om.nll(W.DECAY_TRUE, cols)
-    dt = time.perf_counter() - t0
-    v = args.steps * n_sample / dt
+    if wl == "decay_toys_4096":
+        # each step: the oracle fits one toy of the batch
+        v, s = oracle_toy_fits_per_s(max(3.0, 1.5 * args.steps))
+        unit = "toy fits/s"
+    else:
+        import oracle
+
+        ctor, theta, _, f32, _ = WORKLOADS[wl]
+        spec = W.model_for(ctor)
+        om = oracle.Model(spec.nodes, spec.root)
+        n_sample = 200_000 if wl != "gauss_poly1_1e4" else 10_000
+        cols = om.generate(theta, W.SEED_BASE + 1, 0, 0, n_sample)
+        for _ in range(args.warmup):
+            om.nll(theta, cols)
+        t1 = time.perf_counter()
+        for _ in range(args.steps):
+            om.nll(theta, cols)
+        dt = time.perf_counter() - t1
+        v = args.steps * n_sample / dt
+        s = f"each step: one oracle NLL+gradient pass over {n_sample} events of the {ctor}"
+        unit = "events/s"
+    dt_all = time.perf_counter() - t0
     line = {
-        "impl": "reference", "metric": METRIC, "value": v, "unit": "events/s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+        "impl": "reference", "metric": METRIC, "value": v, "unit": unit, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * dt_all / max(1, args.steps), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n_events": N_EVENTS, "sample_events_per_step": n_sample},
-        "cpu_baseline": {"value": v, "unit": "events/s", "cores": 1, "kind": "oracle",
-                         "sample": f"each step: one oracle NLL+gradient pass over {n_sample} events of the workload"},
-        "e2e": {"value": v, "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "config": {"workload": wl},
+        "cpu_baseline": {"value": v, "unit": unit, "cores": 1, "kind": "oracle", "sample": s},
+        "e2e": {"value": v, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
 
 
-def run_ours(args):
-    import torch
+# ------------------------------------------------------------------- ours
 
-    from paper_2003_12861_gb300 import _lib as L
-    from paper_2003_12861_gb300 import api
+def transcendental_ceiling(api, model_spec, slow_fraction, n_events, bytes_per_event, peaks, peak_kind):
+    """ALU ceiling: per event the fast set {exp per Gauss/exp/decay leaf, log,
+    reciprocal}; events in the decay resolution region add {exp, erfc} per
+    decay leaf; rates measured in-run by the library's probe."""
+    kinds = [n.kind for n in model_spec.nodes]
+    n_exp = sum(k in ("gauss", "exp", "gaussexp") for k in kinds)
+    n_ge = sum(k == "gaussexp" for k in kinds)
+    fast = api.probe(2, n_exp=n_exp, n_log=1, n_rcp=1)
+    full = api.probe(2, n_exp=n_exp + n_ge, n_erfc=n_ge, n_log=1, n_rcp=1) if n_ge else fast
+    t_event = 1.0 / fast + slow_fraction * (1.0 / full - 1.0 / fast)
+    alu = 1.0 / t_event
+    hbm = peaks["hbm_gbs"] * 1e9 / bytes_per_event
+    basis = (f"transcendental set per event measured in-run: fast {{{n_exp} exp, log, rcp}} {fast/1e9:.2f} "
+             f"Gevent/s, slow {{{n_exp + n_ge} exp, {n_ge} erfc, log, rcp}} {full/1e9:.2f} Gevent/s, slow "
+             f"fraction {slow_fraction:.4f}; HBM ceiling {hbm/1e9:.0f} Gevent/s at {peaks['hbm_gbs']} GB/s "
+             f"({peak_kind}) x {bytes_per_event} B/event")
+    return alu, hbm, basis
 
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
 
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    L.load()
+def roofline(api, model, spec, data, kern_ms, kern_n, n_events, bpe, peaks, peak_kind, slow_frac=None):
+    if slow_frac is None:
+        slow_frac = api.slow_events(data) / max(1, n_events)
+    alu, hbm, basis = transcendental_ceiling(api, spec, slow_frac, n_events, bpe, peaks, peak_kind)
+    ceiling = min(alu, hbm)
+    avg = kern_ms / max(1, kern_n)
+    achieved = n_events / (avg * 1e-3)
+    return {
+        "bound": "alu" if alu < hbm else "hbm", "achieved": achieved / 1e9, "peak": ceiling / 1e9,
+        "unit": "Gevent/s", "frac": achieved / ceiling, "traffic": None,
+        "kernel": model.describe(), "kernel_avg_ms": avg, "kernel_launches": kern_n, "peak_basis": basis,
+        "fp64_fma_tflops_measured": api.probe(0) / 1e12,
+        "hbm_frac": achieved * bpe / (peaks["hbm_gbs"] * 1e9),
+    }
 
-    spec = W.decay_model()
+
+def run_events(args, api, torch, dist, rank, world, local):
+    wl = args.workload
+    ctor, theta_true, n, f32, bpe = WORKLOADS[wl]
+    spec = W.model_for(ctor)
     model = api.Model.from_spec(spec)
-    n = N_EVENTS
-    data = api.generate_toys(model, W.DECAY_TRUE, W.SEED_BASE + 1 + 1000 * rank, [float(n)], poisson=False)
+    data = api.generate_toys(model, theta_true, W.SEED_BASE + 1 + 1000 * rank, [float(n)], poisson=False,
+                             f32=[f32] * spec.n_obs)
     assert data.n_events == n
+    tune = api.autotune(model, data, passes=3)
     P = model.n_free
     stream = torch.cuda.Stream()
-    theta = torch.tensor(W.DECAY_TRUE * (1 + 0.02 * np.cos(np.arange(P))), dtype=torch.float64, device="cuda")
+    theta = torch.tensor(theta_true * (1 + 0.02 * np.cos(np.arange(P))), dtype=torch.float64, device="cuda")
     out = torch.zeros(1 + P, dtype=torch.float64, device="cuda")
     flags = torch.zeros(1, dtype=torch.int32, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2 (129 MB)
@@ -188,7 +264,6 @@ def run_ours(args):
         for _ in range(args.warmup):
             step()
     stream.synchronize()
-
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     if dist:
@@ -207,88 +282,167 @@ def run_ours(args):
     api.kernel_timing(False)
     if dist:
         dist.barrier()
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_ms = sum(step_ms)
+    total_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
     kern_ms, kern_n = api.kernel_time(reset=True)
-    slow = api.slow_events(data)
     if dist:
         t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
     value = world * n * args.steps / (total_ms * 1e-3)
 
-    # End to end through the C ABI with host buffers.
-    host_col = torch.empty(n, dtype=torch.float64, pin_memory=True)
-    host_col.copy_(torch.from_numpy(data.read(0)))
-    e2e_data = api.Data.upload(model, [host_col.numpy()])
+    # End to end through the C ABI with host buffers (pinned columns).
+    host_cols = []
+    for c in range(spec.n_obs):
+        hc = torch.empty(n, dtype=torch.float32 if f32 else torch.float64, pin_memory=True)
+        hc.copy_(torch.from_numpy(data.read(c).astype(np.float32 if f32 else np.float64)))
+        host_cols.append(hc)
+    e2e_data = api.Data.upload(model, [h.numpy() for h in host_cols], f32=[f32] * spec.n_obs)
     th_host = theta.cpu().numpy()
     for _ in range(2):
-        api.refill(e2e_data, [host_col])
+        api.refill(e2e_data, host_cols)
         api.nll_grad(model, e2e_data, th_host)
     k_e2e = max(3, args.steps // 4)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(k_e2e):
-        api.refill(e2e_data, [host_col])
-        nll_v, g_v = api.nll_grad(model, e2e_data, th_host)
+        api.refill(e2e_data, host_cols)
+        api.nll_grad(model, e2e_data, th_host)
     e2e_s = time.perf_counter() - t0
     if dist:
         t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
-    e2e = {"value": world * n * k_e2e / e2e_s, "unit": "events/s", "h2d_bytes_per_step": n * 8 + P * 8,
+    e2e = {"value": world * n * k_e2e / e2e_s, "unit": "events/s", "h2d_bytes_per_step": n * bpe + P * 8,
            "d2h_bytes_per_step": (1 + P) * 8 + 4, "steps": k_e2e}
-
     if rank != 0:
-        if dist:
-            dist.destroy_process_group()
-        return 0
-
-    # Roofline: the ALU ceiling is the per-event transcendental work this
-    # dataset needs (fast set for every event, the slow set's extra for events
-    # in the resolution region), at the rate the probe measures for the
-    # library's own implementations; the HBM ceiling is column bytes over the
-    # measured copy bandwidth.
+        return None
     peaks, peak_kind = measured_peaks()
-    fast = api.probe(2, n_exp=1, n_log=1, n_rcp=1)
-    full = api.probe(2, n_exp=2, n_erfc=1, n_log=1, n_rcp=1)
-    f_slow = slow / n
-    t_event = 1.0 / fast + f_slow * (1.0 / full - 1.0 / fast)
-    alu_ceiling = 1.0 / t_event
-    hbm_ceiling = peaks["hbm_gbs"] * 1e9 / BYTES_PER_EVENT
-    ceiling = min(alu_ceiling, hbm_ceiling)
-    kern_avg_ms = kern_ms / max(1, kern_n)
-    achieved = n / (kern_avg_ms * 1e-3)
-    dfma = api.probe(0)
-    roofline = {
-        "bound": "alu" if alu_ceiling < hbm_ceiling else "hbm",
-        "achieved": achieved / 1e9, "peak": ceiling / 1e9, "unit": "Gevent/s", "frac": achieved / ceiling,
-        "traffic": None,
-        "kernel": "events_generic<grad> (fused event + adjoint + reduction tree)",
-        "kernel_avg_ms": kern_avg_ms, "kernel_launches": kern_n,
-        "peak_basis": (f"transcendental set per event measured in-run: fast {{exp,log,rcp}} {fast/1e9:.2f} "
-                       f"Gevent/s, slow {{2 exp,erfc,log,rcp}} {full/1e9:.2f} Gevent/s, slow fraction "
-                       f"{f_slow:.4f}; HBM ceiling {hbm_ceiling/1e9:.0f} Gevent/s at {peaks['hbm_gbs']} GB/s "
-                       f"({peak_kind}) x {BYTES_PER_EVENT} B/event"),
-        "fp64_fma_tflops_measured": dfma / 1e12,
-        "hbm_frac": achieved * BYTES_PER_EVENT / (peaks["hbm_gbs"] * 1e9),
-    }
-    clocks = clk.summary()
     line = {
-        "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n_events_per_gpu": n, "columns": "1 x f64 (t)", "free_parameters": P,
-                   "l2": "flushed between steps (256 MiB write)", "kernel_program": model.describe()},
-        "roofline": roofline,
-        "e2e": e2e,
-        "gpu_launches": 2 * args.steps,
-        "clocks": clocks,
+        "value": value, "unit": "events/s", "ms_per_step": total_ms / args.steps,
+        "dtype": "f64", "config": {"workload": wl, "n_events_per_gpu": n,
+                                   "columns": f"{spec.n_obs} x {'f32' if f32 else 'f64'}",
+                                   "free_parameters": P, "l2": "flushed between steps (256 MiB write)",
+                                   "tile": {"threads_per_block": tune[0], "blocks_per_sm": tune[1]}},
+        "roofline": roofline(api, model, spec, data, kern_ms, kern_n, n, bpe, peaks, peak_kind),
+        "e2e": e2e, "gpu_launches": 2 * args.steps, "clocks": clk.summary(),
         "nll_check": float(out[0].item()),
     }
-    if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline()
-    print(json.dumps(line), flush=True)
+    if wl == "gauss_poly1_1e4":
+        # the configuration's full fit from its stated start, end to end
+        host = api.Data.upload(model, [data.read(0)])
+        t0 = time.perf_counter()
+        r = api.fit(model, host, want_cov=True)
+        line["fit"] = {"wall_ms": 1e3 * (time.perf_counter() - t0), "n_evals": int(r["n_evals"][0]),
+                       "status": int(r["status"][0]), "theta": r["theta"][0].tolist()}
+        line["us_per_eval"] = 1e3 * total_ms / args.steps
+    return line
+
+
+def run_toys(args, api, torch, dist, rank, world, local):
+    spec = W.decay_model()
+    model = api.Model.from_spec(spec)
+    S = 4096
+    seed = W.SEED_BASE + 2
+    mean = W.toy_mean_sizes(S, seed)
+    th = W.toy_thetas(S, seed)
+    data = api.generate_toys(model, th, seed + 1000 * rank, mean, poisson=True)
+    n_events = data.n_events
+    tune = api.autotune(model, data, passes=2)
+    P = model.n_free
+    # roofline pass: one ragged persistent launch over all toys
+    stream = torch.cuda.Stream()
+    theta = torch.tensor(np.tile(W.DECAY_START, S), dtype=torch.float64, device="cuda")
+    out = torch.zeros(S * (1 + P), dtype=torch.float64, device="cuda")
+    flags = torch.zeros(S, dtype=torch.int32, device="cuda")
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            api.nll_grad_async(model, data, theta, out, flags, stream=stream)
+        stream.synchronize()
+        api.kernel_time(reset=True)
+        api.kernel_timing(True)
+        for _ in range(5):
+            api.nll_grad_async(model, data, theta, out, flags, stream=stream)
+        stream.synchronize()
+        api.kernel_timing(False)
+    kern_ms, kern_n = api.kernel_time(reset=True)
+    slow_frac = api.slow_events(data) / n_events
+
+    for _ in range(args.warmup):
+        api.fit(model, data, want_cov=False)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    evals, conv = [], []
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            r = api.fit(model, data, want_cov=False)
+            evals.append(r["n_evals"])
+            conv.append(r["status"] == 0)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([dt], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dt = float(t.item())
+    value = world * S * args.steps / dt
+    ev = np.concatenate(evals)
+    # end to end: host columns uploaded, fitted, results read back
+    cols = [data.read(0)]
+    off = data.offsets()
+    t0 = time.perf_counter()
+    hd = api.Data.upload(model, cols, offsets=off)
+    api.fit(model, hd, want_cov=False)
+    e2e_s = time.perf_counter() - t0
+    if rank != 0:
+        return None
+    peaks, peak_kind = measured_peaks()
+    rl = roofline(api, model, spec, data, kern_ms, kern_n, n_events, 8, peaks, peak_kind, slow_frac)
+    rounds = int(ev.max())
+    rl["toy_fits_per_s_ceiling"] = rl["peak"] * 1e9 / (n_events * float(ev.mean())) * S
+    return {
+        "value": value, "unit": "toy fits/s", "ms_per_step": 1e3 * dt / args.steps, "dtype": "f64",
+        "config": {"workload": "decay_toys_4096", "toys": S, "events": int(n_events),
+                   "sizes": "Poisson(N), N log-uniform in [1e3, 1e5]", "start": "plain default start",
+                   "tol_edm": 1e-7, "tile": {"threads_per_block": tune[0], "blocks_per_sm": tune[1]},
+                   "eval_step": "CUDA graph replay, one ragged persistent launch per round"},
+        "roofline": rl,
+        "e2e": {"value": world * S / e2e_s, "unit": "toy fits/s", "h2d_bytes_per_step": int(n_events) * 8,
+                "d2h_bytes_per_step": S * (P + 3) * 8},
+        "gpu_launches": int(2 * rounds * args.steps),
+        "clocks": clk.summary(),
+        "fits": {"mean_evals": float(ev.mean()), "max_evals": int(ev.max()),
+                 "converged_frac": float(np.concatenate(conv).mean())},
+    }
+
+
+def run_ours(args):
+    import torch
+
+    from paper_2003_12861_gb300 import _lib as L
+    from paper_2003_12861_gb300 import api
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    L.load()
+    if args.workload == "decay_toys_4096":
+        line = run_toys(args, api, torch, dist, rank, world, local)
+    else:
+        line = run_events(args, api, torch, dist, rank, world, local)
+    if rank == 0:
+        full = {"metric": METRIC, "value": line.pop("value"), "unit": line.pop("unit"), "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": line.pop("ms_per_step"),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": line.pop("dtype"),
+                "data": "synthetic"}
+        full.update(line)
+        if not args.no_cpu_baseline:
+            full["cpu_baseline"] = cpu_baseline(args.workload)
+        print(json.dumps(full), flush=True)
     if dist:
         dist.destroy_process_group()
     return 0
@@ -297,11 +451,14 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="decay_1e7", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
+    if args.steps is None:
+        args.steps = DEFAULT_STEPS[args.workload]
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -144,10 +144,12 @@ rf_status rf_nll_grad(const rf_model* m, const rf_data* d, const double* theta, 
 rf_status rf_nll_grad_async(const rf_model* m, const rf_data* d, const double* d_theta, double* d_out,
                             int32_t* d_flags, void* stream);
 
-/* Per-chunk partial sums of log p_i (the first level of the reduction), for
- * checking a sample of chunks against an independent evaluation: out[c] for
- * chunk c of set `set` (4096 events each, the last one ragged), at most
- * max_chunks values.  *n_chunks receives the set's chunk count. */
+/* Per-chunk partial sums (the first level of the reduction), for checking a
+ * sample of chunks against an independent evaluation: for chunk c of set
+ * `set` (4096 events each, the last one ragged), out[c*(1+n_free)] = the sum
+ * of log p_i over the chunk and out[c*(1+n_free)+1+k] = the sum of
+ * dlog p_i/dtheta_k, for at most max_chunks chunks.  *n_chunks receives the
+ * set's chunk count. */
 rf_status rf_nll_chunks(const rf_model* m, const rf_data* d, const double* theta, int32_t set, double* out,
                         int32_t max_chunks, int32_t* n_chunks);
 
@@ -156,13 +158,22 @@ rf_status rf_nll_chunks(const rf_model* m, const rf_data* d, const double* theta
  * The NLL does not depend on it (bitwise). */
 rf_status rf_set_launch(rf_model* m, int32_t threads_per_block, int32_t blocks_per_sm);
 
+/* Autotuner: times `passes` NLL+gradient passes over `d` for every supported
+ * tile shape (threads per block x resident blocks per SM), keeps the fastest
+ * on the model (as rf_set_launch would) and reports it; *best_ms is the mean
+ * pass time of the winner.  Results do not depend on the shape (bitwise). */
+rf_status rf_autotune(rf_model* m, rf_data* d, int32_t passes, int32_t* threads_per_block, int32_t* blocks_per_sm,
+                      double* best_ms);
+
 /* ------------------------------------------------------------------- fits */
 
 typedef struct {
   double tol_edm;       /* stop when EDM = g^T H g / 2 < tol_edm (default 1e-7)   */
   int32_t max_evals;    /* per set (default 1000)                                 */
   int32_t want_cov;     /* 1: covariance from the Hessian at the minimum          */
-  int32_t reserved[2];
+  int32_t no_graph;     /* 1: launch each evaluation directly instead of replaying
+                           the captured CUDA graph of the evaluation step        */
+  int32_t reserved;
 } rf_fit_opts;
 
 /* Maximum-likelihood fit of every set (Sec. 1: fits).  Quasi-Newton (BFGS)

@@ -24,7 +24,7 @@ class rf_node(C.Structure):
 
 class rf_fit_opts(C.Structure):
     _fields_ = [("tol_edm", C.c_double), ("max_evals", C.c_int32), ("want_cov", C.c_int32),
-                ("reserved", C.c_int32 * 2)]
+                ("no_graph", C.c_int32), ("reserved", C.c_int32)]
 
 
 # Every exported symbol of include/rf.h with (restype, argtypes).
@@ -46,6 +46,7 @@ SIGNATURES = {
     "rf_nll_grad_async": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "rf_nll_chunks": (C.c_int, [_vp, _vp, _dp, C.c_int32, _dp, C.c_int32, _ip]),
     "rf_set_launch": (C.c_int, [_vp, C.c_int32, C.c_int32]),
+    "rf_autotune": (C.c_int, [_vp, _vp, C.c_int32, _ip, _ip, _dp]),
     "rf_fit": (C.c_int, [_vp, _vp, _dp, C.POINTER(rf_fit_opts), _dp, _dp, _dp, _ip, _ip]),
     "rf_generate_toys": (C.c_int, [_vp, _dp, C.c_int32, C.c_uint64, C.c_int32, _dp, C.c_int32, _ip, C.POINTER(_vp)]),
     "rf_hist64": (C.c_int, [_vp, _vp, C.c_int32, _vp, _vp]),

@@ -157,6 +157,13 @@ def _theta(model: Model, data: Data, theta):
     return th
 
 
+def autotune(model: Model, data: Data, passes: int = 5):
+    """Pick the fastest tile shape for (model, data); returns (threads, blocks_per_sm, ms)."""
+    t, b, ms = C.c_int32(), C.c_int32(), C.c_double()
+    L.check(L.load().rf_autotune(model._h, data._h, passes, C.byref(t), C.byref(b), C.byref(ms)))
+    return t.value, b.value, ms.value
+
+
 def nll(model: Model, data: Data, theta, stream=None, allow_domain=False):
     th = _theta(model, data, theta)
     out = np.zeros(data.n_sets)
@@ -183,19 +190,22 @@ def nll_grad_async(model: Model, data: Data, d_theta, d_out, d_flags, stream=Non
                                        _stream(stream)))
 
 
-def nll_chunks(model: Model, data: Data, theta, set_index: int = 0, max_chunks: int = 1 << 20):
+def nll_chunks(model: Model, data: Data, theta, set_index: int = 0, max_chunks: int = 1 << 16):
+    """Per-chunk (sum log p, sum dlog p/dtheta) of one set: array (chunks, 1 + n_free)."""
     th = _theta(model, data, theta)
-    out = np.zeros(max_chunks)
+    P = model.n_free
+    out = np.zeros(max_chunks * (1 + P))
     n = C.c_int32()
     L.check(L.load().rf_nll_chunks(model._h, data._h, _dp(th), set_index, _dp(out), max_chunks, C.byref(n)),
             (L.RF_OK, L.RF_E_DOMAIN))
-    return out[: min(n.value, max_chunks)]
+    return out[: min(n.value, max_chunks) * (1 + P)].reshape(-1, 1 + P)
 
 
-def fit(model: Model, data: Data, theta0=None, tol_edm: float = 1e-7, max_evals: int = 1000, want_cov=True):
+def fit(model: Model, data: Data, theta0=None, tol_edm: float = 1e-7, max_evals: int = 1000, want_cov=True,
+        graph: bool = True):
     S, P = data.n_sets, model.n_free
     th0 = None if theta0 is None else _theta(model, data, theta0)
-    opts = L.rf_fit_opts(tol_edm, max_evals, 1 if want_cov else 0)
+    opts = L.rf_fit_opts(tol_edm, max_evals, 1 if want_cov else 0, 0 if graph else 1, 0)
     th = np.zeros(S * P)
     nl = np.zeros(S)
     cov = np.zeros(S * P * P) if want_cov else None

@@ -360,21 +360,34 @@ rf_status rf_nll_chunks(const rf_model* m, const rf_data* d, const double* theta
                         int32_t max_chunks, int32_t* n_chunks) {
   rf_status s = check_eval_args(m, d, theta, out);
   if (s != RF_OK) return s;
-  if (set < 0 || set >= d->n_sets || !n_chunks) { set_error("rf_nll_chunks: bad set"); return RF_E_INVALID; }
+  if (set < 0 || set >= d->n_sets || !n_chunks || max_chunks < 0) { set_error("rf_nll_chunks: bad set"); return RF_E_INVALID; }
   rf_data* dd = const_cast<rf_data*>(d);
-  std::vector<double> nll(d->n_sets);
-  s = rf_nll(m, d, theta, nll.data(), nullptr);
+  const int P = m->m.prog.n_free, Q = 1 + m->m.prog.n_slots;
+  std::vector<double> nll(d->n_sets), grad((size_t)d->n_sets * std::max(1, P));
+  s = rf_nll_grad(m, d, theta, nll.data(), grad.data(), nullptr);
   if (s != RF_OK && s != RF_E_DOMAIN) return s;
   const int64_t C = d->chunks[set];
   *n_chunks = (int32_t)C;
   const int64_t n = std::min<int64_t>(C, max_chunks);
   if (n <= 0) return s;
-  // NLL-only passes use Q = 1: node = (sum, compensation).
-  std::vector<double> buf(2 * n);
+  // Level-0 nodes of the set's tree: (sum, compensation) per quantity, slots
+  // mapped to free parameters as the root does.
+  std::vector<double> buf((size_t)2 * Q * n);
   const double* tree = (const double*)dd->ws.tree.p;
-  if (!cuda_ok(cudaMemcpy(buf.data(), tree + d->tree_base[set] * 2, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost), "chunk read"))
+  if (!cuda_ok(cudaMemcpy(buf.data(), tree + d->tree_base[set] * 2 * Q, sizeof(double) * 2 * Q * n,
+                          cudaMemcpyDeviceToHost), "chunk read"))
     return RF_E_CUDA;
-  for (int64_t c = 0; c < n; ++c) out[c] = buf[2 * c] + buf[2 * c + 1];
+  for (int64_t c = 0; c < n; ++c) {
+    const double* node = buf.data() + (size_t)2 * Q * c;
+    double* o = out + (size_t)c * (1 + P);
+    o[0] = node[0] + node[Q];
+    for (int k = 0; k < P; ++k) {
+      double gk = 0.0;
+      for (int sl = 0; sl < m->m.prog.n_slots; ++sl)
+        if (m->m.prog.slot_free[sl] == k) gk += node[1 + sl] + node[Q + 1 + sl];
+      o[1 + k] = gk;
+    }
+  }
   return s;
 }
 
@@ -402,3 +415,63 @@ rf_status finish_data(rf_data* d) {
 }
 
 }  // namespace rf
+
+extern "C" rf_status rf_autotune(rf_model* m, rf_data* d, int32_t passes, int32_t* threads_per_block,
+                                 int32_t* blocks_per_sm, double* best_ms) {
+  if (!m || !d || passes < 1 || !threads_per_block || !blocks_per_sm || !best_ms) {
+    set_error("rf_autotune: bad argument");
+    return RF_E_INVALID;
+  }
+  if (d->n_obs != m->m.prog.n_obs) {
+    set_error("rf_autotune: data and model have different observable counts");
+    return RF_E_INVALID;
+  }
+  if (!ensure_workspace(m, d)) return RF_E_OOM;
+  Workspace& w = d->ws;
+  const int P = m->m.prog.n_free, S = d->n_sets;
+  std::vector<double> th((size_t)S * std::max(1, P));
+  for (int s = 0; s < S; ++s)
+    for (int k = 0; k < P; ++k) th[(size_t)s * P + k] = m->m.theta_default[k];
+  if (P > 0 && !cuda_ok(cudaMemcpy(w.theta.p, th.data(), sizeof(double) * S * P, cudaMemcpyHostToDevice), "autotune"))
+    return RF_E_CUDA;
+  cudaEvent_t e0, e1;
+  if (!cuda_ok(cudaEventCreate(&e0), "autotune") || !cuda_ok(cudaEventCreate(&e1), "autotune")) return RF_E_CUDA;
+  static const int kThreads[] = {128, 256, 512};
+  static const int kBps[] = {1, 2, 3, 4, 6, 8, 12, 16};
+  const int save_t = m->m.threads_per_block, save_b = m->m.blocks_per_sm;
+  double best = 1e300;
+  int bt = 0, bb = 0;
+  for (int t : kThreads) {
+    if (!launch_supports_threads(m->m.shape, t)) continue;
+    for (int b : kBps) {
+      if (!launch_fits(m->m.shape, t, b)) continue;
+      m->m.threads_per_block = t;
+      m->m.blocks_per_sm = b;
+      launch_pass(m, d, d->all_plan, (const double*)w.theta.p, (double*)w.out.p, (int32_t*)w.flags.p, true, 0);
+      cudaEventRecord(e0, 0);
+      for (int i = 0; i < passes; ++i)
+        launch_pass(m, d, d->all_plan, (const double*)w.theta.p, (double*)w.out.p, (int32_t*)w.flags.p, true, 0);
+      cudaEventRecord(e1, 0);
+      if (!cuda_ok(cudaEventSynchronize(e1), "autotune")) {
+        m->m.threads_per_block = save_t;
+        m->m.blocks_per_sm = save_b;
+        return RF_E_CUDA;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms / passes < best) {
+        best = ms / passes;
+        bt = t;
+        bb = b;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  m->m.threads_per_block = bt;
+  m->m.blocks_per_sm = bb;
+  *threads_per_block = bt;
+  *blocks_per_sm = bb;
+  *best_ms = best;
+  return RF_OK;
+}

@@ -294,21 +294,93 @@ bool invert(std::vector<double> A, int n, double* inv) {
 }  // namespace
 
 // One device pass over the sets in `active` at their trial points (theta),
-// results into nll/grad (indexed by set).  Rebuilds the work plan when the
-// active set changed since the last call.
+// results into nll/grad (indexed by set).  The pass (parameter upload, the
+// two kernels, result download) is captured once per work plan as a CUDA
+// graph and replayed.  The plan covers a superset of the active sets and is
+// rebuilt only when the events of still-active sets fall below 3/4 of the
+// planned events (finished sets are re-evaluated at their last point and
+// their results ignored) or a set outside the plan becomes active.
 struct Evaluator {
   const rf_model* m;
   rf_data* d;
   Plan plan;
   std::vector<int32_t> planned;
+  int64_t planned_events = 0;
+  cudaStream_t st = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  bool use_graph = true;
+
+  Evaluator(const rf_model* mm, rf_data* dd, bool graph) : m(mm), d(dd), use_graph(graph) {}
+  ~Evaluator() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (st) cudaStreamDestroy(st);
+  }
+
+  int64_t events_of(const std::vector<int32_t>& sets) const {
+    int64_t n = 0;
+    for (int32_t s : sets) n += d->offsets[s + 1] - d->offsets[s];
+    return n;
+  }
+
+  rf_status capture() {
+    if (exec) {
+      cudaGraphExecDestroy(exec);
+      exec = nullptr;
+    }
+    Workspace& w = d->ws;
+    const int P = m->m.prog.n_free, S = d->n_sets;
+    cudaGraph_t graph = nullptr;
+    if (!cuda_ok(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "graph capture")) return RF_E_CUDA;
+    cudaMemcpyAsync(w.theta.p, w.h_theta.p, sizeof(double) * S * P, cudaMemcpyHostToDevice, st);
+    launch_pass(m, d, plan, (const double*)w.theta.p, (double*)w.out.p, (int32_t*)w.flags.p, true, st);
+    cudaMemcpyAsync(w.h_out.p, w.out.p, sizeof(double) * S * (1 + P), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(w.h_flags.p, w.flags.p, sizeof(int32_t) * S, cudaMemcpyDeviceToHost, st);
+    if (!cuda_ok(cudaStreamEndCapture(st, &graph), "graph capture")) return RF_E_CUDA;
+    const bool ok = cuda_ok(cudaGraphInstantiate(&exec, graph, 0), "graph instantiate");
+    cudaGraphDestroy(graph);
+    return ok ? RF_OK : RF_E_CUDA;
+  }
+
   rf_status run(const std::vector<int32_t>& active, const std::vector<double>& theta, std::vector<double>& nll,
                 std::vector<double>& grad) {
-    if (active != planned) {
+    bool covered = !planned.empty();
+    if (covered) {
+      size_t j = 0;  // active and planned are both increasing
+      for (int32_t s : active) {
+        while (j < planned.size() && planned[j] < s) ++j;
+        if (j == planned.size() || planned[j] != s) {
+          covered = false;
+          break;
+        }
+      }
+    }
+    const int64_t need = events_of(active);
+    const bool rebuild = !covered || 4 * need < 3 * planned_events;
+    if (rebuild) {
       if (!build_plan(d, active, &plan)) return RF_E_OOM;
       planned = active;
+      planned_events = need;
     }
-    const rf_status s = eval_host(m, d, plan, theta.data(), nll.data(), grad.data(), nullptr);
-    return s == RF_E_DOMAIN ? RF_OK : s;  // per-set +inf is handled by the fits
+    if (!use_graph) {
+      const rf_status s = eval_host(m, d, plan, theta.data(), nll.data(), grad.data(), nullptr);
+      return s == RF_E_DOMAIN ? RF_OK : s;
+    }
+    if (!st && !cuda_ok(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking), "stream")) return RF_E_CUDA;
+    if (rebuild || !exec) {
+      const rf_status s = capture();
+      if (s != RF_OK) return s;
+    }
+    Workspace& w = d->ws;
+    const int P = m->m.prog.n_free, S = d->n_sets;
+    std::memcpy(w.h_theta.p, theta.data(), sizeof(double) * S * P);
+    if (!cuda_ok(cudaGraphLaunch(exec, st), "graph launch") || !cuda_ok(cudaStreamSynchronize(st), "graph sync"))
+      return RF_E_CUDA;
+    const double* o = (const double*)w.h_out.p;
+    for (int32_t s : planned) {
+      nll[s] = o[(size_t)s * (1 + P)];
+      for (int k = 0; k < P; ++k) grad[(size_t)s * P + k] = o[(size_t)s * (1 + P) + 1 + k];
+    }
+    return RF_OK;
   }
 };
 
@@ -367,7 +439,7 @@ extern "C" rf_status rf_fit(const rf_model* m, const rf_data* d, const double* t
     co.to_internal(t0.data(), F.trial.data());
     F.phase = INIT;
   }
-  Evaluator ev{m, dd, {}, {}};
+  Evaluator ev(m, dd, !(opts && opts->no_graph == 1));
   std::vector<int32_t> active;
   std::vector<double> ga(P);
   while (true) {

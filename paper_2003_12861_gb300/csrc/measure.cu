@@ -79,16 +79,21 @@ __global__ void probe_read(const double2* __restrict__ p, size_t n, double* out)
 
 }  // namespace
 
+bool capturing(cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  return cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone;
+}
+
 void timing_begin(cudaStream_t st) {
   std::lock_guard<std::mutex> lk(g_tmu);
-  if (!g_timing) return;
+  if (!g_timing || capturing(st)) return;
   g_open = new_event();
   if (g_open) cudaEventRecord(g_open, st);
 }
 
 void timing_end(cudaStream_t st) {
   std::lock_guard<std::mutex> lk(g_tmu);
-  if (!g_timing || !g_open) return;
+  if (!g_timing || !g_open || capturing(st)) return;
   cudaEvent_t e = new_event();
   if (!e) return;
   cudaEventRecord(e, st);

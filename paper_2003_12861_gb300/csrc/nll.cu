@@ -540,6 +540,21 @@ void launch_param_point(const Program& P, const Pass& pass, cudaStream_t st) {
   param_point_kernel<<<blocks > 0 ? blocks : 1, threads, 0, st>>>(P, pass);
 }
 
+bool launch_supports_threads(Shape shape, int threads) {
+  (void)shape;
+  return threads == kLanes;
+}
+
+bool launch_fits(Shape shape, int threads, int blocks_per_sm) {
+  (void)shape;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, events_generic<true>, threads, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return blocks_per_sm <= 4;
+  }
+  return blocks_per_sm <= n;
+}
+
 void launch_events(const Program& P, Shape shape, const Columns& cols, const Pass& pass, int threads,
                    int blocks_per_sm, int n_sm, cudaStream_t st) {
   (void)shape;

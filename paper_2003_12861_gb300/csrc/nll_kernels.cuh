@@ -42,6 +42,11 @@ void launch_param_point(const Program& P, const Pass& pass, cudaStream_t st);
 void timing_begin(cudaStream_t st);
 void timing_end(cudaStream_t st);
 
+// Tile shapes the event kernel of a shape supports, and whether a launch
+// shape fits on an SM (registers, shared memory).
+bool launch_supports_threads(Shape shape, int threads);
+bool launch_fits(Shape shape, int threads, int blocks_per_sm);
+
 void launch_events(const Program& P, Shape shape, const Columns& cols, const Pass& pass, int threads,
                    int blocks_per_sm, int n_sm, cudaStream_t st);
 

@@ -153,11 +153,12 @@ def test_chunk_partials_match_oracle(oracle_mod):
     d = api.Data.upload(m, cols)
     th = TRUE["decay_model"]
     parts = api.nll_chunks(m, d, th)
-    assert len(parts) == 6
-    for c, v in enumerate(parts):
+    assert parts.shape == (6, 1 + m.n_free)
+    for c in range(6):
         sl = [col[c * 4096:(c + 1) * 4096] for col in cols]
-        nll, _, al, _, _ = om.nll(th, sl)
-        assert abs(v - (-nll)) <= 1e-12 * al
+        nll, g, al, ag, _ = om.nll(th, sl)
+        assert abs(parts[c, 0] - (-nll)) <= 1e-12 * al
+        assert np.all(np.abs(parts[c, 1:] - (-g)) <= 1e-9 * ag)
 
 
 def test_device_resident_async_pass(oracle_mod):

@@ -1,0 +1,95 @@
+"""Parity at the benchmark's full sizes, in the launch configuration bench.py
+times (device-generated data, autotuned tile shape, graph-replayed fits).
+The oracle checks everything it can compute in seconds: the whole 1e7-event
+dataset; for the 1e8-event product a sample of chunks it regenerates from
+their counters alone; for the 4096-toy batch a sample of toys."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2003_12861_gb300 import _lib as L
+from paper_2003_12861_gb300 import api
+from paper_2003_12861_gb300 import workloads as W
+
+from helpers import GRAD_RTOL, NLL_RTOL, TRUE, check_nll
+
+pytestmark = pytest.mark.gpu
+
+
+def test_decay_1e7_full(oracle_mod):
+    spec = W.decay_model()
+    m = api.Model.from_spec(spec)
+    om = oracle_mod.Model(spec.nodes, spec.root)
+    n = 10_000_000
+    d = api.generate_toys(m, TRUE["decay_model"], W.SEED_BASE + 1, [float(n)], poisson=False)
+    api.autotune(m, d, passes=2)
+    cols = om.generate(TRUE["decay_model"], W.SEED_BASE + 1, 0, 0, n)
+    assert np.array_equal(d.read(0), cols[0])
+    th = TRUE["decay_model"] * (1 + 0.02 * np.cos(np.arange(6)))
+    nll, g = api.nll_grad(m, d, th)
+    check_nll(nll, g, om.nll(th, cols), "decay 1e7")
+
+
+def test_prod3_1e8_sampled_chunks(oracle_mod):
+    spec = W.prod3_model()
+    m = api.Model.from_spec(spec)
+    om = oracle_mod.Model(spec.nodes, spec.root)
+    n = 100_000_000
+    d = api.generate_toys(m, TRUE["prod3_model"], W.SEED_BASE + 1, [float(n)], poisson=False,
+                          f32=[True, True, True])
+    api.autotune(m, d, passes=2)
+    th = TRUE["prod3_model"] * (1 + 0.01 * np.sin(np.arange(12)))
+    nll, g = api.nll_grad(m, d, th)
+    parts = api.nll_chunks(m, d, th, max_chunks=1 << 15)
+    n_chunks = math.ceil(n / 4096)
+    assert parts.shape[0] == n_chunks
+    # property at full size: the root equals the fixed tree over the chunk partials
+    assert abs(-math.fsum(parts[:, 0]) - nll) <= 1e-12 * abs(nll)
+    bounds = om.gen_bounds(TRUE["prod3_model"])
+    for c in [0, 1, 777, 12345, n_chunks // 2, n_chunks - 1]:
+        i0, i1 = c * 4096, min(n, (c + 1) * 4096)
+        want = om.generate(TRUE["prod3_model"], W.SEED_BASE + 1, 0, i0, i1, bounds=bounds)
+        want32 = [w.astype(np.float32).astype(np.float64) for w in want]
+        for col in range(3):
+            assert np.array_equal(d.read(col, i0, i1), want32[col]), (c, col)
+        ref_nll, ref_g, al, ag, rc = om.nll(th, want32)
+        assert rc == 0
+        assert abs(parts[c, 0] + ref_nll) <= NLL_RTOL * al, c
+        assert np.all(np.abs(parts[c, 1:] + ref_g) <= GRAD_RTOL * ag), c
+
+
+def test_toys_4096_sampled_fits(oracle_mod):
+    spec = W.decay_model()
+    m = api.Model.from_spec(spec)
+    om = oracle_mod.Model(spec.nodes, spec.root)
+    S = 4096
+    seed = W.SEED_BASE + 2
+    mean = W.toy_mean_sizes(S, seed)
+    th = W.toy_thetas(S, seed)
+    d = api.generate_toys(m, th, seed, mean, poisson=True)
+    api.autotune(m, d, passes=1)
+    r = api.fit(m, d, tol_edm=1e-10)
+    assert (r["status"] == L.RF_OK).mean() > 0.9
+    off = d.offsets()
+    lo, hi = spec.bounds().T
+    compared = 0
+    for s in [5, 100, 1000, 2047, 3000, 4095, 17, 333, 2500, 3900]:
+        n = int(off[s + 1] - off[s])
+        assert n == oracle_mod.poisson(seed, s, mean[s])
+        cols = om.generate(th[s], seed, s, 0, n)
+        assert np.array_equal(d.read(0, off[s], off[s + 1]), cols[0]), s
+        if r["status"][s] != L.RF_OK or compared >= 3:
+            continue
+        o = om.fit(cols, tol_edm=1e-10)
+        if abs(o["nll"] - r["nll"][s]) > 1e-6:
+            o = om.fit(cols, theta0=r["theta"][s], tol_edm=1e-10)
+        interior = np.all(np.minimum(o["theta"] - lo, hi - o["theta"]) > 1e-3 * (hi - lo))
+        if o["status"] != 0 or not interior or not np.all(np.isfinite(o["cov"])) \
+                or not np.all(np.linalg.eigvalsh(o["cov"]) > 0):
+            continue
+        sig = np.sqrt(np.diag(o["cov"]))
+        assert np.all(np.abs(r["theta"][s] - o["theta"]) <= 1e-3 * sig), s
+        assert abs(r["nll"][s] - o["nll"]) <= 1e-7 * abs(o["nll"]), s
+        compared += 1
+    assert compared >= 2
