@@ -210,6 +210,45 @@ rf_status rf_generate_toys(const rf_model* m, const double* theta, int32_t theta
  * clamped to [0, 63].  d_out: DEVICE float, n_sets x 64. */
 rf_status rf_hist64(const rf_model* m, const rf_data* d, int32_t col, float* d_out, void* stream);
 
+/* ------------------------------------------------------------ learned start */
+
+/* A multilayer perceptron that maps the 64-bin histogram of a toy dataset
+ * (rf_hist64) to a starting point for its fit.  The paper has no learned
+ * component; this is the learned-start configuration: n_in inputs,
+ * n_hidden_layers hidden layers of n_hidden GELU (erf form) units, n_out
+ * linear outputs.  GEMM operands are rounded to BF16 (nearest even) and
+ * multiplied on the tensor cores with FP32 accumulation; master weights are
+ * FP32.  Weights start Uniform(+-1/sqrt(fan_in)) from `seed`, biases 0.
+ * Parameters (flat FP32): per layer W[n_in x n_out] row-major, then b[n_out]. */
+rf_status rf_mlp_create(int32_t n_in, int32_t n_hidden, int32_t n_hidden_layers, int32_t n_out, uint64_t seed,
+                        rf_mlp** out);
+void rf_mlp_destroy(rf_mlp* n);
+int64_t rf_mlp_n_params(const rf_mlp* n);
+rf_status rf_mlp_get_params(const rf_mlp* n, float* host);        /* n_params FP32 master weights */
+rf_status rf_mlp_set_params(rf_mlp* n, const float* host);
+/* d_y[batch x n_out] = net(d_x[batch x n_in]); DEVICE pointers, asynchronous.
+ * After rf_mlp_train with standardise = 1 the outputs are mapped back to
+ * the targets' units (output * sd + mean). */
+rf_status rf_mlp_forward(rf_mlp* n, const float* d_x, int32_t batch, float* d_y, void* stream);
+/* Forward + backward of the mean-squared error against d_t (DEVICE,
+ * batch x n_out, in the net's raw output units); *loss (host, may be NULL;
+ * synchronises when given) and the gradient kept inside the net for
+ * rf_mlp_adam, and copied to d_grad (DEVICE, n_params floats) if not NULL. */
+rf_status rf_mlp_grad(rf_mlp* n, const float* d_x, const float* d_t, int32_t batch, float* loss, float* d_grad,
+                      void* stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) with the last gradient. */
+rf_status rf_mlp_adam(rf_mlp* n, float lr, void* stream);
+/* Train on rows x (n_in, n_out) DEVICE arrays: `epochs` passes of shuffled
+ * mini-batches (seeded permutation, the ragged remainder dropped), Adam with
+ * a cosine decay of the learning rate from lr to 0; standardise = 1 trains
+ * on per-output standardised targets and keeps the affine map for
+ * rf_mlp_forward.  *final_loss = the mean loss of the last epoch. */
+rf_status rf_mlp_train(rf_mlp* n, const float* d_x, const float* d_t, int32_t rows, int32_t batch, int32_t epochs,
+                       float lr, uint64_t seed, int32_t standardise, float* final_loss);
+/* Checkpoint: dimensions, step, master weights, Adam moments, output map. */
+rf_status rf_mlp_save(const rf_mlp* n, const char* path);
+rf_status rf_mlp_load(const char* path, rf_mlp** out);
+
 /* ------------------------------------------------------------ measurement */
 
 /* Re-copy host columns (same count and dtypes as the dataset was created

@@ -56,6 +56,18 @@ SIGNATURES = {
     "rf_slow_events": (C.c_int, [_vp, _i64p]),
     "rf_probe": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, _dp]),
     "rf_nll_grad_noalloc": (C.c_int, [_vp, C.POINTER(_vp), _ip, C.c_int64, _vp, _vp, _vp, _vp]),
+    "rf_mlp_create": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_uint64, C.POINTER(_vp)]),
+    "rf_mlp_destroy": (None, [_vp]),
+    "rf_mlp_n_params": (C.c_int64, [_vp]),
+    "rf_mlp_get_params": (C.c_int, [_vp, C.POINTER(C.c_float)]),
+    "rf_mlp_set_params": (C.c_int, [_vp, C.POINTER(C.c_float)]),
+    "rf_mlp_forward": (C.c_int, [_vp, _vp, C.c_int32, _vp, _vp]),
+    "rf_mlp_grad": (C.c_int, [_vp, _vp, _vp, C.c_int32, C.POINTER(C.c_float), _vp, _vp]),
+    "rf_mlp_adam": (C.c_int, [_vp, C.c_float, _vp]),
+    "rf_mlp_train": (C.c_int, [_vp, _vp, _vp, C.c_int32, C.c_int32, C.c_int32, C.c_float, C.c_uint64, C.c_int32,
+                               C.POINTER(C.c_float)]),
+    "rf_mlp_save": (C.c_int, [_vp, C.c_char_p]),
+    "rf_mlp_load": (C.c_int, [C.c_char_p, C.POINTER(_vp)]),
     "rf_last_error": (C.c_char_p, []),
     "rf_version": (C.c_char_p, []),
 }

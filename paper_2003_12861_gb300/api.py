@@ -282,3 +282,65 @@ def nll_grad_noalloc(model: Model, cols, d_theta, d_out, d_flags, stream=None):
     L.check(L.load().rf_nll_grad_noalloc(model._h, ptrs, dt, n, C.c_void_p(d_theta.data_ptr()),
                                          C.c_void_p(d_out.data_ptr()), C.c_void_p(d_flags.data_ptr()),
                                          _stream(stream)))
+
+
+# ----------------------------------------------------------- learned start
+
+class MLP:
+    """The learned-start network (rf_mlp_*): histogram -> fit start."""
+
+    def __init__(self, n_in=64, n_hidden=128, n_hidden_layers=3, n_out=6, seed=0, _handle=None):
+        lib = L.load()
+        if _handle is None:
+            h = C.c_void_p()
+            L.check(lib.rf_mlp_create(n_in, n_hidden, n_hidden_layers, n_out, seed, C.byref(h)))
+            _handle = h
+        self._h = _handle
+        self.n_params = lib.rf_mlp_n_params(self._h)
+
+    @classmethod
+    def load(cls, path: str):
+        h = C.c_void_p()
+        L.check(L.load().rf_mlp_load(path.encode(), C.byref(h)))
+        return cls(_handle=h)
+
+    def save(self, path: str):
+        L.check(L.load().rf_mlp_save(self._h, path.encode()))
+
+    def get_params(self) -> np.ndarray:
+        out = np.zeros(self.n_params, dtype=np.float32)
+        L.check(L.load().rf_mlp_get_params(self._h, out.ctypes.data_as(C.POINTER(C.c_float))))
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        L.check(L.load().rf_mlp_set_params(self._h, p.ctypes.data_as(C.POINTER(C.c_float))))
+
+    def forward(self, d_x, d_y, stream=None):
+        L.check(L.load().rf_mlp_forward(self._h, C.c_void_p(d_x.data_ptr()), d_x.shape[0],
+                                        C.c_void_p(d_y.data_ptr()), _stream(stream)))
+
+    def grad(self, d_x, d_t, d_grad=None, stream=None):
+        loss = C.c_float()
+        L.check(L.load().rf_mlp_grad(self._h, C.c_void_p(d_x.data_ptr()), C.c_void_p(d_t.data_ptr()),
+                                     d_x.shape[0], C.byref(loss),
+                                     C.c_void_p(d_grad.data_ptr()) if d_grad is not None else None,
+                                     _stream(stream)))
+        return loss.value
+
+    def adam(self, lr: float, stream=None):
+        L.check(L.load().rf_mlp_adam(self._h, lr, _stream(stream)))
+
+    def train(self, d_x, d_t, batch=1024, epochs=10, lr=1e-3, seed=0, standardise=True):
+        loss = C.c_float()
+        L.check(L.load().rf_mlp_train(self._h, C.c_void_p(d_x.data_ptr()), C.c_void_p(d_t.data_ptr()),
+                                      d_x.shape[0], batch, epochs, lr, seed, 1 if standardise else 0,
+                                      C.byref(loss)))
+        return loss.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            L.load().rf_mlp_destroy(self._h)
+            self._h = None
+
+    __del__ = close
