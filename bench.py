@@ -49,8 +49,10 @@ WORKLOADS = {
     "prod3_1e8_f32": ("prod3_model", W.PROD3_TRUE, 100_000_000, True, 12),
     "gauss_poly1_1e4": ("gauss_poly1_model", W.GAUSS_POLY1_TRUE, 10_000, False, 8),
     "decay_toys_4096": ("decay_model", W.DECAY_TRUE, 0, False, 8),
+    "learned_start": ("decay_model", W.DECAY_TRUE, 0, False, 8),
 }
-DEFAULT_STEPS = {"decay_1e7": 400, "prod3_1e8_f32": 40, "gauss_poly1_1e4": 2000, "decay_toys_4096": 3}
+DEFAULT_STEPS = {"decay_1e7": 400, "prod3_1e8_f32": 40, "gauss_poly1_1e4": 2000, "decay_toys_4096": 3,
+                 "learned_start": 1}
 
 
 def dist_env():
@@ -157,7 +159,7 @@ def oracle_toy_fits_per_s(seconds: float):
 
 
 def cpu_baseline(wl: str):
-    if wl == "decay_toys_4096":
+    if wl in ("decay_toys_4096", "learned_start"):
         v, s = oracle_toy_fits_per_s(15.0)
         return {"value": v, "unit": "toy fits/s", "cores": 1, "kind": "oracle", "sample": s}
     v, s = oracle_events_per_s(wl, 12.0, 400_000 if wl != "gauss_poly1_1e4" else 10_000)
@@ -170,7 +172,7 @@ def run_reference(args):
         return 0
     wl = args.workload
     t0 = time.perf_counter()
-    if wl == "decay_toys_4096":
+    if wl in ("decay_toys_4096", "learned_start"):
         # each step: the oracle fits one toy of the batch
         v, s = oracle_toy_fits_per_s(max(3.0, 1.5 * args.steps))
         unit = "toy fits/s"
@@ -416,6 +418,41 @@ def run_toys(args, api, torch, dist, rank, world, local):
     }
 
 
+def run_learned(args, api, torch, dist, rank, world, local):
+    """Learned start: train on plain-fitted toys (setup, untimed), then time
+    the 1e4 fresh evaluation toys fitted from the network's start (with the
+    plain fit as fallback) next to the same toys fitted from the plain start."""
+    from paper_2003_12861_gb300 import learned
+
+    spec = W.decay_model()
+    model = api.Model.from_spec(spec)
+    seed = W.SEED_BASE + 4 + 1000 * rank
+    X, Y, tinfo = learned.build_training_set(model, args.train_toys, seed)
+    net, ninfo = learned.train(X, Y, epochs=args.epochs, batch=1024, lr=1e-3, seed=seed)
+    warm = learned.compare(net, model, 512, seed + 999)
+    del warm
+    with ClockSampler(local) as clk:
+        r = None
+        for _ in range(args.steps):
+            r = learned.compare(net, model, 10_000, seed + 777)
+    if rank != 0:
+        return None
+    return {
+        "value": r["learned"]["toy_fits_per_s"] * world, "unit": "toy fits/s",
+        "ms_per_step": 1e3 * r["learned"]["wall_s"], "dtype": "f64 likelihood, bf16 x bf16 -> f32 network",
+        "config": {"workload": "learned_start", "train_toys": tinfo["toys"], "train_converged": tinfo["converged"],
+                   "eval_toys": 10_000, "sizes": "Poisson(N), N log-uniform in [1e3, 1e5]",
+                   "theta": "uniform +-30% around the decay model's values", "network": "64-128-128-128-6 GELU",
+                   "epochs": args.epochs},
+        "learned_vs_plain": r,
+        "training": {"build_s": tinfo["seconds"], "train_s": ninfo["seconds"], "final_loss": ninfo["final_loss"]},
+        "e2e": {"value": r["learned"]["toy_fits_per_s"] * world, "unit": "toy fits/s",
+                "h2d_bytes_per_step": 8 * 10_000 * 6, "d2h_bytes_per_step": 10_000 * 9 * 8,
+                "note": "histogram, network, fits and fallback through the public API, host results"},
+        "gpu_launches": None, "clocks": clk.summary(),
+    }
+
+
 def run_ours(args):
     import torch
 
@@ -432,6 +469,8 @@ def run_ours(args):
     L.load()
     if args.workload == "decay_toys_4096":
         line = run_toys(args, api, torch, dist, rank, world, local)
+    elif args.workload == "learned_start":
+        line = run_learned(args, api, torch, dist, rank, world, local)
     else:
         line = run_events(args, api, torch, dist, rank, world, local)
     if rank == 0:
@@ -456,6 +495,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="decay_1e7", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--train-toys", type=int, default=1_000_000, help="learned_start: training toys")
+    ap.add_argument("--epochs", type=int, default=20, help="learned_start: training epochs")
     args = ap.parse_args()
     if args.steps is None:
         args.steps = DEFAULT_STEPS[args.workload]
