@@ -208,19 +208,23 @@ def run_reference(args):
 
 # ------------------------------------------------------------------- ours
 
-def transcendental_ceiling(api, model_spec, slow_fraction, n_events, bytes_per_event, peaks, peak_kind):
+def transcendental_ceiling(api, model_spec, slow_fraction, n_events, bytes_per_event, peaks, peak_kind, ff=True):
     """ALU ceiling: per event the fast set {exp per Gauss/exp/decay leaf, log,
     reciprocal}; events in the decay resolution region add {exp, erfc} per
-    decay leaf; rates measured in-run by the library's probe."""
+    decay leaf; rates measured in-run by the library's probe with the
+    implementations the kernel uses (float-float, or CUDA's FP64 functions
+    for the generic FP64 interpreter)."""
     kinds = [n.kind for n in model_spec.nodes]
     n_exp = sum(k in ("gauss", "exp", "gaussexp") for k in kinds)
     n_ge = sum(k == "gaussexp" for k in kinds)
-    fast = api.probe(2, n_exp=n_exp, n_log=1, n_rcp=1)
-    full = api.probe(2, n_exp=n_exp + n_ge, n_erfc=n_ge, n_log=1, n_rcp=1) if n_ge else fast
+    kind = 4 if ff else 2
+    fast = api.probe(kind, n_exp=n_exp, n_log=1, n_rcp=1)
+    full = api.probe(kind, n_exp=n_exp + n_ge, n_erfc=n_ge, n_log=1, n_rcp=1) if n_ge else fast
     t_event = 1.0 / fast + slow_fraction * (1.0 / full - 1.0 / fast)
     alu = 1.0 / t_event
     hbm = peaks["hbm_gbs"] * 1e9 / bytes_per_event
-    basis = (f"transcendental set per event measured in-run: fast {{{n_exp} exp, log, rcp}} {fast/1e9:.2f} "
+    basis = (f"transcendental set per event measured in-run ({'float-float' if ff else 'CUDA FP64'} "
+             f"implementations): fast {{{n_exp} exp, log, rcp}} {fast/1e9:.2f} "
              f"Gevent/s, slow {{{n_exp + n_ge} exp, {n_ge} erfc, log, rcp}} {full/1e9:.2f} Gevent/s, slow "
              f"fraction {slow_fraction:.4f}; HBM ceiling {hbm/1e9:.0f} Gevent/s at {peaks['hbm_gbs']} GB/s "
              f"({peak_kind}) x {bytes_per_event} B/event")
@@ -230,7 +234,8 @@ def transcendental_ceiling(api, model_spec, slow_fraction, n_events, bytes_per_e
 def roofline(api, model, spec, data, kern_ms, kern_n, n_events, bpe, peaks, peak_kind, slow_frac=None):
     if slow_frac is None:
         slow_frac = api.slow_events(data) / max(1, n_events)
-    alu, hbm, basis = transcendental_ceiling(api, spec, slow_frac, n_events, bpe, peaks, peak_kind)
+    ff = "kernel=ff_" in model.describe()
+    alu, hbm, basis = transcendental_ceiling(api, spec, slow_frac, n_events, bpe, peaks, peak_kind, ff)
     ceiling = min(alu, hbm)
     avg = kern_ms / max(1, kern_n)
     achieved = n_events / (avg * 1e-3)

@@ -278,8 +278,17 @@ rf_status rf_slow_events(const rf_data* d, int64_t* count);
  *           complementary error functions, n_log logarithms and n_rcp
  *           reciprocals per event                   -> *rate in events/s
  *   kind 3: streaming read of a device buffer       -> *rate in bytes/s
+ *   kind 4: as kind 2 with the library's float-float implementations
+ *           (exp, erfcx for erfc, log, reciprocal)  -> *rate in events/s
  * Each probe allocates and frees its own scratch. */
 rf_status rf_probe(int32_t kind, int32_t n_exp, int32_t n_erfc, int32_t n_log, int32_t n_rcp, double* rate);
+
+/* Elementwise evaluation of the library's float-float elementary functions
+ * (fn 0 exp, 1 log, 2 reciprocal, 3 erfcx) and of CUDA's FP64 ones (fn 10
+ * exp, 11 log, 12 reciprocal, 13 erfcx) on DEVICE arrays of n doubles, for
+ * validating the former against the latter.  A float-float result outside
+ * the function's working range is NaN. */
+rf_status rf_math_eval(int32_t fn, const double* d_x, double* d_y, int64_t n, void* stream);
 
 /* --------------------------------------------------- allocation-free pass */
 

@@ -68,6 +68,7 @@ SIGNATURES = {
                                C.POINTER(C.c_float)]),
     "rf_mlp_save": (C.c_int, [_vp, C.c_char_p]),
     "rf_mlp_load": (C.c_int, [C.c_char_p, C.POINTER(_vp)]),
+    "rf_math_eval": (C.c_int, [C.c_int32, _vp, _vp, C.c_int64, _vp]),
     "rf_last_error": (C.c_char_p, []),
     "rf_version": (C.c_char_p, []),
 }

@@ -344,3 +344,10 @@ class MLP:
             self._h = None
 
     __del__ = close
+
+
+def math_eval(fn: int, d_x, d_y, stream=None):
+    """Library float-float functions (0 exp, 1 log, 2 rcp, 3 erfcx) or CUDA's
+    FP64 ones (10-13) elementwise on CUDA float64 tensors."""
+    L.check(L.load().rf_math_eval(fn, C.c_void_p(d_x.data_ptr()), C.c_void_p(d_y.data_ptr()), d_x.numel(),
+                                  _stream(stream)))

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "api_internal.h"
+#include "nll_ff.cuh"
 #include "nll_kernels.cuh"
 
 namespace rf {
@@ -113,7 +114,8 @@ bool ensure_workspace(const rf_model* m, rf_data* d) {
             w.tree.ensure(sizeof(double) * std::max<int64_t>(1, d->total_nodes) * 2 * Q) &&
             w.tree_bad.ensure(sizeof(int32_t) * std::max<int64_t>(1, d->total_nodes)) &&
             w.tickets.ensure(sizeof(int32_t) * std::max<int64_t>(1, d->total_nodes)) &&
-            w.counter.ensure(sizeof(int32_t)) && w.slow.ensure(sizeof(unsigned long long)) && w.h_theta.ensure(sizeof(double) * S * std::max(1, P.n_free)) &&
+            w.counter.ensure(sizeof(int32_t)) && w.slow.ensure(sizeof(unsigned long long)) &&
+            (m->m.shape == SHAPE_GENERIC || w.ffc.ensure(sizeof(float) * S * kFFConst)) && w.h_theta.ensure(sizeof(double) * S * std::max(1, P.n_free)) &&
             w.h_out.ensure(sizeof(double) * S * (1 + P.n_free)) && w.h_flags.ensure(sizeof(int32_t) * S);
   if (!ok) return false;
   if (!cuda_ok(cudaMemset(w.tickets.p, 0, sizeof(int32_t) * std::max<int64_t>(1, d->total_nodes)), "ticket reset"))
@@ -152,6 +154,8 @@ Pass make_pass(const rf_model* m, rf_data* d, const Plan& plan, const double* d_
   p.flags = d_flags;
   p.Q = grad ? 1 + m->m.prog.n_slots : 1;
   p.want_grad = grad ? 1 : 0;
+  p.ff_shape = m->m.shape;
+  p.ffc = m->m.shape == SHAPE_GENERIC ? nullptr : (float*)w.ffc.p;
   return p;
 }
 
@@ -227,7 +231,7 @@ int32_t rf_model_n_obs(const rf_model* m) { return m ? m->m.prog.n_obs : 0; }
 
 rf_status rf_model_describe(const rf_model* m, char* buf, int32_t cap) {
   if (!m || !buf || cap <= 0) { set_error("rf_model_describe: bad argument"); return RF_E_INVALID; }
-  static const char* shapes[] = {"generic", "sum_gauss_poly1", "sum_gaussexp_cheb2", "prod3"};
+  static const char* shapes[] = {"generic_fp64", "ff_sum_gauss_poly1", "ff_sum_gaussexp_cheb2", "ff_prod3"};
   std::snprintf(buf, cap, "%s kernel=%s pdf_nodes=%d free=%d slots=%d consts=%d", m->m.signature.c_str(),
                 shapes[m->m.shape], m->m.prog.n_pdf, m->m.prog.n_free, m->m.prog.n_slots, m->m.prog.n_const);
   return RF_OK;

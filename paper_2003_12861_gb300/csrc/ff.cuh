@@ -1,0 +1,219 @@
+// Float-float ("double-float") arithmetic and elementary functions on the
+// FP32 pipe.  On GB300 an FP64 operation costs about 58 FP32 operations of
+// issue throughput, so a value carried as an unevaluated sum hi + lo of two
+// floats (~48 significant bits) and the error-free transformations of
+// Knuth (two-sum), Dekker (fast two-sum) and the FMA two-product are far
+// cheaper than FP64 while accurate to a few 1e-15 relative.
+//
+// Elementary functions (tables in ff_tables.h, generated from the
+// mathematics by gen_ff_tables.py):
+//   ff_exp  Tang's table-driven exponential (ACM TOMS 1989): x = k ln2/256 + r,
+//           exp(x) = 2^(k>>8) 2^((k&255)/256) (1 + r + r^2/2 + r^3/6 + r^4/24).
+//   ff_log  Tang's table-driven logarithm (ACM TOMS 1990): x = 2^e m with
+//           m in [sqrt2/2, sqrt2), m = F (1 + r), F = 1 + j/256, log1p(r) to r^5.
+//   ff_rcp  one Newton step from the hardware reciprocal estimate.
+//   ff_erfcx exp(y^2) erfc(y), y >= 0: piecewise Chebyshev interpolants.
+// Each function sets ok = false when its argument or result leaves the
+// range in which the pair keeps its precision; callers then take an FP64
+// path.  Plain float operations below use the _rn intrinsics wherever an
+// error-free transformation must not be contracted into an FMA.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "ff_tables.h"
+
+namespace rf {
+
+struct ff {
+  float hi, lo;
+};
+
+// Shared-memory copies of the tables (filled by ff_load_tables).
+struct FFTables {
+  float exp_tab[512];
+  float log_tab[514];
+  float invf_tab[514];
+  float erfcx[6 * 17 * 2];
+};
+
+__device__ __forceinline__ void ff_load_tables(FFTables& t) {
+  for (int i = threadIdx.x; i < 512; i += blockDim.x) t.exp_tab[i] = kExpTab[i];
+  for (int i = threadIdx.x; i < 514; i += blockDim.x) {
+    t.log_tab[i] = kLogTab[i];
+    t.invf_tab[i] = kInvFTab[i];
+  }
+  for (int i = threadIdx.x; i < 6 * 17 * 2; i += blockDim.x) t.erfcx[i] = kErfcxCoef[i];
+}
+
+__device__ __forceinline__ ff ff_from_double(double d) {
+  const float h = __double2float_rn(d);
+  return {h, __double2float_rn(d - (double)h)};
+}
+__device__ __forceinline__ double ff_to_double(ff a) { return (double)a.hi + (double)a.lo; }
+
+// ---------------------------------------------------- error-free transforms
+__device__ __forceinline__ ff two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ ff fast_two_sum(float a, float b) {  // |a| >= |b| (or a == 0)
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ ff two_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return {p, __fmaf_rn(a, b, -p)};
+}
+
+// ------------------------------------------------------------- arithmetic
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+  ff s = two_sum(a.hi, b.hi);
+  s.lo = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+  return fast_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ ff ff_neg(ff a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ ff ff_sub(ff a, ff b) { return ff_add(a, ff_neg(b)); }
+__device__ __forceinline__ ff ff_add_f(ff a, float b) {
+  ff s = two_sum(a.hi, b);
+  s.lo = __fadd_rn(s.lo, a.lo);
+  return fast_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+  ff p = two_prod(a.hi, b.hi);
+  p.lo = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, p.lo));
+  return fast_two_sum(p.hi, p.lo);
+}
+__device__ __forceinline__ ff ff_mul_f(ff a, float b) {
+  ff p = two_prod(a.hi, b);
+  p.lo = __fmaf_rn(a.lo, b, p.lo);
+  return fast_two_sum(p.hi, p.lo);
+}
+__device__ __forceinline__ ff ff_sqr(ff a) {
+  ff p = two_prod(a.hi, a.hi);
+  p.lo = __fmaf_rn(__fmul_rn(2.0f, a.hi), a.lo, p.lo);
+  return fast_two_sum(p.hi, p.lo);
+}
+__device__ __forceinline__ ff ff_scale(ff a, float pow2) { return {__fmul_rn(a.hi, pow2), __fmul_rn(a.lo, pow2)}; }
+
+// Running sum without renormalisation per step: hi accumulates through an
+// exact two-sum, lo collects the errors and the addends' low parts.
+__device__ __forceinline__ void ff_acc(ff& acc, ff x) {
+  const ff s = two_sum(acc.hi, x.hi);
+  acc.lo = __fadd_rn(acc.lo, __fadd_rn(s.lo, x.lo));
+  acc.hi = s.hi;
+}
+
+// ---------------------------------------------------------------- exp
+__device__ __forceinline__ ff ff_exp(const FFTables& T, ff x, bool& ok) {
+  const float kf = rintf(__fmul_rn(x.hi, kExpK));
+  ok = ok && fabsf(x.hi) < 80.0f;
+  const int k = ok ? (int)kf : 0;
+  const float kk = ok ? kf : 0.0f;
+  // r = x - k ln2/256, the large cancellation exact
+  const float t1 = __fmaf_rn(-kk, kLn2_256_1, x.hi);
+  const ff p2 = two_prod(kk, kLn2_256_2);
+  const ff s = two_sum(t1, -p2.hi);
+  const ff s2 = two_sum(s.hi, x.lo);  // the input's low word can exceed |r| * 2^-24
+  float lo = __fadd_rn(s.lo, s2.lo);
+  lo = __fsub_rn(lo, p2.lo);
+  lo = __fmaf_rn(-kk, kLn2_256_3, lo);
+  const ff r = fast_two_sum(s2.hi, lo);
+  // exp(r) - 1 = r + r^2/2 + r^3/6 + r^4/24, |r| <= ln2/512
+  ff sq = two_prod(r.hi, r.hi);
+  sq.lo = __fmaf_rn(__fmul_rn(2.0f, r.hi), r.lo, sq.lo);
+  const float q = __fmul_rn(__fmul_rn(r.hi, sq.hi), __fmaf_rn(r.hi, 1.0f / 24.0f, 1.0f / 6.0f));
+  ff pp = fast_two_sum(r.hi, __fmul_rn(0.5f, sq.hi));
+  pp.lo = __fadd_rn(pp.lo, __fadd_rn(r.lo, __fmaf_rn(0.5f, sq.lo, q)));
+  // 2^(j/256) (1 + p)
+  const int j = k & 255, m = k >> 8;
+  const ff t = {T.exp_tab[2 * j], T.exp_tab[2 * j + 1]};
+  ff tp = two_prod(t.hi, pp.hi);
+  tp.lo = __fmaf_rn(t.hi, pp.lo, __fmaf_rn(t.lo, pp.hi, tp.lo));
+  ff res = fast_two_sum(t.hi, tp.hi);
+  res.lo = __fadd_rn(res.lo, __fadd_rn(t.lo, tp.lo));
+  res = fast_two_sum(res.hi, res.lo);
+  ok = ok && m >= -100 && m <= 100;
+  const float sc = __int_as_float(((ok ? m : 0) + 127) << 23);
+  return ff_scale(res, sc);
+}
+
+// ---------------------------------------------------------------- log
+__device__ __forceinline__ ff ff_log(const FFTables& T, ff a, bool& ok) {
+  ok = ok && a.hi > 7.9e-31f && a.hi < 1.2e30f;  // 2^-100 .. 2^100
+  const float ah = ok ? a.hi : 1.0f, al = ok ? a.lo : 0.0f;
+  const int bits = __float_as_int(ah);
+  int e = ((bits >> 23) & 0xff) - 127;
+  float m = __int_as_float((bits & 0x007fffff) | 0x3f800000);
+  float ml = __fmul_rn(al, __int_as_float((127 - e) << 23));
+  if (m > 1.41421356f) {  // m in [sqrt2/2, sqrt2): no cancellation of e ln2 against log F near 1
+    m = __fmul_rn(m, 0.5f);
+    ml = __fmul_rn(ml, 0.5f);
+    e += 1;
+  }
+  const int j = __float2int_rn(__fmul_rn(__fsub_rn(m, 1.0f), 256.0f));  // -75 .. 106
+  const float F = __fmaf_rn((float)j, 1.0f / 256.0f, 1.0f);
+  const ff f = two_sum(__fsub_rn(m, F), ml);
+  const int jt = j + 128;
+  const ff iF = {T.invf_tab[2 * jt], T.invf_tab[2 * jt + 1]};
+  const ff r = ff_mul(f, iF);
+  // log1p(r) = r - r^2/2 + r^3/3 - r^4/4 + r^5/5, |r| <= 1/362
+  ff sq = two_prod(r.hi, r.hi);
+  sq.lo = __fmaf_rn(__fmul_rn(2.0f, r.hi), r.lo, sq.lo);
+  const float q = __fmul_rn(__fmul_rn(r.hi, sq.hi),
+                            __fmaf_rn(r.hi, __fmaf_rn(r.hi, 0.2f, -0.25f), 1.0f / 3.0f));
+  ff lp = fast_two_sum(r.hi, __fmul_rn(-0.5f, sq.hi));
+  lp.lo = __fadd_rn(lp.lo, __fadd_rn(r.lo, __fmaf_rn(-0.5f, sq.lo, q)));
+  // + e ln2 + log F
+  const float ef = (float)e;
+  const ff lf = {T.log_tab[2 * jt], T.log_tab[2 * jt + 1]};
+  const ff e2 = two_prod(ef, kLn2_2);
+  ff s = two_sum(__fmul_rn(ef, kLn2_1), lf.hi);  // e*ln2_1 exact (16-bit constant)
+  s.lo = __fadd_rn(s.lo, __fadd_rn(lf.lo, __fmaf_rn(ef, kLn2_3, e2.lo)));
+  ff s2 = two_sum(s.hi, e2.hi);
+  s2.lo = __fadd_rn(s2.lo, s.lo);
+  s2 = fast_two_sum(s2.hi, s2.lo);
+  ff out = two_sum(s2.hi, lp.hi);
+  out.lo = __fadd_rn(out.lo, __fadd_rn(s2.lo, lp.lo));
+  return fast_two_sum(out.hi, out.lo);
+}
+
+// ---------------------------------------------------------------- rcp
+__device__ __forceinline__ ff ff_rcp(ff a) {
+  float y0;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y0) : "f"(a.hi));
+  const ff p = two_prod(a.hi, y0);
+  float e = __fsub_rn(1.0f, p.hi);
+  e = __fsub_rn(e, p.lo);
+  e = __fmaf_rn(-a.lo, y0, e);
+  return fast_two_sum(y0, __fmul_rn(y0, e));
+}
+
+// -------------------------------------------------------------- erfcx
+// y >= 0.  Pieces 0-2: y in [0,0.5), [0.5,1), [1,2); pieces 3-5: w = 1/y in
+// (0.25,0.5], (0.125,0.25], [0,0.125] with erfcx(y) = w h(w).
+__device__ __forceinline__ ff ff_erfcx(const FFTables& T, ff y, bool& ok) {
+  ok = ok && y.hi >= 0.0f && y.hi < 1e30f;
+  int piece;
+  ff v;
+  if (y.hi < 2.0f) {
+    piece = y.hi < 0.5f ? 0 : (y.hi < 1.0f ? 1 : 2);
+    v = y;
+  } else {
+    v = ff_rcp(y);
+    piece = v.hi > 0.25f ? 3 : (v.hi > 0.125f ? 4 : 5);
+  }
+  // x = (v - mid) / half, exact scaling by a power of two
+  const ff x = ff_scale(ff_add_f(v, -kErfcxMid[piece]), kErfcxInvHalf[piece]);
+  const float* c = T.erfcx + piece * 34;
+  const int kf = kErfcxFF[piece];  // 1 <= kf <= 16: tail a_16..a_kf in float
+  float s = c[2 * 16];
+  for (int k = 15; k >= kf; --k) s = __fmaf_rn(s, x.hi, c[2 * k]);
+  ff acc = {s, 0.0f};
+  for (int k = kf - 1; k >= 0; --k) acc = ff_add(ff_mul(acc, x), ff{c[2 * k], c[2 * k + 1]});
+  return piece >= 3 ? ff_mul(acc, v) : acc;
+}
+
+}  // namespace rf

@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "api_internal.h"
+#include "ff.cuh"
 #include "nll_kernels.cuh"
 
 namespace rf {
@@ -66,6 +67,51 @@ __global__ void probe_trans(double* out, int events, int n_exp, int n_erfc, int 
     x += 1e-6;
   }
   out[blockIdx.x * blockDim.x + threadIdx.x] = acc;
+}
+
+// The same per-event set with the library's float-float implementations.
+__global__ void probe_trans_ff(double* out, int events, int n_exp, int n_erfc, int n_log, int n_rcp) {
+  __shared__ FFTables T;
+  ff_load_tables(T);
+  __syncthreads();
+  ff acc = {0.f, 0.f};
+  bool ok = true;
+  ff x = ff_from_double(0.5 + (blockIdx.x * blockDim.x + threadIdx.x) * 1e-9);
+  const ff step = {1e-6f, 0.f};
+  for (int i = 0; i < events; ++i) {
+    for (int k = 0; k < n_exp; ++k) ff_acc(acc, ff_exp(T, ff_mul_f(x, -(1.0f + 0.25f * k)), ok));
+    for (int k = 0; k < n_erfc; ++k) ff_acc(acc, ff_erfcx(T, ff_add_f(ff_mul_f(x, 1.0f + 0.25f * k), 0.3f), ok));
+    for (int k = 0; k < n_log; ++k) ff_acc(acc, ff_log(T, ff_add_f(x, (float)k), ok));
+    for (int k = 0; k < n_rcp; ++k) ff_acc(acc, ff_rcp(ff_add_f(x, (float)k)));
+    x = ff_add(x, step);
+  }
+  out[blockIdx.x * blockDim.x + threadIdx.x] = ok ? ff_to_double(acc) : -1.0;
+}
+
+// Elementwise evaluation of the library's float-float functions (fn 0-3) and
+// of CUDA's FP64 functions (fn 10-13), for validation.
+__global__ void math_eval_kernel(int fn, const double* __restrict__ x, double* __restrict__ y, int64_t n) {
+  __shared__ FFTables T;
+  ff_load_tables(T);
+  __syncthreads();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double xv = x[i];
+    bool ok = true;
+    ff r = {0.f, 0.f};
+    double out = 0.0;
+    switch (fn) {
+      case 0: r = ff_exp(T, ff_from_double(xv), ok); out = ff_to_double(r); break;
+      case 1: r = ff_log(T, ff_from_double(xv), ok); out = ff_to_double(r); break;
+      case 2: r = ff_rcp(ff_from_double(xv)); out = ff_to_double(r); break;
+      case 3: r = ff_erfcx(T, ff_from_double(xv), ok); out = ff_to_double(r); break;
+      case 10: out = exp(xv); break;
+      case 11: out = log(xv); break;
+      case 12: out = 1.0 / xv; break;
+      case 13: out = erfcx(xv); break;
+      default: ok = false;
+    }
+    y[i] = ok ? out : __longlong_as_double(0x7ff8000000000000ll);
+  }
 }
 
 __global__ void probe_read(const double2* __restrict__ p, size_t n, double* out) {
@@ -165,7 +211,7 @@ rf_status rf_data_refill(rf_data* d, const void* const* cols, void* stream) {
 }
 
 rf_status rf_probe(int32_t kind, int32_t n_exp, int32_t n_erfc, int32_t n_log, int32_t n_rcp, double* rate) {
-  if (!rate || kind < 0 || kind > 3 || n_exp < 0 || n_erfc < 0 || n_log < 0 || n_rcp < 0) {
+  if (!rate || kind < 0 || kind > 4 || n_exp < 0 || n_erfc < 0 || n_log < 0 || n_rcp < 0) {
     set_error("rf_probe: bad argument");
     return RF_E_INVALID;
   }
@@ -198,6 +244,10 @@ rf_status rf_probe(int32_t kind, int32_t n_exp, int32_t n_erfc, int32_t n_log, i
       const int ev = 128;
       probe_trans<<<blocks, threads>>>((double*)out.p, ev, n_exp, n_erfc, n_log, n_rcp);
       work = (double)ev * threads * blocks;
+    } else if (kind == 4) {
+      const int ev = 512;
+      probe_trans_ff<<<blocks, threads>>>((double*)out.p, ev, n_exp, n_erfc, n_log, n_rcp);
+      work = (double)ev * threads * blocks;
     } else {
       probe_read<<<nsm * 4, 512>>>((const double2*)buf.p, n2, (double*)out.p);
       work = (double)n2 * sizeof(double2);
@@ -213,6 +263,17 @@ rf_status rf_probe(int32_t kind, int32_t n_exp, int32_t n_erfc, int32_t n_log, i
   if (!cuda_ok(cudaGetLastError(), "probe")) return RF_E_CUDA;
   *rate = best;
   return RF_OK;
+}
+
+rf_status rf_math_eval(int32_t fn, const double* d_x, double* d_y, int64_t n, void* stream) {
+  if (!d_x || !d_y || n < 0 || !((fn >= 0 && fn <= 3) || (fn >= 10 && fn <= 13))) {
+    set_error("rf_math_eval: bad argument");
+    return RF_E_INVALID;
+  }
+  if (n == 0) return RF_OK;
+  const int64_t blocks = std::min<int64_t>((n + 255) / 256, 4096);
+  math_eval_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(fn, d_x, d_y, n);
+  return cuda_ok(cudaGetLastError(), "rf_math_eval") ? RF_OK : RF_E_CUDA;
 }
 
 }  // extern "C"

@@ -13,6 +13,7 @@
 #include <cmath>
 #include <cstdio>
 
+#include "nll_ff.cuh"
 #include "nll_kernels.cuh"
 
 namespace rf {
@@ -166,6 +167,7 @@ __global__ void param_point_kernel(const __grid_constant__ Program P, Pass pass)
     }
   }
   pass.flags[s] = bad ? kThetaBad : 0;
+  if (!bad && pass.ff_shape != SHAPE_GENERIC && pass.ffc) prepare_ff(P, pass.ff_shape, C, pass.ffc + (size_t)s * kFFConst);
   if (pass.offsets[s + 1] == pass.offsets[s]) {  // no events: the empty sum
     double* o = pass.out + (size_t)s * (1 + P.n_free);
     o[0] = bad ? INFINITY : 0.0;
@@ -456,6 +458,21 @@ __device__ void climb_tree(const Program& P, const Pass& pass, Smem& sm, int set
   }
 }
 
+// Writes a chunk's totals (Q values in sm.wsum[0]) to its level-0 tree node
+// and climbs the tree.
+__device__ void write_chunk(const Program& P, const Pass& pass, Smem& sm, int bad, int set, int chunk,
+                            int64_t n_events) {
+  const int tid = threadIdx.x;
+  const int Q = pass.Q;
+  const int64_t node = pass.tree_base[set] + chunk;
+  if (tid < Q) {
+    pass.tree[node * 2 * Q + tid] = sm.wsum[0][tid];
+    pass.tree[node * 2 * Q + Q + tid] = 0.0;
+  }
+  if (tid == 0) pass.tree_bad[node] = bad;
+  climb_tree(P, pass, sm, set, chunk, n_events);
+}
+
 // Writes the chunk's partial (warp sums merged in a fixed order) to its
 // level-0 tree node and climbs the tree.
 __device__ void finish_chunk(const Program& P, const Pass& pass, Smem& sm, double* acc, int bad, int set,
@@ -532,6 +549,129 @@ __global__ void __launch_bounds__(kLanes) events_generic(const __grid_constant__
   }
 }
 
+// Float-float fused event kernel of a specialised shape.  Same chunk/lane
+// geometry, queues and reduction tree as the generic kernel; per lane the
+// shape's moments are summed in float-float; events in the decay resolution
+// region are queued (ballot order) and evaluated after the fast pass; events
+// outside the float-float range take the FP64 interpreter (a third queue,
+// FP64 sums).  At the chunk end the warps' moments are merged in fixed order
+// and mapped to (sum log p, slot gradients) by the set's matrix K.
+template <int kShape, bool kGrad>
+__global__ void __launch_bounds__(kLanes) events_ff(const __grid_constant__ Program P,
+                                                    const __grid_constant__ Columns cols, Pass pass) {
+  constexpr int NA = kGrad ? ff_nacc(kShape) : 1;
+  constexpr int NAK = ff_nacc(kShape);
+  __shared__ Smem sm;
+  __shared__ FFTables T;
+  __shared__ float kc[kFFConst];
+  __shared__ ff wacc[kWarps][16];
+  __shared__ int fbq[kWarps][kPerLane * 32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int Q = pass.Q;
+  ff_load_tables(T);
+  int col[3];
+  if (kShape == SHAPE_PROD3) {
+    col[0] = P.node[0].col; col[1] = P.node[3].col; col[2] = P.node[6].col;
+  } else {
+    col[0] = col[1] = col[2] = P.node[0].col;
+  }
+  const unsigned lt = (1u << lane) - 1u;
+  while (true) {
+    if (tid == 0) sm.item = atomicAdd(pass.counter, 1);
+    __syncthreads();
+    const int it = sm.item;
+    if (it >= pass.n_items) break;
+    const int set = pass.items[it].x, chunk = pass.items[it].y;
+    const int64_t s_begin = pass.offsets[set], s_end = pass.offsets[set + 1];
+    const int64_t base = s_begin + (int64_t)chunk * kChunk;
+    for (int i = tid; i < P.n_const; i += kLanes) sm.C[i] = pass.consts[(size_t)set * P.n_const + i];
+    for (int i = tid; i < kFFConst; i += kLanes) kc[i] = pass.ffc[(size_t)set * kFFConst + i];
+    __syncthreads();
+    ff acc[NA];
+#pragma unroll
+    for (int j = 0; j < NA; ++j) acc[j] = {0.0f, 0.0f};
+    int qs = 0, qf = 0;
+    for (int k = 0; k < kPerLane; ++k) {
+      const int64_t e = base + tid + (int64_t)k * kLanes;
+      int st = 0;
+      if (e < s_end) st = ff_event<kShape, kGrad, false>(T, kc, col, cols, e, acc);
+      const unsigned bs = __ballot_sync(0xffffffffu, st == 1), bf = __ballot_sync(0xffffffffu, st == 2);
+      if (st == 1) sm.queue[warp][qs + __popc(bs & lt)] = (int)(e - base);
+      if (st == 2) fbq[warp][qf + __popc(bf & lt)] = (int)(e - base);
+      qs += __popc(bs);
+      qf += __popc(bf);
+    }
+    __syncwarp();
+    if (lane == 0 && qs > 0 && pass.slow) atomicAdd(pass.slow, (unsigned long long)qs);
+    for (int j0 = 0; j0 < qs; j0 += 32) {
+      const int j = j0 + lane;
+      int st = 0;
+      if (j < qs) st = ff_event<kShape, kGrad, true>(T, kc, col, cols, base + sm.queue[warp][j], acc);
+      const unsigned bf = __ballot_sync(0xffffffffu, st == 2);
+      if (st == 2) fbq[warp][qf + __popc(bf & lt)] = sm.queue[warp][j];
+      qf += __popc(bf);
+    }
+    __syncwarp();
+    // FP64 fallback for events outside the float-float range
+    double acc64[kQMax];
+    int bad = 0;
+    const bool any_fb = __syncthreads_or(qf > 0);
+    if (any_fb) {
+      for (int q = 0; q < kQMax; ++q) acc64[q] = 0.0;
+      double x[kMaxObs];
+      for (int j = lane; j < qf; j += 32) {
+        const int64_t e = base + fbq[warp][j];
+        for (int c = 0; c < P.n_obs; ++c) x[c] = load_col(cols, c, e);
+        eval_generic<true, kGrad>(P, sm.C, x, acc64, &bad);
+      }
+    }
+    // moments: warp butterfly (float-float), lane 0 holds the warp's sums
+#pragma unroll
+    for (int j = 0; j < NA; ++j) {
+      ff v = acc[j];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const ff w = {__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+        v = ff_add(v, w);
+      }
+      if (lane == 0) wacc[warp][j] = v;
+    }
+    if (any_fb) {
+      for (int q = 0; q < Q; ++q) {
+        const double w = warp_sum(acc64[q]);
+        if (lane == 0) sm.wsum[warp][q] = w;
+      }
+      bad = warp_sum_int(bad);
+      if (lane == 0) sm.wbad[warp] = bad;
+    }
+    __syncthreads();
+    double v = 0.0;
+    if (tid < Q) {
+      // merge the warps in fixed order, then out_q = sum_j K[q][j] M_j
+      const float* K = kc + ff_koff(kShape);
+      ff out = {0.0f, 0.0f};
+#pragma unroll
+      for (int j = 0; j < NA; ++j) {
+        const ff Mj = ff_add(ff_add(wacc[0][j], wacc[1][j]), ff_add(wacc[2][j], wacc[3][j]));
+        out = ff_add(out, ff_mul(ff{K[2 * (tid * NAK + j)], K[2 * (tid * NAK + j) + 1]}, Mj));
+      }
+      v = ff_to_double(out);
+      if (any_fb) {
+        Pair a = merge({sm.wsum[0][tid], 0.0}, {sm.wsum[1][tid], 0.0});
+        Pair b = merge({sm.wsum[2][tid], 0.0}, {sm.wsum[3][tid], 0.0});
+        Pair r = merge(a, b);
+        v += r.s + r.c;
+      }
+    }
+    __syncthreads();
+    if (tid < Q) sm.wsum[0][tid] = v;
+    const int bad_all = any_fb ? sm.wbad[0] + sm.wbad[1] + sm.wbad[2] + sm.wbad[3] : 0;
+    __syncthreads();
+    write_chunk(P, pass, sm, bad_all, set, chunk, s_end - s_begin);
+    __syncthreads();
+  }
+}
+
 }  // namespace
 
 void launch_param_point(const Program& P, const Pass& pass, cudaStream_t st) {
@@ -545,10 +685,23 @@ bool launch_supports_threads(Shape shape, int threads) {
   return threads == kLanes;
 }
 
+template <int kShape>
+const void* ff_kernel(bool grad) {
+  return grad ? (const void*)events_ff<kShape, true> : (const void*)events_ff<kShape, false>;
+}
+
+const void* event_kernel(Shape shape, bool grad) {
+  switch (shape) {
+    case SHAPE_SUM_GAUSSEXP_CHEB2: return ff_kernel<SHAPE_SUM_GAUSSEXP_CHEB2>(grad);
+    case SHAPE_SUM_GAUSS_POLY1: return ff_kernel<SHAPE_SUM_GAUSS_POLY1>(grad);
+    case SHAPE_PROD3: return ff_kernel<SHAPE_PROD3>(grad);
+    default: return grad ? (const void*)events_generic<true> : (const void*)events_generic<false>;
+  }
+}
+
 bool launch_fits(Shape shape, int threads, int blocks_per_sm) {
-  (void)shape;
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, events_generic<true>, threads, 0) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, event_kernel(shape, true), threads, 0) != cudaSuccess) {
     cudaGetLastError();
     return blocks_per_sm <= 4;
   }
@@ -557,17 +710,30 @@ bool launch_fits(Shape shape, int threads, int blocks_per_sm) {
 
 void launch_events(const Program& P, Shape shape, const Columns& cols, const Pass& pass, int threads,
                    int blocks_per_sm, int n_sm, cudaStream_t st) {
-  (void)shape;
   (void)threads;
   if (pass.n_items == 0) return;
   const int bps = blocks_per_sm > 0 ? blocks_per_sm : 8;
   int grid = n_sm * bps;
   if (grid > pass.n_items) grid = pass.n_items;
+  const Shape sh = (pass.ff_shape != SHAPE_GENERIC && pass.ffc) ? shape : SHAPE_GENERIC;
   timing_begin(st);
-  if (pass.want_grad)
-    events_generic<true><<<grid, kLanes, 0, st>>>(P, cols, pass);
-  else
-    events_generic<false><<<grid, kLanes, 0, st>>>(P, cols, pass);
+  switch (sh) {
+    case SHAPE_SUM_GAUSSEXP_CHEB2:
+      if (pass.want_grad) events_ff<SHAPE_SUM_GAUSSEXP_CHEB2, true><<<grid, kLanes, 0, st>>>(P, cols, pass);
+      else events_ff<SHAPE_SUM_GAUSSEXP_CHEB2, false><<<grid, kLanes, 0, st>>>(P, cols, pass);
+      break;
+    case SHAPE_SUM_GAUSS_POLY1:
+      if (pass.want_grad) events_ff<SHAPE_SUM_GAUSS_POLY1, true><<<grid, kLanes, 0, st>>>(P, cols, pass);
+      else events_ff<SHAPE_SUM_GAUSS_POLY1, false><<<grid, kLanes, 0, st>>>(P, cols, pass);
+      break;
+    case SHAPE_PROD3:
+      if (pass.want_grad) events_ff<SHAPE_PROD3, true><<<grid, kLanes, 0, st>>>(P, cols, pass);
+      else events_ff<SHAPE_PROD3, false><<<grid, kLanes, 0, st>>>(P, cols, pass);
+      break;
+    default:
+      if (pass.want_grad) events_generic<true><<<grid, kLanes, 0, st>>>(P, cols, pass);
+      else events_generic<false><<<grid, kLanes, 0, st>>>(P, cols, pass);
+  }
   timing_end(st);
 }
 

@@ -1,0 +1,328 @@
+// Float-float event programs of the graph shapes the library specialises.
+//
+// The event pass is the hot loop of the likelihood (Sec. 4: every
+// observable-dependent node is recomputed for every event).  For the shapes
+// below the whole per-event program runs in float-float arithmetic (ff.cuh)
+// on the FP32 pipe.  The gradient is not accumulated per parameter: every
+// parameter derivative of log p_i is a linear combination, with
+// parameter-point constants, of a few per-event moments (1/p_i, t_i/p_i,
+// e_i/p_i, ...), so the kernel sums the moments and one matrix K per set maps
+// the summed moments to (sum log p, d/dtheta_slot) at the end of each chunk.
+// K and the per-event constants are computed in FP64 once per parameter point.
+//
+// Shapes (program order = the topological order of rf_model_create):
+//   DECAY     SUM(GAUSSEXP(t; tau,mu,sigma), CHEB2(t; c1,c2); f)      Q = 7
+//   GP1       SUM(GAUSS(x; mu,sigma), POLY1(x; a1); f)                 Q = 5
+//   PROD3     PROD(SUM(GAUSS(m), CHEB1(m); fm), DECAY(t), POLY2(c))    Q = 13
+#pragma once
+
+#include "ff.cuh"
+#include "nll_kernels.cuh"
+
+namespace rf {
+
+constexpr int kFFConst = 512;  // floats per set: per-event constants, then K (Q x NACC pairs)
+constexpr float kSlowZf = -7.0f;
+
+// Number of moment accumulators (index 0 = log p) and of output quantities.
+__host__ __device__ constexpr int ff_nacc(int shape) {
+  return shape == SHAPE_SUM_GAUSSEXP_CHEB2 ? 8 : shape == SHAPE_SUM_GAUSS_POLY1 ? 6 : shape == SHAPE_PROD3 ? 16 : 0;
+}
+__host__ __device__ constexpr int ff_q(int shape) {
+  return shape == SHAPE_SUM_GAUSSEXP_CHEB2 ? 7 : shape == SHAPE_SUM_GAUSS_POLY1 ? 5 : shape == SHAPE_PROD3 ? 13 : 0;
+}
+// Offset of K in the set's float block, after the per-event constants.
+__host__ __device__ constexpr int ff_koff(int shape) {
+  return shape == SHAPE_SUM_GAUSSEXP_CHEB2 ? 24 : shape == SHAPE_SUM_GAUSS_POLY1 ? 16 : shape == SHAPE_PROD3 ? 44 : 0;
+}
+
+// ------------------------------------------------ parameter-point side (FP64)
+
+__device__ __forceinline__ void put_ff(float* o, double v) {
+  const float h = __double2float_rn(v);
+  o[0] = h;
+  o[1] = __double2float_rn(v - (double)h);
+}
+
+// Per-event constants of a decay sub-model (22 floats at o) and its rows of K.
+// ge: GAUSSEXP constants [mu, 1/sigma, s, 1/tau, 1/I, dlogI/dtau, dlogI/dmu,
+// dlogI/dsigma]; ch: CHEB2 [2/(b-a), (a+b)/(b-a), 1/I, dlogI/dc1, dlogI/dc2,
+// c1, c2]; sm: SUM [f, 1-f].  The kernel evaluates the normalised signal
+// density v = shape/I with log(1/I) folded into the exponent, so that no
+// factor leaves the float range while the product matters.  Moments at
+// column m0: E = v/p, E t, 1/p, t/p, t^2/p, E R, E R u (u = (t - mu)/sigma).
+// Rows r0.. for tau, mu, sigma, c1, c2, f.
+static __device__ void prep_decay(const double* ge, const double* ch, const double* sm, float* o, double* K, int nacc,
+                           int r0, int m0) {
+  const double mu = ge[0], is = ge[1], s = ge[2], it = ge[3], iIs = ge[4];
+  const double dIt = ge[5], dIm = ge[6], dIs = ge[7];
+  const double c0 = ch[0], c1p = ch[1], iIb = ch[2], dI1 = ch[3], dI2 = ch[4], a1 = ch[5], a2 = ch[6];
+  const double f = sm[0], fl = sm[1];
+  const double lIs = log(iIs);
+  const double S[3] = {1.0 - a1 * c1p + a2 * (2.0 * c1p * c1p - 1.0), a1 * c0 - 4.0 * a2 * c0 * c1p,
+                       2.0 * a2 * c0 * c0};
+  const double T1[3] = {-c1p, c0, 0.0};
+  const double T2[3] = {2.0 * c1p * c1p - 1.0, -4.0 * c0 * c1p, 2.0 * c0 * c0};
+  const double r2 = 0.70710678118654752440;
+  put_ff(o + 0, 0.5 * s * s + mu * it + lIs);  // log v = A + log(1/I), A = s^2/2 + mu/tau - t/tau
+  put_ff(o + 2, it);
+  put_ff(o + 4, f);
+  for (int j = 0; j < 3; ++j) put_ff(o + 6 + 2 * j, fl * iIb * S[j]);
+  o[12] = (float)((s + mu * is) * r2);  // z ~ zc - t zs (decides the slow path only)
+  o[13] = (float)(is * r2);
+  put_ff(o + 14, mu);
+  put_ff(o + 16, is);
+  put_ff(o + 18, s);
+  put_ff(o + 20, lIs);
+  double* rt = K + (r0 + 0) * nacc;  // tau
+  rt[m0 + 1] = f * s * is * it;
+  rt[m0 + 0] = -f * (s * mu * is * it + s * s * it + dIt);
+  rt[m0 + 5] = f * s * it * r2;
+  double* rm = K + (r0 + 1) * nacc;  // mu
+  rm[m0 + 0] = f * (it - dIm);
+  rm[m0 + 5] = -f * is * r2;
+  double* rs = K + (r0 + 2) * nacc;  // sigma: dz/dsigma = (1/tau + u/sigma)/sqrt2
+  rs[m0 + 0] = f * (s * it - dIs);
+  rs[m0 + 5] = -f * it * r2;
+  rs[m0 + 6] = -f * is * r2;
+  for (int j = 0; j < 3; ++j) {
+    K[(r0 + 3) * nacc + m0 + 2 + j] = fl * iIb * (T1[j] - dI1 * S[j]);
+    K[(r0 + 4) * nacc + m0 + 2 + j] = fl * iIb * (T2[j] - dI2 * S[j]);
+    K[(r0 + 5) * nacc + m0 + 2 + j] = -iIb * S[j];
+  }
+  K[(r0 + 5) * nacc + m0 + 0] = 1.0;
+}
+
+// Gauss + linear background (POLY1 or CHEB1) sub-model: constants (16
+// floats) and rows for mu, sigma, background coefficient, fraction.  The
+// kernel evaluates the normalised Gaussian density (log(1/I) folded into the
+// exponent); the moments are centred so that their combination does not
+// cancel: at m0, G = v/p, G u, G u^2 (u = (x - mu)/sigma), 1/p, y/p, with
+// y = c0 x - c1 the background's own variable (x for POLY1, the mapped x'
+// for CHEB1), in which its shape is 1 + b y.  bg = (c0, c1, b, iIb, dIb).
+static __device__ void prep_gauss_lin(const double* g, const double* bg, const double* sm, float* o, double* K, int nacc,
+                               int r0, int m0) {
+  const double mu = g[0], is = g[1], iIg = g[2], dIm = g[3], dIs = g[4];
+  const double c0 = bg[0], c1 = bg[1], b = bg[2], iIb = bg[3], dIb = bg[4];
+  const double f = sm[0], fl = sm[1];
+  put_ff(o + 0, mu);
+  put_ff(o + 2, is);
+  put_ff(o + 4, f);
+  put_ff(o + 6, fl * iIb);
+  put_ff(o + 8, fl * iIb * b);
+  put_ff(o + 10, c0);
+  put_ff(o + 12, c1);
+  put_ff(o + 14, log(iIg));
+  K[(r0 + 0) * nacc + m0 + 1] = f * is;  // mu: u/sigma - dlogI/dmu
+  K[(r0 + 0) * nacc + m0 + 0] = -f * dIm;
+  K[(r0 + 1) * nacc + m0 + 2] = f * is;  // sigma: u^2/sigma - dlogI/dsigma
+  K[(r0 + 1) * nacc + m0 + 0] = -f * dIs;
+  K[(r0 + 2) * nacc + m0 + 3] = -fl * iIb * dIb;  // background: y - (1 + b y) dlogI/db
+  K[(r0 + 2) * nacc + m0 + 4] = fl * iIb * (1.0 - dIb * b);
+  K[(r0 + 3) * nacc + m0 + 0] = 1.0;  // fraction
+  K[(r0 + 3) * nacc + m0 + 3] = -iIb;
+  K[(r0 + 3) * nacc + m0 + 4] = -iIb * b;
+}
+
+// Writes the set's float block: per-event constants, then K as float pairs.
+static __device__ void prepare_ff(const Program& P, int shape, const double* C, float* out) {
+  double K[13 * 16];
+  const int nacc = ff_nacc(shape), Q = ff_q(shape);
+  for (int i = 0; i < Q * nacc; ++i) K[i] = 0.0;
+  K[0] = 1.0;  // sum log p
+  if (shape == SHAPE_SUM_GAUSSEXP_CHEB2) {
+    prep_decay(C + P.node[0].cofs, C + P.node[1].cofs, C + P.node[2].cofs, out, K, nacc, 1, 1);
+  } else if (shape == SHAPE_SUM_GAUSS_POLY1) {
+    const double* pl = C + P.node[1].cofs;  // POLY1 [1/I, dlogI/da1, a1]
+    const double bg[5] = {1.0, 0.0, pl[2], pl[0], pl[1]};
+    prep_gauss_lin(C + P.node[0].cofs, bg, C + P.node[2].cofs, out, K, nacc, 1, 1);
+  } else if (shape == SHAPE_PROD3) {
+    const double* cb = C + P.node[1].cofs;  // CHEB1 [c0, c1', 1/I, dlogI/dc, c]
+    const double bg[5] = {cb[0], cb[1], cb[4], cb[2], cb[3]};
+    prep_gauss_lin(C + P.node[0].cofs, bg, C + P.node[2].cofs, out, K, nacc, 1, 1);
+    prep_decay(C + P.node[3].cofs, C + P.node[4].cofs, C + P.node[5].cofs, out + 16, K, nacc, 5, 6);
+    const double* pa = C + P.node[6].cofs;  // POLY2 [1/I, dlogI/da1, dlogI/da2, a1, a2]
+    const double Sa[3] = {1.0, pa[3], pa[4]};
+    for (int j = 0; j < 3; ++j) put_ff(out + 38 + 2 * j, pa[0] * Sa[j]);
+    for (int k = 0; k < 2; ++k) {
+      for (int j = 0; j < 3; ++j) K[(11 + k) * nacc + 13 + j] = -pa[0] * pa[1 + k] * Sa[j];
+      K[(11 + k) * nacc + 13 + 1 + k] += pa[0];
+    }
+  }
+  float* Ko = out + ff_koff(shape);
+  for (int i = 0; i < Q * nacc; ++i) put_ff(Ko + 2 * i, K[i]);
+}
+
+// ----------------------------------------------------- event side (FF)
+
+// A double observable as a float pair, from its bits (no FP64 instruction):
+// hi = the top 24 significand bits, lo = the remaining 29 rounded to a float.
+// ok = false for values the pair cannot hold (|d| < 2^-74 except 0, >= 2^128).
+__device__ __forceinline__ ff ff_split(double d, bool& ok) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const unsigned hi32 = (unsigned)(b >> 32), lo32 = (unsigned)b;
+  const int ex = (int)((hi32 >> 20) & 0x7ffu);
+  if ((b << 1) == 0ull) return {0.0f, 0.0f};
+  ok = ok && ex >= 949 && ex <= 1150;
+  const int exs = ok ? ex : 1023;
+  const unsigned sign = hi32 & 0x80000000u;
+  const unsigned m23 = ((hi32 & 0xfffffu) << 3) | (lo32 >> 29);
+  const float h = __uint_as_float(sign | ((unsigned)(exs - 896) << 23) | m23);
+  const float scale = __uint_as_float(sign | ((unsigned)(exs - 948) << 23));
+  const float l = __fmul_rn(__uint2float_rn(lo32 & 0x1fffffffu), scale);
+  return {h, l};
+}
+
+__device__ __forceinline__ ff ld_ff(const Columns& cols, int c, int64_t e, bool& ok) {
+  if (cols.is_f32[c]) return {__ldg((const float*)cols.ptr[c] + e), 0.0f};
+  return ff_split(__ldg((const double*)cols.ptr[c] + e), ok);
+}
+
+__device__ __forceinline__ ff ldc(const float* k, int i) { return {k[i], k[i + 1]}; }
+
+// exp, with arguments below -69 giving 0 and setting `dropped`: such a term
+// (a normalised density below 1e-30) is negligible when the event's total
+// density is at least 1e-14, which the caller then checks.
+__device__ __forceinline__ ff ff_exp0(const FFTables& T, ff x, bool& ok, bool& dropped) {
+  if (x.hi < -69.0f) {
+    dropped = true;
+    return {0.0f, 0.0f};
+  }
+  return ff_exp(T, x, ok);
+}
+
+// Normalised decay signal density v and the derivative ratio R at t (the
+// constants fold log(1/I) into every exponent).  Fast path (z < -7):
+// v = exp(A)/I, R = 0.  Otherwise the resolution region:
+// z >= 0: v = exp(-u^2/2) erfcx(z) / (2I), R = 2 / (sqrt(pi) erfcx(z));
+// z < 0:  v = exp(A)/I - exp(-u^2/2) erfcx(|z|) / (2I),
+//         R = 2 q / (sqrt(pi) (2 - q erfcx(|z|))), q = exp(-z^2).
+template <bool kSlow>
+__device__ __forceinline__ ff decay_shape(const FFTables& T, const float* k, ff t, ff* R, ff* uo, bool& ok,
+                                          bool& dropped) {
+  const ff logv = ff_sub(ldc(k, 0), ff_mul(t, ldc(k, 2)));
+  if (!kSlow) {
+    *R = {0.0f, 0.0f};
+    return ff_exp0(T, logv, ok, dropped);
+  }
+  const ff u = ff_mul(ff_sub(t, ldc(k, 14)), ldc(k, 16));
+  *uo = u;
+  const ff z = ff_mul(ff_sub(ldc(k, 18), u), ff{kSqrt1_2_hi, kSqrt1_2_lo});
+  const bool neg = z.hi < 0.0f;
+  const ff y = neg ? ff_neg(z) : z;
+  const ff ex = ff_erfcx(T, y, ok);
+  const ff G = ff_exp0(T, ff_add(ff_scale(ff_sqr(u), -0.5f), ldc(k, 20)), ok, dropped);
+  const ff half_g_ex = ff_scale(ff_mul(G, ex), 0.5f);
+  const ff two_over_sqrtpi = {kTwoInvSqrtPi_hi, kTwoInvSqrtPi_lo};
+  if (!neg) {
+    *R = ff_mul(two_over_sqrtpi, ff_rcp(ex));
+    return half_g_ex;
+  }
+  bool dq = false;  // exp(-z^2) only scales R
+  const ff q = ff_exp0(T, ff_neg(ff_sqr(z)), ok, dq);
+  *R = ff_mul(ff_mul(two_over_sqrtpi, q), ff_rcp(ff_sub(ff{2.0f, 0.0f}, ff_mul(q, ex))));
+  return ff_sub(ff_exp0(T, logv, ok, dropped), half_g_ex);
+}
+
+// Per-shape event programs.  Each adds the event's moments to acc and
+// returns 0, or returns 1 (needs the decay slow path) / 2 (outside the
+// float-float range: take the FP64 fallback) without touching acc.
+template <int kShape, bool kGrad, bool kSlow>
+__device__ __forceinline__ int ff_event(const FFTables& T, const float* k, const int* col, const Columns& cols,
+                                        int64_t e, ff* acc) {
+  bool ok = true, dropped = false;
+  if constexpr (kShape == SHAPE_SUM_GAUSSEXP_CHEB2) {
+    const ff t = ld_ff(cols, col[0], e, ok);
+    if (!kSlow && __fmaf_rn(-t.hi, k[13], k[12]) >= kSlowZf) return ok ? 1 : 2;
+    ff R, u;
+    const ff vs = decay_shape<kSlow>(T, k, t, &R, &u, ok, dropped);
+    const ff pb = ff_add(ff_mul(ff_add(ff_mul(ldc(k, 10), t), ldc(k, 8)), t), ldc(k, 6));
+    const ff p = ff_add(ff_mul(ldc(k, 4), vs), pb);
+    const ff lp = ff_log(T, p, ok);
+    if (!ok || (dropped && p.hi < 1e-14f)) return 2;
+    ff_acc(acc[0], lp);
+    if constexpr (kGrad) {
+      const ff ip = ff_rcp(p);
+      const ff E = ff_mul(vs, ip);
+      const ff ipt = ff_mul(ip, t);
+      ff_acc(acc[1], E);
+      ff_acc(acc[2], ff_mul(E, t));
+      ff_acc(acc[3], ip);
+      ff_acc(acc[4], ipt);
+      ff_acc(acc[5], ff_mul(ipt, t));
+      if (kSlow) {
+        const ff ER = ff_mul(E, R);
+        ff_acc(acc[6], ER);
+        ff_acc(acc[7], ff_mul(ER, u));
+      }
+    }
+    return 0;
+  } else if constexpr (kShape == SHAPE_SUM_GAUSS_POLY1) {
+    const ff x = ld_ff(cols, col[0], e, ok);
+    const ff u = ff_mul(ff_sub(x, ldc(k, 0)), ldc(k, 2));
+    const ff g = ff_exp0(T, ff_add(ff_scale(ff_sqr(u), -0.5f), ldc(k, 14)), ok, dropped);
+    const ff p = ff_add(ff_mul(ldc(k, 4), g), ff_add(ff_mul(ldc(k, 8), x), ldc(k, 6)));
+    const ff lp = ff_log(T, p, ok);
+    if (!ok || (dropped && p.hi < 1e-14f)) return 2;
+    ff_acc(acc[0], lp);
+    if constexpr (kGrad) {
+      const ff ip = ff_rcp(p);
+      const ff G = ff_mul(g, ip);
+      const ff Gu = ff_mul(G, u);
+      ff_acc(acc[1], G);
+      ff_acc(acc[2], Gu);
+      ff_acc(acc[3], ff_mul(Gu, u));
+      ff_acc(acc[4], ip);
+      ff_acc(acc[5], ff_mul(ip, x));
+    }
+    return 0;
+  } else {  // PROD3
+    const ff t = ld_ff(cols, col[1], e, ok);
+    const float* kd = k + 16;
+    if (!kSlow && __fmaf_rn(-t.hi, kd[13], kd[12]) >= kSlowZf) return ok ? 1 : 2;
+    const ff m = ld_ff(cols, col[0], e, ok);
+    const ff c = ld_ff(cols, col[2], e, ok);
+    const ff um = ff_mul(ff_sub(m, ldc(k, 0)), ldc(k, 2));
+    bool dm = false;
+    const ff g = ff_exp0(T, ff_add(ff_scale(ff_sqr(um), -0.5f), ldc(k, 14)), ok, dm);
+    const ff ym = ff_sub(ff_mul(m, ldc(k, 10)), ldc(k, 12));
+    const ff pm = ff_add(ff_mul(ldc(k, 4), g), ff_add(ff_mul(ldc(k, 8), ym), ldc(k, 6)));
+    ff R, u;
+    const ff vs = decay_shape<kSlow>(T, kd, t, &R, &u, ok, dropped);
+    const ff pt = ff_add(ff_mul(ldc(kd, 4), vs),
+                         ff_add(ff_mul(ff_add(ff_mul(ldc(kd, 10), t), ldc(kd, 8)), t), ldc(kd, 6)));
+    const ff pa = ff_add(ff_mul(ff_add(ff_mul(ldc(k, 42), c), ldc(k, 40)), c), ldc(k, 38));
+    const ff lp = ff_log(T, ff_mul(ff_mul(pm, pt), pa), ok);
+    if (!ok || (dm && pm.hi < 1e-14f) || (dropped && pt.hi < 1e-14f)) return 2;
+    ff_acc(acc[0], lp);
+    if constexpr (kGrad) {
+      const ff ipm = ff_rcp(pm), ipt = ff_rcp(pt), ipa = ff_rcp(pa);
+      const ff G = ff_mul(g, ipm);
+      const ff Gu = ff_mul(G, um);
+      ff_acc(acc[1], G);
+      ff_acc(acc[2], Gu);
+      ff_acc(acc[3], ff_mul(Gu, um));
+      ff_acc(acc[4], ipm);
+      ff_acc(acc[5], ff_mul(ipm, ym));
+      const ff E = ff_mul(vs, ipt);
+      const ff it_ = ff_mul(ipt, t);
+      ff_acc(acc[6], E);
+      ff_acc(acc[7], ff_mul(E, t));
+      ff_acc(acc[8], ipt);
+      ff_acc(acc[9], it_);
+      ff_acc(acc[10], ff_mul(it_, t));
+      if (kSlow) {
+        const ff ER = ff_mul(E, R);
+        ff_acc(acc[11], ER);
+        ff_acc(acc[12], ff_mul(ER, u));
+      }
+      const ff iac = ff_mul(ipa, c);
+      ff_acc(acc[13], ipa);
+      ff_acc(acc[14], iac);
+      ff_acc(acc[15], ff_mul(iac, c));
+    }
+    return 0;
+  }
+}
+
+}  // namespace rf

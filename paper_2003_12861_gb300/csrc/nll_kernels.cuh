@@ -33,6 +33,8 @@ struct Pass {
   unsigned long long* slow; // events that took a slow path in this pass (reset by K1)
   int32_t Q;                // quantities per node: 1 + n_slots (or 1 for NLL only)
   int32_t want_grad;
+  int32_t ff_shape;         // specialised float-float event program (Shape), 0 = generic
+  float* ffc;               // n_sets x 512 floats of its parameter-point constants, or null
 };
 
 constexpr int32_t kThetaBad = 1 << 30;

@@ -21,6 +21,7 @@
 #include <mutex>
 
 #include "api_internal.h"
+#include "nll_ff.cuh"
 #include "nll_kernels.cuh"
 
 namespace rf {
@@ -38,7 +39,7 @@ size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Byte offsets of the pass's scratch inside the array.
 struct Layout {
-  size_t consts, items, bad, tickets, tree, total;
+  size_t consts, ffc, items, bad, tickets, tree, total;
 };
 
 // Header (first 256 bytes): int32 counter @0, u64 slow-event count @8,
@@ -46,7 +47,8 @@ struct Layout {
 Layout layout_for(int64_t chunks, int64_t nodes, int n_const, int Q) {
   Layout L{};
   L.consts = 256;
-  L.items = L.consts + up256(sizeof(double) * (size_t)(n_const > 0 ? n_const : 1));
+  L.ffc = L.consts + up256(sizeof(double) * (size_t)(n_const > 0 ? n_const : 1));
+  L.items = L.ffc + up256(sizeof(float) * kFFConst);
   L.bad = L.items + up256(sizeof(int2) * (size_t)(chunks > 0 ? chunks : 1));
   L.tickets = L.bad + up256(sizeof(int32_t) * (size_t)(nodes > 0 ? nodes : 1));
   L.tree = L.tickets + up256(sizeof(int32_t) * (size_t)(nodes > 0 ? nodes : 1));
@@ -152,6 +154,8 @@ extern "C" rf_status rf_nll_grad_noalloc(const rf_model* m, const void* const* d
   pass.flags = d_flags;
   pass.Q = Q;
   pass.want_grad = 1;
+  pass.ff_shape = m->m.shape;
+  pass.ffc = (float*)(base + L.ffc);
   launch_param_point(P, pass, st);
   launch_events(P, m->m.shape, cols, pass, m->m.threads_per_block, m->m.blocks_per_sm, sm_count(), st);
   return cuda_ok(cudaGetLastError(), "rf_nll_grad_noalloc launch") ? RF_OK : RF_E_CUDA;

@@ -24,6 +24,18 @@ def thetas(which):
         # events near mu_r the erfc branch of the slow path.
         out.append(np.array([1.2, 0.3, 0.2, -0.1, 0.02, 0.4]))
         out.append(np.array([0.4, -0.2, 0.6, 0.1, -0.05, 0.7]))
+        # float-float edge regimes: a decay that underflows long before t = 10,
+        # a pure signal (the total density itself underflows), no signal
+        out.append(np.array([0.12, 0.0, 0.05, -0.2, 0.05, 0.2]))
+        out.append(np.array([0.3, 0.0, 0.05, -0.2, 0.05, 1.0]))
+        out.append(np.array([1.5, 0.0, 0.05, -0.2, 0.05, 0.0]))
+    if which == "gauss_poly1_model":
+        out.append(np.array([5.0, 0.05, 0.3, -0.05]))   # narrow: far tails underflow
+        out.append(np.array([9.9, 0.3, 1.0, 0.0]))      # pure Gaussian at the range edge
+    if which == "prod3_model":
+        e = t.copy()
+        e[0], e[1] = 5.205, 0.003                       # mass peak at the range edge, narrow
+        out.append(e)
     return out
 
 
