@@ -297,10 +297,11 @@ rf_status rf_math_eval(int32_t fn, const double* d_x, double* d_y, int64_t n, vo
  * this serves callers that cannot call cudaMalloc while they run (an online
  * filter or service that reserves all GPU memory at start-up, where an
  * allocation mid-run has unbounded latency and may fail).  Its scratch lives
- * in a static 2 MiB device array inside the library (held by every GPU that
- * loads it, until exit); a dataset whose scratch would not fit -- beyond
- * about 6.5e7 events for a model with 6 free parameters, 3.7e7 with 12 --
- * is rejected with RF_E_INVALID and a message giving the limit.
+ * in a static 16 MiB device array inside the library (held by every GPU that
+ * loads it, until exit); a dataset whose scratch would not fit -- for the
+ * float-float shapes beyond about 7.5e7 events with 6 gradient slots, 5.7e7
+ * with 12; for the generic kernel about 5e8 and 3e8 -- is rejected with
+ * RF_E_INVALID and a message giving the limit.
  *   d_cols : n_obs DEVICE column pointers (host array of pointers), dtype per
  *            column (NULL = all RF_F64), n_events events each.
  *   d_theta: DEVICE n_free parameters; d_out: DEVICE 1 + n_free doubles (NLL,

@@ -108,6 +108,7 @@ bool ensure_workspace(const rf_model* m, rf_data* d) {
   const int Q = 1 + P.n_slots;
   if (w.ready && w.n_const == P.n_const && w.n_free == P.n_free && w.Q == Q) return true;
   const size_t S = d->n_sets;
+  const size_t nodes = (size_t)std::max<int64_t>(1, d->total_nodes);
   bool ok = w.consts.ensure(sizeof(double) * S * std::max(1, P.n_const)) &&
             w.theta.ensure(sizeof(double) * S * std::max(1, P.n_free)) &&
             w.out.ensure(sizeof(double) * S * (1 + P.n_free)) && w.flags.ensure(sizeof(int32_t) * S) &&
@@ -115,7 +116,12 @@ bool ensure_workspace(const rf_model* m, rf_data* d) {
             w.tree_bad.ensure(sizeof(int32_t) * std::max<int64_t>(1, d->total_nodes)) &&
             w.tickets.ensure(sizeof(int32_t) * std::max<int64_t>(1, d->total_nodes)) &&
             w.counter.ensure(sizeof(int32_t)) && w.slow.ensure(sizeof(unsigned long long)) &&
-            (m->m.shape == SHAPE_GENERIC || w.ffc.ensure(sizeof(float) * S * kFFConst)) && w.h_theta.ensure(sizeof(double) * S * std::max(1, P.n_free)) &&
+            (m->m.shape == SHAPE_GENERIC ||
+             (w.ffc.ensure(sizeof(float) * S * kFFConst) &&
+              w.part_m.ensure(sizeof(float) * nodes * kParts * kPartFloats) &&
+              w.part_fb.ensure(sizeof(double) * nodes * kParts * Q) &&
+              w.part_info.ensure(sizeof(int32_t) * nodes * kParts))) &&
+            w.h_theta.ensure(sizeof(double) * S * std::max(1, P.n_free)) &&
             w.h_out.ensure(sizeof(double) * S * (1 + P.n_free)) && w.h_flags.ensure(sizeof(int32_t) * S);
   if (!ok) return false;
   if (!cuda_ok(cudaMemset(w.tickets.p, 0, sizeof(int32_t) * std::max<int64_t>(1, d->total_nodes)), "ticket reset"))
@@ -156,6 +162,9 @@ Pass make_pass(const rf_model* m, rf_data* d, const Plan& plan, const double* d_
   p.want_grad = grad ? 1 : 0;
   p.ff_shape = m->m.shape;
   p.ffc = m->m.shape == SHAPE_GENERIC ? nullptr : (float*)w.ffc.p;
+  p.part_m = (float*)w.part_m.p;
+  p.part_fb = (double*)w.part_fb.p;
+  p.part_info = (int32_t*)w.part_info.p;
   return p;
 }
 

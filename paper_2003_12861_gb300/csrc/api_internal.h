@@ -43,7 +43,7 @@ struct Plan {
 struct Workspace {
   bool ready = false;
   int n_const = -1, n_free = -1, Q = -1;
-  DevBuf consts, theta, out, flags, tree, tree_bad, tickets, counter, slow, ffc;
+  DevBuf consts, theta, out, flags, tree, tree_bad, tickets, counter, slow, ffc, part_m, part_fb, part_info;
   HostBuf h_theta, h_out, h_flags;
 };
 

@@ -359,16 +359,21 @@ __device__ bool eval_generic(const Program& P, const double* __restrict__ C, con
 }
 
 constexpr int kWarps = kLanes / 32;   // warps per chunk group
+// Resident blocks per SM the float-float kernels are compiled for (their
+// register budget: 80 registers for 6 blocks, 96 for 5).
+__host__ __device__ constexpr int ff_min_blocks(int shape) { return shape == SHAPE_PROD3 ? 5 : 6; }
 constexpr int kQMax = 1 + kMaxSlots;
 
-struct Smem {
+template <class QT, int kQueue>
+struct SmemT {
   double C[kMaxConst];
   double wsum[kWarps][kQMax];
   int wbad[kWarps];
-  int queue[kWarps][kPerLane * 32];
+  QT queue[kWarps][kQueue];
   int item;
   int last;
 };
+using Smem = SmemT<int, kPerLane * 32>;
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -394,7 +399,8 @@ __device__ __forceinline__ Pair warp_merge(Pair p) {
 // two-sum merges; the block that completes the root writes the set's result.
 // The tree is fixed by the set's chunk count, so the result does not depend
 // on which block ran which chunk, or in which order.
-__device__ void climb_tree(const Program& P, const Pass& pass, Smem& sm, int set, int chunk, int64_t n_events) {
+template <class S>
+__device__ void climb_tree(const Program& P, const Pass& pass, S& sm, int set, int chunk, int64_t n_events) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int Q = pass.Q;
   const int64_t base = pass.tree_base[set];
@@ -460,7 +466,8 @@ __device__ void climb_tree(const Program& P, const Pass& pass, Smem& sm, int set
 
 // Writes a chunk's totals (Q values in sm.wsum[0]) to its level-0 tree node
 // and climbs the tree.
-__device__ void write_chunk(const Program& P, const Pass& pass, Smem& sm, int bad, int set, int chunk,
+template <class S>
+__device__ void write_chunk(const Program& P, const Pass& pass, S& sm, int bad, int set, int chunk,
                             int64_t n_events) {
   const int tid = threadIdx.x;
   const int Q = pass.Q;
@@ -549,23 +556,76 @@ __global__ void __launch_bounds__(kLanes) events_generic(const __grid_constant__
   }
 }
 
-// Float-float fused event kernel of a specialised shape.  Same chunk/lane
-// geometry, queues and reduction tree as the generic kernel; per lane the
-// shape's moments are summed in float-float; events in the decay resolution
-// region are queued (ballot order) and evaluated after the fast pass; events
-// outside the float-float range take the FP64 interpreter (a third queue,
-// FP64 sums).  At the chunk end the warps' moments are merged in fixed order
-// and mapped to (sum log p, slot gradients) by the set's matrix K.
+// Sums v[0..N) over the lanes of a warp with the xor butterfly (offsets 16,
+// 8, 4, 2, 1).  At each of the first log2(N) levels a lane pair splits the
+// values in two halves and each lane adds one half (reduce-scatter), so a
+// lane adds N/2 + N/4 + ... values instead of 5 N; every value still gets the
+// plain butterfly's pairwise tree (float-float addition is commutative and
+// deterministic).  Afterwards v[0] of lane l holds the sum of value index
+// ff_lane_index<N>(l), on every lane with that index.
+template <int N>
+__device__ __forceinline__ void warp_ff_reduce(ff* v, int lane) {
+  static_assert(N == 1 || N == 2 || N == 4 || N == 8 || N == 16, "power of two up to 16");
+  int h = N / 2;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    if (h >= 1) {
+      const bool up = (lane & o) != 0;
+#pragma unroll
+      for (int j = 0; j < N / 2; ++j) {
+        if (j < h) {
+          const ff send = up ? v[j] : v[j + h];
+          const ff keep = up ? v[j + h] : v[j];
+          const ff r = {__shfl_xor_sync(0xffffffffu, send.hi, o), __shfl_xor_sync(0xffffffffu, send.lo, o)};
+          v[j] = ff_add(keep, r);
+        }
+      }
+      h >>= 1;
+    } else {
+      const ff r = {__shfl_xor_sync(0xffffffffu, v[0].hi, o), __shfl_xor_sync(0xffffffffu, v[0].lo, o)};
+      v[0] = ff_add(v[0], r);
+    }
+  }
+}
+template <int N>
+__device__ __forceinline__ int ff_lane_index(int lane) {
+  int idx = 0, h = N / 2;
+#pragma unroll
+  for (int o = 16; o > 0 && h >= 1; o >>= 1, h >>= 1) idx += (lane & o) ? h : 0;
+  return idx;
+}
+// Lanes whose bits below the halving levels are zero (one writer per index).
+template <int N>
+__device__ __forceinline__ bool ff_lane_writes(int lane) {
+  constexpr int levels = N >= 16 ? 4 : N >= 8 ? 3 : N >= 4 ? 2 : N >= 2 ? 1 : 0;
+  return (lane & ((32 >> levels) - 1)) == 0;
+}
+__host__ __device__ constexpr int pow2_at_least(int n) { return n <= 1 ? 1 : n <= 2 ? 2 : n <= 4 ? 4 : n <= 8 ? 8 : 16; }
+
+// Float-float fused event kernel of a specialised shape.  Persistent blocks
+// of 128 threads take work units from the counter: unit u is part u % 4 of
+// work item u / 4 (a quarter of a 4096-event chunk, 8 events per lane), so
+// the last round of units is short.  Per lane the shape's moments are summed
+// in float-float; events in the decay resolution region are queued per warp
+// (ballot order) and evaluated after the fast pass; events outside the
+// float-float range take the FP64 interpreter (FP64 sums).  At the end of a
+// part the warps' moments are merged in fixed order and stored as the part's
+// record; the block that completes the chunk's last part (arrival ticket)
+// merges the four records in part order, maps the moments to (sum log p,
+// slot gradients) with the set's matrix K and climbs the reduction tree.
+// Every sum has a fixed order, so the result does not depend on the launch.
 template <int kShape, bool kGrad>
-__global__ void __launch_bounds__(kLanes) events_ff(const __grid_constant__ Program P,
-                                                    const __grid_constant__ Columns cols, Pass pass) {
+__global__ void __launch_bounds__(kLanes, ff_min_blocks(kShape)) events_ff(const __grid_constant__ Program P,
+                                                                  const __grid_constant__ Columns cols, Pass pass) {
   constexpr int NA = kGrad ? ff_nacc(kShape) : 1;
+  constexpr int NP = pow2_at_least(NA);
   constexpr int NAK = ff_nacc(kShape);
-  __shared__ Smem sm;
+  constexpr int kPartK = kPerLane / kParts;
+  __shared__ SmemT<short, kPartK * 32> sm;
   __shared__ FFTables T;
   __shared__ float kc[kFFConst];
   __shared__ ff wacc[kWarps][16];
-  __shared__ int fbq[kWarps][kPerLane * 32];
+  __shared__ unsigned fbmask[kLanes];  // per lane: its events (bit k) that need the FP64 path
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int Q = pass.Q;
   ff_load_tables(T);
@@ -576,66 +636,80 @@ __global__ void __launch_bounds__(kLanes) events_ff(const __grid_constant__ Prog
     col[0] = col[1] = col[2] = P.node[0].col;
   }
   const unsigned lt = (1u << lane) - 1u;
+  const int n_units = pass.n_items * kParts;
+  int kc_set = -1, c_set = -1;  // sets whose constants the block holds (block-uniform)
   while (true) {
     if (tid == 0) sm.item = atomicAdd(pass.counter, 1);
     __syncthreads();
-    const int it = sm.item;
-    if (it >= pass.n_items) break;
+    const int u = sm.item;
+    if (u >= n_units) break;
+    const int it = u / kParts, part = u % kParts;
     const int set = pass.items[it].x, chunk = pass.items[it].y;
     const int64_t s_begin = pass.offsets[set], s_end = pass.offsets[set + 1];
     const int64_t base = s_begin + (int64_t)chunk * kChunk;
-    for (int i = tid; i < P.n_const; i += kLanes) sm.C[i] = pass.consts[(size_t)set * P.n_const + i];
-    for (int i = tid; i < kFFConst; i += kLanes) kc[i] = pass.ffc[(size_t)set * kFFConst + i];
+    if (set != kc_set) {
+      for (int i = tid; i < kFFConst; i += kLanes) kc[i] = pass.ffc[(size_t)set * kFFConst + i];
+      kc_set = set;
+    }
+    fbmask[tid] = 0u;
     __syncthreads();
-    ff acc[NA];
+    ff acc[NP];
 #pragma unroll
-    for (int j = 0; j < NA; ++j) acc[j] = {0.0f, 0.0f};
-    int qs = 0, qf = 0;
-    for (int k = 0; k < kPerLane; ++k) {
-      const int64_t e = base + tid + (int64_t)k * kLanes;
+    for (int j = 0; j < NP; ++j) acc[j] = {0.0f, 0.0f};
+    int qs = 0;
+    unsigned myfb = 0u;
+    const int k0 = part * kPartK;
+    // the next event's observables are loaded one iteration ahead
+    int64_t e = base + tid + (int64_t)k0 * kLanes;
+    FFIn<kShape> nxt;
+    if (e < s_end) nxt = ff_load<kShape>(cols, col, e);
+#pragma unroll 1
+    for (int k = k0; k < k0 + kPartK; ++k, e += kLanes) {
+      const FFIn<kShape> cur = nxt;
+      if (k + 1 < k0 + kPartK && e + kLanes < s_end) nxt = ff_load<kShape>(cols, col, e + kLanes);
       int st = 0;
-      if (e < s_end) st = ff_event<kShape, kGrad, false>(T, kc, col, cols, e, acc);
-      const unsigned bs = __ballot_sync(0xffffffffu, st == 1), bf = __ballot_sync(0xffffffffu, st == 2);
-      if (st == 1) sm.queue[warp][qs + __popc(bs & lt)] = (int)(e - base);
-      if (st == 2) fbq[warp][qf + __popc(bf & lt)] = (int)(e - base);
+      if (e < s_end) st = ff_event<kShape, kGrad, false>(T, kc, cur, acc);
+      const unsigned bs = __ballot_sync(0xffffffffu, st == 1);
+      if (st == 1) sm.queue[warp][qs + __popc(bs & lt)] = (short)(e - base);
+      if (st == 2) myfb |= 1u << k;
       qs += __popc(bs);
-      qf += __popc(bf);
     }
     __syncwarp();
     if (lane == 0 && qs > 0 && pass.slow) atomicAdd(pass.slow, (unsigned long long)qs);
     for (int j0 = 0; j0 < qs; j0 += 32) {
       const int j = j0 + lane;
-      int st = 0;
-      if (j < qs) st = ff_event<kShape, kGrad, true>(T, kc, col, cols, base + sm.queue[warp][j], acc);
-      const unsigned bf = __ballot_sync(0xffffffffu, st == 2);
-      if (st == 2) fbq[warp][qf + __popc(bf & lt)] = sm.queue[warp][j];
-      qf += __popc(bf);
+      if (j < qs) {
+        const int off = sm.queue[warp][j];
+        if (ff_event<kShape, kGrad, true>(T, kc, ff_load<kShape>(cols, col, base + off), acc) == 2)
+          atomicOr(&fbmask[off % kLanes], 1u << (off / kLanes));  // owner lane, event bit
+      }
     }
-    __syncwarp();
-    // FP64 fallback for events outside the float-float range
+    __syncthreads();
+    myfb |= fbmask[tid];
+    // FP64 fallback for events outside the float-float range: each lane
+    // evaluates its own flagged events in event order.
     double acc64[kQMax];
     int bad = 0;
-    const bool any_fb = __syncthreads_or(qf > 0);
+    const bool any_fb = __syncthreads_or(myfb != 0u);
     if (any_fb) {
+      if (set != c_set) {
+        for (int i = tid; i < P.n_const; i += kLanes) sm.C[i] = pass.consts[(size_t)set * P.n_const + i];
+        c_set = set;
+      }
+      __syncthreads();
       for (int q = 0; q < kQMax; ++q) acc64[q] = 0.0;
       double x[kMaxObs];
-      for (int j = lane; j < qf; j += 32) {
-        const int64_t e = base + fbq[warp][j];
+      while (myfb) {
+        const int k = __ffs(myfb) - 1;
+        myfb &= myfb - 1u;
+        const int64_t e = base + tid + (int64_t)k * kLanes;
         for (int c = 0; c < P.n_obs; ++c) x[c] = load_col(cols, c, e);
         eval_generic<true, kGrad>(P, sm.C, x, acc64, &bad);
       }
     }
-    // moments: warp butterfly (float-float), lane 0 holds the warp's sums
-#pragma unroll
-    for (int j = 0; j < NA; ++j) {
-      ff v = acc[j];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const ff w = {__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
-        v = ff_add(v, w);
-      }
-      if (lane == 0) wacc[warp][j] = v;
-    }
+    // the part's moments: reduce-scatter butterfly, then the warps in order
+    warp_ff_reduce<NP>(acc, lane);
+    if (ff_lane_writes<NP>(lane)) wacc[warp][ff_lane_index<NP>(lane)] = acc[0];
     if (any_fb) {
       for (int q = 0; q < Q; ++q) {
         const double w = warp_sum(acc64[q]);
@@ -645,27 +719,58 @@ __global__ void __launch_bounds__(kLanes) events_ff(const __grid_constant__ Prog
       if (lane == 0) sm.wbad[warp] = bad;
     }
     __syncthreads();
+    const int64_t leaf = pass.tree_base[set] + chunk;
+    const int64_t rec = leaf * kParts + part;
+    if (tid < NA) {
+      const ff M = ff_add(ff_add(wacc[0][tid], wacc[1][tid]), ff_add(wacc[2][tid], wacc[3][tid]));
+      pass.part_m[rec * kPartFloats + 2 * tid] = M.hi;
+      pass.part_m[rec * kPartFloats + 2 * tid + 1] = M.lo;
+    }
+    if (any_fb && tid < Q) {
+      const Pair a = merge({sm.wsum[0][tid], 0.0}, {sm.wsum[1][tid], 0.0});
+      const Pair b = merge({sm.wsum[2][tid], 0.0}, {sm.wsum[3][tid], 0.0});
+      const Pair r = merge(a, b);
+      pass.part_fb[rec * Q + tid] = r.s + r.c;
+    }
+    if (tid == 0)
+      pass.part_info[rec] = (any_fb ? 1 : 0) | ((any_fb ? sm.wbad[0] + sm.wbad[1] + sm.wbad[2] + sm.wbad[3] : 0) << 1);
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+      const int t = atomicAdd(&pass.tickets[leaf], 1);
+      sm.last = (t == kParts - 1);
+      if (sm.last) pass.tickets[leaf] = 0;
+    }
+    __syncthreads();
+    if (!sm.last) continue;
+    __threadfence();
+    // The chunk: parts merged in part order, out_q = sum_j K[q][j] M_j.
     double v = 0.0;
+    int info[kParts];
+#pragma unroll
+    for (int p = 0; p < kParts; ++p) info[p] = __ldcg(pass.part_info + leaf * kParts + p);
     if (tid < Q) {
-      // merge the warps in fixed order, then out_q = sum_j K[q][j] M_j
       const float* K = kc + ff_koff(kShape);
+      const float* pm = pass.part_m + leaf * kParts * kPartFloats;
       ff out = {0.0f, 0.0f};
 #pragma unroll
       for (int j = 0; j < NA; ++j) {
-        const ff Mj = ff_add(ff_add(wacc[0][j], wacc[1][j]), ff_add(wacc[2][j], wacc[3][j]));
+        ff Mj = {__ldcg(pm + 2 * j), __ldcg(pm + 2 * j + 1)};
+#pragma unroll
+        for (int p = 1; p < kParts; ++p)
+          Mj = ff_add(Mj, ff{__ldcg(pm + p * kPartFloats + 2 * j), __ldcg(pm + p * kPartFloats + 2 * j + 1)});
         out = ff_add(out, ff_mul(ff{K[2 * (tid * NAK + j)], K[2 * (tid * NAK + j) + 1]}, Mj));
       }
       v = ff_to_double(out);
-      if (any_fb) {
-        Pair a = merge({sm.wsum[0][tid], 0.0}, {sm.wsum[1][tid], 0.0});
-        Pair b = merge({sm.wsum[2][tid], 0.0}, {sm.wsum[3][tid], 0.0});
-        Pair r = merge(a, b);
-        v += r.s + r.c;
-      }
+#pragma unroll
+      for (int p = 0; p < kParts; ++p)
+        if (info[p] & 1) v += __ldcg(pass.part_fb + (leaf * kParts + p) * Q + tid);
     }
+    int bad_all = 0;
+#pragma unroll
+    for (int p = 0; p < kParts; ++p) bad_all += info[p] >> 1;
     __syncthreads();
     if (tid < Q) sm.wsum[0][tid] = v;
-    const int bad_all = any_fb ? sm.wbad[0] + sm.wbad[1] + sm.wbad[2] + sm.wbad[3] : 0;
     __syncthreads();
     write_chunk(P, pass, sm, bad_all, set, chunk, s_end - s_begin);
     __syncthreads();
@@ -714,8 +819,9 @@ void launch_events(const Program& P, Shape shape, const Columns& cols, const Pas
   if (pass.n_items == 0) return;
   const int bps = blocks_per_sm > 0 ? blocks_per_sm : 8;
   int grid = n_sm * bps;
-  if (grid > pass.n_items) grid = pass.n_items;
   const Shape sh = (pass.ff_shape != SHAPE_GENERIC && pass.ffc) ? shape : SHAPE_GENERIC;
+  const int64_t units = sh == SHAPE_GENERIC ? (int64_t)pass.n_items : (int64_t)pass.n_items * kParts;
+  if (grid > units) grid = (int)units;
   timing_begin(st);
   switch (sh) {
     case SHAPE_SUM_GAUSSEXP_CHEB2:

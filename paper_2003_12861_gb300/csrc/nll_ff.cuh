@@ -227,12 +227,30 @@ __device__ __forceinline__ ff decay_shape(const FFTables& T, const float* k, ff 
 // Per-shape event programs.  Each adds the event's moments to acc and
 // returns 0, or returns 1 (needs the decay slow path) / 2 (outside the
 // float-float range: take the FP64 fallback) without touching acc.
+// The event's observables, split to float-float: x[0] (DECAY, GP1) or
+// (m, t, c) (PROD3); ok is false if one is outside the float-float range.
+template <int kShape>
+struct FFIn {
+  ff x[kShape == SHAPE_PROD3 ? 3 : 1];
+  bool ok;
+};
+template <int kShape>
+__device__ __forceinline__ FFIn<kShape> ff_load(const Columns& cols, const int* col, int64_t e) {
+  FFIn<kShape> in;
+  in.ok = true;
+  in.x[0] = ld_ff(cols, col[0], e, in.ok);
+  if constexpr (kShape == SHAPE_PROD3) {
+    in.x[1] = ld_ff(cols, col[1], e, in.ok);
+    in.x[2] = ld_ff(cols, col[2], e, in.ok);
+  }
+  return in;
+}
+
 template <int kShape, bool kGrad, bool kSlow>
-__device__ __forceinline__ int ff_event(const FFTables& T, const float* k, const int* col, const Columns& cols,
-                                        int64_t e, ff* acc) {
-  bool ok = true, dropped = false;
+__device__ __forceinline__ int ff_event(const FFTables& T, const float* k, const FFIn<kShape>& in, ff* acc) {
+  bool ok = in.ok, dropped = false;
   if constexpr (kShape == SHAPE_SUM_GAUSSEXP_CHEB2) {
-    const ff t = ld_ff(cols, col[0], e, ok);
+    const ff t = in.x[0];
     if (!kSlow && __fmaf_rn(-t.hi, k[13], k[12]) >= kSlowZf) return ok ? 1 : 2;
     ff R, u;
     const ff vs = decay_shape<kSlow>(T, k, t, &R, &u, ok, dropped);
@@ -258,7 +276,7 @@ __device__ __forceinline__ int ff_event(const FFTables& T, const float* k, const
     }
     return 0;
   } else if constexpr (kShape == SHAPE_SUM_GAUSS_POLY1) {
-    const ff x = ld_ff(cols, col[0], e, ok);
+    const ff x = in.x[0];
     const ff u = ff_mul(ff_sub(x, ldc(k, 0)), ldc(k, 2));
     const ff g = ff_exp0(T, ff_add(ff_scale(ff_sqr(u), -0.5f), ldc(k, 14)), ok, dropped);
     const ff p = ff_add(ff_mul(ldc(k, 4), g), ff_add(ff_mul(ldc(k, 8), x), ldc(k, 6)));
@@ -277,11 +295,11 @@ __device__ __forceinline__ int ff_event(const FFTables& T, const float* k, const
     }
     return 0;
   } else {  // PROD3
-    const ff t = ld_ff(cols, col[1], e, ok);
+    const ff t = in.x[1];
     const float* kd = k + 16;
     if (!kSlow && __fmaf_rn(-t.hi, kd[13], kd[12]) >= kSlowZf) return ok ? 1 : 2;
-    const ff m = ld_ff(cols, col[0], e, ok);
-    const ff c = ld_ff(cols, col[2], e, ok);
+    const ff m = in.x[0];
+    const ff c = in.x[2];
     const ff um = ff_mul(ff_sub(m, ldc(k, 0)), ldc(k, 2));
     bool dm = false;
     const ff g = ff_exp0(T, ff_add(ff_scale(ff_sqr(um), -0.5f), ldc(k, 14)), ok, dm);

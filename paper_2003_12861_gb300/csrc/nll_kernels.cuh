@@ -35,7 +35,18 @@ struct Pass {
   int32_t want_grad;
   int32_t ff_shape;         // specialised float-float event program (Shape), 0 = generic
   float* ffc;               // n_sets x 512 floats of its parameter-point constants, or null
+  // Float-float kernels: per chunk, kParts part records (indexed by the
+  // chunk's level-0 tree node x kParts + part).
+  float* part_m;            // 32 floats per part: its moment sums (float-float pairs)
+  double* part_fb;          // Q doubles per part: its FP64 fallback sums (valid if info bit 0)
+  int32_t* part_info;       // per part: bit 0 = fallback sums present, bits 1.. = bad events
 };
+
+// Work units per chunk of the float-float kernels: part p of a chunk covers
+// its events [1024 p, 1024 (p + 1)), i.e. lane l's events l + 128 k for
+// k in [8 p, 8 p + 8).
+constexpr int kParts = 4;
+constexpr int kPartFloats = 32;
 
 constexpr int32_t kThetaBad = 1 << 30;
 

@@ -28,7 +28,7 @@ namespace rf {
 
 namespace {
 
-constexpr size_t kScratchBytes = size_t(2) << 20;  // 2 MiB per device
+constexpr size_t kScratchBytes = size_t(16) << 20;  // 16 MiB per device
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
@@ -39,12 +39,12 @@ size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Byte offsets of the pass's scratch inside the array.
 struct Layout {
-  size_t consts, ffc, items, bad, tickets, tree, total;
+  size_t consts, ffc, items, bad, tickets, tree, part_m, part_fb, part_info, total;
 };
 
 // Header (first 256 bytes): int32 counter @0, u64 slow-event count @8,
 // int64 offsets[2] @16, int64 tree base @32, int32 active set @40.
-Layout layout_for(int64_t chunks, int64_t nodes, int n_const, int Q) {
+Layout layout_for(int64_t chunks, int64_t nodes, int n_const, int Q, bool parts) {
   Layout L{};
   L.consts = 256;
   L.ffc = L.consts + up256(sizeof(double) * (size_t)(n_const > 0 ? n_const : 1));
@@ -52,7 +52,12 @@ Layout layout_for(int64_t chunks, int64_t nodes, int n_const, int Q) {
   L.bad = L.items + up256(sizeof(int2) * (size_t)(chunks > 0 ? chunks : 1));
   L.tickets = L.bad + up256(sizeof(int32_t) * (size_t)(nodes > 0 ? nodes : 1));
   L.tree = L.tickets + up256(sizeof(int32_t) * (size_t)(nodes > 0 ? nodes : 1));
-  L.total = L.tree + sizeof(double) * 2 * (size_t)Q * (size_t)(nodes > 0 ? nodes : 1);
+  // float-float kernels only: the part records of every chunk
+  const size_t nn = parts ? (size_t)(nodes > 0 ? nodes : 1) : 0;
+  L.part_m = L.tree + up256(sizeof(double) * 2 * (size_t)Q * (size_t)(nodes > 0 ? nodes : 1));
+  L.part_fb = L.part_m + up256(sizeof(float) * kParts * kPartFloats * nn);
+  L.part_info = L.part_fb + up256(sizeof(double) * kParts * (size_t)Q * nn);
+  L.total = L.part_info + sizeof(int32_t) * kParts * nn;
   return L;
 }
 
@@ -95,7 +100,7 @@ extern "C" rf_status rf_nll_grad_noalloc(const rf_model* m, const void* const* d
   const int64_t chunks = (n_events + kChunk - 1) / kChunk;
   const int64_t nodes = tree_nodes(chunks);
   const int Q = 1 + P.n_slots;
-  const Layout L = layout_for(chunks, nodes, P.n_const, Q);
+  const Layout L = layout_for(chunks, nodes, P.n_const, Q, m->m.shape != SHAPE_GENERIC);
   if (L.total > kScratchBytes || chunks > (int64_t)0x7fffffff) {
     const double per_chunk = (double)L.total / (double)(chunks > 0 ? chunks : 1);
     char msg[256];
@@ -156,6 +161,9 @@ extern "C" rf_status rf_nll_grad_noalloc(const rf_model* m, const void* const* d
   pass.want_grad = 1;
   pass.ff_shape = m->m.shape;
   pass.ffc = (float*)(base + L.ffc);
+  pass.part_m = (float*)(base + L.part_m);
+  pass.part_fb = (double*)(base + L.part_fb);
+  pass.part_info = (int32_t*)(base + L.part_info);
   launch_param_point(P, pass, st);
   launch_events(P, m->m.shape, cols, pass, m->m.threads_per_block, m->m.blocks_per_sm, sm_count(), st);
   return cuda_ok(cudaGetLastError(), "rf_nll_grad_noalloc launch") ? RF_OK : RF_E_CUDA;
