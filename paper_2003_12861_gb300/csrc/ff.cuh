@@ -35,6 +35,8 @@ struct FFTables {
   float log_tab[514];
   float invf_tab[514];
   float erfcx[6 * 17 * 2];
+  float erfcx_mid[6], erfcx_ihalf[6];
+  int erfcx_kf[6];
 };
 
 __device__ __forceinline__ void ff_load_tables(FFTables& t) {
@@ -44,6 +46,11 @@ __device__ __forceinline__ void ff_load_tables(FFTables& t) {
     t.invf_tab[i] = kInvFTab[i];
   }
   for (int i = threadIdx.x; i < 6 * 17 * 2; i += blockDim.x) t.erfcx[i] = kErfcxCoef[i];
+  for (int i = threadIdx.x; i < 6; i += blockDim.x) {
+    t.erfcx_mid[i] = kErfcxMid[i];
+    t.erfcx_ihalf[i] = kErfcxInvHalf[i];
+    t.erfcx_kf[i] = kErfcxFF[i];
+  }
 }
 
 __device__ __forceinline__ ff ff_from_double(double d) {
@@ -206,9 +213,9 @@ __device__ __forceinline__ ff ff_erfcx(const FFTables& T, ff y, bool& ok) {
     piece = v.hi > 0.25f ? 3 : (v.hi > 0.125f ? 4 : 5);
   }
   // x = (v - mid) / half, exact scaling by a power of two
-  const ff x = ff_scale(ff_add_f(v, -kErfcxMid[piece]), kErfcxInvHalf[piece]);
+  const ff x = ff_scale(ff_add_f(v, -T.erfcx_mid[piece]), T.erfcx_ihalf[piece]);
   const float* c = T.erfcx + piece * 34;
-  const int kf = kErfcxFF[piece];  // 1 <= kf <= 16: tail a_16..a_kf in float
+  const int kf = T.erfcx_kf[piece];  // 1 <= kf <= 16: tail a_16..a_kf in float
   float s = c[2 * 16];
   for (int k = 15; k >= kf; --k) s = __fmaf_rn(s, x.hi, c[2 * k]);
   ff acc = {s, 0.0f};

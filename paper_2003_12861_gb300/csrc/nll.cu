@@ -22,22 +22,31 @@ namespace {
 
 constexpr double kSqrt1_2 = 0.70710678118654752440;
 constexpr double kSqrt2Pi = 2.50662827463100050242;
+constexpr double kInvSqrt2Pi = 0.39894228040143267794;
 constexpr double kInvSqrtPi = 0.56418958354775628695;
 constexpr double kTwoInvSqrtPi = 1.12837916709551257390;
 // Below this z the erfc factor of the decay-resolution convolution equals 2
 // to better than 1e-22 relative and its derivative term is below 1e-21 of
 // the exponential's, so the event takes the one-exponential fast path.
 constexpr double kSlowZ = -7.0;
+// Up to this many active sets K1 runs one block per set (latency), beyond
+// one thread per set (throughput).
+constexpr int kBlockK1MaxSets = 256;
 
 __device__ __forceinline__ double param_of(const PNode& q, int j, const double* th) {
   return q.pfree[j] >= 0 ? th[q.pfree[j]] : q.pfixed[j];
 }
 
-// Phi(be) - Phi(al), using erfc on the tail side to keep far-tail precision.
-__device__ double normal_mass(double al, double be) {
-  if (al >= 0.0) return 0.5 * (erfc(al * kSqrt1_2) - erfc(be * kSqrt1_2));
-  if (be <= 0.0) return 0.5 * (erfc(-be * kSqrt1_2) - erfc(-al * kSqrt1_2));
-  return 0.5 * (erf(be * kSqrt1_2) - erf(al * kSqrt1_2));
+// Phi(be) - Phi(al) from one term per end, using erfc on the tail side to
+// keep far-tail precision: case 0 (al >= 0) e(x) = erfc(x/sqrt2), mass
+// (e(al) - e(be))/2; case 1 (be <= 0) e(x) = erfc(-x/sqrt2), case 2
+// e(x) = erf(x/sqrt2), both with mass (e(be) - e(al))/2.
+__device__ __forceinline__ int mass_case(double al, double be) { return al >= 0.0 ? 0 : be <= 0.0 ? 1 : 2; }
+__device__ __forceinline__ double mass_term(int cs, double x) {
+  return cs == 0 ? erfc(x * kSqrt1_2) : cs == 1 ? erfc(-x * kSqrt1_2) : erf(x * kSqrt1_2);
+}
+__device__ __forceinline__ double mass_of(int cs, double ea, double eb) {
+  return cs == 0 ? 0.5 * (ea - eb) : 0.5 * (eb - ea);
 }
 
 // Decay (x) resolution at one point t, with d/d(tau, mu, sigma).
@@ -55,6 +64,48 @@ __device__ void gaussexp_point(double t, double tau, double mu, double sigma, do
   for (int k = 0; k < 3; ++k) df[k] = val * dA[k] - g * kInvSqrtPi * dz[k];
 }
 
+// What a Gaussian or decay-resolution node needs at one end of its range:
+// x the standardised end (al or be), t the end itself.  e = the mass term,
+// p = exp(-x^2/2), and for the decay the convolution f(t) with d/d(tau, mu,
+// sigma).
+struct EndVals {
+  double e, p, f, df[3];
+};
+__device__ __forceinline__ void end_vals(int cs, double x, bool decay, double t, double tau, double mu, double sg,
+                                         EndVals& v) {
+  v.e = mass_term(cs, x);
+  v.p = exp(-0.5 * x * x);
+  if (decay) {
+    gaussexp_point(t, tau, mu, sg, &v.f, v.df);
+  } else {
+    v.f = 0.0;
+    v.df[0] = v.df[1] = v.df[2] = 0.0;
+  }
+}
+// Both ends: kPair = false evaluates them in turn; kPair = true has lane 0
+// of the warp evaluate the lower end and lane 1 the upper end at the same
+// time (all 32 lanes call; one FP64 instruction stream serves both ends).
+template <bool kPair>
+__device__ __forceinline__ void both_ends(int cs, double al, double be, bool decay, double lo, double hi, double tau,
+                                          double mu, double sg, EndVals& a, EndVals& b) {
+  if (!kPair) {
+    end_vals(cs, al, decay, lo, tau, mu, sg, a);
+    end_vals(cs, be, decay, hi, tau, mu, sg, b);
+    return;
+  }
+  const bool up = (threadIdx.x & 1) != 0;
+  EndVals v;
+  end_vals(cs, up ? be : al, decay, up ? hi : lo, tau, mu, sg, v);
+  const unsigned all = 0xffffffffu;
+  a.e = __shfl_sync(all, v.e, 0); b.e = __shfl_sync(all, v.e, 1);
+  a.p = __shfl_sync(all, v.p, 0); b.p = __shfl_sync(all, v.p, 1);
+  a.f = __shfl_sync(all, v.f, 0); b.f = __shfl_sync(all, v.f, 1);
+  for (int k = 0; k < 3; ++k) {
+    a.df[k] = __shfl_sync(all, v.df[k], 0);
+    b.df[k] = __shfl_sync(all, v.df[k], 1);
+  }
+}
+
 // Mean of exp(y w) on w in [0, 1]: 1/(1 - e^-y) - 1/y; series near 0.
 __device__ double trunc_exp_mean01(double y) {
   if (fabs(y) < 1e-3) return 0.5 + y * (1.0 / 12.0) - y * y * y * (1.0 / 720.0);
@@ -63,9 +114,125 @@ __device__ double trunc_exp_mean01(double y) {
 
 // ------------------------------------------------------------------- K1
 
-// One thread per active set: the constant block of every node (see the
-// layout in rf_internal.h).  Also resets the event kernel's work counter and
-// finishes sets without events.
+// Constants of pdf node q at the parameter point th into c (the layout in
+// rf_internal.h); returns false if th is outside the node's domain.  With
+// kPair the whole warp calls (GAUSS and GAUSSEXP only), lanes 0 and 1 share
+// the two range ends, and lane 0 writes.
+template <bool kPair>
+__device__ bool node_consts(const PNode& q, const double* th, double* c) {
+  const bool writer = !kPair || (threadIdx.x & 31) == 0;
+  bool bad = false;
+  const double lo = q.lo, hi = q.hi;
+  switch (q.kind) {
+    case GAUSS: {
+      const double mu = param_of(q, 0, th), sg = param_of(q, 1, th);
+      if (!(sg > 0.0)) { bad = true; break; }
+      const double isg = 1.0 / sg;
+      const double al = (lo - mu) * isg, be = (hi - mu) * isg;
+      const int cs = mass_case(al, be);
+      EndVals A, B;
+      both_ends<kPair>(cs, al, be, false, lo, hi, 1.0, mu, sg, A, B);
+      const double I = sg * kSqrt2Pi * mass_of(cs, A.e, B.e);
+      const double dmu = A.p - B.p;
+      const double dsg = I * isg - (be * B.p - al * A.p);
+      if (!(I > 0.0)) bad = true;
+      const double iI = 1.0 / I;
+      if (writer) { c[0] = mu; c[1] = isg; c[2] = iI; c[3] = dmu * iI; c[4] = dsg * iI; }
+      break;
+    }
+    case EXPO: {
+      const double cc = param_of(q, 0, th), L = hi - lo;
+      const double xref = cc > 0.0 ? hi : lo;
+      double Iref;
+      if (cc == 0.0) Iref = L;
+      else if (cc > 0.0) Iref = -expm1(-cc * L) / cc;
+      else Iref = expm1(cc * L) / cc;
+      c[0] = cc; c[1] = xref; c[2] = 1.0 / Iref; c[3] = lo + L * trunc_exp_mean01(cc * L);
+      break;
+    }
+    case GAUSSEXP: {
+      const double tau = param_of(q, 0, th), mu = param_of(q, 1, th), sg = param_of(q, 2, th);
+      if (!(tau > 0.0) || !(sg > 0.0)) { bad = true; break; }
+      const double isg = 1.0 / sg;
+      const double al = (lo - mu) * isg, be = (hi - mu) * isg;
+      const int cs = mass_case(al, be);
+      EndVals A, B;
+      both_ends<kPair>(cs, al, be, true, lo, hi, tau, mu, sg, A, B);
+      const double D = mass_of(cs, A.e, B.e);
+      const double br = D - B.f + A.f;
+      const double I = tau * br;
+      const double pa = A.p * kInvSqrt2Pi, pb = B.p * kInvSqrt2Pi;
+      const double dD[3] = {0.0, -(pb - pa) * isg, -(be * pb - al * pa) * isg};
+      if (!(I > 0.0)) bad = true;
+      const double iI = 1.0 / I;
+      if (writer) {
+        c[0] = mu; c[1] = isg; c[2] = sg / tau; c[3] = 1.0 / tau; c[4] = iI;
+        for (int k = 0; k < 3; ++k) c[5 + k] = ((k == 0 ? br : 0.0) + tau * (dD[k] - B.df[k] + A.df[k])) * iI;
+      }
+      break;
+    }
+    case CHEB: {
+      const int np = q.n_par;
+      double sum = 2.0;
+      for (int k = 1; k <= np; ++k) {
+        const double ck = param_of(q, k - 1, th);
+        const double Tk = (k % 2 == 0) ? 2.0 / (1.0 - (double)k * k) : 0.0;
+        sum += ck * Tk;
+        c[3 + np + k - 1] = ck;
+        c[3 + k - 1] = 0.5 * (hi - lo) * Tk;  // dI/dc_k, divided below
+      }
+      const double I = 0.5 * (hi - lo) * sum;
+      if (!(I > 0.0)) bad = true;
+      c[0] = 2.0 / (hi - lo); c[1] = (hi + lo) / (hi - lo); c[2] = 1.0 / I;
+      for (int k = 0; k < np; ++k) c[3 + k] /= I;
+      break;
+    }
+    case POLY: {
+      const int np = q.n_par;
+      double I = hi - lo, ph = hi, pl = lo;
+      for (int k = 1; k <= np; ++k) {
+        ph *= hi; pl *= lo;
+        const double ak = param_of(q, k - 1, th);
+        const double Pk = (ph - pl) / (k + 1);
+        I += ak * Pk;
+        c[1 + np + k - 1] = ak;
+        c[1 + k - 1] = Pk;
+      }
+      if (!(I > 0.0)) bad = true;
+      c[0] = 1.0 / I;
+      for (int k = 0; k < np; ++k) c[1 + k] /= I;
+      break;
+    }
+    case SUM: {
+      double fs = 0.0;
+      for (int j = 0; j < q.n_par; ++j) {
+        const double f = param_of(q, j, th);
+        c[j] = f;
+        fs += f;
+      }
+      c[q.n_par] = 1.0 - fs;
+      break;
+    }
+    default: break;
+  }
+  return !bad;
+}
+
+// Finishes a set after its constants: domain flag, float-float constants,
+// and the result of a set without events.
+__device__ void finish_param_point(const Program& P, const Pass& pass, int s, bool bad, const double* C) {
+  pass.flags[s] = bad ? kThetaBad : 0;
+  if (!bad && pass.ff_shape != SHAPE_GENERIC && pass.ffc) prepare_ff(P, pass.ff_shape, C, pass.ffc + (size_t)s * kFFConst);
+  if (pass.offsets[s + 1] == pass.offsets[s]) {  // no events: the empty sum
+    double* o = pass.out + (size_t)s * (1 + P.n_free);
+    o[0] = bad ? INFINITY : 0.0;
+    if (pass.want_grad)
+      for (int k = 0; k < P.n_free; ++k) o[1 + k] = 0.0;
+  }
+}
+
+// K1, one thread per active set (many sets: toy fits).  Also resets the
+// event kernel's work counter.
 __global__ void param_point_kernel(const __grid_constant__ Program P, Pass pass) {
   const int a = blockIdx.x * blockDim.x + threadIdx.x;
   if (a == 0) {
@@ -77,103 +244,38 @@ __global__ void param_point_kernel(const __grid_constant__ Program P, Pass pass)
   const double* th = pass.theta + (size_t)s * P.n_free;
   double* C = pass.consts + (size_t)s * P.n_const;
   bool bad = false;
-  for (int n = 0; n < P.n_pdf; ++n) {
+  for (int n = 0; n < P.n_pdf; ++n) bad |= !node_consts<false>(P.node[n], th, C + P.node[n].cofs);
+  finish_param_point(P, pass, s, bad, C);
+}
+
+// K1, one block per active set (few sets: one large fit).  Every FP64 warp
+// instruction occupies the SM sub-partition's FP64 unit for many cycles, so
+// a lone thread's chain of transcendentals is slow; here node n runs on warp
+// n % 4, i.e. on the four sub-partitions at once, a Gaussian or decay node
+// evaluates its two range ends on two lanes at once, and the float-float
+// constants follow once all nodes are done.
+__global__ void __launch_bounds__(128) param_point_block_kernel(const __grid_constant__ Program P, Pass pass) {
+  __shared__ int sbad;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (blockIdx.x == 0 && tid == 0) {
+    *pass.counter = 0;
+    if (pass.slow) *pass.slow = 0ull;
+  }
+  if (tid == 0) sbad = 0;
+  __syncthreads();
+  const int s = pass.sets[blockIdx.x];
+  const double* th = pass.theta + (size_t)s * P.n_free;
+  double* C = pass.consts + (size_t)s * P.n_const;
+  bool bad = false;
+  for (int n = warp; n < P.n_pdf; n += 4) {  // warp-uniform
     const PNode& q = P.node[n];
-    double* c = C + q.cofs;
-    const double lo = q.lo, hi = q.hi;
-    switch (q.kind) {
-      case GAUSS: {
-        const double mu = param_of(q, 0, th), sg = param_of(q, 1, th);
-        if (!(sg > 0.0)) { bad = true; break; }
-        const double al = (lo - mu) / sg, be = (hi - mu) / sg;
-        const double I = sg * kSqrt2Pi * normal_mass(al, be);
-        const double ea = exp(-0.5 * al * al), eb = exp(-0.5 * be * be);
-        const double dmu = ea - eb;
-        const double dsg = I / sg - (be * eb - al * ea);
-        if (!(I > 0.0)) bad = true;
-        c[0] = mu; c[1] = 1.0 / sg; c[2] = 1.0 / I; c[3] = dmu / I; c[4] = dsg / I;
-        break;
-      }
-      case EXPO: {
-        const double cc = param_of(q, 0, th), L = hi - lo;
-        const double xref = cc > 0.0 ? hi : lo;
-        double Iref;
-        if (cc == 0.0) Iref = L;
-        else if (cc > 0.0) Iref = -expm1(-cc * L) / cc;
-        else Iref = expm1(cc * L) / cc;
-        c[0] = cc; c[1] = xref; c[2] = 1.0 / Iref; c[3] = lo + L * trunc_exp_mean01(cc * L);
-        break;
-      }
-      case GAUSSEXP: {
-        const double tau = param_of(q, 0, th), mu = param_of(q, 1, th), sg = param_of(q, 2, th);
-        if (!(tau > 0.0) || !(sg > 0.0)) { bad = true; break; }
-        const double al = (lo - mu) / sg, be = (hi - mu) / sg;
-        double fa, fb, dfa[3], dfb[3];
-        gaussexp_point(lo, tau, mu, sg, &fa, dfa);
-        gaussexp_point(hi, tau, mu, sg, &fb, dfb);
-        const double D = normal_mass(al, be);
-        const double br = D - fb + fa;
-        const double I = tau * br;
-        const double pa = exp(-0.5 * al * al) / kSqrt2Pi, pb = exp(-0.5 * be * be) / kSqrt2Pi;
-        const double dD[3] = {0.0, -(pb - pa) / sg, -(be * pb - al * pa) / sg};
-        if (!(I > 0.0)) bad = true;
-        c[0] = mu; c[1] = 1.0 / sg; c[2] = sg / tau; c[3] = 1.0 / tau; c[4] = 1.0 / I;
-        for (int k = 0; k < 3; ++k) c[5 + k] = ((k == 0 ? br : 0.0) + tau * (dD[k] - dfb[k] + dfa[k])) / I;
-        break;
-      }
-      case CHEB: {
-        const int np = q.n_par;
-        double sum = 2.0;
-        for (int k = 1; k <= np; ++k) {
-          const double ck = param_of(q, k - 1, th);
-          const double Tk = (k % 2 == 0) ? 2.0 / (1.0 - (double)k * k) : 0.0;
-          sum += ck * Tk;
-          c[3 + np + k - 1] = ck;
-          c[3 + k - 1] = 0.5 * (hi - lo) * Tk;  // dI/dc_k, divided below
-        }
-        const double I = 0.5 * (hi - lo) * sum;
-        if (!(I > 0.0)) bad = true;
-        c[0] = 2.0 / (hi - lo); c[1] = (hi + lo) / (hi - lo); c[2] = 1.0 / I;
-        for (int k = 0; k < np; ++k) c[3 + k] /= I;
-        break;
-      }
-      case POLY: {
-        const int np = q.n_par;
-        double I = hi - lo, ph = hi, pl = lo;
-        for (int k = 1; k <= np; ++k) {
-          ph *= hi; pl *= lo;
-          const double ak = param_of(q, k - 1, th);
-          const double Pk = (ph - pl) / (k + 1);
-          I += ak * Pk;
-          c[1 + np + k - 1] = ak;
-          c[1 + k - 1] = Pk;
-        }
-        if (!(I > 0.0)) bad = true;
-        c[0] = 1.0 / I;
-        for (int k = 0; k < np; ++k) c[1 + k] /= I;
-        break;
-      }
-      case SUM: {
-        double fs = 0.0;
-        for (int j = 0; j < q.n_par; ++j) {
-          const double f = param_of(q, j, th);
-          c[j] = f;
-          fs += f;
-        }
-        c[q.n_par] = 1.0 - fs;
-        break;
-      }
-      default: break;
-    }
+    if (q.kind == GAUSS || q.kind == GAUSSEXP) bad |= !node_consts<true>(q, th, C + q.cofs);
+    else if (lane == 0) bad |= !node_consts<false>(q, th, C + q.cofs);
   }
-  pass.flags[s] = bad ? kThetaBad : 0;
-  if (!bad && pass.ff_shape != SHAPE_GENERIC && pass.ffc) prepare_ff(P, pass.ff_shape, C, pass.ffc + (size_t)s * kFFConst);
-  if (pass.offsets[s + 1] == pass.offsets[s]) {  // no events: the empty sum
-    double* o = pass.out + (size_t)s * (1 + P.n_free);
-    o[0] = bad ? INFINITY : 0.0;
-    if (pass.want_grad)
-      for (int k = 0; k < P.n_free; ++k) o[1 + k] = 0.0;
-  }
+  if (lane == 0 && bad) atomicOr(&sbad, 1);
+  __threadfence_block();
+  __syncthreads();
+  if (tid == 0) finish_param_point(P, pass, s, sbad != 0, C);
 }
 
 // ------------------------------------------------------------------- K2
@@ -638,11 +740,15 @@ __global__ void __launch_bounds__(kLanes, ff_min_blocks(kShape)) events_ff(const
   const unsigned lt = (1u << lane) - 1u;
   const int n_units = pass.n_items * kParts;
   int kc_set = -1, c_set = -1;  // sets whose constants the block holds (block-uniform)
+  // One unit of lookahead: thread 0 claims the next unit while the block
+  // works on the current one, so the claim's round trip is hidden.
+  int next_u = tid == 0 ? atomicAdd(pass.counter, 1) : 0;
   while (true) {
-    if (tid == 0) sm.item = atomicAdd(pass.counter, 1);
+    if (tid == 0) sm.item = next_u;
     __syncthreads();
     const int u = sm.item;
     if (u >= n_units) break;
+    if (tid == 0) next_u = atomicAdd(pass.counter, 1);
     const int it = u / kParts, part = u % kParts;
     const int set = pass.items[it].x, chunk = pass.items[it].y;
     const int64_t s_begin = pass.offsets[set], s_end = pass.offsets[set + 1];
@@ -661,12 +767,12 @@ __global__ void __launch_bounds__(kLanes, ff_min_blocks(kShape)) events_ff(const
     const int k0 = part * kPartK;
     // the next event's observables are loaded one iteration ahead
     int64_t e = base + tid + (int64_t)k0 * kLanes;
-    FFIn<kShape> nxt;
-    if (e < s_end) nxt = ff_load<kShape>(cols, col, e);
+    FFRaw<kShape> nxt;
+    if (e < s_end) nxt = ff_load_raw<kShape>(cols, col, e);
 #pragma unroll 1
     for (int k = k0; k < k0 + kPartK; ++k, e += kLanes) {
-      const FFIn<kShape> cur = nxt;
-      if (k + 1 < k0 + kPartK && e + kLanes < s_end) nxt = ff_load<kShape>(cols, col, e + kLanes);
+      const FFIn<kShape> cur = ff_split_in<kShape>(cols, col, nxt);
+      if (k + 1 < k0 + kPartK && e + kLanes < s_end) nxt = ff_load_raw<kShape>(cols, col, e + kLanes);
       int st = 0;
       if (e < s_end) st = ff_event<kShape, kGrad, false>(T, kc, cur, acc);
       const unsigned bs = __ballot_sync(0xffffffffu, st == 1);
@@ -734,7 +840,7 @@ __global__ void __launch_bounds__(kLanes, ff_min_blocks(kShape)) events_ff(const
     }
     if (tid == 0)
       pass.part_info[rec] = (any_fb ? 1 : 0) | ((any_fb ? sm.wbad[0] + sm.wbad[1] + sm.wbad[2] + sm.wbad[3] : 0) << 1);
-    __threadfence();
+    if (tid < 2 * 32) __threadfence();  // the record's writers (tid < NA, Q <= 33)
     __syncthreads();
     if (tid == 0) {
       const int t = atomicAdd(&pass.tickets[leaf], 1);
@@ -780,6 +886,10 @@ __global__ void __launch_bounds__(kLanes, ff_min_blocks(kShape)) events_ff(const
 }  // namespace
 
 void launch_param_point(const Program& P, const Pass& pass, cudaStream_t st) {
+  if (pass.n_active > 0 && pass.n_active <= kBlockK1MaxSets) {
+    param_point_block_kernel<<<pass.n_active, 128, 0, st>>>(P, pass);
+    return;
+  }
   const int threads = 128;
   const int blocks = (pass.n_active + threads - 1) / threads;
   param_point_kernel<<<blocks > 0 ? blocks : 1, threads, 0, st>>>(P, pass);

@@ -38,7 +38,35 @@ __host__ __device__ constexpr int ff_koff(int shape) {
 
 // ------------------------------------------------ parameter-point side (FP64)
 
+// A double observable as a float pair, from its bits (no FP64 instruction):
+// hi = the top 24 significand bits, lo = the remaining 29 rounded to a float.
+// ok = false for values the pair cannot hold (|d| < 2^-74 except 0, >= 2^128).
+__device__ __forceinline__ ff ff_split(double d, bool& ok) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const unsigned hi32 = (unsigned)(b >> 32), lo32 = (unsigned)b;
+  const int ex = (int)((hi32 >> 20) & 0x7ffu);
+  if ((b << 1) == 0ull) return {0.0f, 0.0f};
+  ok = ok && ex >= 949 && ex <= 1150;
+  const int exs = ok ? ex : 1023;
+  const unsigned sign = hi32 & 0x80000000u;
+  const unsigned m23 = ((hi32 & 0xfffffu) << 3) | (lo32 >> 29);
+  const float h = __uint_as_float(sign | ((unsigned)(exs - 896) << 23) | m23);
+  const float scale = __uint_as_float(sign | ((unsigned)(exs - 948) << 23));
+  const float l = __fmul_rn(__uint2float_rn(lo32 & 0x1fffffffu), scale);
+  return {h, l};
+}
+
+// A parameter-point constant as a float pair at o[0], o[1].  The split
+// works on the bits (integer pipe); only values outside the pair's range
+// take the FP64 conversions, whose warp instructions are slow on this GPU.
 __device__ __forceinline__ void put_ff(float* o, double v) {
+  bool ok = true;
+  const ff p = ff_split(v, ok);
+  if (ok) {
+    o[0] = p.hi;
+    o[1] = p.lo;
+    return;
+  }
   const float h = __double2float_rn(v);
   o[0] = h;
   o[1] = __double2float_rn(v - (double)h);
@@ -155,24 +183,6 @@ static __device__ void prepare_ff(const Program& P, int shape, const double* C, 
 
 // ----------------------------------------------------- event side (FF)
 
-// A double observable as a float pair, from its bits (no FP64 instruction):
-// hi = the top 24 significand bits, lo = the remaining 29 rounded to a float.
-// ok = false for values the pair cannot hold (|d| < 2^-74 except 0, >= 2^128).
-__device__ __forceinline__ ff ff_split(double d, bool& ok) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
-  const unsigned hi32 = (unsigned)(b >> 32), lo32 = (unsigned)b;
-  const int ex = (int)((hi32 >> 20) & 0x7ffu);
-  if ((b << 1) == 0ull) return {0.0f, 0.0f};
-  ok = ok && ex >= 949 && ex <= 1150;
-  const int exs = ok ? ex : 1023;
-  const unsigned sign = hi32 & 0x80000000u;
-  const unsigned m23 = ((hi32 & 0xfffffu) << 3) | (lo32 >> 29);
-  const float h = __uint_as_float(sign | ((unsigned)(exs - 896) << 23) | m23);
-  const float scale = __uint_as_float(sign | ((unsigned)(exs - 948) << 23));
-  const float l = __fmul_rn(__uint2float_rn(lo32 & 0x1fffffffu), scale);
-  return {h, l};
-}
-
 __device__ __forceinline__ ff ld_ff(const Columns& cols, int c, int64_t e, bool& ok) {
   if (cols.is_f32[c]) return {__ldg((const float*)cols.ptr[c] + e), 0.0f};
   return ff_split(__ldg((const double*)cols.ptr[c] + e), ok);
@@ -234,16 +244,45 @@ struct FFIn {
   ff x[kShape == SHAPE_PROD3 ? 3 : 1];
   bool ok;
 };
+// The raw bits of an event's observables (a double, or a float in the low
+// word), loaded ahead of use; ff_split_in converts them when needed, so a
+// prefetch does not make the warp wait for its load early.
 template <int kShape>
-__device__ __forceinline__ FFIn<kShape> ff_load(const Columns& cols, const int* col, int64_t e) {
+struct FFRaw {
+  unsigned long long b[kShape == SHAPE_PROD3 ? 3 : 1];
+};
+__device__ __forceinline__ unsigned long long ld_raw(const Columns& cols, int c, int64_t e) {
+  if (cols.is_f32[c]) return (unsigned long long)__float_as_uint(__ldg((const float*)cols.ptr[c] + e));
+  return (unsigned long long)__double_as_longlong(__ldg((const double*)cols.ptr[c] + e));
+}
+__device__ __forceinline__ ff split_raw(const Columns& cols, int c, unsigned long long b, bool& ok) {
+  if (cols.is_f32[c]) return {__uint_as_float((unsigned)b), 0.0f};
+  return ff_split(__longlong_as_double((long long)b), ok);
+}
+template <int kShape>
+__device__ __forceinline__ FFRaw<kShape> ff_load_raw(const Columns& cols, const int* col, int64_t e) {
+  FFRaw<kShape> r;
+  r.b[0] = ld_raw(cols, col[0], e);
+  if constexpr (kShape == SHAPE_PROD3) {
+    r.b[1] = ld_raw(cols, col[1], e);
+    r.b[2] = ld_raw(cols, col[2], e);
+  }
+  return r;
+}
+template <int kShape>
+__device__ __forceinline__ FFIn<kShape> ff_split_in(const Columns& cols, const int* col, const FFRaw<kShape>& r) {
   FFIn<kShape> in;
   in.ok = true;
-  in.x[0] = ld_ff(cols, col[0], e, in.ok);
+  in.x[0] = split_raw(cols, col[0], r.b[0], in.ok);
   if constexpr (kShape == SHAPE_PROD3) {
-    in.x[1] = ld_ff(cols, col[1], e, in.ok);
-    in.x[2] = ld_ff(cols, col[2], e, in.ok);
+    in.x[1] = split_raw(cols, col[1], r.b[1], in.ok);
+    in.x[2] = split_raw(cols, col[2], r.b[2], in.ok);
   }
   return in;
+}
+template <int kShape>
+__device__ __forceinline__ FFIn<kShape> ff_load(const Columns& cols, const int* col, int64_t e) {
+  return ff_split_in<kShape>(cols, col, ff_load_raw<kShape>(cols, col, e));
 }
 
 template <int kShape, bool kGrad, bool kSlow>
