@@ -231,7 +231,39 @@ def transcendental_ceiling(api, model_spec, slow_fraction, n_events, bytes_per_e
     return alu, hbm, basis
 
 
-def roofline(api, model, spec, data, kern_ms, kern_n, n_events, bpe, peaks, peak_kind, slow_frac=None):
+KERNEL_SOURCES = ["nll.cu", "nll_ff.cuh", "ff.cuh", "ff_tables.h", "nll_kernels.cuh", "rf_internal.h"]
+
+
+def kernel_digest():
+    """First 16 hex digits of SHA-256 over the event kernel's sources."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2003_12861_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload):
+    """DRAM bytes per launch of the fused kernel from the committed ncu
+    summary of this workload, or None when there is none or the kernel
+    sources changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", f"{workload}_events_ff.md")
+    if not os.path.exists(path):
+        return None
+    fields = {}
+    with open(path) as fh:
+        for line in fh:
+            if ":" in line and line.split(":")[0] in ("kernel_source_digest", "dram_bytes_per_launch"):
+                k, v = line.split(":", 1)
+                fields[k] = v.strip()
+    if fields.get("kernel_source_digest") != kernel_digest() or "dram_bytes_per_launch" not in fields:
+        return None
+    return int(fields["dram_bytes_per_launch"])
+
+
+def roofline(api, model, spec, data, kern_ms, kern_n, n_events, bpe, peaks, peak_kind, slow_frac=None,
+             workload=None):
     if slow_frac is None:
         slow_frac = api.slow_events(data) / max(1, n_events)
     ff = "kernel=ff_" in model.describe()
@@ -241,7 +273,8 @@ def roofline(api, model, spec, data, kern_ms, kern_n, n_events, bpe, peaks, peak
     achieved = n_events / (avg * 1e-3)
     return {
         "bound": "alu" if alu < hbm else "hbm", "achieved": achieved / 1e9, "peak": ceiling / 1e9,
-        "unit": "Gevent/s", "frac": achieved / ceiling, "traffic": None,
+        "unit": "Gevent/s", "frac": achieved / ceiling,
+        "traffic": profiled_traffic(workload) if workload else None,
         "kernel": model.describe(), "kernel_avg_ms": avg, "kernel_launches": kern_n, "peak_basis": basis,
         "fp64_fma_tflops_measured": api.probe(0) / 1e12,
         "hbm_frac": achieved * bpe / (peaks["hbm_gbs"] * 1e9),
@@ -330,7 +363,7 @@ def run_events(args, api, torch, dist, rank, world, local):
                                    "columns": f"{spec.n_obs} x {'f32' if f32 else 'f64'}",
                                    "free_parameters": P, "l2": "flushed between steps (256 MiB write)",
                                    "tile": {"threads_per_block": tune[0], "blocks_per_sm": tune[1]}},
-        "roofline": roofline(api, model, spec, data, kern_ms, kern_n, n, bpe, peaks, peak_kind),
+        "roofline": roofline(api, model, spec, data, kern_ms, kern_n, n, bpe, peaks, peak_kind, workload=wl),
         "e2e": e2e, "gpu_launches": 2 * args.steps, "clocks": clk.summary(),
         "nll_check": float(out[0].item()),
     }
