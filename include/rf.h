@@ -108,8 +108,11 @@ rf_status rf_model_describe(const rf_model* m, char* buf, int32_t cap);
  * type dtype[c] (dtype NULL = all RF_F64).  Ragged sets (toy datasets):
  * offsets[0..n_sets] with offsets[0] = 0 and offsets[n_sets] = n_events
  * (offsets NULL and n_sets = 1 for one dataset).  cols_on_device = 0: host
- * arrays, copied into library-owned device memory; = 1: device pointers,
- * borrowed (not copied).  Events are kept in the given order. */
+ * arrays, copied into library-owned device memory; = 1: borrowed (not
+ * copied) device, managed or pinned host memory -- pinned host columns are
+ * read in place by the kernels over the host link, so no copy precedes a
+ * pass; other host memory is refused with RF_E_INVALID.  Events are kept in
+ * the given order. */
 rf_status rf_data_upload(const rf_model* m, const void* const* cols, const int32_t* dtype, int64_t n_events,
                          const int64_t* offsets, int32_t n_sets, int32_t cols_on_device, rf_data** out);
 void rf_data_destroy(rf_data* d);
@@ -249,6 +252,24 @@ rf_status rf_mlp_train(rf_mlp* n, const float* d_x, const float* d_t, int32_t ro
 rf_status rf_mlp_save(const rf_mlp* n, const char* path);
 rf_status rf_mlp_load(const char* path, rf_mlp** out);
 
+/* rf_nll_grad with the events coming from HOST memory: host_cols (n_obs
+ * pointers, the dataset's layout and dtypes) are copied into the dataset's
+ * library-owned device columns and evaluated in one call -- the whole
+ * data path of a fit whose events live in host memory.  The work items are
+ * cut into up to 8 segments of >= 512 Ki events (the last two a half and a
+ * quarter of the others);
+ * segment k's copy (on the
+ * library's copy stream) overlaps the event passes over earlier segments
+ * (on four library compute streams that start after the parameter-point
+ * kernel on `stream` and that `stream` waits for), so the call takes about
+ * the copy time plus one segment's pass.
+ * Pinned host memory is required for the overlap (pageable memory works,
+ * serialised).  nll, grad: HOST as in rf_nll_grad.  Returns after the
+ * results are on the host.  RF_E_INVALID for a dataset that borrows its
+ * columns. */
+rf_status rf_nll_grad_stream(const rf_model* m, rf_data* d, const void* const* host_cols, const double* theta,
+                             double* nll, double* grad, void* stream);
+
 /* ------------------------------------------------------------ measurement */
 
 /* Re-copy host columns (same count and dtypes as the dataset was created
@@ -273,13 +294,15 @@ rf_status rf_slow_events(const rf_data* d, int64_t* count);
 /* Throughput probes for the roofline, run on the current device:
  *   kind 0: FP64 fused multiply-add rate            -> *rate in FLOP/s
  *   kind 1: FP32 fused multiply-add rate            -> *rate in FLOP/s
- *   kind 2: per-event transcendental set on register data, with the
- *           library's own implementations: n_exp exponentials, n_erfc
+ *   kind 2: per-event transcendental set on register data, with CUDA's
+ *           FP64 functions (the generic kernel's): n_exp exponentials, n_erfc
  *           complementary error functions, n_log logarithms and n_rcp
  *           reciprocals per event                   -> *rate in events/s
  *   kind 3: streaming read of a device buffer       -> *rate in bytes/s
  *   kind 4: as kind 2 with the library's float-float implementations
  *           (exp, erfcx for erfc, log, reciprocal)  -> *rate in events/s
+ *   kind 5: streaming read of pinned host memory by the SMs, in place over
+ *           the host link                           -> *rate in bytes/s
  * Each probe allocates and frees its own scratch. */
 rf_status rf_probe(int32_t kind, int32_t n_exp, int32_t n_erfc, int32_t n_log, int32_t n_rcp, double* rate);
 
@@ -289,6 +312,40 @@ rf_status rf_probe(int32_t kind, int32_t n_exp, int32_t n_erfc, int32_t n_log, i
  * validating the former against the latter.  A float-float result outside
  * the function's working range is NaN. */
 rf_status rf_math_eval(int32_t fn, const double* d_x, double* d_y, int64_t n, void* stream);
+
+/* ----------------------------------------------------- sharded evaluation */
+
+/* The likelihood is a sum over independent events (Sec. 4), so one dataset
+ * can be split over several GPUs -- one process each -- and the shards' sums
+ * combined in one exchange step (Sec. 5 names parallelisation as the next
+ * step).  Shards are contiguous: rf_shard splits n items (events of one
+ * set, or the sets of a toy batch) into `world` ranges whose boundaries are
+ * multiples of `align` (use 4096, the reduction's chunk, for events; 1 for
+ * sets): rank r gets [*lo, *hi), floor(r C / world) .. floor((r+1) C /
+ * world) in units of align, C = ceil(n / align), the last range ending at n.
+ * Ranges are disjoint and cover [0, n).  Host only; RF_E_INVALID for n < 0,
+ * align < 1, world < 1 or rank outside [0, world). */
+rf_status rf_shard(int64_t n, int64_t align, int32_t rank, int32_t world, int64_t* lo, int64_t* hi);
+
+/* One shard's partial sums: as rf_nll_grad_async, but d_pairs (DEVICE,
+ * n_sets x (1 + n_free) x 2 doubles) receives per set the compensated pairs
+ * (sum, compensation) of sum_i log p_i and of sum_i d log p_i / d theta_k
+ * (not negated; a free parameter's slots merged in slot order), and d_flags
+ * (DEVICE, n_sets int32) the bad-event count (+2^30 if theta is outside a
+ * pdf's domain).  Launches only. */
+rf_status rf_nll_grad_partial(const rf_model* m, const rf_data* d, const double* d_theta, double* d_pairs,
+                              int32_t* d_flags, void* stream);
+
+/* The exchange step: merges the shards' pairs in rank order 0 .. world-1
+ * with exact two-sum merges (so the result is fixed by the shard layout,
+ * independent of which rank's message arrived first) and finishes each set:
+ * out[s x (1+n_free)] = NLL = -(s + c) (+inf when flagged), then the
+ * gradient -(s + c).  pairs: HOST, world x n_sets x (1 + n_free) x 2;
+ * flags: HOST, world x n_sets; flags_out: HOST, n_sets (bad-event counts
+ * summed, +2^30 if any shard flagged the domain).  Host only; returns
+ * RF_E_DOMAIN when some set is flagged. */
+rf_status rf_combine_partials(const double* pairs, const int32_t* flags, int32_t world, int32_t n_sets,
+                              int32_t n_free, double* out, int32_t* flags_out);
 
 /* --------------------------------------------------- allocation-free pass */
 

@@ -56,6 +56,10 @@ SIGNATURES = {
     "rf_slow_events": (C.c_int, [_vp, _i64p]),
     "rf_probe": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, _dp]),
     "rf_nll_grad_noalloc": (C.c_int, [_vp, C.POINTER(_vp), _ip, C.c_int64, _vp, _vp, _vp, _vp]),
+    "rf_nll_grad_stream": (C.c_int, [_vp, _vp, C.POINTER(_vp), _dp, _dp, _dp, _vp]),
+    "rf_shard": (C.c_int, [C.c_int64, C.c_int64, C.c_int32, C.c_int32, _i64p, _i64p]),
+    "rf_nll_grad_partial": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    "rf_combine_partials": (C.c_int, [_dp, _ip, C.c_int32, C.c_int32, C.c_int32, _dp, _ip]),
     "rf_mlp_create": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_uint64, C.POINTER(_vp)]),
     "rf_mlp_destroy": (None, [_vp]),
     "rf_mlp_n_params": (C.c_int64, [_vp]),

@@ -190,6 +190,92 @@ def nll_grad_async(model: Model, data: Data, d_theta, d_out, d_flags, stream=Non
                                        _stream(stream)))
 
 
+def nll_grad_stream(model: Model, data: Data, host_cols, theta, stream=None, allow_domain=False):
+    """rf_nll_grad with the events in host memory (pinned torch tensors or
+    numpy arrays, the dataset's layout and dtypes): copies overlap the pass.
+    Returns (nll, grad) like nll_grad."""
+    th = _theta(model, data, theta)
+    S, P = data.n_sets, model.n_free
+    ptrs = (C.c_void_p * len(host_cols))(*[C.c_void_p(c.data_ptr() if hasattr(c, "data_ptr") else
+                                                        c.ctypes.data) for c in host_cols])
+    nll = np.zeros(S)
+    g = np.zeros(S * max(P, 1))
+    allow = (L.RF_OK, L.RF_E_DOMAIN) if allow_domain else (L.RF_OK,)
+    L.check(L.load().rf_nll_grad_stream(model._h, data._h, ptrs, _dp(th), _dp(nll), _dp(g), _stream(stream)), allow)
+    g = g[: S * P].reshape(S, P)
+    return (nll, g) if S > 1 else (nll[0], g[0])
+
+
+# ------------------------------------------------------- sharded evaluation
+
+def shard(n: int, align: int, rank: int, world: int):
+    """Rank `rank`'s contiguous range [lo, hi) of n items split over `world`
+    ranks at multiples of `align` (4096 for events, 1 for sets)."""
+    lo, hi = C.c_int64(), C.c_int64()
+    L.check(L.load().rf_shard(int(n), int(align), int(rank), int(world), C.byref(lo), C.byref(hi)))
+    return lo.value, hi.value
+
+
+def nll_grad_partial(model: Model, data: Data, d_theta, d_pairs, d_flags, stream=None):
+    """One shard's compensated partial sums: torch tensors (float64 theta,
+    float64 pairs of n_sets x (1 + n_free) x 2, int32 flags); launches only."""
+    L.check(L.load().rf_nll_grad_partial(model._h, data._h, C.c_void_p(d_theta.data_ptr()),
+                                         C.c_void_p(d_pairs.data_ptr()), C.c_void_p(d_flags.data_ptr()),
+                                         _stream(stream)))
+
+
+def combine_partials(pairs, flags):
+    """The exchange step: pairs (world, n_sets, 1 + n_free, 2) and flags
+    (world, n_sets) from every shard, merged in rank order.  Returns (out of
+    n_sets x (1 + n_free): NLL then gradient, flags)."""
+    pairs = np.ascontiguousarray(pairs, dtype=np.float64)
+    flags = np.ascontiguousarray(flags, dtype=np.int32)
+    world, S, Q, two = pairs.shape
+    assert two == 2 and flags.shape == (world, S)
+    out = np.zeros((S, Q))
+    fo = np.zeros(S, dtype=np.int32)
+    L.check(L.load().rf_combine_partials(_dp(pairs), flags.ctypes.data_as(C.POINTER(C.c_int32)), world, S, Q - 1,
+                                         _dp(out), fo.ctypes.data_as(C.POINTER(C.c_int32))),
+            (L.RF_OK, L.RF_E_DOMAIN))
+    return out, fo
+
+
+def gather_partials(pairs, flags, group=None):
+    """all_gather of every rank's (pairs, flags) over torch.distributed, in
+    rank order (the exchange's one collective)."""
+    import torch
+    import torch.distributed as dist
+
+    world = dist.get_world_size(group)
+    dev = torch.device("cuda") if dist.get_backend(group) == "nccl" else torch.device("cpu")
+    p = torch.as_tensor(np.ascontiguousarray(pairs, dtype=np.float64)).to(dev)
+    f = torch.as_tensor(np.ascontiguousarray(flags, dtype=np.int32)).to(dev)
+    ps = [torch.empty_like(p) for _ in range(world)]
+    fs = [torch.empty_like(f) for _ in range(world)]
+    dist.all_gather(ps, p, group=group)
+    dist.all_gather(fs, f, group=group)
+    return np.stack([t.cpu().numpy() for t in ps]), np.stack([t.cpu().numpy() for t in fs])
+
+
+def nll_grad_sharded(model: Model, shard_data: Data, theta, group=None):
+    """NLL and gradient of a dataset split over the ranks of `group`: this
+    rank evaluates its shard (shard_data) on its GPU, the ranks exchange
+    their compensated partial sums once, and every rank merges them in rank
+    order.  theta: n_sets x n_free (the same on every rank).  Returns
+    (nll, grad, flags) of the whole dataset."""
+    import torch
+
+    S, P = shard_data.n_sets, model.n_free
+    th = torch.as_tensor(_theta(model, shard_data, theta).reshape(S, max(P, 1)), dtype=torch.float64).cuda()
+    pairs = torch.zeros((S, 1 + P, 2), dtype=torch.float64, device="cuda")
+    flags = torch.zeros(S, dtype=torch.int32, device="cuda")
+    nll_grad_partial(model, shard_data, th, pairs, flags)
+    torch.cuda.synchronize()
+    allp, allf = gather_partials(pairs.cpu().numpy(), flags.cpu().numpy(), group)
+    out, fo = combine_partials(allp, allf)
+    return out[:, 0], out[:, 1:], fo
+
+
 def nll_chunks(model: Model, data: Data, theta, set_index: int = 0, max_chunks: int = 1 << 16):
     """Per-chunk (sum log p, sum dlog p/dtheta) of one set: array (chunks, 1 + n_free)."""
     th = _theta(model, data, theta)

@@ -34,6 +34,15 @@ int sm_count() {
 }
 
 DevBuf::~DevBuf() { release(); }
+Workspace::~Workspace() {
+  for (cudaEvent_t& e : seg_ev)
+    if (e) cudaEventDestroy(e);
+  for (cudaEvent_t& e : comp_ev)
+    if (e) cudaEventDestroy(e);
+  for (cudaStream_t& c : comp_stream)
+    if (c) cudaStreamDestroy(c);
+  if (copy_stream) cudaStreamDestroy(copy_stream);
+}
 void DevBuf::release() {
   if (p) cudaFree(p);
   p = nullptr;
@@ -165,6 +174,7 @@ Pass make_pass(const rf_model* m, rf_data* d, const Plan& plan, const double* d_
   p.part_m = (float*)w.part_m.p;
   p.part_fb = (double*)w.part_fb.p;
   p.part_info = (int32_t*)w.part_info.p;
+  p.pairs = nullptr;
   return p;
 }
 
@@ -187,6 +197,8 @@ bool launch_pass(const rf_model* m, rf_data* d, const Plan& plan, const double* 
 }
 
 // Host-buffer evaluation of the sets in `plan` (theta/out indexed by set).
+rf_status finish_host(const rf_model* m, rf_data* d, const Plan& plan, double* nll, double* grad, cudaStream_t st);
+
 rf_status eval_host(const rf_model* m, rf_data* d, const Plan& plan, const double* theta, double* nll,
                     double* grad, cudaStream_t st) {
   if (!ensure_workspace(m, d)) return RF_E_OOM;
@@ -197,6 +209,13 @@ rf_status eval_host(const rf_model* m, rf_data* d, const Plan& plan, const doubl
     return RF_E_CUDA;
   if (!launch_pass(m, d, plan, (const double*)w.theta.p, (double*)w.out.p, (int32_t*)w.flags.p, grad != nullptr, st))
     return RF_E_CUDA;
+  return finish_host(m, d, plan, nll, grad, st);
+}
+
+// Downloads a pass's results (issued on st), waits, and fills nll / grad.
+rf_status finish_host(const rf_model* m, rf_data* d, const Plan& plan, double* nll, double* grad, cudaStream_t st) {
+  Workspace& w = d->ws;
+  const int P = m->m.prog.n_free, S = d->n_sets;
   if (!cuda_ok(cudaMemcpyAsync(w.h_out.p, w.out.p, sizeof(double) * S * (1 + P), cudaMemcpyDeviceToHost, st), "result download") ||
       !cuda_ok(cudaMemcpyAsync(w.h_flags.p, w.flags.p, sizeof(int32_t) * S, cudaMemcpyDeviceToHost, st), "flag download") ||
       !cuda_ok(cudaStreamSynchronize(st), "stream sync"))
@@ -291,7 +310,23 @@ rf_status rf_data_upload(const rf_model* m, const void* const* cols, const int32
     if (d->dtype[c] != RF_F64 && d->dtype[c] != RF_F32) { delete d; set_error("rf_data_upload: dtype must be RF_F64 or RF_F32"); return RF_E_INVALID; }
     const size_t bytes = (size_t)n_events * (d->dtype[c] == RF_F32 ? 4 : 8);
     if (cols_on_device) {
-      d->cols[c] = const_cast<void*>(n_events > 0 ? cols[c] : nullptr);
+      d->cols[c] = nullptr;
+      if (n_events > 0) {
+        // Device or managed memory, or pinned host memory that the GPU reads
+        // in place (over the host link; its device address may differ);
+        // anything else would fault in the kernel and is refused here.
+        cudaPointerAttributes a{};
+        if (cudaPointerGetAttributes(&a, cols[c]) != cudaSuccess) cudaGetLastError();
+        if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) {
+          d->cols[c] = const_cast<void*>(cols[c]);
+        } else if (a.type == cudaMemoryTypeHost && a.devicePointer) {
+          d->cols[c] = a.devicePointer;
+        } else {
+          delete d;
+          set_error("rf_data_upload: borrowed columns must be device, managed or pinned host memory");
+          return RF_E_INVALID;
+        }
+      }
     } else {
       if (!d->col_bufs[c].ensure(bytes)) { delete d; return RF_E_OOM; }
       d->cols[c] = d->col_bufs[c].p;
@@ -367,6 +402,22 @@ rf_status rf_nll_grad_async(const rf_model* m, const rf_data* d, const double* d
   rf_data* dd = const_cast<rf_data*>(d);
   if (!ensure_workspace(m, dd)) return RF_E_OOM;
   return launch_pass(m, dd, dd->all_plan, d_theta, d_out, d_flags, true, (cudaStream_t)stream) ? RF_OK : RF_E_CUDA;
+}
+
+rf_status rf_nll_grad_partial(const rf_model* m, const rf_data* d, const double* d_theta, double* d_pairs,
+                              int32_t* d_flags, void* stream) {
+  rf_status s = check_eval_args(m, d, d_theta, d_pairs);
+  if (s != RF_OK) return s;
+  if (!d_flags) { set_error("rf_nll_grad_partial: d_flags is NULL"); return RF_E_INVALID; }
+  rf_data* dd = const_cast<rf_data*>(d);
+  if (!ensure_workspace(m, dd)) return RF_E_OOM;
+  Pass pass = make_pass(m, dd, dd->all_plan, d_theta, (double*)dd->ws.out.p, d_flags, true);
+  pass.pairs = d_pairs;
+  const cudaStream_t st = (cudaStream_t)stream;
+  launch_param_point(m->m.prog, pass, st);
+  launch_events(m->m.prog, m->m.shape, make_columns(dd), pass, m->m.threads_per_block, m->m.blocks_per_sm,
+                sm_count(), st);
+  return cuda_ok(cudaGetLastError(), "kernel launch") ? RF_OK : RF_E_CUDA;
 }
 
 rf_status rf_nll_chunks(const rf_model* m, const rf_data* d, const double* theta, int32_t set, double* out,
@@ -487,4 +538,115 @@ extern "C" rf_status rf_autotune(rf_model* m, rf_data* d, int32_t passes, int32_
   *blocks_per_sm = bb;
   *best_ms = best;
   return RF_OK;
+}
+
+namespace rf {
+
+// Event range [first, last) of work items [i0, i1) of the all-sets plan
+// (items run set by set, chunk by chunk, over back-to-back sets).
+static void item_events(const rf_data* d, int64_t i0, int64_t i1, int64_t* first, int64_t* last) {
+  int64_t it = 0;
+  *first = *last = -1;
+  for (int s = 0; s < d->n_sets && it < i1; ++s) {
+    const int64_t c = d->chunks[s];
+    if (it + c > i0) {
+      const int64_t k0 = std::max<int64_t>(i0 - it, 0), k1 = std::min<int64_t>(i1 - it, c);
+      const int64_t e0 = d->offsets[s] + k0 * kChunk, e1 = std::min(d->offsets[s] + k1 * kChunk, d->offsets[s + 1]);
+      if (*first < 0) *first = e0;
+      *last = e1;
+    }
+    it += c;
+  }
+  if (*first < 0) *first = *last = 0;
+}
+
+}  // namespace rf
+
+extern "C" rf_status rf_nll_grad_stream(const rf_model* m, rf_data* d, const void* const* host_cols,
+                                        const double* theta, double* nll, double* grad, void* stream) {
+  rf_status s = check_eval_args(m, d, theta, nll);
+  if (s != RF_OK) return s;
+  if (!grad || !host_cols || !d->owns_cols) {
+    set_error("rf_nll_grad_stream: bad argument or a dataset with borrowed columns");
+    return RF_E_INVALID;
+  }
+  if (!ensure_workspace(m, d)) return RF_E_OOM;
+  Workspace& w = d->ws;
+  const cudaStream_t st = (cudaStream_t)stream;
+  if (!w.copy_stream) {
+    bool ok = cuda_ok(cudaStreamCreateWithFlags(&w.copy_stream, cudaStreamNonBlocking), "rf_nll_grad_stream");
+    for (cudaStream_t& c : w.comp_stream)
+      ok = ok && cuda_ok(cudaStreamCreateWithFlags(&c, cudaStreamNonBlocking), "rf_nll_grad_stream");
+    for (cudaEvent_t& e : w.seg_ev)
+      ok = ok && cuda_ok(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "rf_nll_grad_stream");
+    for (cudaEvent_t& e : w.comp_ev)
+      ok = ok && cuda_ok(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "rf_nll_grad_stream");
+    if (!ok) return RF_E_CUDA;
+  }
+  if (!w.seg_counters.ensure(sizeof(int32_t) * kMaxSegments)) return RF_E_OOM;
+  const Plan& plan = d->all_plan;
+  const int P = m->m.prog.n_free, S = d->n_sets;
+  // Up to 8 segments of >= 128 chunks (512 Ki events); the last two are a
+  // half and a quarter of the others, so the pass left after the last copy
+  // is short.
+  const int64_t n_items = plan.n_items;
+  const int K = (int)std::max<int64_t>(1, std::min<int64_t>(8, n_items / 128));
+  int64_t bound[kMaxSegments + 1];
+  {
+    int64_t wsum = 0, wc[kMaxSegments + 1];
+    wc[0] = 0;
+    for (int k = 0; k < K; ++k) wc[k + 1] = (wsum += (K >= 3 && k == K - 1) ? 1 : (K >= 3 && k == K - 2) ? 2 : 4);
+    for (int k = 0; k <= K; ++k) bound[k] = n_items * wc[k] / wsum;
+  }
+  // theta, then K1, on `stream`; the copy stream starts after everything
+  // already queued there (a previous pass may still read the columns); the
+  // compute streams start after K1.
+  std::memcpy(w.h_theta.p, theta, sizeof(double) * S * P);
+  if (P > 0 && !cuda_ok(cudaMemcpyAsync(w.theta.p, w.h_theta.p, sizeof(double) * S * P, cudaMemcpyHostToDevice, st),
+                        "theta upload"))
+    return RF_E_CUDA;
+  Pass pass = make_pass(m, d, plan, (const double*)w.theta.p, (double*)w.out.p, (int32_t*)w.flags.p, true);
+  pass.counter = (int32_t*)w.seg_counters.p;
+  pass.n_counters = K;
+  cudaEvent_t ev_start = w.seg_ev[kMaxSegments], ev_k1 = w.seg_ev[kMaxSegments + 1];
+  if (!cuda_ok(cudaEventRecord(ev_start, st), "rf_nll_grad_stream") ||
+      !cuda_ok(cudaStreamWaitEvent(w.copy_stream, ev_start, 0), "rf_nll_grad_stream"))
+    return RF_E_CUDA;
+  launch_param_point(m->m.prog, pass, st);
+  if (!cuda_ok(cudaEventRecord(ev_k1, st), "rf_nll_grad_stream")) return RF_E_CUDA;
+  const int n_comp = std::min(K, kCompStreams);
+  for (int j = 0; j < n_comp; ++j)
+    if (!cuda_ok(cudaStreamWaitEvent(w.comp_stream[j], ev_k1, 0), "rf_nll_grad_stream")) return RF_E_CUDA;
+  const Columns cols = make_columns(d);
+  for (int k = 0; k < K; ++k) {
+    const int64_t i0 = bound[k], i1 = bound[k + 1];
+    int64_t e0, e1;
+    item_events(d, i0, i1, &e0, &e1);
+    if (k == 0) e0 = 0;                 // events before the first item: none, but copy from 0
+    if (k == K - 1) e1 = d->n_events;   // and to the end
+    for (int c = 0; c < d->n_obs; ++c) {
+      const size_t es = d->dtype[c] == RF_F32 ? 4 : 8;
+      if (e1 > e0 &&
+          !cuda_ok(cudaMemcpyAsync((char*)d->cols[c] + e0 * es, (const char*)host_cols[c] + e0 * es, (e1 - e0) * es,
+                                   cudaMemcpyHostToDevice, w.copy_stream),
+                   "rf_nll_grad_stream copy"))
+        return RF_E_CUDA;
+    }
+    const cudaStream_t cs = w.comp_stream[k % n_comp];
+    if (!cuda_ok(cudaEventRecord(w.seg_ev[k], w.copy_stream), "rf_nll_grad_stream") ||
+        !cuda_ok(cudaStreamWaitEvent(cs, w.seg_ev[k], 0), "rf_nll_grad_stream"))
+      return RF_E_CUDA;
+    Pass seg = pass;
+    seg.items = (const int2*)plan.items.p + i0;
+    seg.n_items = (int32_t)(i1 - i0);
+    seg.counter = pass.counter + k;
+    launch_events(m->m.prog, m->m.shape, cols, seg, m->m.threads_per_block, m->m.blocks_per_sm, sm_count(), cs);
+  }
+  // `stream` waits for every compute stream, then downloads the results.
+  for (int j = 0; j < n_comp; ++j)
+    if (!cuda_ok(cudaEventRecord(w.comp_ev[j], w.comp_stream[j]), "rf_nll_grad_stream") ||
+        !cuda_ok(cudaStreamWaitEvent(st, w.comp_ev[j], 0), "rf_nll_grad_stream"))
+      return RF_E_CUDA;
+  if (!cuda_ok(cudaGetLastError(), "kernel launch")) return RF_E_CUDA;
+  return finish_host(m, d, plan, nll, grad, st);
 }

@@ -40,11 +40,28 @@ struct Plan {
 };
 
 // Per-dataset evaluation buffers for the model last used with it.
+// Segments of the streamed host-column pass (rf_nll_grad_stream).
+constexpr int kMaxSegments = 16;
+// Compute streams the segments rotate over, so that one segment's pass
+// starts while the previous one finishes its last work units.
+constexpr int kCompStreams = 4;
+
 struct Workspace {
   bool ready = false;
   int n_const = -1, n_free = -1, Q = -1;
   DevBuf consts, theta, out, flags, tree, tree_bad, tickets, counter, slow, ffc, part_m, part_fb, part_info;
   HostBuf h_theta, h_out, h_flags;
+  // rf_nll_grad_stream: its copy stream, compute streams and events
+  // (created on first use)
+  cudaStream_t copy_stream = nullptr;
+  cudaStream_t comp_stream[kCompStreams] = {};
+  cudaEvent_t seg_ev[kMaxSegments + 2] = {};
+  cudaEvent_t comp_ev[kCompStreams] = {};
+  DevBuf seg_counters;
+  Workspace() = default;
+  Workspace(const Workspace&) = delete;
+  Workspace& operator=(const Workspace&) = delete;
+  ~Workspace();
 };
 
 bool cuda_ok(cudaError_t e, const char* what);

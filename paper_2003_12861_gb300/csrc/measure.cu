@@ -4,6 +4,8 @@
 // read bandwidth).
 #include <cuda_runtime.h>
 
+#include <cstring>
+
 #include <algorithm>
 #include <cmath>
 #include <mutex>
@@ -211,7 +213,7 @@ rf_status rf_data_refill(rf_data* d, const void* const* cols, void* stream) {
 }
 
 rf_status rf_probe(int32_t kind, int32_t n_exp, int32_t n_erfc, int32_t n_log, int32_t n_rcp, double* rate) {
-  if (!rate || kind < 0 || kind > 4 || n_exp < 0 || n_erfc < 0 || n_log < 0 || n_rcp < 0) {
+  if (!rate || kind < 0 || kind > 5 || n_exp < 0 || n_erfc < 0 || n_log < 0 || n_rcp < 0) {
     set_error("rf_probe: bad argument");
     return RF_E_INVALID;
   }
@@ -222,11 +224,21 @@ rf_status rf_probe(int32_t kind, int32_t n_exp, int32_t n_erfc, int32_t n_log, i
   cudaEvent_t e0 = new_event(), e1 = new_event();
   if (!e0 || !e1) return RF_E_CUDA;
   DevBuf buf;
+  HostBuf hbuf;
+  const double2* src = nullptr;
   size_t n2 = 0;
   if (kind == 3) {
     n2 = (size_t)1 << 27;  // 2 GiB of double2
     if (!buf.ensure(n2 * sizeof(double2))) return RF_E_OOM;
     if (!cuda_ok(cudaMemset(buf.p, 0, n2 * sizeof(double2)), "probe memset")) return RF_E_CUDA;
+    src = (const double2*)buf.p;
+  } else if (kind == 5) {
+    n2 = (size_t)1 << 25;  // 512 MiB of pinned host memory, read in place by the SMs
+    if (!hbuf.ensure(n2 * sizeof(double2))) return RF_E_OOM;
+    std::memset(hbuf.p, 0, n2 * sizeof(double2));
+    void* dp = nullptr;
+    if (!cuda_ok(cudaHostGetDevicePointer(&dp, hbuf.p, 0), "probe host pointer")) return RF_E_CUDA;
+    src = (const double2*)dp;
   }
   double best = 0.0;
   for (int rep = 0; rep < 4; ++rep) {
@@ -249,7 +261,7 @@ rf_status rf_probe(int32_t kind, int32_t n_exp, int32_t n_erfc, int32_t n_log, i
       probe_trans_ff<<<blocks, threads>>>((double*)out.p, ev, n_exp, n_erfc, n_log, n_rcp);
       work = (double)ev * threads * blocks;
     } else {
-      probe_read<<<nsm * 4, 512>>>((const double2*)buf.p, n2, (double*)out.p);
+      probe_read<<<nsm * 4, 512>>>(src, n2, (double*)out.p);
       work = (double)n2 * sizeof(double2);
     }
     cudaEventRecord(e1);

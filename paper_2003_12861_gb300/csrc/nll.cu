@@ -223,7 +223,9 @@ __device__ bool node_consts(const PNode& q, const double* th, double* c) {
 __device__ void finish_param_point(const Program& P, const Pass& pass, int s, bool bad, const double* C) {
   pass.flags[s] = bad ? kThetaBad : 0;
   if (!bad && pass.ff_shape != SHAPE_GENERIC && pass.ffc) prepare_ff(P, pass.ff_shape, C, pass.ffc + (size_t)s * kFFConst);
-  if (pass.offsets[s + 1] == pass.offsets[s]) {  // no events: the empty sum
+  if (pass.offsets[s + 1] == pass.offsets[s] && pass.pairs) {  // no events: empty pairs
+    for (int k = 0; k < 2 * (1 + P.n_free); ++k) pass.pairs[(size_t)s * 2 * (1 + P.n_free) + k] = 0.0;
+  } else if (pass.offsets[s + 1] == pass.offsets[s]) {  // no events: the empty sum
     double* o = pass.out + (size_t)s * (1 + P.n_free);
     o[0] = bad ? INFINITY : 0.0;
     if (pass.want_grad)
@@ -236,7 +238,7 @@ __device__ void finish_param_point(const Program& P, const Pass& pass, int s, bo
 __global__ void param_point_kernel(const __grid_constant__ Program P, Pass pass) {
   const int a = blockIdx.x * blockDim.x + threadIdx.x;
   if (a == 0) {
-    *pass.counter = 0;
+    for (int i = 0; i < (pass.n_counters > 1 ? pass.n_counters : 1); ++i) pass.counter[i] = 0;
     if (pass.slow) *pass.slow = 0ull;
   }
   if (a >= pass.n_active) return;
@@ -258,7 +260,7 @@ __global__ void __launch_bounds__(128) param_point_block_kernel(const __grid_con
   __shared__ int sbad;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (blockIdx.x == 0 && tid == 0) {
-    *pass.counter = 0;
+    for (int i = 0; i < (pass.n_counters > 1 ? pass.n_counters : 1); ++i) pass.counter[i] = 0;
     if (pass.slow) *pass.slow = 0ull;
   }
   if (tid == 0) sbad = 0;
@@ -548,7 +550,21 @@ __device__ void climb_tree(const Program& P, const Pass& pass, S& sm, int set, i
   __threadfence();
   __syncthreads();
   const int64_t root = base + lvl;
-  if (tid == 0) {
+  if (tid == 0 && pass.pairs) {
+    pass.flags[set] += __ldcg(pass.tree_bad + root);
+    double* pr = pass.pairs + (size_t)set * 2 * (1 + P.n_free);
+    pr[0] = __ldcg(pass.tree + root * 2 * Q);
+    pr[1] = __ldcg(pass.tree + root * 2 * Q + Q);
+    for (int k = 0; k < P.n_free; ++k) {
+      Pair g{0.0, 0.0};
+      if (pass.want_grad)
+        for (int sl = 0; sl < P.n_slots; ++sl)
+          if (P.slot_free[sl] == k)
+            g = merge(g, {__ldcg(pass.tree + root * 2 * Q + 1 + sl), __ldcg(pass.tree + root * 2 * Q + Q + 1 + sl)});
+      pr[2 + 2 * k] = g.s;
+      pr[3 + 2 * k] = g.c;
+    }
+  } else if (tid == 0) {
     const int flag = pass.flags[set] + __ldcg(pass.tree_bad + root);
     pass.flags[set] = flag;
     double* o = pass.out + (size_t)set * (1 + P.n_free);

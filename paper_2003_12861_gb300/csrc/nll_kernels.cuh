@@ -28,6 +28,7 @@ struct Pass {
   int32_t* tree_bad;        // bad-event count per tree node
   int32_t* tickets;         // arrival counters per tree node (self-resetting)
   int32_t* counter;         // work-item counter of the persistent grid
+  int32_t n_counters;       // counters K1 resets (several launches over item ranges), 0 = 1
   double* out;              // n_sets x (1 + n_free): nll, gradient
   int32_t* flags;           // n_sets: events with pdf <= 0 / not finite (+2^30: theta outside domain)
   unsigned long long* slow; // events that took a slow path in this pass (reset by K1)
@@ -40,6 +41,10 @@ struct Pass {
   float* part_m;            // 32 floats per part: its moment sums (float-float pairs)
   double* part_fb;          // Q doubles per part: its FP64 fallback sums (valid if info bit 0)
   int32_t* part_info;       // per part: bit 0 = fallback sums present, bits 1.. = bad events
+  // Partial mode (null otherwise): per set (1 + n_free) (sum, compensation)
+  // pairs of (sum log p, d/dtheta_k sum log p), not negated, for a later
+  // ordered combine across shards; out is not written.
+  double* pairs;
 };
 
 // Work units per chunk of the float-float kernels: part p of a chunk covers
