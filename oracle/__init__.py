@@ -20,7 +20,8 @@ _SRC = os.path.join(_HERE, "oracle.cpp")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 # The oracle's own numbering of node kinds (independent of the CUDA library's).
-_KIND = {"obs": 0, "param": 1, "gauss": 2, "exp": 3, "gaussexp": 4, "cheb": 5, "poly": 6, "sum": 7, "prod": 8}
+_KIND = {"obs": 0, "param": 1, "gauss": 2, "exp": 3, "gaussexp": 4, "cheb": 5, "poly": 6, "sum": 7, "prod": 8,
+         "poisson": 9, "extend": 10}
 
 
 def build(force: bool = False) -> str:

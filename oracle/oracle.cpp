@@ -26,6 +26,14 @@
 //   POLY     1 + sum_k a_k x^k      (Fig. 1: polynomial background)
 //   SUM      sum_j f_j p_j, last fraction 1 - sum f_j, each p_j normalised
 //   PROD     product of factors over disjoint observables
+//   POISSON  lambda^k exp(-lambda) / k!, k = floor(x) (at most b-1), on an
+//            observable range [a, b] with integer bounds 0 <= a < b: the
+//            count k as a step density of unit-width steps; its integral is
+//            the Poisson mass of k = a .. b-1 (Sec. 4.1 lists the batched
+//            Poisson PDF)
+//   EXTEND   root only: the pdf below it, and the NLL gains the extended
+//            term nu - N log nu for N events and expected count nu (the
+//            Poisson probability of observing N, up to the constant log N!)
 //
 // Also here: a BFGS fitter (Sec. 1: "compute likelihoods and perform fits"),
 // the Philox4x32-10 counter-based generator (Salmon et al., SC'11), Poisson
@@ -55,7 +63,8 @@ constexpr double kSqrt2 = 1.41421356237309504880;
 constexpr double kSqrtPi = 1.77245385090551602730;
 constexpr double kSqrt2Pi = 2.50662827463100050242;
 
-enum Kind { OBS = 0, PARAM = 1, GAUSS = 2, EXPO = 3, GAUSSEXP = 4, CHEB = 5, POLY = 6, SUM = 7, PROD = 8 };
+enum Kind { OBS = 0, PARAM = 1, GAUSS = 2, EXPO = 3, GAUSSEXP = 4, CHEB = 5, POLY = 6, SUM = 7, PROD = 8,
+            POISSON = 9, EXTEND = 10 };
 
 struct Node {
   int kind = 0;
@@ -78,8 +87,8 @@ struct Model {
 
 thread_local std::string g_err;
 
-bool is_leaf_pdf(int k) { return k == GAUSS || k == EXPO || k == GAUSSEXP || k == CHEB || k == POLY; }
-bool is_pdf(int k) { return is_leaf_pdf(k) || k == SUM || k == PROD; }
+bool is_leaf_pdf(int k) { return k == GAUSS || k == EXPO || k == GAUSSEXP || k == CHEB || k == POLY || k == POISSON; }
+bool is_pdf(int k) { return is_leaf_pdf(k) || k == SUM || k == PROD || k == EXTEND; }
 
 // A dual number: value and derivatives in the n free parameters.
 struct Dual {
@@ -229,6 +238,20 @@ bool leaf_norm(const Model& m, const Node& n, const double* theta, double* I, do
       *I = s;
       return true;
     }
+    case POISSON: {
+      // I = sum_{k=a}^{b-1} P(k), dI/dlambda = sum P(k) (k/lambda - 1), summed term by term.
+      const double lam = q[0];
+      if (!(lam > 0)) return false;
+      Neumaier s, ds;
+      for (double k = a; k < b; k += 1.0) {
+        const double pk = std::exp(k * std::log(lam) - lam - std::lgamma(k + 1.0));
+        s.add(pk);
+        ds.add(pk * (k / lam - 1.0));
+      }
+      *I = s.value();
+      dI[0] = ds.value();
+      return true;
+    }
   }
   return false;
 }
@@ -270,6 +293,12 @@ void leaf_shape(const Model& m, const Node& n, const double* theta, double x, do
       double s = 1.0, xk = 1.0;
       for (int k = 1; k <= np; ++k) { xk *= x; s += q[k - 1] * xk; df[k - 1] = xk; }
       *f = s;
+      return;
+    }
+    case POISSON: {
+      const double k = std::min(std::floor(x), b - 1.0);
+      *f = std::exp(k * std::log(q[0]) - q[0] - std::lgamma(k + 1.0));
+      df[0] = *f * (k / q[0] - 1.0);
       return;
     }
   }
@@ -332,6 +361,8 @@ Dual eval_event(const Model& m, const Norms& nm, const double* theta, const doub
         const int fi = param_index(m, n.in[nc + j]);
         if (fi >= 0) r.d[fi] += val[n.in[j]].v - last.v;
       }
+    } else if (n.kind == EXTEND) {
+      r = val[n.in[0]];  // per event the pdf below; the extended term is per dataset
     } else if (n.kind == PROD) {
       // Product rule over the factors.
       r.v = 1.0;
@@ -363,6 +394,10 @@ bool collect_obs(Model& m, int idx, std::string* why) {
     }
     return true;
   }
+  if (n.kind == EXTEND) {
+    n.obs = m.nodes[n.in[0]].obs;
+    return true;
+  }
   if (n.kind == PROD) {
     for (int c : n.in) {
       for (int o : m.nodes[c].obs) {
@@ -385,7 +420,9 @@ bool topo(Model& m, int idx, std::vector<int>& state, std::string* why) {
   if (state[idx] == 1) { *why = "cycle in the graph"; return false; }
   state[idx] = 1;
   const Node& n = m.nodes[idx];
-  if (n.kind == SUM || n.kind == PROD) {
+  if (n.kind == EXTEND) {
+    if (!topo(m, n.in[0], state, why)) return false;
+  } else if (n.kind == SUM || n.kind == PROD) {
     const int nc = n.kind == SUM ? ((int)n.in.size() + 1) / 2 : (int)n.in.size();
     for (int j = 0; j < nc; ++j)
       if (!topo(m, n.in[j], state, why)) return false;
@@ -474,7 +511,9 @@ int64_t poisson(uint64_t seed, uint32_t set, double mu) {
 // (nested) PROD at the root.
 void gen_factors(const Model& m, int idx, std::vector<int>* out) {
   const Node& n = m.nodes[idx];
-  if (n.kind == PROD) {
+  if (n.kind == EXTEND) {
+    gen_factors(m, n.in[0], out);
+  } else if (n.kind == PROD) {
     for (int c : n.in) gen_factors(m, c, out);
   } else {
     out->push_back(idx);
@@ -531,7 +570,7 @@ orc_model* orc_model_new(int n, const int* kinds, const int* n_in, const int* in
       if (c < 0 || c >= n) { ok = false; why = "input index out of range"; }
     if (!ok) break;
     if (is_leaf_pdf(nd.kind)) {
-      int want = nd.kind == GAUSS ? 3 : nd.kind == EXPO ? 2 : nd.kind == GAUSSEXP ? 4 : -1;
+      int want = nd.kind == GAUSS ? 3 : nd.kind == EXPO ? 2 : nd.kind == GAUSSEXP ? 4 : nd.kind == POISSON ? 2 : -1;
       if ((want > 0 && (int)nd.in.size() != want) || nd.in.size() < 1 || nd.in.size() > 8) { ok = false; why = "leaf arity"; }
       else if (m->nodes[nd.in[0]].kind != OBS) { ok = false; why = "leaf input 0 must be an observable"; }
       else
@@ -547,7 +586,21 @@ orc_model* orc_model_new(int n, const int* kinds, const int* n_in, const int* in
     } else if (nd.kind == PROD) {
       if (nd.in.empty()) { ok = false; why = "PROD arity"; }
       for (int c : nd.in)
-        if (!is_pdf(m->nodes[c].kind)) { ok = false; why = "PROD inputs"; }
+        if (!is_pdf(m->nodes[c].kind) || m->nodes[c].kind == EXTEND) { ok = false; why = "PROD inputs"; }
+    } else if (nd.kind == EXTEND) {
+      if (nd.in.size() != 2 || !is_pdf(m->nodes[nd.in[0]].kind) || m->nodes[nd.in[0]].kind == EXTEND ||
+          m->nodes[nd.in[1]].kind != PARAM) { ok = false; why = "EXTEND inputs: [pdf, expected count]"; }
+      else if (i != root) { ok = false; why = "EXTEND must be the root"; }
+    }
+    if (ok && nd.kind == POISSON) {
+      const Node& ob = m->nodes[nd.in[0]];
+      if (!(ob.lo >= 0) || ob.lo != std::floor(ob.lo) || ob.hi != std::floor(ob.hi) || !(ob.hi > ob.lo) ||
+          ob.hi - ob.lo > 100000) { ok = false; why = "POISSON range must have integer bounds 0 <= a < b <= a + 1e5"; }
+    }
+    if (ok && nd.kind == SUM) {
+      const int nc = ((int)nd.in.size() + 1) / 2;
+      for (int j = 0; j < nc; ++j)
+        if (m->nodes[nd.in[j]].kind == EXTEND) { ok = false; why = "EXTEND must be the root"; }
     }
   }
   if (ok) {
@@ -642,8 +695,26 @@ int orc_nll(const orc_model* h, const double* theta, const double* const* cols, 
       sga[k].add(std::fabs(g));
     }
   }
-  *nll = bad ? kInf : -s0.value();
-  if (abs_logp) *abs_logp = sa.value();
+  // Extended likelihood: + nu - N log nu (the Poisson probability of N
+  // events given nu, without the constant log N!), d/dnu = 1 - N/nu.
+  double ext = 0.0, ext_abs = 0.0;
+  const Node& top = m.nodes[m.root];
+  if (top.kind == EXTEND) {
+    const double nu = param_value(m, top.in[1], theta);
+    if (!(nu > 0)) {
+      *nll = kInf;
+      return -2;
+    }
+    ext = nu - (double)N * std::log(nu);
+    ext_abs = nu + std::fabs((double)N * std::log(nu));
+    const int fi = param_index(m, top.in[1]);
+    if (fi >= 0) {
+      sg[fi].add(-(1.0 - (double)N / nu));
+      sga[fi].add(1.0 + (double)N / nu);
+    }
+  }
+  *nll = bad ? kInf : ext - s0.value();
+  if (abs_logp) *abs_logp = sa.value() + ext_abs;
   for (int k = 0; k < P; ++k) {
     if (grad) grad[k] = -sg[k].value();
     if (abs_grad) abs_grad[k] = sga[k].value();

@@ -21,6 +21,8 @@ cheb       [obs, c1, ..., cn]             (1 + sum c_k T_k, implicit c0 = 1)
 poly       [obs, a1, ..., an]             (1 + sum a_k x^k, implicit a0 = 1)
 sum        [pdf_1..pdf_n, f_1..f_{n-1}]   (last fraction = 1 - sum f)
 prod       [pdf_1..pdf_n]                 (disjoint observables)
+poisson    [obs, lambda]                  (count k = floor(x); integer range)
+extend     [pdf, nu]                      (root only: extended likelihood)
 =========  ==========================================================
 
 The five workloads (sizes, true values and ranges) are the ones the
@@ -35,7 +37,7 @@ from typing import List, Sequence
 
 import numpy as np
 
-KINDS = ("obs", "param", "gauss", "exp", "gaussexp", "cheb", "poly", "sum", "prod")
+KINDS = ("obs", "param", "gauss", "exp", "gaussexp", "cheb", "poly", "sum", "prod", "poisson", "extend")
 
 
 @dataclass(frozen=True)
