@@ -64,7 +64,16 @@ typedef enum {
   RF_SUM = 7,      /* in = [pdf_1..pdf_n, f_1..f_{n-1}], 2 <= n <= 4: sum f_j pdf_j
                       with f_n = 1 - sum f_j; each pdf_j normalised on its own;
                       all components over the same observables                        */
-  RF_PROD = 8      /* in = [pdf_1..pdf_n], n <= 8, over disjoint observables          */
+  RF_PROD = 8,     /* in = [pdf_1..pdf_n], n <= 8, over disjoint observables          */
+  RF_POISSON = 9,  /* in = [obs, lambda]  lambda^k exp(-lambda) / k!, k = floor(x)
+                      (at most hi-1): the count as a step density of unit steps on
+                      an observable range with integer bounds 0 <= lo < hi <=
+                      lo + 1e5; normalised by the Poisson mass of k = lo..hi-1
+                      (Sec. 4.1 lists the batched Poisson PDF)                        */
+  RF_EXTEND = 10   /* root only, in = [pdf, nu]: extended likelihood, the NLL of a
+                      dataset of N events gains nu - N log nu (the Poisson
+                      probability of N given the expected count nu, without the
+                      constant log N!); nu <= 0 is outside the domain              */
 } rf_kind;
 
 typedef enum { RF_F64 = 0, RF_F32 = 1 } rf_dtype;
@@ -333,6 +342,8 @@ rf_status rf_shard(int64_t n, int64_t align, int32_t rank, int32_t world, int64_
  * (not negated; a free parameter's slots merged in slot order), and d_flags
  * (DEVICE, n_sets int32) the bad-event count (+2^30 if theta is outside a
  * pdf's domain).  Launches only. */
+/* (Not for extended models, whose term needs the whole dataset's size:
+ * RF_E_INVALID.) */
 rf_status rf_nll_grad_partial(const rf_model* m, const rf_data* d, const double* d_theta, double* d_pairs,
                               int32_t* d_flags, void* stream);
 

@@ -13,7 +13,8 @@ LIB_PATH = os.path.join(HERE, "librfgpu.so")
 RF_OK, RF_E_INVALID, RF_E_OOM, RF_E_CUDA, RF_E_DOMAIN, RF_E_NOT_CONVERGED, RF_E_TIMEOUT = range(7)
 STATUS_NAMES = {0: "RF_OK", 1: "RF_E_INVALID", 2: "RF_E_OOM", 3: "RF_E_CUDA", 4: "RF_E_DOMAIN",
                 5: "RF_E_NOT_CONVERGED", 6: "RF_E_TIMEOUT"}
-KIND = {"obs": 0, "param": 1, "gauss": 2, "exp": 3, "gaussexp": 4, "cheb": 5, "poly": 6, "sum": 7, "prod": 8}
+KIND = {"obs": 0, "param": 1, "gauss": 2, "exp": 3, "gaussexp": 4, "cheb": 5, "poly": 6, "sum": 7, "prod": 8,
+        "poisson": 9, "extend": 10}
 RF_F64, RF_F32 = 0, 1
 
 

@@ -409,6 +409,10 @@ rf_status rf_nll_grad_partial(const rf_model* m, const rf_data* d, const double*
   rf_status s = check_eval_args(m, d, d_theta, d_pairs);
   if (s != RF_OK) return s;
   if (!d_flags) { set_error("rf_nll_grad_partial: d_flags is NULL"); return RF_E_INVALID; }
+  if (m->m.extended) {
+    set_error("rf_nll_grad_partial: an extended model's term depends on the whole dataset's size");
+    return RF_E_INVALID;
+  }
   rf_data* dd = const_cast<rf_data*>(d);
   if (!ensure_workspace(m, dd)) return RF_E_OOM;
   Pass pass = make_pass(m, dd, dd->all_plan, d_theta, (double*)dd->ws.out.p, d_flags, true);

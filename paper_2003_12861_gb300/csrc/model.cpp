@@ -21,12 +21,13 @@ namespace rf {
 
 namespace {
 
-bool is_leaf(int k) { return k == GAUSS || k == EXPO || k == GAUSSEXP || k == CHEB || k == POLY; }
-bool is_pdf(int k) { return is_leaf(k) || k == SUM || k == PROD; }
+bool is_leaf(int k) { return k == GAUSS || k == EXPO || k == GAUSSEXP || k == CHEB || k == POLY || k == POISSON; }
+bool is_pdf(int k) { return is_leaf(k) || k == SUM || k == PROD; }  // EXTEND: only as the root
 
 std::string kind_name(int k) {
-  static const char* names[] = {"OBS", "PARAM", "GAUSS", "EXP", "GAUSSEXP", "CHEB", "POLY", "SUM", "PROD"};
-  return (k >= 0 && k <= 8) ? names[k] : "?";
+  static const char* names[] = {"OBS", "PARAM", "GAUSS", "EXP", "GAUSSEXP", "CHEB", "POLY", "SUM", "PROD",
+                                "POISSON", "EXTEND"};
+  return (k >= 0 && k <= 10) ? names[k] : "?";
 }
 
 }  // namespace
@@ -46,7 +47,7 @@ rf_status compile_model(const rf_node* nodes, int n, int root, Model* m) {
   int n_obs = 0, n_free = 0;
   for (int i = 0; i < n; ++i) {
     const rf_node& nd = nodes[i];
-    if (nd.kind < 0 || nd.kind > 8) return fail("unknown kind", i);
+    if (nd.kind < 0 || nd.kind > 10) return fail("unknown kind", i);
     if (nd.n_in < 0 || nd.n_in > 8) return fail("n_in must be 0..8", i);
     for (int j = 0; j < nd.n_in; ++j)
       if (nd.in[j] < 0 || nd.in[j] >= n || nd.in[j] == i) return fail("input index out of range", i);
@@ -66,12 +67,22 @@ rf_status compile_model(const rf_node* nodes, int n, int root, Model* m) {
         m->hi.push_back(nd.hi);
       }
     } else if (is_leaf(nd.kind)) {
-      const int want = nd.kind == GAUSS ? 3 : nd.kind == EXPO ? 2 : nd.kind == GAUSSEXP ? 4 : -1;
+      const int want = nd.kind == GAUSS ? 3 : nd.kind == EXPO || nd.kind == POISSON ? 2 : nd.kind == GAUSSEXP ? 4 : -1;
       if (want > 0 && nd.n_in != want) return fail("wrong number of inputs for this pdf", i);
       if (want < 0 && (nd.n_in < 1 || nd.n_in > 1 + kMaxPar)) return fail("CHEB/POLY take an observable and 0..7 coefficients", i);
       if (nodes[nd.in[0]].kind != OBS) return fail("input 0 of a pdf must be an OBS node", i);
       for (int j = 1; j < nd.n_in; ++j)
         if (nodes[nd.in[j]].kind != PARAM) return fail("pdf parameters must be PARAM nodes", i);
+      if (nd.kind == POISSON) {
+        const rf_node& ob = nodes[nd.in[0]];
+        if (!(ob.lo >= 0.0) || ob.lo != std::floor(ob.lo) || ob.hi != std::floor(ob.hi) ||
+            ob.hi - ob.lo > kMaxPoissonRange)
+          return fail("a POISSON observable needs integer bounds 0 <= lo < hi <= lo + 100000", i);
+      }
+    } else if (nd.kind == EXTEND) {
+      if (i != root) return fail("EXTEND must be the root", i);
+      if (nd.n_in != 2 || !is_pdf(nodes[nd.in[0]].kind) || nodes[nd.in[1]].kind != PARAM)
+        return fail("EXTEND takes [pdf, expected count]", i);
     } else if (nd.kind == SUM) {
       if (nd.n_in < 3 || nd.n_in % 2 == 0) return fail("SUM takes n pdfs and n-1 fractions, 2 <= n <= 4", i);
       const int nc = (nd.n_in + 1) / 2;
@@ -88,6 +99,15 @@ rf_status compile_model(const rf_node* nodes, int n, int root, Model* m) {
   }
   if (n_obs > kMaxObs) return fail("more than 8 observables", -1);
   if (n_free > kMaxFree) return fail("more than 16 free parameters", -1);
+  // An EXTEND root: the program is its pdf; the extended term is per set.
+  int ext = 0, ext_free = -1;
+  double ext_fixed = 0.0;
+  if (nodes[root].kind == EXTEND) {
+    ext = 1;
+    ext_free = free_index[nodes[root].in[1]];
+    ext_fixed = nodes[nodes[root].in[1]].value;
+    root = nodes[root].in[0];
+  }
   if (!is_pdf(nodes[root].kind)) return fail("root is not a pdf", root);
 
   // Dependency order of the PDFs under the root (children first); cycle check.
@@ -135,6 +155,9 @@ rf_status compile_model(const rf_node* nodes, int n, int root, Model* m) {
   P.n_pdf = (int)order.size();
   P.n_obs = n_obs;
   P.n_free = n_free;
+  P.ext = ext;
+  P.ext_free = ext_free;
+  P.ext_fixed = ext_fixed;
   std::vector<int> prog_index(n, -1);
   int cofs = 0, slot = 0;
   for (int pi = 0; pi < P.n_pdf; ++pi) {
@@ -199,6 +222,7 @@ rf_status compile_model(const rf_node* nodes, int n, int root, Model* m) {
     return s;
   };
   m->signature = sig(root);
+  m->extended = ext != 0;
   m->shape = SHAPE_GENERIC;
   if (m->signature == "SUM(GAUSS,POLY1)") m->shape = SHAPE_SUM_GAUSS_POLY1;
   if (m->signature == "SUM(GAUSSEXP,CHEB2)") m->shape = SHAPE_SUM_GAUSSEXP_CHEB2;

@@ -187,6 +187,34 @@ __device__ bool node_consts(const PNode& q, const double* th, double* c) {
       for (int k = 0; k < np; ++k) c[3 + k] /= I;
       break;
     }
+    case POISSON: {
+      // I = sum_{k=lo}^{hi-1} pmf(k): from the mode outward by the ratio
+      // recursion pmf(k+1) = pmf(k) lambda/(k+1), stopping once the terms
+      // are below 1e-18 of the sum (the tails decrease geometrically).
+      // dI/dlambda telescopes to pmf(lo-1) - pmf(hi-1).
+      const double lam = param_of(q, 0, th);
+      if (!(lam > 0.0)) { bad = true; break; }
+      const double ll = log(lam);
+      const double km = fmin(fmax(floor(lam), lo), hi - 1.0);
+      const double pm = exp(km * ll - lam - lgamma(km + 1.0));
+      double I = pm, p = pm;
+      for (double k = km + 1.0; k < hi; k += 1.0) {
+        p *= lam / k;
+        I += p;
+        if (p < 1e-18 * I) break;
+      }
+      p = pm;
+      for (double k = km; k > lo; k -= 1.0) {
+        p *= k / lam;
+        I += p;
+        if (p < 1e-18 * I) break;
+      }
+      const double pb = exp((hi - 1.0) * ll - lam - lgamma(hi));
+      const double pa = lo > 0.0 ? exp((lo - 1.0) * ll - lam - lgamma(lo)) : 0.0;
+      if (!(I > 0.0)) bad = true;
+      if (writer) { c[0] = lam; c[1] = ll; c[2] = 1.0 / lam; c[3] = 1.0 / I; c[4] = (pa - pb) / I; }
+      break;
+    }
     case POLY: {
       const int np = q.n_par;
       double I = hi - lo, ph = hi, pl = lo;
@@ -218,18 +246,34 @@ __device__ bool node_consts(const PNode& q, const double* th, double* c) {
   return !bad;
 }
 
+// Extended likelihood: nu - N log nu for a set of N events and its
+// derivative 1 - N/nu (the Poisson probability of N given nu, without the
+// constant log N!).  nu <= 0 is flagged by the parameter-point kernel.
+__device__ __forceinline__ void extended_term(const Program& P, const Pass& pass, int set, double N, double* t,
+                                              double* dt) {
+  const double nu = P.ext_free >= 0 ? pass.theta[(size_t)set * P.n_free + P.ext_free] : P.ext_fixed;
+  *t = nu - (N > 0.0 ? N * log(nu) : 0.0);
+  *dt = 1.0 - N / nu;
+}
+
 // Finishes a set after its constants: domain flag, float-float constants,
 // and the result of a set without events.
 __device__ void finish_param_point(const Program& P, const Pass& pass, int s, bool bad, const double* C) {
+  if (P.ext) {
+    const double nu = P.ext_free >= 0 ? pass.theta[(size_t)s * P.n_free + P.ext_free] : P.ext_fixed;
+    if (!(nu > 0.0)) bad = true;
+  }
   pass.flags[s] = bad ? kThetaBad : 0;
   if (!bad && pass.ff_shape != SHAPE_GENERIC && pass.ffc) prepare_ff(P, pass.ff_shape, C, pass.ffc + (size_t)s * kFFConst);
   if (pass.offsets[s + 1] == pass.offsets[s] && pass.pairs) {  // no events: empty pairs
     for (int k = 0; k < 2 * (1 + P.n_free); ++k) pass.pairs[(size_t)s * 2 * (1 + P.n_free) + k] = 0.0;
-  } else if (pass.offsets[s + 1] == pass.offsets[s]) {  // no events: the empty sum
+  } else if (pass.offsets[s + 1] == pass.offsets[s]) {  // no events: the empty sum (+ nu if extended)
     double* o = pass.out + (size_t)s * (1 + P.n_free);
-    o[0] = bad ? INFINITY : 0.0;
+    double ext = 0.0, dext = 0.0;
+    if (P.ext && !bad) extended_term(P, pass, s, 0.0, &ext, &dext);
+    o[0] = bad ? INFINITY : ext;
     if (pass.want_grad)
-      for (int k = 0; k < P.n_free; ++k) o[1 + k] = 0.0;
+      for (int k = 0; k < P.n_free; ++k) o[1 + k] = k == P.ext_free ? dext : 0.0;
   }
 }
 
@@ -352,6 +396,11 @@ __device__ bool eval_generic(const Program& P, const double* __restrict__ C, con
         v[n] = (1.0 + sh) * c[0];
         break;
       }
+      case POISSON: {
+        const double k = fmin(floor(x[q.col]), q.hi - 1.0);
+        v[n] = exp(k * c[1] - c[0] - lgamma(k + 1.0)) * c[3];
+        break;
+      }
       case SUM: {
         double r = 0.0;
         for (int j = 0; j < q.n_child; ++j) r += c[j] * v[q.child[j]];
@@ -395,6 +444,11 @@ __device__ bool eval_generic(const Program& P, const double* __restrict__ C, con
       }
       case EXPO: {
         g[s0] += a * v[n] * (x[q.col] - c[3]);
+        break;
+      }
+      case POISSON: {
+        const double k = fmin(floor(x[q.col]), q.hi - 1.0);
+        g[s0] += a * v[n] * (k * c[2] - 1.0 - c[4]);
         break;
       }
       case GAUSSEXP: {
@@ -569,14 +623,16 @@ __device__ void climb_tree(const Program& P, const Pass& pass, S& sm, int set, i
     pass.flags[set] = flag;
     double* o = pass.out + (size_t)set * (1 + P.n_free);
     const double s0 = __ldcg(pass.tree + root * 2 * Q) + __ldcg(pass.tree + root * 2 * Q + Q);
-    o[0] = flag ? INFINITY : -s0;
+    double ext = 0.0, dext = 0.0;
+    if (P.ext) extended_term(P, pass, set, (double)n_events, &ext, &dext);
+    o[0] = flag ? INFINITY : ext - s0;
     if (pass.want_grad) {
       for (int k = 0; k < P.n_free; ++k) {
         double gk = 0.0;
         for (int sl = 0; sl < P.n_slots; ++sl)
           if (P.slot_free[sl] == k)
             gk += __ldcg(pass.tree + root * 2 * Q + 1 + sl) + __ldcg(pass.tree + root * 2 * Q + Q + 1 + sl);
-        o[1 + k] = -gk;
+        o[1 + k] = (k == P.ext_free ? dext : 0.0) - gk;
       }
     }
   }

@@ -25,7 +25,11 @@ constexpr int kLanes = 128;
 constexpr int kPerLane = kChunk / kLanes;  // 32
 constexpr int kRadix = 32;
 
-enum Kind : int8_t { OBS = 0, PARAM = 1, GAUSS = 2, EXPO = 3, GAUSSEXP = 4, CHEB = 5, POLY = 6, SUM = 7, PROD = 8 };
+enum Kind : int8_t {
+  OBS = 0, PARAM = 1, GAUSS = 2, EXPO = 3, GAUSSEXP = 4, CHEB = 5, POLY = 6, SUM = 7, PROD = 8, POISSON = 9, EXTEND = 10
+};
+// Largest observable range (integers) of a POISSON leaf.
+constexpr int kMaxPoissonRange = 100000;
 
 // One PDF node of the compiled program, in dependency order (children first).
 struct PNode {
@@ -50,6 +54,10 @@ struct Program {
   int32_t n_const;           // doubles per set in the constant block
   int32_t has_slow;          // 1 if some node has a rare slow path (GAUSSEXP)
   int8_t slot_free[kMaxSlots];  // slot -> free parameter (-1: fixed)
+  // Extended likelihood (EXTEND root): the NLL gains nu - N log nu per set.
+  int32_t ext;               // 1 if extended
+  int32_t ext_free;          // nu's free index, or -1 (fixed: ext_fixed)
+  double ext_fixed;
   PNode node[kMaxPdf];
 };
 
@@ -62,6 +70,7 @@ struct Program {
 //   POLY(n)  [1/I, dlogI/da_1..n, a_1..n]
 //   SUM(n)   [f_1..f_{n-1}, 1 - sum f]
 //   PROD     []
+//   POISSON  [lambda, log lambda, 1/lambda, 1/I, dlogI/dlambda]   v = pmf(floor x) / I
 inline int const_size(int kind, int n_par) {
   switch (kind) {
     case GAUSS: return 5;
@@ -70,6 +79,7 @@ inline int const_size(int kind, int n_par) {
     case CHEB: return 3 + 2 * n_par;
     case POLY: return 1 + 2 * n_par;
     case SUM: return n_par + 1;
+    case POISSON: return 5;
     default: return 0;
   }
 }
@@ -94,6 +104,7 @@ struct Model {
   std::vector<double> obs_lo, obs_hi;
   std::vector<int> gen_factors;      // program indices of the generation factors
   std::string signature;
+  bool extended = false;
   int threads_per_block = 0, blocks_per_sm = 0;
 };
 

@@ -94,6 +94,11 @@ __device__ void node_values(const Program& P, const double* __restrict__ C, cons
         v[n] = (1.0 + sh) * c[0];
         break;
       }
+      case POISSON: {
+        const double k = fmin(floor(x[q.col]), q.hi - 1.0);
+        v[n] = exp(k * c[1] - c[0] - lgamma(k + 1.0)) * c[3];
+        break;
+      }
       case SUM: {
         double r = 0.0;
         for (int j = 0; j < q.n_child; ++j) r += c[j] * v[q.child[j]];
