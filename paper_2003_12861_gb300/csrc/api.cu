@@ -505,7 +505,7 @@ extern "C" rf_status rf_autotune(rf_model* m, rf_data* d, int32_t passes, int32_
   cudaEvent_t e0, e1;
   if (!cuda_ok(cudaEventCreate(&e0), "autotune") || !cuda_ok(cudaEventCreate(&e1), "autotune")) return RF_E_CUDA;
   static const int kThreads[] = {128, 256, 512};
-  static const int kBps[] = {1, 2, 3, 4, 6, 8, 12, 16};
+  static const int kBps[] = {1, 2, 3, 4, 5, 6, 7, 8, 12, 16};
   const int save_t = m->m.threads_per_block, save_b = m->m.blocks_per_sm;
   double best = 1e300;
   int bt = 0, bb = 0;
