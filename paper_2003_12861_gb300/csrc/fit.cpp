@@ -15,9 +15,14 @@
 // device pass (the batched toy fit), so a round costs one pass whatever the
 // number of sets.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
+#include <condition_variable>
 #include <cstring>
+#include <functional>
 #include <limits>
+#include <mutex>
+#include <thread>
 #include <vector>
 
 #include "api_internal.h"
@@ -50,7 +55,102 @@ struct Coords {
   }
   // d theta / d x
   double jac(int k, double xk) const { return bounded[k] ? (hi[k] - lo[k]) * 0.5 * std::cos(xk) : 1.0; }
+  // theta and d theta / d x at x, one sine and cosine per bounded parameter
+  void to_theta_jac(const double* x, double* th, double* jc) const {
+    for (int k = 0; k < P; ++k) {
+      if (!bounded[k]) {
+        th[k] = x[k];
+        jc[k] = 1.0;
+        continue;
+      }
+      const double sn = std::sin(x[k]), cs = std::cos(x[k]);
+      th[k] = lo[k] + (hi[k] - lo[k]) * (sn + 1.0) * 0.5;
+      jc[k] = (hi[k] - lo[k]) * 0.5 * cs;
+    }
+  }
 };
+
+// A fixed set of worker threads for the per-set host work of a round (the
+// sets' state machines are independent, so the split does not change any
+// result).  run(n, f) calls f(i) for i in [0, n) on the caller and the
+// workers, chunk by chunk, and returns when all are done.
+class Pool {
+ public:
+  explicit Pool(int threads) {
+    for (int t = 1; t < threads; ++t) workers_.emplace_back([this] { loop(); });
+  }
+  ~Pool() {
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      stop_ = true;
+    }
+    cv_.notify_all();
+    for (std::thread& t : workers_) t.join();
+  }
+  int size() const { return 1 + (int)workers_.size(); }
+  void run(int64_t n, const std::function<void(int64_t)>& f) {
+    if (workers_.empty() || n < 1024) {
+      for (int64_t i = 0; i < n; ++i) f(i);
+      return;
+    }
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      job_ = &f;
+      n_ = n;
+      next_.store(0);
+      busy_ = (int)workers_.size();
+      ++gen_;
+    }
+    cv_.notify_all();
+    work(f, n);
+    std::unique_lock<std::mutex> lk(mu_);
+    done_cv_.wait(lk, [this] { return busy_ == 0; });
+    job_ = nullptr;
+  }
+
+ private:
+  static constexpr int64_t kChunk = 64;
+  void work(const std::function<void(int64_t)>& f, int64_t n) {
+    while (true) {
+      const int64_t i0 = next_.fetch_add(kChunk);
+      if (i0 >= n) return;
+      const int64_t i1 = std::min(n, i0 + kChunk);
+      for (int64_t i = i0; i < i1; ++i) f(i);
+    }
+  }
+  void loop() {
+    uint64_t seen = 0;
+    while (true) {
+      const std::function<void(int64_t)>* f;
+      int64_t n;
+      {
+        std::unique_lock<std::mutex> lk(mu_);
+        cv_.wait(lk, [&] { return stop_ || gen_ != seen; });
+        if (stop_) return;
+        seen = gen_;
+        f = job_;
+        n = n_;
+      }
+      work(*f, n);
+      std::lock_guard<std::mutex> lk(mu_);
+      if (--busy_ == 0) done_cv_.notify_one();
+    }
+  }
+  std::vector<std::thread> workers_;
+  std::mutex mu_;
+  std::condition_variable cv_, done_cv_;
+  const std::function<void(int64_t)>* job_ = nullptr;
+  int64_t n_ = 0;
+  std::atomic<int64_t> next_{0};
+  int busy_ = 0;
+  uint64_t gen_ = 0;
+  bool stop_ = false;
+};
+
+int pool_threads() {
+  const unsigned hc = std::thread::hardware_concurrency();
+  return (int)std::max(1u, std::min(8u, hc / 2));
+}
 
 double dot(const double* a, const double* b, int n) {
   double s = 0.0;
@@ -135,31 +235,31 @@ struct SetFit {
   }
 
   // Accept the step to alpha with value fa and gradient ga.
-  void accept(double a, double fa, const std::vector<double>& ga, double tol, int max_evals) {
-    std::vector<double> s(P), y(P);
+  void accept(double a, double fa, const double* ga, double tol, int max_evals) {
+    double s[kMaxFree], y[kMaxFree];
     for (int k = 0; k < P; ++k) {
       s[k] = a * p[k];
       y[k] = ga[k] - g[k];
     }
-    const double sy = dot(s.data(), y.data(), P);
+    const double sy = dot(s, y, P);
     if (first_step && sy > 0.0) {  // N&W eq. 6.20
-      const double sc = sy / dot(y.data(), y.data(), P);
+      const double sc = sy / dot(y, y, P);
       for (double& h : H) h *= sc;
     }
     first_step = false;
     if (sy > 1e-300) {
       const double rho = 1.0 / sy;
-      std::vector<double> Hy(P, 0.0);
+      double Hy[kMaxFree] = {0.0};
       for (int i = 0; i < P; ++i)
         for (int j = 0; j < P; ++j) Hy[i] += H[i * P + j] * y[j];
-      const double yHy = dot(y.data(), Hy.data(), P);
+      const double yHy = dot(y, Hy, P);
       for (int i = 0; i < P; ++i)
         for (int j = 0; j < P; ++j)
           H[i * P + j] += -rho * (Hy[i] * s[j] + s[i] * Hy[j]) + (rho * rho * yHy + rho) * s[i] * s[j];
     }
     for (int k = 0; k < P; ++k) x[k] += s[k];
     f = fa;
-    g = ga;
+    std::copy(ga, ga + P, g.begin());
     if (edm() < tol) {
       status = RF_OK;
       phase = DONE;
@@ -186,7 +286,7 @@ struct SetFit {
   }
 
   // Deliver f, gradient (internal) at the last trial point.
-  void deliver(double fa, const std::vector<double>& ga, double tol, int max_evals) {
+  void deliver(double fa, const double* ga, double tol, int max_evals) {
     ++evals;
     if (phase == INIT) {
       x = trial;
@@ -196,29 +296,30 @@ struct SetFit {
         return;
       }
       f = fa;
-      g = ga;
+      std::copy(ga, ga + P, g.begin());
       if (edm_identity_small(tol)) return;
       new_direction();
       return;
     }
     const double a = a_cur;
-    const double da = std::isfinite(fa) ? dot(ga.data(), p.data(), P) : std::numeric_limits<double>::quiet_NaN();
+    const double da = std::isfinite(fa) ? dot(ga, p.data(), P) : std::numeric_limits<double>::quiet_NaN();
     ++trials;
     const bool too_many = trials >= kMaxLineTrials || evals >= max_evals;
     if (phase == BRACKET) {
       if (!(fa <= f + kC1 * a * d0) || (trials > 1 && fa >= f_prev)) {
-        a_lo = a_prev; f_lo = f_prev; d_lo = d_prev; g_lo = (a_prev == 0.0) ? g : g_lo;
+        a_lo = a_prev; f_lo = f_prev; d_lo = d_prev;
+        if (a_prev == 0.0) g_lo = g;
         a_hi = a; f_hi = fa; d_hi = da;
         phase = ZOOM;
       } else if (std::fabs(da) <= -kC2 * d0) {
         accept(a, fa, ga, tol, max_evals);
         return;
       } else if (da >= 0.0) {
-        a_lo = a; f_lo = fa; d_lo = da; g_lo = ga;
+        a_lo = a; f_lo = fa; d_lo = da; std::copy(ga, ga + P, g_lo.begin());
         a_hi = a_prev; f_hi = f_prev; d_hi = d_prev;
         phase = ZOOM;
       } else {
-        a_prev = a; f_prev = fa; d_prev = da; g_lo = ga;
+        a_prev = a; f_prev = fa; d_prev = da; std::copy(ga, ga + P, g_lo.begin());
         if (too_many) {
           accept(a, fa, ga, tol, max_evals);  // sufficient decrease holds here
           return;
@@ -237,11 +338,11 @@ struct SetFit {
         if (da * (a_hi - a_lo) >= 0.0) {
           a_hi = a_lo; f_hi = f_lo; d_hi = d_lo;
         }
-        a_lo = a; f_lo = fa; d_lo = da; g_lo = ga;
+        a_lo = a; f_lo = fa; d_lo = da; std::copy(ga, ga + P, g_lo.begin());
       }
     }
     if (too_many) {
-      if (a_lo > 0.0) accept(a_lo, f_lo, g_lo, tol, max_evals);
+      if (a_lo > 0.0) accept(a_lo, f_lo, g_lo.data(), tol, max_evals);
       else line_failed(tol, max_evals);
       return;
     }
@@ -432,6 +533,7 @@ extern "C" rf_status rf_fit(const rf_model* m, const rf_data* d, const double* t
     F.g.assign(P, 0.0);
     F.p.assign(P, 0.0);
     F.trial.assign(P, 0.0);
+    F.g_lo.assign(P, 0.0);
     F.H.assign(P * P, 0.0);
     for (int k = 0; k < P; ++k) F.H[k * P + k] = 1.0;
     std::vector<double> t0(P);
@@ -440,23 +542,26 @@ extern "C" rf_status rf_fit(const rf_model* m, const rf_data* d, const double* t
     F.phase = INIT;
   }
   Evaluator ev(m, dd, !(opts && opts->no_graph == 1));
+  Pool pool(S >= 1024 ? pool_threads() : 1);
   std::vector<int32_t> active;
-  std::vector<double> ga(P);
+  std::vector<double> jc((size_t)S * std::max(P, 1));
   while (true) {
     active.clear();
     for (int s = 0; s < S; ++s)
-      if (fits[s].phase != DONE) {
-        active.push_back(s);
-        co.to_theta(fits[s].trial.data(), &th[(size_t)s * P]);
-      }
+      if (fits[s].phase != DONE) active.push_back(s);
     if (active.empty()) break;
+    pool.run((int64_t)active.size(), [&](int64_t i) {
+      const int s = active[i];
+      co.to_theta_jac(fits[s].trial.data(), &th[(size_t)s * P], &jc[(size_t)s * P]);
+    });
     const rf_status st = ev.run(active, th, nll, grad);
     if (st != RF_OK) return st;
-    for (int s : active) {
-      SetFit& F = fits[s];
-      for (int k = 0; k < P; ++k) ga[k] = grad[(size_t)s * P + k] * co.jac(k, F.trial[k]);
-      F.deliver(nll[s], ga, tol, max_evals);
-    }
+    pool.run((int64_t)active.size(), [&](int64_t i) {
+      const int s = active[i];
+      double ga[kMaxFree];
+      for (int k = 0; k < P; ++k) ga[k] = grad[(size_t)s * P + k] * jc[(size_t)s * P + k];
+      fits[s].deliver(nll[s], ga, tol, max_evals);
+    });
   }
   for (int s = 0; s < S; ++s) {
     co.to_theta(fits[s].x.data(), theta_hat + (size_t)s * P);
