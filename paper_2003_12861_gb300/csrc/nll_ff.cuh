@@ -22,7 +22,11 @@
 namespace rf {
 
 constexpr int kFFConst = 512;  // floats per set: per-event constants, then K (Q x NACC pairs)
-constexpr float kSlowZf = -7.0f;
+// Below this z the resolution term of the decay is dropped: erfc(z) = 2 -
+// erfc(-z) with erfc(5.5) / 2 < 4e-15 (below the float-float precision of
+// the other terms) and the derivative ratio carries exp(-z^2) < 8e-14, far
+// below the gradient tolerance.
+constexpr float kSlowZf = -5.5f;
 
 // Number of moment accumulators (index 0 = log p) and of output quantities.
 __host__ __device__ constexpr int ff_nacc(int shape) {
@@ -202,7 +206,7 @@ __device__ __forceinline__ ff ff_exp0(const FFTables& T, ff x, bool& ok, bool& d
 }
 
 // Normalised decay signal density v and the derivative ratio R at t (the
-// constants fold log(1/I) into every exponent).  Fast path (z < -7):
+// constants fold log(1/I) into every exponent).  Fast path (z < -5.5):
 // v = exp(A)/I, R = 0.  Otherwise the resolution region:
 // z >= 0: v = exp(-u^2/2) erfcx(z) / (2I), R = 2 / (sqrt(pi) erfcx(z));
 // z < 0:  v = exp(A)/I - exp(-u^2/2) erfcx(|z|) / (2I),
