@@ -309,8 +309,6 @@ def run_events(args, api, torch, dist, rank, world, local):
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    api.kernel_time(reset=True)
-    api.kernel_timing(True)
     with ClockSampler(local) as clk:
         with torch.cuda.stream(stream):
             for i in range(args.steps):
@@ -319,10 +317,19 @@ def run_events(args, api, torch, dist, rank, world, local):
                 step()
                 ends[i].record(stream)
         torch.cuda.synchronize()
-    api.kernel_timing(False)
     if dist:
         dist.barrier()
     total_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    # The fused kernel's own duration (for the roofline), in separate steps:
+    # the timing events between K1 and K2 would break their overlap above.
+    api.kernel_time(reset=True)
+    api.kernel_timing(True)
+    with torch.cuda.stream(stream):
+        for i in range(min(args.steps, 50)):
+            flush.zero_()
+            step()
+    torch.cuda.synchronize()
+    api.kernel_timing(False)
     kern_ms, kern_n = api.kernel_time(reset=True)
     if dist:
         t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")

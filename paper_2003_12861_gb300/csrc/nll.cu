@@ -33,6 +33,13 @@ constexpr double kSlowZ = -7.0;
 // one thread per set (throughput).
 constexpr int kBlockK1MaxSets = 256;
 
+// Programmatic dependent launch: K1 lets the event kernel be scheduled at
+// once; the event kernel stages its tables, then waits for K1's completion
+// (and memory) before it reads anything K1 writes.  Without a programmatic
+// dependency (a plain launch) the wait returns at once.
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ __forceinline__ double param_of(const PNode& q, int j, const double* th) {
   return q.pfree[j] >= 0 ? th[q.pfree[j]] : q.pfixed[j];
 }
@@ -82,27 +89,19 @@ __device__ __forceinline__ void end_vals(int cs, double x, bool decay, double t,
     v.df[0] = v.df[1] = v.df[2] = 0.0;
   }
 }
-// Both ends: kPair = false evaluates them in turn; kPair = true has lane 0
-// of the warp evaluate the lower end and lane 1 the upper end at the same
-// time (all 32 lanes call; one FP64 instruction stream serves both ends).
-template <bool kPair>
-__device__ __forceinline__ void both_ends(int cs, double al, double be, bool decay, double lo, double hi, double tau,
-                                          double mu, double sg, EndVals& a, EndVals& b) {
-  if (!kPair) {
-    end_vals(cs, al, decay, lo, tau, mu, sg, a);
-    end_vals(cs, be, decay, hi, tau, mu, sg, b);
-    return;
-  }
-  const bool up = (threadIdx.x & 1) != 0;
-  EndVals v;
-  end_vals(cs, up ? be : al, decay, up ? hi : lo, tau, mu, sg, v);
-  const unsigned all = 0xffffffffu;
-  a.e = __shfl_sync(all, v.e, 0); b.e = __shfl_sync(all, v.e, 1);
-  a.p = __shfl_sync(all, v.p, 0); b.p = __shfl_sync(all, v.p, 1);
-  a.f = __shfl_sync(all, v.f, 0); b.f = __shfl_sync(all, v.f, 1);
-  for (int k = 0; k < 3; ++k) {
-    a.df[k] = __shfl_sync(all, v.df[k], 0);
-    b.df[k] = __shfl_sync(all, v.df[k], 1);
+// One part of an end's work, for K1's job split: part 0 the mass term and
+// p, part 1 the decay convolution; end 0 = lo, 1 = hi.  The same expressions
+// as end_vals, so the split does not change any bit.
+__device__ __forceinline__ void end_part(int cs, double x, bool decay, double t, double tau, double mu, double sg,
+                                         int part, EndVals& v) {
+  if (part == 0) {
+    v.e = mass_term(cs, x);
+    v.p = exp(-0.5 * x * x);
+  } else if (decay) {
+    gaussexp_point(t, tau, mu, sg, &v.f, v.df);
+  } else {
+    v.f = 0.0;
+    v.df[0] = v.df[1] = v.df[2] = 0.0;
   }
 }
 
@@ -115,12 +114,10 @@ __device__ double trunc_exp_mean01(double y) {
 // ------------------------------------------------------------------- K1
 
 // Constants of pdf node q at the parameter point th into c (the layout in
-// rf_internal.h); returns false if th is outside the node's domain.  With
-// kPair the whole warp calls (GAUSS and GAUSSEXP only), lanes 0 and 1 share
-// the two range ends, and lane 0 writes.
-template <bool kPair>
-__device__ bool node_consts(const PNode& q, const double* th, double* c) {
-  const bool writer = !kPair || (threadIdx.x & 31) == 0;
+// rf_internal.h); returns false if th is outside the node's domain.  A
+// Gaussian or decay node takes its two range ends from `ends` when K1 has
+// computed them as separate jobs, else computes them in turn.
+__device__ bool node_consts(const PNode& q, const double* th, double* c, const EndVals* ends) {
   bool bad = false;
   const double lo = q.lo, hi = q.hi;
   switch (q.kind) {
@@ -131,13 +128,19 @@ __device__ bool node_consts(const PNode& q, const double* th, double* c) {
       const double al = (lo - mu) * isg, be = (hi - mu) * isg;
       const int cs = mass_case(al, be);
       EndVals A, B;
-      both_ends<kPair>(cs, al, be, false, lo, hi, 1.0, mu, sg, A, B);
+      if (ends) {
+        A = ends[0];
+        B = ends[1];
+      } else {
+        end_vals(cs, al, false, lo, 1.0, mu, sg, A);
+        end_vals(cs, be, false, hi, 1.0, mu, sg, B);
+      }
       const double I = sg * kSqrt2Pi * mass_of(cs, A.e, B.e);
       const double dmu = A.p - B.p;
       const double dsg = I * isg - (be * B.p - al * A.p);
       if (!(I > 0.0)) bad = true;
       const double iI = 1.0 / I;
-      if (writer) { c[0] = mu; c[1] = isg; c[2] = iI; c[3] = dmu * iI; c[4] = dsg * iI; }
+      c[0] = mu; c[1] = isg; c[2] = iI; c[3] = dmu * iI; c[4] = dsg * iI;
       break;
     }
     case EXPO: {
@@ -157,7 +160,13 @@ __device__ bool node_consts(const PNode& q, const double* th, double* c) {
       const double al = (lo - mu) * isg, be = (hi - mu) * isg;
       const int cs = mass_case(al, be);
       EndVals A, B;
-      both_ends<kPair>(cs, al, be, true, lo, hi, tau, mu, sg, A, B);
+      if (ends) {
+        A = ends[0];
+        B = ends[1];
+      } else {
+        end_vals(cs, al, true, lo, tau, mu, sg, A);
+        end_vals(cs, be, true, hi, tau, mu, sg, B);
+      }
       const double D = mass_of(cs, A.e, B.e);
       const double br = D - B.f + A.f;
       const double I = tau * br;
@@ -165,10 +174,8 @@ __device__ bool node_consts(const PNode& q, const double* th, double* c) {
       const double dD[3] = {0.0, -(pb - pa) * isg, -(be * pb - al * pa) * isg};
       if (!(I > 0.0)) bad = true;
       const double iI = 1.0 / I;
-      if (writer) {
-        c[0] = mu; c[1] = isg; c[2] = sg / tau; c[3] = 1.0 / tau; c[4] = iI;
-        for (int k = 0; k < 3; ++k) c[5 + k] = ((k == 0 ? br : 0.0) + tau * (dD[k] - B.df[k] + A.df[k])) * iI;
-      }
+      c[0] = mu; c[1] = isg; c[2] = sg / tau; c[3] = 1.0 / tau; c[4] = iI;
+      for (int k = 0; k < 3; ++k) c[5 + k] = ((k == 0 ? br : 0.0) + tau * (dD[k] - B.df[k] + A.df[k])) * iI;
       break;
     }
     case CHEB: {
@@ -212,7 +219,7 @@ __device__ bool node_consts(const PNode& q, const double* th, double* c) {
       const double pb = exp((hi - 1.0) * ll - lam - lgamma(hi));
       const double pa = lo > 0.0 ? exp((lo - 1.0) * ll - lam - lgamma(lo)) : 0.0;
       if (!(I > 0.0)) bad = true;
-      if (writer) { c[0] = lam; c[1] = ll; c[2] = 1.0 / lam; c[3] = 1.0 / I; c[4] = (pa - pb) / I; }
+      c[0] = lam; c[1] = ll; c[2] = 1.0 / lam; c[3] = 1.0 / I; c[4] = (pa - pb) / I;
       break;
     }
     case POLY: {
@@ -280,6 +287,7 @@ __device__ void finish_param_point(const Program& P, const Pass& pass, int s, bo
 // K1, one thread per active set (many sets: toy fits).  Also resets the
 // event kernel's work counter.
 __global__ void param_point_kernel(const __grid_constant__ Program P, Pass pass) {
+  pdl_launch_dependents();
   const int a = blockIdx.x * blockDim.x + threadIdx.x;
   if (a == 0) {
     for (int i = 0; i < (pass.n_counters > 1 ? pass.n_counters : 1); ++i) pass.counter[i] = 0;
@@ -290,18 +298,23 @@ __global__ void param_point_kernel(const __grid_constant__ Program P, Pass pass)
   const double* th = pass.theta + (size_t)s * P.n_free;
   double* C = pass.consts + (size_t)s * P.n_const;
   bool bad = false;
-  for (int n = 0; n < P.n_pdf; ++n) bad |= !node_consts<false>(P.node[n], th, C + P.node[n].cofs);
+  for (int n = 0; n < P.n_pdf; ++n) bad |= !node_consts(P.node[n], th, C + P.node[n].cofs, nullptr);
   finish_param_point(P, pass, s, bad, C);
 }
 
 // K1, one block per active set (few sets: one large fit).  Every FP64 warp
-// instruction occupies the SM sub-partition's FP64 unit for many cycles, so
-// a lone thread's chain of transcendentals is slow; here node n runs on warp
-// n % 4, i.e. on the four sub-partitions at once, a Gaussian or decay node
-// evaluates its two range ends on two lanes at once, and the float-float
-// constants follow once all nodes are done.
-__global__ void __launch_bounds__(128) param_point_block_kernel(const __grid_constant__ Program P, Pass pass) {
+// instruction occupies a sub-partition's FP64 unit for many cycles, so a lone
+// thread's chain of transcendentals is slow; here the work is cut into jobs
+// on separate warps (the four sub-partitions' FP64 units run at once): per
+// Gaussian node the mass term and density at each range end (2 jobs), per
+// decay node also the convolution at each end (4 jobs); then every node's
+// constants on its own warp; then the float-float constants.
+constexpr int kK1Warps = 8;
+__global__ void __launch_bounds__(kK1Warps * 32) param_point_block_kernel(const __grid_constant__ Program P,
+                                                                          Pass pass) {
+  __shared__ EndVals ends[kMaxPdf][2];
   __shared__ int sbad;
+  pdl_launch_dependents();
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (blockIdx.x == 0 && tid == 0) {
     for (int i = 0; i < (pass.n_counters > 1 ? pass.n_counters : 1); ++i) pass.counter[i] = 0;
@@ -312,14 +325,36 @@ __global__ void __launch_bounds__(128) param_point_block_kernel(const __grid_con
   const int s = pass.sets[blockIdx.x];
   const double* th = pass.theta + (size_t)s * P.n_free;
   double* C = pass.consts + (size_t)s * P.n_const;
-  bool bad = false;
-  for (int n = warp; n < P.n_pdf; n += 4) {  // warp-uniform
-    const PNode& q = P.node[n];
-    if (q.kind == GAUSS || q.kind == GAUSSEXP) bad |= !node_consts<true>(q, th, C + q.cofs);
-    else if (lane == 0) bad |= !node_consts<false>(q, th, C + q.cofs);
+  // jobs: (node, end, part), numbered in node order
+  if (lane == 0) {
+    int j = 0;
+    for (int n = 0; n < P.n_pdf; ++n) {
+      const PNode& q = P.node[n];
+      if (q.kind != GAUSS && q.kind != GAUSSEXP) continue;
+      const bool decay = q.kind == GAUSSEXP;
+      const int parts = decay ? 2 : 1;
+      for (int e = 0; e < 2; ++e)
+        for (int part = 0; part < parts; ++part, ++j) {
+          if (j % kK1Warps != warp) continue;
+          const double tau = decay ? param_of(q, 0, th) : 1.0;
+          const double mu = param_of(q, decay ? 1 : 0, th), sg = param_of(q, decay ? 2 : 1, th);
+          if (!(sg > 0.0) || !(tau > 0.0)) continue;  // flagged when the node is finished
+          const double isg = 1.0 / sg;
+          const double al = (q.lo - mu) * isg, be = (q.hi - mu) * isg;
+          end_part(mass_case(al, be), e ? be : al, decay, e ? q.hi : q.lo, tau, mu, sg, part, ends[n][e]);
+        }
+    }
   }
-  if (lane == 0 && bad) atomicOr(&sbad, 1);
-  __threadfence_block();
+  __syncthreads();
+  if (lane == 0) {
+    bool bad = false;
+    for (int n = warp; n < P.n_pdf; n += kK1Warps) {
+      const PNode& q = P.node[n];
+      const bool split = q.kind == GAUSS || q.kind == GAUSSEXP;
+      bad |= !node_consts(q, th, C + q.cofs, split ? ends[n] : nullptr);
+    }
+    if (bad) atomicOr(&sbad, 1);
+  }
   __syncthreads();
   if (tid == 0) finish_param_point(P, pass, s, sbad != 0, C);
 }
@@ -690,6 +725,7 @@ __global__ void __launch_bounds__(kLanes) events_generic(const __grid_constant__
   __shared__ Smem sm;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int Q = kGrad ? 1 + P.n_slots : 1;
+  pdl_wait();
   while (true) {
     if (tid == 0) sm.item = atomicAdd(pass.counter, 1);
     __syncthreads();
@@ -812,6 +848,7 @@ __global__ void __launch_bounds__(kLanes, ff_min_blocks(kShape)) events_ff(const
   const unsigned lt = (1u << lane) - 1u;
   const int n_units = pass.n_items * kParts;
   int kc_set = -1, c_set = -1;  // sets whose constants the block holds (block-uniform)
+  pdl_wait();  // K1 has reset the counter and written the constants
   // One unit of lookahead: thread 0 claims the next unit while the block
   // works on the current one, so the claim's round trip is hidden.
   int next_u = tid == 0 ? atomicAdd(pass.counter, 1) : 0;
@@ -959,7 +996,7 @@ __global__ void __launch_bounds__(kLanes, ff_min_blocks(kShape)) events_ff(const
 
 void launch_param_point(const Program& P, const Pass& pass, cudaStream_t st) {
   if (pass.n_active > 0 && pass.n_active <= kBlockK1MaxSets) {
-    param_point_block_kernel<<<pass.n_active, 128, 0, st>>>(P, pass);
+    param_point_block_kernel<<<pass.n_active, kK1Warps * 32, 0, st>>>(P, pass);
     return;
   }
   const int threads = 128;
@@ -995,6 +1032,24 @@ bool launch_fits(Shape shape, int threads, int blocks_per_sm) {
   return blocks_per_sm <= n;
 }
 
+// Launches an event kernel as a programmatic dependent of the stream's
+// previous kernel (K1).
+template <class... Args>
+void launch_dependent(void (*kernel)(Args...), int grid, cudaStream_t st, const Program& P, const Columns& cols,
+                      const Pass& pass) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(kLanes);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, P, cols, pass);
+}
+
 void launch_events(const Program& P, Shape shape, const Columns& cols, const Pass& pass, int threads,
                    int blocks_per_sm, int n_sm, cudaStream_t st) {
   (void)threads;
@@ -1007,20 +1062,20 @@ void launch_events(const Program& P, Shape shape, const Columns& cols, const Pas
   timing_begin(st);
   switch (sh) {
     case SHAPE_SUM_GAUSSEXP_CHEB2:
-      if (pass.want_grad) events_ff<SHAPE_SUM_GAUSSEXP_CHEB2, true><<<grid, kLanes, 0, st>>>(P, cols, pass);
-      else events_ff<SHAPE_SUM_GAUSSEXP_CHEB2, false><<<grid, kLanes, 0, st>>>(P, cols, pass);
+      if (pass.want_grad) launch_dependent(events_ff<SHAPE_SUM_GAUSSEXP_CHEB2, true>, grid, st, P, cols, pass);
+      else launch_dependent(events_ff<SHAPE_SUM_GAUSSEXP_CHEB2, false>, grid, st, P, cols, pass);
       break;
     case SHAPE_SUM_GAUSS_POLY1:
-      if (pass.want_grad) events_ff<SHAPE_SUM_GAUSS_POLY1, true><<<grid, kLanes, 0, st>>>(P, cols, pass);
-      else events_ff<SHAPE_SUM_GAUSS_POLY1, false><<<grid, kLanes, 0, st>>>(P, cols, pass);
+      if (pass.want_grad) launch_dependent(events_ff<SHAPE_SUM_GAUSS_POLY1, true>, grid, st, P, cols, pass);
+      else launch_dependent(events_ff<SHAPE_SUM_GAUSS_POLY1, false>, grid, st, P, cols, pass);
       break;
     case SHAPE_PROD3:
-      if (pass.want_grad) events_ff<SHAPE_PROD3, true><<<grid, kLanes, 0, st>>>(P, cols, pass);
-      else events_ff<SHAPE_PROD3, false><<<grid, kLanes, 0, st>>>(P, cols, pass);
+      if (pass.want_grad) launch_dependent(events_ff<SHAPE_PROD3, true>, grid, st, P, cols, pass);
+      else launch_dependent(events_ff<SHAPE_PROD3, false>, grid, st, P, cols, pass);
       break;
     default:
-      if (pass.want_grad) events_generic<true><<<grid, kLanes, 0, st>>>(P, cols, pass);
-      else events_generic<false><<<grid, kLanes, 0, st>>>(P, cols, pass);
+      if (pass.want_grad) launch_dependent(events_generic<true>, grid, st, P, cols, pass);
+      else launch_dependent(events_generic<false>, grid, st, P, cols, pass);
   }
   timing_end(st);
 }
