@@ -263,15 +263,20 @@ __device__ __forceinline__ void extended_term(const Program& P, const Pass& pass
   *dt = 1.0 - N / nu;
 }
 
-// Finishes a set after its constants: domain flag, float-float constants,
+__device__ bool extended_bad(const Program& P, const Pass& pass, int s) {
+  if (!P.ext) return false;
+  const double nu = P.ext_free >= 0 ? pass.theta[(size_t)s * P.n_free + P.ext_free] : P.ext_fixed;
+  return !(nu > 0.0);
+}
+
+// Finishes a set: domain flag, the float-float constants (unless ff_done),
 // and the result of a set without events.
-__device__ void finish_param_point(const Program& P, const Pass& pass, int s, bool bad, const double* C) {
-  if (P.ext) {
-    const double nu = P.ext_free >= 0 ? pass.theta[(size_t)s * P.n_free + P.ext_free] : P.ext_fixed;
-    if (!(nu > 0.0)) bad = true;
-  }
+__device__ void finish_param_point(const Program& P, const Pass& pass, int s, bool bad, const double* C,
+                                   bool ff_done = false) {
+  bad = bad || extended_bad(P, pass, s);
   pass.flags[s] = bad ? kThetaBad : 0;
-  if (!bad && pass.ff_shape != SHAPE_GENERIC && pass.ffc) prepare_ff(P, pass.ff_shape, C, pass.ffc + (size_t)s * kFFConst);
+  if (!ff_done && !bad && pass.ff_shape != SHAPE_GENERIC && pass.ffc)
+    prepare_ff(P, pass.ff_shape, C, pass.ffc + (size_t)s * kFFConst);
   if (pass.offsets[s + 1] == pass.offsets[s] && pass.pairs) {  // no events: empty pairs
     for (int k = 0; k < 2 * (1 + P.n_free); ++k) pass.pairs[(size_t)s * 2 * (1 + P.n_free) + k] = 0.0;
   } else if (pass.offsets[s + 1] == pass.offsets[s]) {  // no events: the empty sum (+ nu if extended)
@@ -313,6 +318,8 @@ constexpr int kK1Warps = 8;
 __global__ void __launch_bounds__(kK1Warps * 32) param_point_block_kernel(const __grid_constant__ Program P,
                                                                           Pass pass) {
   __shared__ EndVals ends[kMaxPdf][2];
+  __shared__ double Ks[13 * 16];
+  __shared__ double Cs[kMaxConst];  // the set's constant block, copied out at the end
   __shared__ int sbad;
   pdl_launch_dependents();
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -351,12 +358,24 @@ __global__ void __launch_bounds__(kK1Warps * 32) param_point_block_kernel(const 
     for (int n = warp; n < P.n_pdf; n += kK1Warps) {
       const PNode& q = P.node[n];
       const bool split = q.kind == GAUSS || q.kind == GAUSSEXP;
-      bad |= !node_consts(q, th, C + q.cofs, split ? ends[n] : nullptr);
+      bad |= !node_consts(q, th, Cs + q.cofs, split ? ends[n] : nullptr);
     }
     if (bad) atomicOr(&sbad, 1);
   }
   __syncthreads();
-  if (tid == 0) finish_param_point(P, pass, s, sbad != 0, C);
+  // the float-float constants: jobs on separate warps, then K converted by all threads
+  const int shape = pass.ff_shape;
+  const bool ff = shape != SHAPE_GENERIC && pass.ffc && sbad == 0 && !extended_bad(P, pass, s);
+  if (ff) {
+    float* out = pass.ffc + (size_t)s * kFFConst;
+    for (int i = tid; i < ff_q(shape) * ff_nacc(shape); i += blockDim.x) Ks[i] = i == 0 ? 1.0 : 0.0;
+    __syncthreads();
+    if (lane == 0 && warp < ff_jobs(shape)) prepare_ff_job(P, shape, Cs, out, Ks, warp);
+    __syncthreads();
+    ff_convert_K(shape, Ks, out, tid, blockDim.x);
+  }
+  for (int i = tid; i < P.n_const; i += blockDim.x) C[i] = Cs[i];
+  if (tid == 0) finish_param_point(P, pass, s, sbad != 0, Cs, true);
 }
 
 // ------------------------------------------------------------------- K2

@@ -84,17 +84,22 @@ __device__ __forceinline__ void put_ff(float* o, double v) {
 // factor leaves the float range while the product matters.  Moments at
 // column m0: E = v/p, E t, 1/p, t/p, t^2/p, E R, E R u (u = (t - mu)/sigma).
 // Rows r0.. for tau, mu, sigma, c1, c2, f.
-static __device__ void prep_decay(const double* ge, const double* ch, const double* sm, float* o, double* K, int nacc,
-                           int r0, int m0) {
+// The background polynomial of CHEB2 in powers of t: S[j] t^j = 1 + c1
+// T1(x') + c2 T2(x'), x' = c0 t - c1p.
+__device__ __forceinline__ void cheb2_power(const double* ch, double S[3]) {
+  const double c0 = ch[0], c1p = ch[1], a1 = ch[5], a2 = ch[6];
+  S[0] = 1.0 - a1 * c1p + a2 * (2.0 * c1p * c1p - 1.0);
+  S[1] = a1 * c0 - 4.0 * a2 * c0 * c1p;
+  S[2] = 2.0 * a2 * c0 * c0;
+}
+// The per-event constants (job 0 of a decay sub-model).
+static __device__ void prep_decay_consts(const double* ge, const double* ch, const double* sm, float* o) {
   const double mu = ge[0], is = ge[1], s = ge[2], it = ge[3], iIs = ge[4];
-  const double dIt = ge[5], dIm = ge[6], dIs = ge[7];
-  const double c0 = ch[0], c1p = ch[1], iIb = ch[2], dI1 = ch[3], dI2 = ch[4], a1 = ch[5], a2 = ch[6];
+  const double iIb = ch[2];
   const double f = sm[0], fl = sm[1];
   const double lIs = log(iIs);
-  const double S[3] = {1.0 - a1 * c1p + a2 * (2.0 * c1p * c1p - 1.0), a1 * c0 - 4.0 * a2 * c0 * c1p,
-                       2.0 * a2 * c0 * c0};
-  const double T1[3] = {-c1p, c0, 0.0};
-  const double T2[3] = {2.0 * c1p * c1p - 1.0, -4.0 * c0 * c1p, 2.0 * c0 * c0};
+  double S[3];
+  cheb2_power(ch, S);
   const double r2 = 0.70710678118654752440;
   put_ff(o + 0, 0.5 * s * s + mu * it + lIs);  // log v = A + log(1/I), A = s^2/2 + mu/tau - t/tau
   put_ff(o + 2, it);
@@ -106,6 +111,19 @@ static __device__ void prep_decay(const double* ge, const double* ch, const doub
   put_ff(o + 16, is);
   put_ff(o + 18, s);
   put_ff(o + 20, lIs);
+}
+// Its rows of K (job 1).
+static __device__ void prep_decay_K(const double* ge, const double* ch, const double* sm, double* K, int nacc, int r0,
+                                    int m0) {
+  const double mu = ge[0], is = ge[1], s = ge[2], it = ge[3];
+  const double dIt = ge[5], dIm = ge[6], dIs = ge[7];
+  const double c0 = ch[0], c1p = ch[1], iIb = ch[2], dI1 = ch[3], dI2 = ch[4];
+  const double f = sm[0], fl = sm[1];
+  double S[3];
+  cheb2_power(ch, S);
+  const double T1[3] = {-c1p, c0, 0.0};
+  const double T2[3] = {2.0 * c1p * c1p - 1.0, -4.0 * c0 * c1p, 2.0 * c0 * c0};
+  const double r2 = 0.70710678118654752440;
   double* rt = K + (r0 + 0) * nacc;  // tau
   rt[m0 + 1] = f * s * is * it;
   rt[m0 + 0] = -f * (s * mu * is * it + s * s * it + dIt);
@@ -132,10 +150,9 @@ static __device__ void prep_decay(const double* ge, const double* ch, const doub
 // cancel: at m0, G = v/p, G u, G u^2 (u = (x - mu)/sigma), 1/p, y/p, with
 // y = c0 x - c1 the background's own variable (x for POLY1, the mapped x'
 // for CHEB1), in which its shape is 1 + b y.  bg = (c0, c1, b, iIb, dIb).
-static __device__ void prep_gauss_lin(const double* g, const double* bg, const double* sm, float* o, double* K, int nacc,
-                               int r0, int m0) {
-  const double mu = g[0], is = g[1], iIg = g[2], dIm = g[3], dIs = g[4];
-  const double c0 = bg[0], c1 = bg[1], b = bg[2], iIb = bg[3], dIb = bg[4];
+static __device__ void prep_gauss_lin_consts(const double* g, const double* bg, const double* sm, float* o) {
+  const double mu = g[0], is = g[1], iIg = g[2];
+  const double c0 = bg[0], c1 = bg[1], b = bg[2], iIb = bg[3];
   const double f = sm[0], fl = sm[1];
   put_ff(o + 0, mu);
   put_ff(o + 2, is);
@@ -145,6 +162,12 @@ static __device__ void prep_gauss_lin(const double* g, const double* bg, const d
   put_ff(o + 10, c0);
   put_ff(o + 12, c1);
   put_ff(o + 14, log(iIg));
+}
+static __device__ void prep_gauss_lin_K(const double* g, const double* bg, const double* sm, double* K, int nacc,
+                                        int r0, int m0) {
+  const double is = g[1], dIm = g[3], dIs = g[4];
+  const double b = bg[2], iIb = bg[3], dIb = bg[4];
+  const double f = sm[0], fl = sm[1];
   K[(r0 + 0) * nacc + m0 + 1] = f * is;  // mu: u/sigma - dlogI/dmu
   K[(r0 + 0) * nacc + m0 + 0] = -f * dIm;
   K[(r0 + 1) * nacc + m0 + 2] = f * is;  // sigma: u^2/sigma - dlogI/dsigma
@@ -156,33 +179,59 @@ static __device__ void prep_gauss_lin(const double* g, const double* bg, const d
   K[(r0 + 3) * nacc + m0 + 4] = -iIb * b;
 }
 
-// Writes the set's float block: per-event constants, then K as float pairs.
+// The set's float block (per-event constants, then K as float pairs) is
+// written in independent jobs, so that K1 can run them on separate warps:
+// ff_jobs(shape) jobs each fill their part of `out` or rows of K (a zeroed
+// Q x NACC double array with K[0] = 1), then ff_convert_K writes K as float
+// pairs, entry by entry.
+__host__ __device__ constexpr int ff_jobs(int shape) { return shape == SHAPE_PROD3 ? 5 : 2; }
+
+static __device__ void prepare_ff_job(const Program& P, int shape, const double* C, float* out, double* K, int job) {
+  const int nacc = ff_nacc(shape);
+  if (shape == SHAPE_SUM_GAUSSEXP_CHEB2) {
+    const double *ge = C + P.node[0].cofs, *ch = C + P.node[1].cofs, *sm = C + P.node[2].cofs;
+    if (job == 0) prep_decay_consts(ge, ch, sm, out);
+    else prep_decay_K(ge, ch, sm, K, nacc, 1, 1);
+  } else if (shape == SHAPE_SUM_GAUSS_POLY1) {
+    const double* pl = C + P.node[1].cofs;  // POLY1 [1/I, dlogI/da1, a1]
+    const double bg[5] = {1.0, 0.0, pl[2], pl[0], pl[1]};
+    if (job == 0) prep_gauss_lin_consts(C + P.node[0].cofs, bg, C + P.node[2].cofs, out);
+    else prep_gauss_lin_K(C + P.node[0].cofs, bg, C + P.node[2].cofs, K, nacc, 1, 1);
+  } else if (shape == SHAPE_PROD3) {
+    const double* cb = C + P.node[1].cofs;  // CHEB1 [c0, c1', 1/I, dlogI/dc, c]
+    const double bg[5] = {cb[0], cb[1], cb[4], cb[2], cb[3]};
+    const double *ge = C + P.node[3].cofs, *ch = C + P.node[4].cofs, *sm = C + P.node[5].cofs;
+    const double* pa = C + P.node[6].cofs;  // POLY2 [1/I, dlogI/da1, dlogI/da2, a1, a2]
+    const double Sa[3] = {1.0, pa[3], pa[4]};
+    switch (job) {
+      case 0: prep_gauss_lin_consts(C + P.node[0].cofs, bg, C + P.node[2].cofs, out); break;
+      case 1: prep_gauss_lin_K(C + P.node[0].cofs, bg, C + P.node[2].cofs, K, nacc, 1, 1); break;
+      case 2: prep_decay_consts(ge, ch, sm, out + 16); break;
+      case 3: prep_decay_K(ge, ch, sm, K, nacc, 5, 6); break;
+      default:
+        for (int j = 0; j < 3; ++j) put_ff(out + 38 + 2 * j, pa[0] * Sa[j]);
+        for (int k = 0; k < 2; ++k) {
+          for (int j = 0; j < 3; ++j) K[(11 + k) * nacc + 13 + j] = -pa[0] * pa[1 + k] * Sa[j];
+          K[(11 + k) * nacc + 13 + 1 + k] += pa[0];
+        }
+    }
+  }
+}
+
+// K entries [i0, end) with stride, as float pairs after the constants.
+static __device__ void ff_convert_K(int shape, const double* K, float* out, int i0, int stride) {
+  float* Ko = out + ff_koff(shape);
+  for (int i = i0; i < ff_q(shape) * ff_nacc(shape); i += stride) put_ff(Ko + 2 * i, K[i]);
+}
+
+// All jobs in turn (one thread).
 static __device__ void prepare_ff(const Program& P, int shape, const double* C, float* out) {
   double K[13 * 16];
   const int nacc = ff_nacc(shape), Q = ff_q(shape);
   for (int i = 0; i < Q * nacc; ++i) K[i] = 0.0;
   K[0] = 1.0;  // sum log p
-  if (shape == SHAPE_SUM_GAUSSEXP_CHEB2) {
-    prep_decay(C + P.node[0].cofs, C + P.node[1].cofs, C + P.node[2].cofs, out, K, nacc, 1, 1);
-  } else if (shape == SHAPE_SUM_GAUSS_POLY1) {
-    const double* pl = C + P.node[1].cofs;  // POLY1 [1/I, dlogI/da1, a1]
-    const double bg[5] = {1.0, 0.0, pl[2], pl[0], pl[1]};
-    prep_gauss_lin(C + P.node[0].cofs, bg, C + P.node[2].cofs, out, K, nacc, 1, 1);
-  } else if (shape == SHAPE_PROD3) {
-    const double* cb = C + P.node[1].cofs;  // CHEB1 [c0, c1', 1/I, dlogI/dc, c]
-    const double bg[5] = {cb[0], cb[1], cb[4], cb[2], cb[3]};
-    prep_gauss_lin(C + P.node[0].cofs, bg, C + P.node[2].cofs, out, K, nacc, 1, 1);
-    prep_decay(C + P.node[3].cofs, C + P.node[4].cofs, C + P.node[5].cofs, out + 16, K, nacc, 5, 6);
-    const double* pa = C + P.node[6].cofs;  // POLY2 [1/I, dlogI/da1, dlogI/da2, a1, a2]
-    const double Sa[3] = {1.0, pa[3], pa[4]};
-    for (int j = 0; j < 3; ++j) put_ff(out + 38 + 2 * j, pa[0] * Sa[j]);
-    for (int k = 0; k < 2; ++k) {
-      for (int j = 0; j < 3; ++j) K[(11 + k) * nacc + 13 + j] = -pa[0] * pa[1 + k] * Sa[j];
-      K[(11 + k) * nacc + 13 + 1 + k] += pa[0];
-    }
-  }
-  float* Ko = out + ff_koff(shape);
-  for (int i = 0; i < Q * nacc; ++i) put_ff(Ko + 2 * i, K[i]);
+  for (int j = 0; j < ff_jobs(shape); ++j) prepare_ff_job(P, shape, C, out, K, j);
+  ff_convert_K(shape, K, out, 0, 1);
 }
 
 // ----------------------------------------------------- event side (FF)
