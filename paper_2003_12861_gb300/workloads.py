@@ -211,3 +211,57 @@ def toy_thetas(n_sets: int, seed: int, center: np.ndarray = DECAY_TRUE, rel: flo
     half = np.where(center == 0.0, abs_width, half)
     u = rng.random((n_sets, center.size))
     return center + (2.0 * u - 1.0) * half
+
+
+# ---------------------------------------------------- binned (HistFactory)
+
+def binned_model(seed: int = 20031290, channels: int = 28, bins: int = 50, samples: int = 8,
+                 nuisances: int = 253, histosys_per_sample: int = 20, normsys_per_sample: int = 10):
+    """A synthetic HistFactory-style model of the size the paper's ATLAS
+    example has (28 channels, 253 systematics, ~1e4 histograms): per channel
+    `samples` nominal histograms of `bins` bins (smooth random shapes),
+    each sample with normsys (kappa_lo, kappa_hi) and histosys (h_lo, h_hi)
+    modifiers on nuisances drawn from a shared pool, and 3 free normalisation
+    factors (a signal strength on sample 0 of every channel, two background
+    scales on samples 1 and 2).  Returned as plain data:
+    dict(n_bins, bin0[S], nominal[S][bins], constrained[P], modifiers=list of
+    (sample, kind, param, k_lo, k_hi, h_lo, h_hi)), kind 0/1/2 =
+    normfactor/normsys/histosys; parameters 0..2 are the normfactors, 3.. the
+    constrained nuisances."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n_bins = channels * bins
+    bin0, nominal, mods = [], [], []
+    x = (np.arange(bins) + 0.5) / bins
+    P = 3 + nuisances
+    for c in range(channels):
+        for j in range(samples):
+            s = len(nominal)
+            amp = 10 ** rng.uniform(0.5, 3.0)
+            if j == 0:  # a signal bump
+                mu0, w = rng.uniform(0.3, 0.7), rng.uniform(0.05, 0.15)
+                h = amp * np.exp(-0.5 * ((x - mu0) / w) ** 2) + 1e-3 * amp
+            else:       # falling backgrounds
+                h = amp * np.exp(-x * rng.uniform(0.5, 4.0)) * (1 + 0.2 * np.sin(6.28 * x * rng.uniform(0.5, 2)))
+            bin0.append(c * bins)
+            nominal.append(h)
+            if j < 3:
+                mods.append((s, 0, j, 1.0, 1.0, None, None))
+            for k in rng.choice(nuisances, normsys_per_sample, replace=False):
+                mods.append((s, 1, 3 + int(k), float(rng.uniform(0.85, 0.99)), float(rng.uniform(1.01, 1.15)),
+                             None, None))
+            for k in rng.choice(nuisances, histosys_per_sample, replace=False):
+                tilt = rng.uniform(-0.05, 0.05) * (x - 0.5) + rng.uniform(-0.02, 0.02)
+                mods.append((s, 2, 3 + int(k), 1.0, 1.0, h * (1 - tilt - rng.uniform(0, 0.01)),
+                             h * (1 + tilt + rng.uniform(0, 0.01))))
+    constrained = [False] * 3 + [True] * nuisances
+    return {"n_bins": n_bins, "bin0": bin0, "nominal": nominal, "constrained": constrained, "modifiers": mods,
+            "n_params": P}
+
+
+def binned_toy_thetas(n_toys: int, seed: int, n_params: int) -> np.ndarray:
+    """Per-toy parameter points: normfactors uniform in [0.8, 1.2], nuisances
+    standard normal x 0.5."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    th = rng.normal(0.0, 0.5, (n_toys, n_params))
+    th[:, :3] = rng.uniform(0.8, 1.2, (n_toys, 3))
+    return th
