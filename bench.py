@@ -50,9 +50,10 @@ WORKLOADS = {
     "gauss_poly1_1e4": ("gauss_poly1_model", W.GAUSS_POLY1_TRUE, 10_000, False, 8),
     "decay_toys_4096": ("decay_model", W.DECAY_TRUE, 0, False, 8),
     "learned_start": ("decay_model", W.DECAY_TRUE, 0, False, 8),
+    "binned_4096": ("binned_model", None, 0, False, 8),
 }
 DEFAULT_STEPS = {"decay_1e7": 400, "prod3_1e8_f32": 40, "gauss_poly1_1e4": 2000, "decay_toys_4096": 3,
-                 "learned_start": 1}
+                 "learned_start": 1, "binned_4096": 100}
 
 
 def dist_env():
@@ -158,7 +159,28 @@ def oracle_toy_fits_per_s(seconds: float):
     return fits / dt, f"oracle BFGS fits (plain start) of the first {fits} toys of the 4096-toy batch, {dt:.1f} s"
 
 
+def oracle_binned_per_s(seconds: float):
+    """The binned oracle as it stands, single-threaded, on datasets of the
+    binned workload's model (same parameter points, counts drawn at them)."""
+    from oracle import binned as OB
+
+    spec = W.binned_model()
+    om = OB.from_spec(spec)
+    th = W.binned_toy_thetas(64, W.SEED_BASE + 5, spec["n_params"])
+    rng = np.random.Generator(np.random.PCG64(W.SEED_BASE + 6))
+    counts = [rng.poisson(om.expected(t)[0]).astype(float) for t in th[:4]]
+    n, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        om.nll(th[n % 4], counts[n % 4])
+        n += 1
+    dt = time.perf_counter() - t0
+    return n / dt, f"{n} oracle NLL+gradient evaluations of datasets of the binned model, {dt:.1f} s"
+
+
 def cpu_baseline(wl: str):
+    if wl == "binned_4096":
+        v, s = oracle_binned_per_s(10.0)
+        return {"value": v, "unit": "datasets/s", "cores": 1, "kind": "oracle", "sample": s}
     if wl in ("decay_toys_4096", "learned_start"):
         v, s = oracle_toy_fits_per_s(15.0)
         return {"value": v, "unit": "toy fits/s", "cores": 1, "kind": "oracle", "sample": s}
@@ -172,7 +194,10 @@ def run_reference(args):
         return 0
     wl = args.workload
     t0 = time.perf_counter()
-    if wl in ("decay_toys_4096", "learned_start"):
+    if wl == "binned_4096":
+        v, s = oracle_binned_per_s(max(3.0, 0.5 * args.steps))
+        unit = "datasets/s"
+    elif wl in ("decay_toys_4096", "learned_start"):
         # each step: the oracle fits one toy of the batch
         v, s = oracle_toy_fits_per_s(max(3.0, 1.5 * args.steps))
         unit = "toy fits/s"
@@ -496,6 +521,88 @@ def run_learned(args, api, torch, dist, rank, world, local):
     }
 
 
+def binned_flops(spec):
+    """Algorithmic FP64 flops of one binned NLL+gradient evaluation: per
+    (sample, bin) entry its rate (a multiply-add per histosys term, the
+    factor) and its weighted sum; per histosys modifier its weighted slope
+    sum; per bin the weight and the Poisson term."""
+    n_hs = {}
+    for (smp, kind, *_rest) in spec["modifiers"]:
+        if kind == 2:
+            n_hs[smp] = n_hs.get(smp, 0) + 1
+    entries = sum(len(h) * (1 + n_hs.get(s, 0)) for s, h in enumerate(spec["nominal"]))
+    hs_bins = sum(len(spec["nominal"][smp]) for (smp, kind, *_r) in spec["modifiers"] if kind == 2)
+    n_entries = sum(len(h) for h in spec["nominal"])
+    return 2 * (entries + n_entries + hs_bins) + 4 * spec["n_bins"]
+
+
+def run_binned(args, api, torch, dist, rank, world, local):
+    """Binned (HistFactory-style) NLL + gradient of 4096 datasets of the
+    28-channel, 253-nuisance model per step (one batched launch)."""
+    spec = W.binned_model()
+    m = api.BinnedModel(spec)
+    S, P, Bn = 4096, spec["n_params"], spec["n_bins"]
+    th = torch.as_tensor(W.binned_toy_thetas(S, W.SEED_BASE + 5 + 1000 * rank, P)).cuda()
+    nu = torch.zeros((S, Bn), dtype=torch.float64, device="cuda")
+    m.expected(th, nu)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(W.SEED_BASE + 6 + 1000 * rank)
+    counts = torch.poisson(nu, generator=gen)
+    out = torch.zeros((S, 1 + P), dtype=torch.float64, device="cuda")
+    flags = torch.zeros(S, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            m.nll_grad_async(counts, th, out, flags, stream=stream)
+    stream.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        with torch.cuda.stream(stream):
+            for i in range(args.steps):
+                flush.zero_()
+                starts[i].record(stream)
+                m.nll_grad_async(counts, th, out, flags, stream=stream)
+                ends[i].record(stream)
+        torch.cuda.synchronize()
+    total_ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
+    if dist:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms = total_ms / args.steps
+    # end to end: host counts and parameters in, host results out
+    hc, ht = counts.cpu().numpy(), th.cpu().numpy()
+    m.nll_grad(hc, ht)
+    t0 = time.perf_counter()
+    k = 5
+    for _ in range(k):
+        m.nll_grad(hc, ht)
+    e2e_s = (time.perf_counter() - t0) / k
+    if rank != 0:
+        return None
+    fl = binned_flops(spec)
+    fp64 = api.probe(0)
+    achieved = S * fl / (ms * 1e-3)
+    return {
+        "value": world * S / (ms * 1e-3), "unit": "datasets/s", "ms_per_step": ms, "dtype": "f64",
+        "config": {"workload": "binned_4096", "datasets": S, "channels": 28, "bins": Bn, "samples": len(spec["nominal"]),
+                   "parameters": P, "modifiers": len(spec["modifiers"]),
+                   "histograms": len(spec["nominal"]) + 2 * sum(1 for md in spec["modifiers"] if md[1] == 2),
+                   "l2": "flushed between steps (256 MiB write); the model's histograms (3.6 MB) are re-read from L2"},
+        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": fp64 / 1e12, "unit": "TFLOP/s",
+                     "frac": achieved / fp64, "traffic": None,
+                     "peak_basis": f"FP64 FMA rate measured in-run; {fl} algorithmic FP64 flops per dataset"},
+        "e2e": {"value": world * S / e2e_s, "unit": "datasets/s", "h2d_bytes_per_step": S * (Bn + P) * 8,
+                "d2h_bytes_per_step": S * (1 + P) * 8 + S * 4},
+        "gpu_launches": args.steps, "clocks": clk.summary(),
+    }
+
+
 def run_ours(args):
     import torch
 
@@ -514,6 +621,8 @@ def run_ours(args):
         line = run_toys(args, api, torch, dist, rank, world, local)
     elif args.workload == "learned_start":
         line = run_learned(args, api, torch, dist, rank, world, local)
+    elif args.workload == "binned_4096":
+        line = run_binned(args, api, torch, dist, rank, world, local)
     else:
         line = run_events(args, api, torch, dist, rank, world, local)
     if rank == 0:

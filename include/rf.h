@@ -279,6 +279,46 @@ rf_status rf_mlp_load(const char* path, rf_mlp** out);
 rf_status rf_nll_grad_stream(const rf_model* m, rf_data* d, const void* const* host_cols, const double* theta,
                              double* nll, double* grad, void* stream);
 
+/* ---------------------------------------------------- binned likelihood */
+
+/* Binned models built from histograms (Sec. 3: HistFactory -- channels of
+ * samples with +-1 sigma systematic histograms).  Samples s cover contiguous
+ * bins [bin0[s], bin0[s] + nbins[s]) with nominal rates (concatenated in
+ * sample order); modifiers tie a sample to one parameter theta_k:
+ *   RF_MOD_NORMFACTOR  nu *= theta_k (typically a free, unconstrained scale)
+ *   RF_MOD_NORMSYS     nu *= k_hi^alpha (alpha >= 0) or k_lo^-alpha (alpha < 0)
+ *   RF_MOD_HISTOSYS    nu += alpha (h_hi - h) (alpha >= 0) or alpha (h - h_lo),
+ *                      bin by bin, before the factors; h_lo then h_hi (nbins
+ *                      each) follow in hist_data in modifier order
+ * nu_b = sum over the samples on bin b; for bin counts n_b
+ *   NLL = sum_b (nu_b - n_b log nu_b) + sum_{constrained k} theta_k^2 / 2
+ * (Poisson terms without log n_b!, unit-Gaussian constraints without their
+ * normalisation).  Limits: 8192 bins, 2048 samples (and the block's shared
+ * memory: 8 bytes x (2 samples + bins + 256)).  Host arrays are copied. */
+typedef enum { RF_MOD_NORMFACTOR = 0, RF_MOD_NORMSYS = 1, RF_MOD_HISTOSYS = 2 } rf_modifier_kind;
+typedef struct {
+  int32_t sample, kind, param; /* rf_modifier_kind */
+  double k_lo, k_hi;           /* RF_MOD_NORMSYS factors (> 0) */
+} rf_modifier;
+typedef struct rf_binned rf_binned;
+rf_status rf_binned_create(int32_t n_bins, int32_t n_samples, const int32_t* bin0, const int32_t* nbins,
+                           const double* nominal, int32_t n_params, const int32_t* constrained, int32_t n_mods,
+                           const rf_modifier* mods, const double* hist_data, rf_binned** out);
+void rf_binned_destroy(rf_binned* m);
+int32_t rf_binned_n_params(const rf_binned* m);
+/* NLL and gradient of n_sets datasets at once (one parameter point each):
+ * counts HOST n_sets x n_bins, theta HOST n_sets x n_params, nll HOST n_sets,
+ * grad HOST n_sets x n_params.  A dataset with some nu_b <= 0 gets NLL +inf
+ * and the call returns RF_E_DOMAIN.  Deterministic (fixed summation order). */
+rf_status rf_binned_nll_grad(rf_binned* m, int32_t n_sets, const double* counts, const double* theta, double* nll,
+                             double* grad);
+/* The same on DEVICE arrays, asynchronous on `stream`: d_out n_sets x (1 +
+ * n_params) (NLL then gradient), d_flags n_sets (1 = some nu_b <= 0). */
+rf_status rf_binned_nll_grad_async(rf_binned* m, int32_t n_sets, const double* d_counts, const double* d_theta,
+                                   double* d_out, int32_t* d_flags, void* stream);
+/* Expected counts nu_b (DEVICE n_sets x n_bins) at DEVICE theta, for toys. */
+rf_status rf_binned_expected(rf_binned* m, int32_t n_sets, const double* d_theta, double* d_nu, void* stream);
+
 /* ------------------------------------------------------------ measurement */
 
 /* Re-copy host columns (same count and dtypes as the dataset was created

@@ -18,6 +18,11 @@ KIND = {"obs": 0, "param": 1, "gauss": 2, "exp": 3, "gaussexp": 4, "cheb": 5, "p
 RF_F64, RF_F32 = 0, 1
 
 
+class rf_modifier(C.Structure):
+    _fields_ = [("sample", C.c_int32), ("kind", C.c_int32), ("param", C.c_int32), ("k_lo", C.c_double),
+                ("k_hi", C.c_double)]
+
+
 class rf_node(C.Structure):
     _fields_ = [("kind", C.c_int32), ("n_in", C.c_int32), ("in_", C.c_int32 * 8), ("value", C.c_double),
                 ("lo", C.c_double), ("hi", C.c_double), ("is_free", C.c_int32)]
@@ -58,6 +63,13 @@ SIGNATURES = {
     "rf_probe": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, _dp]),
     "rf_nll_grad_noalloc": (C.c_int, [_vp, C.POINTER(_vp), _ip, C.c_int64, _vp, _vp, _vp, _vp]),
     "rf_nll_grad_stream": (C.c_int, [_vp, _vp, C.POINTER(_vp), _dp, _dp, _dp, _vp]),
+    "rf_binned_create": (C.c_int, [C.c_int32, C.c_int32, _ip, _ip, _dp, C.c_int32, _ip, C.c_int32, _vp, _dp,
+                                   C.POINTER(_vp)]),
+    "rf_binned_destroy": (None, [_vp]),
+    "rf_binned_n_params": (C.c_int32, [_vp]),
+    "rf_binned_nll_grad": (C.c_int, [_vp, C.c_int32, _dp, _dp, _dp, _dp]),
+    "rf_binned_nll_grad_async": (C.c_int, [_vp, C.c_int32, _vp, _vp, _vp, _vp, _vp]),
+    "rf_binned_expected": (C.c_int, [_vp, C.c_int32, _vp, _vp, _vp]),
     "rf_shard": (C.c_int, [C.c_int64, C.c_int64, C.c_int32, C.c_int32, _i64p, _i64p]),
     "rf_nll_grad_partial": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "rf_combine_partials": (C.c_int, [_dp, _ip, C.c_int32, C.c_int32, C.c_int32, _dp, _ip]),

@@ -437,3 +437,61 @@ def math_eval(fn: int, d_x, d_y, stream=None):
     FP64 ones (10-13) elementwise on CUDA float64 tensors."""
     L.check(L.load().rf_math_eval(fn, C.c_void_p(d_x.data_ptr()), C.c_void_p(d_y.data_ptr()), d_x.numel(),
                                   _stream(stream)))
+
+
+# ------------------------------------------------------ binned likelihood
+
+class BinnedModel:
+    """A HistFactory-style binned model (rf_binned_*), built from the plain
+    data of workloads.binned_model: n_bins, bin0, nominal, constrained,
+    modifiers = (sample, kind, param, k_lo, k_hi, h_lo, h_hi)."""
+
+    def __init__(self, spec):
+        lib = L.load()
+        nom = [np.ascontiguousarray(h, dtype=np.float64) for h in spec["nominal"]]
+        bin0 = np.ascontiguousarray(spec["bin0"], dtype=np.int32)
+        nb = np.array([len(h) for h in nom], dtype=np.int32)
+        nominal = np.concatenate(nom)
+        con = np.ascontiguousarray([1 if c else 0 for c in spec["constrained"]], dtype=np.int32)
+        mods = spec["modifiers"]
+        arr = (L.rf_modifier * max(1, len(mods)))()
+        hd = []
+        for j, (smp, kind, par, klo, khi, lo, hi) in enumerate(mods):
+            arr[j] = L.rf_modifier(int(smp), int(kind), int(par), float(klo), float(khi))
+            if kind == 2:
+                hd += [np.asarray(lo, dtype=np.float64), np.asarray(hi, dtype=np.float64)]
+        hdata = np.concatenate(hd) if hd else np.zeros(1)
+        ip = C.POINTER(C.c_int32)
+        h = C.c_void_p()
+        L.check(lib.rf_binned_create(int(spec["n_bins"]), len(nom), bin0.ctypes.data_as(ip), nb.ctypes.data_as(ip),
+                                     _dp(nominal), len(con), con.ctypes.data_as(ip), len(mods), C.cast(arr, C.c_void_p),
+                                     _dp(hdata), C.byref(h)))
+        self._h = h
+        self.n_bins = int(spec["n_bins"])
+        self.n_params = lib.rf_binned_n_params(h)
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            L.load().rf_binned_destroy(self._h)
+            self._h = None
+
+    def nll_grad(self, counts, theta, allow_domain=False):
+        """counts (n_sets, n_bins), theta (n_sets, n_params) -> (nll, grad)."""
+        counts = np.ascontiguousarray(np.atleast_2d(counts), dtype=np.float64)
+        theta = np.ascontiguousarray(np.atleast_2d(theta), dtype=np.float64)
+        S = counts.shape[0]
+        nll = np.zeros(S)
+        g = np.zeros((S, self.n_params))
+        allow = (L.RF_OK, L.RF_E_DOMAIN) if allow_domain else (L.RF_OK,)
+        L.check(L.load().rf_binned_nll_grad(self._h, S, _dp(counts), _dp(theta), _dp(nll), _dp(g)), allow)
+        return nll, g
+
+    def nll_grad_async(self, d_counts, d_theta, d_out, d_flags, stream=None):
+        """Device tensors: counts (S, n_bins), theta (S, P), out (S, 1 + P), flags (S,) int32."""
+        L.check(L.load().rf_binned_nll_grad_async(self._h, d_counts.shape[0], C.c_void_p(d_counts.data_ptr()),
+                                                  C.c_void_p(d_theta.data_ptr()), C.c_void_p(d_out.data_ptr()),
+                                                  C.c_void_p(d_flags.data_ptr()), _stream(stream)))
+
+    def expected(self, d_theta, d_nu, stream=None):
+        L.check(L.load().rf_binned_expected(self._h, d_theta.shape[0], C.c_void_p(d_theta.data_ptr()),
+                                            C.c_void_p(d_nu.data_ptr()), _stream(stream)))
