@@ -286,10 +286,15 @@ rf_status rf_nll_grad_stream(const rf_model* m, rf_data* d, const void* const* h
  * bins [bin0[s], bin0[s] + nbins[s]) with nominal rates (concatenated in
  * sample order); modifiers tie a sample to one parameter theta_k:
  *   RF_MOD_NORMFACTOR  nu *= theta_k (typically a free, unconstrained scale)
- *   RF_MOD_NORMSYS     nu *= k_hi^alpha (alpha >= 0) or k_lo^-alpha (alpha < 0)
- *   RF_MOD_HISTOSYS    nu += alpha (h_hi - h) (alpha >= 0) or alpha (h - h_lo),
- *                      bin by bin, before the factors; h_lo then h_hi (nbins
- *                      each) follow in hist_data in modifier order
+ *   RF_MOD_NORMSYS     nu *= exp(a alpha + b g(alpha)), a, b = (log k_hi -+
+ *                      log k_lo) / 2
+ *   RF_MOD_HISTOSYS    nu += a_i alpha + b_i g(alpha) bin by bin, before the
+ *                      factors, a_i = (h_hi - h_lo)/2, b_i = (h_hi + h_lo)/2 -
+ *                      h; h_lo then h_hi (nbins each) follow in hist_data in
+ *                      modifier order
+ * with g = alpha^2 for |alpha| <= 1, 2|alpha| - 1 beyond: quadratic
+ * interpolation between the -1, 0, +1 sigma points and linear extrapolation
+ * (in log for normsys), continuous with its first derivative.
  * nu_b = sum over the samples on bin b; for bin counts n_b
  *   NLL = sum_b (nu_b - n_b log nu_b) + sum_{constrained k} theta_k^2 / 2
  * (Poisson terms without log n_b!, unit-Gaussian constraints without their
@@ -316,6 +321,13 @@ rf_status rf_binned_nll_grad(rf_binned* m, int32_t n_sets, const double* counts,
  * n_params) (NLL then gradient), d_flags n_sets (1 = some nu_b <= 0). */
 rf_status rf_binned_nll_grad_async(rf_binned* m, int32_t n_sets, const double* d_counts, const double* d_theta,
                                    double* d_out, int32_t* d_flags, void* stream);
+/* Maximum-likelihood fits of n_sets binned datasets at once (the batched
+ * BFGS of rf_fit, one device launch per round over the active datasets):
+ * counts HOST n_sets x n_bins, theta0 HOST n_sets x n_params (starts), lo/hi
+ * HOST n_params bounds (lo >= hi: unbounded), results as rf_fit. */
+rf_status rf_binned_fit(rf_binned* m, int32_t n_sets, const double* counts, const double* theta0, const double* lo,
+                        const double* hi, const rf_fit_opts* opts, double* theta_hat, double* nll_min, double* cov,
+                        int32_t* n_evals, int32_t* fit_status);
 /* Expected counts nu_b (DEVICE n_sets x n_bins) at DEVICE theta, for toys. */
 rf_status rf_binned_expected(rf_binned* m, int32_t n_sets, const double* d_theta, double* d_nu, void* stream);
 

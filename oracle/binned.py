@@ -10,11 +10,15 @@ channels of samples with +-1 sigma systematic histograms).  Definitions:
 * samples s with nominal rates h_s[i] on the contiguous bins b0_s + i;
 * modifiers of a sample, each tied to one parameter theta_k:
     normfactor  nu *= theta_k
-    normsys     nu *= eta(alpha) = k_hi^alpha (alpha >= 0), k_lo^(-alpha)
-                (alpha < 0)                      (exponential interpolation)
-    histosys    nu += alpha (h_hi - h) (alpha >= 0), alpha (h - h_lo)
-                (alpha < 0), bin by bin; the factors multiply the sum
-                (piecewise-linear interpolation)
+    normsys     nu *= eta(alpha) = exp(a alpha + b g(alpha)),
+                a = (log k_hi - log k_lo)/2, b = (log k_hi + log k_lo)/2
+    histosys    nu += delta(alpha) = a_i alpha + b_i g(alpha) bin by bin,
+                a_i = (h_hi - h_lo)/2, b_i = (h_hi + h_lo)/2 - h; the
+                factors multiply the sum
+  with g(alpha) = alpha^2 for |alpha| <= 1 and 2|alpha| - 1 beyond: the
+  variation is quadratic inside +-1 sigma and linear outside (in log for
+  normsys), continuous with a continuous first derivative, and reaches
+  k_hi, k_lo and h_hi, h_lo at alpha = +1, -1
   so nu_s[i] = prod(normfactors) prod(eta) (h_s[i] + sum delta_m[i]);
 * expected count of bin b: nu_b = sum of nu_s over the samples on b;
 * NLL(theta) = sum_b (nu_b - n_b log nu_b) + sum over constrained
@@ -32,6 +36,13 @@ from typing import List
 import numpy as np
 
 NORMFACTOR, NORMSYS, HISTOSYS = 0, 1, 2
+
+
+def interp_g(alpha: float):
+    """g(alpha) = alpha^2 inside +-1, 2|alpha| - 1 outside, and g'(alpha)."""
+    if abs(alpha) <= 1.0:
+        return alpha * alpha, 2.0 * alpha
+    return 2.0 * abs(alpha) - 1.0, 2.0 if alpha > 0 else -2.0
 
 
 @dataclass
@@ -71,21 +82,21 @@ class BinnedModel:
             for m in self.modifiers:
                 if m.sample != s:
                     continue
-                a = float(theta[m.param])
+                al = float(theta[m.param])
+                g, dg = interp_g(al)
                 if m.kind == NORMFACTOR:
-                    factor *= a
-                    dlogf[m.param] += 1.0 / a
+                    factor *= al
+                    dlogf[m.param] += 1.0 / al
                 elif m.kind == NORMSYS:
-                    if a >= 0:
-                        factor *= m.k_hi ** a
-                        dlogf[m.param] += np.log(m.k_hi)
-                    else:
-                        factor *= m.k_lo ** (-a)
-                        dlogf[m.param] += -np.log(m.k_lo)
+                    a = 0.5 * (np.log(m.k_hi) - np.log(m.k_lo))
+                    b = 0.5 * (np.log(m.k_hi) + np.log(m.k_lo))
+                    factor *= np.exp(a * al + b * g)
+                    dlogf[m.param] += a + b * dg
                 else:  # HISTOSYS
-                    slope = (np.asarray(m.h_hi) - h) if a >= 0 else (h - np.asarray(m.h_lo))
-                    shape += a * slope
-                    dshape[:, m.param] += slope
+                    a = 0.5 * (np.asarray(m.h_hi) - np.asarray(m.h_lo))
+                    b = 0.5 * (np.asarray(m.h_hi) + np.asarray(m.h_lo)) - h
+                    shape += a * al + b * g
+                    dshape[:, m.param] += a + b * dg
             nu = factor * shape
             dnu = factor * dshape + nu[:, None] * dlogf[None, :]
             out.append(nu)

@@ -70,6 +70,7 @@ SIGNATURES = {
     "rf_binned_nll_grad": (C.c_int, [_vp, C.c_int32, _dp, _dp, _dp, _dp]),
     "rf_binned_nll_grad_async": (C.c_int, [_vp, C.c_int32, _vp, _vp, _vp, _vp, _vp]),
     "rf_binned_expected": (C.c_int, [_vp, C.c_int32, _vp, _vp, _vp]),
+    "rf_binned_fit": (C.c_int, [_vp, C.c_int32, _dp, _dp, _dp, _dp, _vp, _dp, _dp, _dp, _ip, _ip]),
     "rf_shard": (C.c_int, [C.c_int64, C.c_int64, C.c_int32, C.c_int32, _i64p, _i64p]),
     "rf_nll_grad_partial": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "rf_combine_partials": (C.c_int, [_dp, _ip, C.c_int32, C.c_int32, C.c_int32, _dp, _ip]),

@@ -492,6 +492,26 @@ class BinnedModel:
                                                   C.c_void_p(d_theta.data_ptr()), C.c_void_p(d_out.data_ptr()),
                                                   C.c_void_p(d_flags.data_ptr()), _stream(stream)))
 
+    def fit(self, counts, theta0, lo, hi, tol_edm: float = 1e-7, max_evals: int = 1000, want_cov=True):
+        """Batched fits of the datasets (rows of counts) from theta0; bounds
+        lo/hi per parameter.  Returns dict(theta, nll, cov, n_evals, status)."""
+        counts = np.ascontiguousarray(np.atleast_2d(counts), dtype=np.float64)
+        S, P = counts.shape[0], self.n_params
+        th0 = np.ascontiguousarray(np.broadcast_to(np.asarray(theta0, dtype=np.float64), (S, P)))
+        lo = np.ascontiguousarray(lo, dtype=np.float64)
+        hi = np.ascontiguousarray(hi, dtype=np.float64)
+        th = np.zeros((S, P))
+        nl = np.zeros(S)
+        cov = np.zeros((S, P, P)) if want_cov else None
+        ne = np.zeros(S, dtype=np.int32)
+        fs = np.zeros(S, dtype=np.int32)
+        opts = L.rf_fit_opts(tol_edm, max_evals, 1 if want_cov else 0, 0, 0)
+        ip = C.POINTER(C.c_int32)
+        L.check(L.load().rf_binned_fit(self._h, S, _dp(counts), _dp(th0), _dp(lo), _dp(hi),
+                                       C.cast(C.byref(opts), C.c_void_p), _dp(th), _dp(nl),
+                                       _dp(cov) if want_cov else None, ne.ctypes.data_as(ip), fs.ctypes.data_as(ip)))
+        return dict(theta=th, nll=nl, cov=cov, n_evals=ne, status=fs)
+
     def expected(self, d_theta, d_nu, stream=None):
         L.check(L.load().rf_binned_expected(self._h, d_theta.shape[0], C.c_void_p(d_theta.data_ptr()),
                                             C.c_void_p(d_nu.data_ptr()), _stream(stream)))

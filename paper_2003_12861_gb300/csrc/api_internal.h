@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -65,6 +66,17 @@ struct Workspace {
 };
 
 bool cuda_ok(cudaError_t e, const char* what);
+
+// The batched BFGS fit driver (fit.cpp): S independent problems of P
+// parameters, bounds lo/hi (lo >= hi: unbounded), start S x P.  Each round
+// evaluates all active problems' trial points with one call of `eval`
+// (active set indices; theta S x P in; nll S and gradient S x P out, all
+// indexed by set).  cov (S x P x P) may be null.
+using BatchEval = std::function<rf_status(const std::vector<int32_t>&, std::vector<double>&, std::vector<double>&,
+                                          std::vector<double>&)>;
+rf_status fit_batch(int S, int P, const double* lo, const double* hi, const double* start, double tol, int max_evals,
+                    bool want_cov, const BatchEval& eval, double* theta_hat, double* nll_min, double* cov,
+                    int32_t* n_evals, int32_t* fit_status);
 int sm_count();
 int64_t tree_nodes(int64_t chunks);
 

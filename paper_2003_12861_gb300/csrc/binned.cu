@@ -3,13 +3,16 @@
 // channels of samples with +-1 sigma systematic variations).
 //
 // nu_s[i] = prod(normfactors) prod(normsys eta) (h_s[i] + sum histosys
-// delta), eta = k_hi^alpha (alpha >= 0) or k_lo^-alpha, delta = alpha (h_hi
-// - h) or alpha (h - h_lo); nu_b = sum over the samples on bin b; NLL =
-// sum_b (nu_b - n_b log nu_b) + sum over constrained parameters theta^2/2.
-// d NLL / d theta_k = sum_b w_b d nu_b / d theta_k + [constrained] theta_k,
-// w_b = 1 - n_b / nu_b; per modifier of parameter k: a normfactor or normsys
-// on sample s contributes dlog(factor)/dtheta_k sum_i w nu_s[i], a histosys
-// contributes F_s sum_i w slope[i].
+// delta), eta = exp(a alpha + b g(alpha)) with a, b = (log k_hi -+ log
+// k_lo)/2, delta_i = a_i alpha + b_i g(alpha) with a_i = (h_hi - h_lo)/2,
+// b_i = (h_hi + h_lo)/2 - h, g = alpha^2 inside +-1 and 2|alpha| - 1
+// beyond (quadratic interpolation, linear extrapolation: continuous with a
+// continuous derivative, so quasi-Newton fits see no kink); nu_b = sum over
+// the samples on bin b; NLL = sum_b (nu_b - n_b log nu_b) + sum over
+// constrained parameters theta^2/2.  d NLL / d theta_k = sum_b w_b d nu_b /
+// d theta_k + [constrained] theta_k, w_b = 1 - n_b / nu_b; per modifier of
+// parameter k: a normfactor or normsys on sample s contributes dlog(factor)
+// / dtheta_k sum_i w nu_s[i], a histosys F_s sum_i w (a_i + b_i g').
 //
 // One block per dataset (persistent over datasets), FP64 throughout, every
 // sum in a fixed order (each thread's bins / samples / modifiers in index
@@ -32,10 +35,9 @@ constexpr int kBinnedThreads = 256;
 constexpr int kMaxBinnedBins = 8192, kMaxBinnedSamples = 2048;
 
 // Dynamic shared memory of the kernels: theta, F and Ssum per sample, W per
-// bin, one partial sum per thread, then the parameters' signs.
+// bin, one partial sum per thread, g and g' per parameter.
 size_t binned_smem(int n_params, int n_samples, int n_bins) {
-  return sizeof(double) * ((size_t)n_params + 2 * (size_t)n_samples + (size_t)n_bins + kBinnedThreads) +
-         sizeof(int) * (size_t)n_params;
+  return sizeof(double) * (3 * (size_t)n_params + 2 * (size_t)n_samples + (size_t)n_bins + kBinnedThreads);
 }
 
 enum ModKind : int32_t { MOD_NORMFACTOR = 0, MOD_NORMSYS = 1, MOD_HISTOSYS = 2 };
@@ -55,19 +57,19 @@ struct BinnedDev {
   const int32_t* param;
   const int32_t* msample;
   const int32_t* mhs;         // per modifier: its histosys index, or -1
-  const double* lk_lo;        // normsys: log k_lo, log k_hi
-  const double* lk_hi;
+  const double* ns_a;         // normsys: a, b of log eta = a alpha + b g(alpha)
+  const double* ns_b;
   const int32_t* hs_param;    // per histosys: parameter, sample
   const int32_t* hs_sample;
-  const int64_t* hs_ofs;      // per histosys: its slopes (h - h_lo) then (h_hi - h), nb each, in `slope`
-  const double* slope;
-  // The same slopes transposed per sample for the weighted sums: sample s's
-  // histosys j (its j-th in shs order) at local bin i sits at
-  // tbase[s] + i * (histosys of s) + j, in slope_dn (h - h_lo) and slope_up.
+  const int64_t* hs_ofs;      // per histosys: a_i then b_i, nb each, in `coef`
+  const double* coef;
+  // The same coefficients transposed per sample for the weighted sums:
+  // sample s's histosys j (its j-th in shs order) at local bin i sits at
+  // tbase[s] + i * (histosys of s) + j, in coef_a and coef_b.
   const int64_t* tbase;
   const int32_t* g_sample;    // per position in shs: its sample
-  const double* slope_dn;
-  const double* slope_up;
+  const double* coef_a;
+  const double* coef_b;
   const int32_t* bin_start;   // per bin: its entries (CSR, sample order)
   const int32_t* bin_entry;
   const int32_t* pmod_start;  // per parameter: its modifiers (CSR, modifier order)
@@ -75,47 +77,43 @@ struct BinnedDev {
   const int32_t* constrained;
 };
 
-// The slopes of histosys h for a parameter value of sign `up` (1: alpha >=
-// 0, the h_hi side).  The sign is decided once per parameter and dataset as
-// an integer: an FP64 comparison per term would occupy the FP64 unit as
-// long as the multiply-add itself.
-__device__ __forceinline__ const double* hs_slopes(const BinnedDev& m, int h, int n, int up) {
-  return m.slope + m.hs_ofs[h] + (up ? n : 0);
-}
-
-// theta and its signs into smem, then the sample factors F (normfactors and
-// normsys).
-__device__ __forceinline__ void sample_factors(const BinnedDev& m, const double* th_g, double* th, int* up,
-                                               double* F) {
+// theta, g(theta) and g'(theta) into smem (once per parameter and dataset:
+// an FP64 comparison per term would occupy the FP64 unit as long as the
+// multiply-add itself), then the sample factors F: the normfactors times
+// one exponential of the normsys exponents' sum.
+__device__ __forceinline__ void sample_factors(const BinnedDev& m, const double* th_g, double* th, double* gk,
+                                               double* dgk, double* F) {
   for (int k = threadIdx.x; k < m.n_params; k += kBinnedThreads) {
     const double a = th_g[k];
     th[k] = a;
-    up[k] = a >= 0.0;
+    const bool in = fabs(a) <= 1.0;
+    gk[k] = in ? a * a : 2.0 * fabs(a) - 1.0;
+    dgk[k] = in ? 2.0 * a : (a > 0.0 ? 2.0 : -2.0);
   }
   __syncthreads();
   for (int s = threadIdx.x; s < m.n_samples; s += kBinnedThreads) {
-    double f = 1.0;
+    double f = 1.0, le = 0.0;
     for (int j = m.smod_start[s]; j < m.smod_start[s + 1]; ++j) {
-      const int md = m.smod[j];
-      const double a = th[m.param[md]];
-      if (m.kind[md] == MOD_NORMFACTOR) f *= a;
-      else f *= a >= 0.0 ? exp(a * m.lk_hi[md]) : exp(-a * m.lk_lo[md]);
+      const int md = m.smod[j], k = m.param[md];
+      if (m.kind[md] == MOD_NORMFACTOR) f *= th[k];
+      else le = fma(m.ns_b[md], gk[k], fma(m.ns_a[md], th[k], le));
     }
-    F[s] = f;
+    F[s] = le != 0.0 ? f * exp(le) : f;
   }
   __syncthreads();
 }
 
 // nu of every (sample, bin) entry: consecutive threads take consecutive
-// bins of a sample, so its histosys slopes are read coalesced.
-__device__ __forceinline__ void entry_rates(const BinnedDev& m, const double* th, const int* up, const double* F,
+// bins of a sample, so its histosys coefficients are read coalesced.
+__device__ __forceinline__ void entry_rates(const BinnedDev& m, const double* th, const double* gk, const double* F,
                                             double* nu_e) {
   for (int e = threadIdx.x; e < m.n_entries; e += kBinnedThreads) {
     const int s = m.esample[e], i = e - m.eofs[s], n = m.nb[s];
     double shape = m.nominal[e];
     for (int j = m.shs_start[s]; j < m.shs_start[s + 1]; ++j) {
       const int h = m.shs[j], k = m.hs_param[h];
-      shape = fma(th[k], hs_slopes(m, h, n, up[k])[i], shape);
+      const double* c = m.coef + m.hs_ofs[h] + i;
+      shape = fma(c[n], gk[k], fma(c[0], th[k], shape));
     }
     nu_e[e] = F[s] * shape;
   }
@@ -124,25 +122,27 @@ __device__ __forceinline__ void entry_rates(const BinnedDev& m, const double* th
 // out[set]: NLL then gradient (1 + n_params); flags[set]: 1 if some bin has
 // nu <= 0 (NLL +inf).  scratch: per block n_entries (entry rates) +
 // n_hs (histosys sums) doubles.
-__global__ void __launch_bounds__(kBinnedThreads) binned_kernel(const BinnedDev m, int n_sets, const double* counts,
-                                                                 const double* theta, double* out, int32_t* flags,
-                                                                 double* scratch) {
+// sets: null, or the dataset (row of counts) of each of the n_sets points.
+__global__ void __launch_bounds__(kBinnedThreads) binned_kernel(const BinnedDev m, int n_sets, const int32_t* sets,
+                                                                 const double* counts, const double* theta,
+                                                                 double* out, int32_t* flags, double* scratch) {
   extern __shared__ double smem[];
   double* th = smem;
   double* F = th + m.n_params;
   double* Ssum = F + m.n_samples;
   double* W = Ssum + m.n_samples;
   double* part = W + m.n_bins;
-  int* up = (int*)(part + kBinnedThreads);
+  double* gk = part + kBinnedThreads;
+  double* dgk = gk + m.n_params;
   __shared__ int bad;
   const int tid = threadIdx.x;
   double* nu_e = scratch + (size_t)blockIdx.x * (m.n_entries + m.n_hs);
   double* T = nu_e + m.n_entries;
   for (int set = blockIdx.x; set < n_sets; set += gridDim.x) {
-    const double* n = counts + (size_t)set * m.n_bins;
+    const double* n = counts + (size_t)(sets ? sets[set] : set) * m.n_bins;
     if (tid == 0) bad = 0;
-    sample_factors(m, theta + (size_t)set * m.n_params, th, up, F);
-    entry_rates(m, th, up, F, nu_e);
+    sample_factors(m, theta + (size_t)set * m.n_params, th, gk, dgk, F);
+    entry_rates(m, th, gk, F, nu_e);
     __syncthreads();
     // bins: expected count, weight 1 - n/nu, the Poisson term
     double acc = 0.0;
@@ -159,23 +159,26 @@ __global__ void __launch_bounds__(kBinnedThreads) binned_kernel(const BinnedDev 
     }
     part[tid] = acc;
     __syncthreads();
-    // per sample sum_i w nu_s[i] (a thread each); per histosys sum_i w
-    // slope[i] (a warp each: lanes over bins, then a butterfly)
+    // per sample sum_i w nu_s[i]; per histosys sum_i w (a_i + b_i g')
     for (int s = tid; s < m.n_samples; s += kBinnedThreads) {
       double a = 0.0;
       for (int i = 0; i < m.nb[s]; ++i) a += W[m.bin0[s] + i] * nu_e[m.eofs[s] + i];
       Ssum[s] = a;
     }
     // (a thread each, bins in order; consecutive threads read consecutive
-    // slopes of the transposed layout)
+    // coefficients of the transposed layout)
     for (int g = tid; g < m.n_hs; g += kBinnedThreads) {
       const int s = m.g_sample[g], h = m.shs[g];
       const int nh = m.shs_start[s + 1] - m.shs_start[s], j = g - m.shs_start[s];
-      const double* sl = (up[m.hs_param[h]] ? m.slope_up : m.slope_dn) + m.tbase[s] + j;
+      const double* ca = m.coef_a + m.tbase[s] + j;
+      const double* cb = m.coef_b + m.tbase[s] + j;
       const double* w = W + m.bin0[s];
-      double a = 0.0;
-      for (int i = 0; i < m.nb[s]; ++i) a = fma(w[i], sl[(size_t)i * nh], a);
-      T[h] = a;
+      double ta = 0.0, tb = 0.0;
+      for (int i = 0; i < m.nb[s]; ++i) {
+        ta = fma(w[i], ca[(size_t)i * nh], ta);
+        tb = fma(w[i], cb[(size_t)i * nh], tb);
+      }
+      T[h] = fma(dgk[m.hs_param[h]], tb, ta);
     }
     // NLL: the threads' partial sums by a fixed tree
     for (int o = kBinnedThreads / 2; o > 0; o >>= 1) {
@@ -191,7 +194,7 @@ __global__ void __launch_bounds__(kBinnedThreads) binned_kernel(const BinnedDev 
       for (int j = m.pmod_start[k]; j < m.pmod_start[k + 1]; ++j) {
         const int md = m.pmod[j], s = m.msample[md];
         if (m.kind[md] == MOD_NORMFACTOR) g += Ssum[s] / a;
-        else if (m.kind[md] == MOD_NORMSYS) g += Ssum[s] * (up[k] ? m.lk_hi[md] : -m.lk_lo[md]);
+        else if (m.kind[md] == MOD_NORMSYS) g += Ssum[s] * fma(m.ns_b[md], dgk[k], m.ns_a[md]);
         else g += F[s] * T[m.mhs[md]];
       }
       if (m.constrained[k]) g += a;
@@ -215,11 +218,12 @@ __global__ void __launch_bounds__(kBinnedThreads) binned_expected_kernel(const B
   extern __shared__ double smem[];
   double* th = smem;
   double* F = th + m.n_params;
-  int* up = (int*)(F + m.n_samples);
+  double* gk = F + m.n_samples;
+  double* dgk = gk + m.n_params;
   double* nu_e = scratch + (size_t)blockIdx.x * (m.n_entries + m.n_hs);
   for (int set = blockIdx.x; set < n_sets; set += gridDim.x) {
-    sample_factors(m, theta + (size_t)set * m.n_params, th, up, F);
-    entry_rates(m, th, up, F, nu_e);
+    sample_factors(m, theta + (size_t)set * m.n_params, th, gk, dgk, F);
+    entry_rates(m, th, gk, F, nu_e);
     __syncthreads();
     for (int b = threadIdx.x; b < m.n_bins; b += kBinnedThreads) {
       double nu = 0.0;
@@ -238,11 +242,11 @@ __global__ void __launch_bounds__(kBinnedThreads) binned_expected_kernel(const B
 
 struct rf_binned {
   int32_t n_bins = 0, n_samples = 0, n_params = 0, n_mods = 0, n_entries = 0, n_hs = 0;
-  rf::DevBuf bin0, nb, eofs, esample, nominal, smod_start, smod, shs_start, shs, kind, param, msample, mhs, lk_lo,
-      lk_hi, hs_param, hs_sample, hs_ofs, slope, tbase, g_sample, slope_dn, slope_up, bin_start, bin_entry, pmod_start,
-      pmod, constrained;
-  rf::DevBuf scratch, counts, theta, out, flags;
-  rf::HostBuf h_out, h_flags;
+  rf::DevBuf bin0, nb, eofs, esample, nominal, smod_start, smod, shs_start, shs, kind, param, msample, mhs, ns_a,
+      ns_b, hs_param, hs_sample, hs_ofs, coef, tbase, g_sample, coef_a, coef_b, bin_start, bin_entry, pmod_start, pmod,
+      constrained;
+  rf::DevBuf scratch, counts, theta, out, flags, sets;
+  rf::HostBuf h_out, h_flags, h_theta, h_sets;
   rf::BinnedDev dev{};
   int grid = 0;
   size_t smem = 0;
@@ -259,10 +263,10 @@ bool upload(DevBuf& b, const std::vector<T>& v) {
 }
 
 rf_status launch_binned(rf_binned* m, int32_t n_sets, const double* d_counts, const double* d_theta, double* d_out,
-                        int32_t* d_flags, cudaStream_t st) {
+                        int32_t* d_flags, cudaStream_t st, const int32_t* d_sets = nullptr) {
   if (n_sets == 0) return RF_OK;
   const int grid = std::min(n_sets, m->grid);
-  binned_kernel<<<grid, kBinnedThreads, m->smem, st>>>(m->dev, n_sets, d_counts, d_theta, d_out, d_flags,
+  binned_kernel<<<grid, kBinnedThreads, m->smem, st>>>(m->dev, n_sets, d_sets, d_counts, d_theta, d_out, d_flags,
                                                         (double*)m->scratch.p);
   return cuda_ok(cudaGetLastError(), "binned launch") ? RF_OK : RF_E_CUDA;
 }
@@ -297,10 +301,10 @@ rf_status rf_binned_create(int32_t n_bins, int32_t n_samples, const int32_t* bin
     return RF_E_INVALID;
   }
   std::vector<int32_t> kind(n_mods), param(n_mods), msample(n_mods), mhs(n_mods, -1);
-  std::vector<double> lk_lo(n_mods, 0.0), lk_hi(n_mods, 0.0);
+  std::vector<double> ns_a(n_mods, 0.0), ns_b(n_mods, 0.0);
   std::vector<int32_t> hs_param, hs_sample;
   std::vector<int64_t> hs_ofs;
-  std::vector<double> slope;
+  std::vector<double> coef;
   int64_t hd = 0;
   for (int j = 0; j < n_mods; ++j) {
     const rf_modifier& md = mods[j];
@@ -317,8 +321,8 @@ rf_status rf_binned_create(int32_t n_bins, int32_t n_samples, const int32_t* bin
     param[j] = md.param;
     msample[j] = md.sample;
     if (md.kind == RF_MOD_NORMSYS) {
-      lk_lo[j] = std::log(md.k_lo);
-      lk_hi[j] = std::log(md.k_hi);
+      ns_a[j] = 0.5 * (std::log(md.k_hi) - std::log(md.k_lo));
+      ns_b[j] = 0.5 * (std::log(md.k_hi) + std::log(md.k_lo));
     }
     if (md.kind == RF_MOD_HISTOSYS) {
       if (!hist_data) {
@@ -331,9 +335,9 @@ rf_status rf_binned_create(int32_t n_bins, int32_t n_samples, const int32_t* bin
       mhs[j] = (int32_t)hs_param.size();
       hs_param.push_back(md.param);
       hs_sample.push_back(md.sample);
-      hs_ofs.push_back((int64_t)slope.size());
-      for (int i = 0; i < n; ++i) slope.push_back(h[i] - lo[i]);  // alpha < 0
-      for (int i = 0; i < n; ++i) slope.push_back(hi[i] - h[i]);  // alpha >= 0
+      hs_ofs.push_back((int64_t)coef.size());
+      for (int i = 0; i < n; ++i) coef.push_back(0.5 * (hi[i] - lo[i]));
+      for (int i = 0; i < n; ++i) coef.push_back(0.5 * (hi[i] + lo[i]) - h[i]);
       hd += 2 * (int64_t)n;
     }
   }
@@ -358,19 +362,19 @@ rf_status rf_binned_create(int32_t n_bins, int32_t n_samples, const int32_t* bin
     else smod[sfill[msample[j]]++] = j;
     pmod[pfill[param[j]]++] = j;
   }
-  // transposed slopes per sample
+  // transposed coefficients per sample
   std::vector<int64_t> tbase(n_samples);
   std::vector<int32_t> g_sample(shs.size());
-  std::vector<double> slope_dn, slope_up;
+  std::vector<double> coef_a, coef_b;
   for (int s = 0; s < n_samples; ++s) {
     const int nh = shs_start[s + 1] - shs_start[s], n = nbins[s];
-    tbase[s] = (int64_t)slope_dn.size();
+    tbase[s] = (int64_t)coef_a.size();
     for (int g = shs_start[s]; g < shs_start[s + 1]; ++g) g_sample[g] = s;
     for (int i = 0; i < n; ++i)
       for (int j = 0; j < nh; ++j) {
         const int h = shs[shs_start[s] + j];
-        slope_dn.push_back(slope[hs_ofs[h] + i]);
-        slope_up.push_back(slope[hs_ofs[h] + n + i]);
+        coef_a.push_back(coef[hs_ofs[h] + i]);
+        coef_b.push_back(coef[hs_ofs[h] + n + i]);
       }
   }
   std::vector<int32_t> bin_start(n_bins + 1, 0);
@@ -398,10 +402,10 @@ rf_status rf_binned_create(int32_t n_bins, int32_t n_samples, const int32_t* bin
                   upload(m->nominal, vnom) && upload(m->smod_start, smod_start) && upload(m->smod, smod) &&
                   upload(m->shs_start, shs_start) && upload(m->shs, shs) && upload(m->kind, kind) &&
                   upload(m->param, param) && upload(m->msample, msample) && upload(m->mhs, mhs) &&
-                  upload(m->lk_lo, lk_lo) && upload(m->lk_hi, lk_hi) && upload(m->hs_param, hs_param) &&
-                  upload(m->hs_sample, hs_sample) && upload(m->hs_ofs, hs_ofs) && upload(m->slope, slope) &&
-                  upload(m->tbase, tbase) && upload(m->g_sample, g_sample) && upload(m->slope_dn, slope_dn) &&
-                  upload(m->slope_up, slope_up) &&
+                  upload(m->ns_a, ns_a) && upload(m->ns_b, ns_b) && upload(m->hs_param, hs_param) &&
+                  upload(m->hs_sample, hs_sample) && upload(m->hs_ofs, hs_ofs) && upload(m->coef, coef) &&
+                  upload(m->tbase, tbase) && upload(m->g_sample, g_sample) && upload(m->coef_a, coef_a) &&
+                  upload(m->coef_b, coef_b) &&
                   upload(m->bin_start, bin_start) && upload(m->bin_entry, bin_entry) &&
                   upload(m->pmod_start, pmod_start) && upload(m->pmod, pmod) && upload(m->constrained, vcon);
   m->smem = binned_smem(n_params, n_samples, n_bins);
@@ -445,16 +449,16 @@ rf_status rf_binned_create(int32_t n_bins, int32_t n_samples, const int32_t* bin
   D.param = (const int32_t*)m->param.p;
   D.msample = (const int32_t*)m->msample.p;
   D.mhs = (const int32_t*)m->mhs.p;
-  D.lk_lo = (const double*)m->lk_lo.p;
-  D.lk_hi = (const double*)m->lk_hi.p;
+  D.ns_a = (const double*)m->ns_a.p;
+  D.ns_b = (const double*)m->ns_b.p;
   D.hs_param = (const int32_t*)m->hs_param.p;
   D.hs_sample = (const int32_t*)m->hs_sample.p;
   D.hs_ofs = (const int64_t*)m->hs_ofs.p;
-  D.slope = (const double*)m->slope.p;
+  D.coef = (const double*)m->coef.p;
   D.tbase = (const int64_t*)m->tbase.p;
   D.g_sample = (const int32_t*)m->g_sample.p;
-  D.slope_dn = (const double*)m->slope_dn.p;
-  D.slope_up = (const double*)m->slope_up.p;
+  D.coef_a = (const double*)m->coef_a.p;
+  D.coef_b = (const double*)m->coef_b.p;
   D.bin_start = (const int32_t*)m->bin_start.p;
   D.bin_entry = (const int32_t*)m->bin_entry.p;
   D.pmod_start = (const int32_t*)m->pmod_start.p;
@@ -522,6 +526,61 @@ rf_status rf_binned_expected(rf_binned* m, int32_t n_sets, const double* d_theta
   binned_expected_kernel<<<std::min(n_sets, m->grid), kBinnedThreads, m->smem, (cudaStream_t)stream>>>(
       m->dev, n_sets, d_theta, d_nu, (double*)m->scratch.p);
   return cuda_ok(cudaGetLastError(), "binned launch") ? RF_OK : RF_E_CUDA;
+}
+
+rf_status rf_binned_fit(rf_binned* m, int32_t n_sets, const double* counts, const double* theta0, const double* lo,
+                        const double* hi, const rf_fit_opts* opts, double* theta_hat, double* nll_min, double* cov,
+                        int32_t* n_evals, int32_t* fit_status) {
+  if (!m || n_sets < 0 || (n_sets > 0 && (!counts || !theta0 || !lo || !hi || !theta_hat || !nll_min || !n_evals ||
+                                          !fit_status))) {
+    set_error("rf_binned_fit: bad argument");
+    return RF_E_INVALID;
+  }
+  if (n_sets == 0) return RF_OK;
+  const int P = m->n_params, B = m->n_bins, S = n_sets;
+  const double tol = (opts && opts->tol_edm > 0.0) ? opts->tol_edm : 1e-7;
+  const int max_evals = (opts && opts->max_evals > 0) ? opts->max_evals : 1000;
+  const bool want_cov = opts && opts->want_cov && cov;
+  if (!m->counts.ensure(sizeof(double) * (size_t)S * B) || !m->theta.ensure(sizeof(double) * (size_t)S * std::max(P, 1)) ||
+      !m->out.ensure(sizeof(double) * (size_t)S * (1 + P)) || !m->flags.ensure(sizeof(int32_t) * S) ||
+      !m->sets.ensure(sizeof(int32_t) * S) || !m->h_out.ensure(sizeof(double) * (size_t)S * (1 + P)) ||
+      !m->h_theta.ensure(sizeof(double) * (size_t)S * std::max(P, 1)) || !m->h_sets.ensure(sizeof(int32_t) * S))
+    return RF_E_OOM;
+  if (!cuda_ok(cudaMemcpy(m->counts.p, counts, sizeof(double) * (size_t)S * B, cudaMemcpyHostToDevice), "binned fit"))
+    return RF_E_CUDA;
+  cudaStream_t st = nullptr;
+  // One round: the active sets' points packed, one launch, results scattered.
+  auto eval = [&](const std::vector<int32_t>& active, std::vector<double>& th, std::vector<double>& nll,
+                  std::vector<double>& grad) -> rf_status {
+    const int n = (int)active.size();
+    double* ht = (double*)m->h_theta.p;
+    int32_t* hs = (int32_t*)m->h_sets.p;
+    for (int a = 0; a < n; ++a) {
+      hs[a] = active[a];
+      std::memcpy(ht + (size_t)a * P, &th[(size_t)active[a] * P], sizeof(double) * P);
+    }
+    if (!cuda_ok(cudaMemcpyAsync(m->theta.p, ht, sizeof(double) * (size_t)n * P, cudaMemcpyHostToDevice, st),
+                 "binned fit") ||
+        !cuda_ok(cudaMemcpyAsync(m->sets.p, hs, sizeof(int32_t) * n, cudaMemcpyHostToDevice, st), "binned fit"))
+      return RF_E_CUDA;
+    const rf_status r = launch_binned(m, n, (const double*)m->counts.p, (const double*)m->theta.p, (double*)m->out.p,
+                                      (int32_t*)m->flags.p, st, (const int32_t*)m->sets.p);
+    if (r != RF_OK) return r;
+    if (!cuda_ok(cudaMemcpyAsync(m->h_out.p, m->out.p, sizeof(double) * (size_t)n * (1 + P), cudaMemcpyDeviceToHost,
+                                 st),
+                 "binned fit") ||
+        !cuda_ok(cudaStreamSynchronize(st), "binned fit"))
+      return RF_E_CUDA;
+    const double* o = (const double*)m->h_out.p;
+    for (int a = 0; a < n; ++a) {
+      const int s = active[a];
+      nll[s] = o[(size_t)a * (1 + P)];
+      for (int k = 0; k < P; ++k) grad[(size_t)s * P + k] = o[(size_t)a * (1 + P) + 1 + k];
+    }
+    return RF_OK;
+  };
+  return fit_batch(S, P, lo, hi, theta0, tol, max_evals, want_cov, eval, theta_hat, nll_min,
+                   want_cov ? cov : nullptr, n_evals, fit_status);
 }
 
 }  // extern "C"

@@ -485,6 +485,109 @@ struct Evaluator {
   }
 };
 
+// The batched fit driver: S independent problems of P parameters with
+// bounds lo/hi (lo >= hi: unbounded), started at `start` (S x P).  Each
+// round asks every active problem for one trial point and evaluates all of
+// them with one call of `eval` (active sets, theta S x P in, nll S and
+// gradient S x P out, indexed by set).  cov (S x P x P) may be null.
+rf_status fit_batch(int S, int P, const double* lo, const double* hi, const double* start, double tol, int max_evals,
+                    bool want_cov, const BatchEval& eval, double* theta_hat, double* nll_min, double* cov,
+                    int32_t* n_evals, int32_t* fit_status) {
+  (void)want_cov;
+  Coords co;
+  co.P = P;
+  co.lo.assign(lo, lo + P);
+  co.hi.assign(hi, hi + P);
+  co.bounded.resize(P);
+  for (int k = 0; k < P; ++k)
+    co.bounded[k] = co.lo[k] < co.hi[k] && std::isfinite(co.lo[k]) && std::isfinite(co.hi[k]);
+
+  std::vector<SetFit> fits(S);
+  std::vector<double> th((size_t)S * P), nll(S), grad((size_t)S * P);
+  for (int s = 0; s < S; ++s) {
+    SetFit& F = fits[s];
+    F.P = P;
+    F.x.assign(P, 0.0);
+    F.g.assign(P, 0.0);
+    F.p.assign(P, 0.0);
+    F.trial.assign(P, 0.0);
+    F.g_lo.assign(P, 0.0);
+    F.H.assign(P * P, 0.0);
+    for (int k = 0; k < P; ++k) F.H[k * P + k] = 1.0;
+    co.to_internal(start + (size_t)s * P, F.trial.data());
+    F.phase = INIT;
+  }
+  Pool pool(S >= 1024 ? pool_threads() : 1);
+  std::vector<int32_t> active;
+  std::vector<double> jc((size_t)S * std::max(P, 1));
+  while (true) {
+    active.clear();
+    for (int s = 0; s < S; ++s)
+      if (fits[s].phase != DONE) active.push_back(s);
+    if (active.empty()) break;
+    pool.run((int64_t)active.size(), [&](int64_t i) {
+      const int s = active[i];
+      co.to_theta_jac(fits[s].trial.data(), &th[(size_t)s * P], &jc[(size_t)s * P]);
+    });
+    const rf_status st = eval(active, th, nll, grad);
+    if (st != RF_OK) return st;
+    pool.run((int64_t)active.size(), [&](int64_t i) {
+      const int s = active[i];
+      double ga[kMaxFree];
+      for (int k = 0; k < P; ++k) ga[k] = grad[(size_t)s * P + k] * jc[(size_t)s * P + k];
+      fits[s].deliver(nll[s], ga, tol, max_evals);
+    });
+  }
+  for (int s = 0; s < S; ++s) {
+    co.to_theta(fits[s].x.data(), theta_hat + (size_t)s * P);
+    nll_min[s] = fits[s].status == RF_E_DOMAIN ? kInf : fits[s].f;
+    n_evals[s] = fits[s].evals;
+    fit_status[s] = fits[s].status;
+  }
+  if (cov) {
+    // Central differences of the analytic gradient, all sets per pass; the
+    // step is 1e-3 of each parameter's BFGS error estimate.
+    std::vector<double> Hs((size_t)S * P * P, 0.0), h((size_t)S * P);
+    std::vector<int32_t> ok_sets;
+    for (int s = 0; s < S; ++s) {
+      if (fits[s].status == RF_E_DOMAIN) continue;
+      ok_sets.push_back(s);
+      for (int k = 0; k < P; ++k) {
+        const double jk = co.jac(k, fits[s].x[k]);
+        const double sig = std::sqrt(std::max(0.0, fits[s].H[k * P + k])) * std::fabs(jk);
+        const double t = theta_hat[(size_t)s * P + k];
+        double hk = 1e-3 * sig;
+        if (!(hk > 1e-9 * std::max(1.0, std::fabs(t)))) hk = 1e-6 * std::max(1.0, std::fabs(t));
+        h[(size_t)s * P + k] = hk;
+      }
+    }
+    std::vector<double> gp((size_t)S * P), gm((size_t)S * P);
+    for (int k = 0; k < P && !ok_sets.empty(); ++k) {
+      for (int sign = 0; sign < 2; ++sign) {
+        for (int s : ok_sets) {
+          for (int j = 0; j < P; ++j) th[(size_t)s * P + j] = theta_hat[(size_t)s * P + j];
+          th[(size_t)s * P + k] += (sign == 0 ? 1.0 : -1.0) * h[(size_t)s * P + k];
+        }
+        const rf_status st = eval(ok_sets, th, nll, sign == 0 ? gp : gm);
+        if (st != RF_OK) return st;
+      }
+      for (int s : ok_sets)
+        for (int j = 0; j < P; ++j)
+          Hs[(size_t)s * P * P + j * P + k] =
+              (gp[(size_t)s * P + j] - gm[(size_t)s * P + j]) / (2.0 * h[(size_t)s * P + k]);
+    }
+    for (int s = 0; s < S; ++s) {
+      double* c = cov + (size_t)s * P * P;
+      std::vector<double> A(Hs.begin() + (size_t)s * P * P, Hs.begin() + (size_t)(s + 1) * P * P);
+      for (int i = 0; i < P; ++i)
+        for (int j = 0; j < i; ++j) A[i * P + j] = A[j * P + i] = 0.5 * (A[i * P + j] + A[j * P + i]);
+      if (fits[s].status == RF_E_DOMAIN || !invert(A, P, c))
+        std::fill(c, c + P * P, std::numeric_limits<double>::quiet_NaN());
+    }
+  }
+  return RF_OK;
+}
+
 }  // namespace rf
 
 using namespace rf;
@@ -516,99 +619,12 @@ extern "C" rf_status rf_fit(const rf_model* m, const rf_data* d, const double* t
     return s == RF_E_DOMAIN ? RF_OK : s;
   }
 
-  Coords co;
-  co.P = P;
-  co.lo = m->m.lo;
-  co.hi = m->m.hi;
-  co.bounded.resize(P);
-  for (int k = 0; k < P; ++k)
-    co.bounded[k] = co.lo[k] < co.hi[k] && std::isfinite(co.lo[k]) && std::isfinite(co.hi[k]);
-
-  std::vector<SetFit> fits(S);
-  std::vector<double> th((size_t)S * P), nll(S), grad((size_t)S * P);
-  for (int s = 0; s < S; ++s) {
-    SetFit& F = fits[s];
-    F.P = P;
-    F.x.assign(P, 0.0);
-    F.g.assign(P, 0.0);
-    F.p.assign(P, 0.0);
-    F.trial.assign(P, 0.0);
-    F.g_lo.assign(P, 0.0);
-    F.H.assign(P * P, 0.0);
-    for (int k = 0; k < P; ++k) F.H[k * P + k] = 1.0;
-    std::vector<double> t0(P);
-    for (int k = 0; k < P; ++k) t0[k] = theta0 ? theta0[(size_t)s * P + k] : m->m.theta_default[k];
-    co.to_internal(t0.data(), F.trial.data());
-    F.phase = INIT;
-  }
+  std::vector<double> start((size_t)S * P);
+  for (int s = 0; s < S; ++s)
+    for (int k = 0; k < P; ++k) start[(size_t)s * P + k] = theta0 ? theta0[(size_t)s * P + k] : m->m.theta_default[k];
   Evaluator ev(m, dd, !(opts && opts->no_graph == 1));
-  Pool pool(S >= 1024 ? pool_threads() : 1);
-  std::vector<int32_t> active;
-  std::vector<double> jc((size_t)S * std::max(P, 1));
-  while (true) {
-    active.clear();
-    for (int s = 0; s < S; ++s)
-      if (fits[s].phase != DONE) active.push_back(s);
-    if (active.empty()) break;
-    pool.run((int64_t)active.size(), [&](int64_t i) {
-      const int s = active[i];
-      co.to_theta_jac(fits[s].trial.data(), &th[(size_t)s * P], &jc[(size_t)s * P]);
-    });
-    const rf_status st = ev.run(active, th, nll, grad);
-    if (st != RF_OK) return st;
-    pool.run((int64_t)active.size(), [&](int64_t i) {
-      const int s = active[i];
-      double ga[kMaxFree];
-      for (int k = 0; k < P; ++k) ga[k] = grad[(size_t)s * P + k] * jc[(size_t)s * P + k];
-      fits[s].deliver(nll[s], ga, tol, max_evals);
-    });
-  }
-  for (int s = 0; s < S; ++s) {
-    co.to_theta(fits[s].x.data(), theta_hat + (size_t)s * P);
-    nll_min[s] = fits[s].status == RF_E_DOMAIN ? kInf : fits[s].f;
-    n_evals[s] = fits[s].evals;
-    fit_status[s] = fits[s].status;
-  }
-  if (want_cov) {
-    // Central differences of the analytic gradient, all sets per pass; the
-    // step is 1e-3 of each parameter's BFGS error estimate.
-    std::vector<double> Hs((size_t)S * P * P, 0.0), h((size_t)S * P);
-    std::vector<int32_t> ok_sets;
-    for (int s = 0; s < S; ++s) {
-      if (fits[s].status == RF_E_DOMAIN) continue;
-      ok_sets.push_back(s);
-      for (int k = 0; k < P; ++k) {
-        const double jk = co.jac(k, fits[s].x[k]);
-        const double sig = std::sqrt(std::max(0.0, fits[s].H[k * P + k])) * std::fabs(jk);
-        const double t = theta_hat[(size_t)s * P + k];
-        double hk = 1e-3 * sig;
-        if (!(hk > 1e-9 * std::max(1.0, std::fabs(t)))) hk = 1e-6 * std::max(1.0, std::fabs(t));
-        h[(size_t)s * P + k] = hk;
-      }
-    }
-    std::vector<double> gp((size_t)S * P), gm((size_t)S * P);
-    for (int k = 0; k < P && !ok_sets.empty(); ++k) {
-      for (int sign = 0; sign < 2; ++sign) {
-        for (int s : ok_sets) {
-          for (int j = 0; j < P; ++j) th[(size_t)s * P + j] = theta_hat[(size_t)s * P + j];
-          th[(size_t)s * P + k] += (sign == 0 ? 1.0 : -1.0) * h[(size_t)s * P + k];
-        }
-        const rf_status st = ev.run(ok_sets, th, nll, sign == 0 ? gp : gm);
-        if (st != RF_OK) return st;
-      }
-      for (int s : ok_sets)
-        for (int j = 0; j < P; ++j)
-          Hs[(size_t)s * P * P + j * P + k] =
-              (gp[(size_t)s * P + j] - gm[(size_t)s * P + j]) / (2.0 * h[(size_t)s * P + k]);
-    }
-    for (int s = 0; s < S; ++s) {
-      double* c = cov + (size_t)s * P * P;
-      std::vector<double> A(Hs.begin() + (size_t)s * P * P, Hs.begin() + (size_t)(s + 1) * P * P);
-      for (int i = 0; i < P; ++i)
-        for (int j = 0; j < i; ++j) A[i * P + j] = A[j * P + i] = 0.5 * (A[i * P + j] + A[j * P + i]);
-      if (fits[s].status == RF_E_DOMAIN || !invert(A, P, c))
-        std::fill(c, c + P * P, std::numeric_limits<double>::quiet_NaN());
-    }
-  }
-  return RF_OK;
+  return fit_batch(S, P, m->m.lo.data(), m->m.hi.data(), start.data(), tol, max_evals, want_cov,
+                   [&](const std::vector<int32_t>& active, std::vector<double>& th, std::vector<double>& nll,
+                       std::vector<double>& grad) { return ev.run(active, th, nll, grad); },
+                   theta_hat, nll_min, want_cov ? cov : nullptr, n_evals, fit_status);
 }

@@ -97,3 +97,34 @@ def test_async_matches_host_call():
     torch.cuda.synchronize()
     o = out.cpu().numpy()
     assert np.array_equal(o[:, 0], nll) and np.array_equal(o[:, 1:], g)
+
+
+def test_batched_binned_fits_match_scipy_on_the_oracle():
+    # Minimum of the oracle's NLL by scipy's L-BFGS-B (a library minimiser on
+    # the oracle's NLL and gradient) vs the library's batched fit.
+    from scipy.optimize import minimize
+    spec = W.binned_model(channels=3, bins=20, samples=4, nuisances=12, histosys_per_sample=4, normsys_per_sample=3)
+    om = B.from_spec(spec)
+    m = api.BinnedModel(spec)
+    P = spec["n_params"]
+    lo = np.array([0.01] * 3 + [-5.0] * (P - 3))
+    hi = np.array([5.0] * 3 + [5.0] * (P - 3))
+    truth = W.binned_toy_thetas(24, 17, P)
+    rng = np.random.Generator(np.random.PCG64(7))
+    counts = np.array([rng.poisson(om.expected(t)[0]) for t in truth], dtype=float)
+    start = np.concatenate([[1.0, 1.0, 1.0], np.zeros(P - 3)])
+    r = m.fit(counts, start, lo, hi, tol_edm=1e-10, want_cov=True)
+    assert np.all(r["status"] == 0)
+    for t in range(0, 24, 3):
+        f = lambda x: om.nll(x, counts[t])[:2]
+        # the oracle's own gradient vanishes at the fitted point: its EDM
+        # with the fit's covariance is below that of a 1e-3 sigma offset in
+        # every parameter (0.5 x 1e-6 x P)
+        g = om.nll(r["theta"][t], counts[t])[1]
+        assert 0.5 * g @ r["cov"][t] @ g < 0.5e-6 * P
+        # and a library minimiser (gradient-norm stopping, so |NLL| ~ 1e5
+        # does not stop it early) on the oracle finds the same point
+        ref = minimize(f, start, jac=True, method="BFGS", options={"gtol": 1e-8, "maxiter": 5000})
+        sig = np.sqrt(np.diag(r["cov"][t]))
+        assert np.all(np.abs(r["theta"][t] - ref.x) < 1e-3 * sig), (t, np.abs(r["theta"][t] - ref.x) / sig)
+        assert abs(r["nll"][t] - ref.fun) < 1e-6

@@ -75,18 +75,45 @@ def test_gradient_richardson(th):
             t = th.copy()
             t[k] += d
             return m.nll(t, n)[0]
-        # one-sided where the interpolation has a kink at 0
         h = 1e-3
-        if th[k] == 0.0 and k > 0:
-            d1 = (f(h) - f(0.0)) / h
-            d2 = (f(h / 2) - f(0.0)) / (h / 2)
-            num = 2 * d2 - d1
-            assert abs(num - g[k]) < 1e-5 * max(1.0, abs(g[k]))
-            continue
         c1 = (f(h) - f(-h)) / (2 * h)
         c2 = (f(h / 2) - f(-h / 2)) / h
         num = (4 * c2 - c1) / 3
-        assert abs(num - g[k]) < 1e-7 * max(1.0, abs(g[k]))
+        # g'' jumps at |alpha| = 1, where the extrapolation has a kink of
+        # size O(h) in the second derivative only
+        assert abs(num - g[k]) < 1e-6 * max(1.0, abs(g[k]))
+
+
+@pytest.mark.parametrize("alpha", [-1.0, 0.0, 1.0])
+def test_interpolation_is_continuously_differentiable(alpha):
+    # value and first derivative agree from both sides at 0 and +-1
+    h0, lo, hi = np.array([10.0]), np.array([7.0]), np.array([14.5])
+    m = B.BinnedModel(1, [0], [h0], [True, True], [B.Modifier(0, B.HISTOSYS, 0, h_lo=lo, h_hi=hi),
+                                                   B.Modifier(0, B.NORMSYS, 1, 0.8, 1.3)])
+    for k in range(2):
+        def nu(a):
+            t = np.zeros(2)
+            t[k] = a
+            return m.expected(t)[0][0]
+        e = 1e-7
+        left = (nu(alpha) - nu(alpha - e)) / e
+        right = (nu(alpha + e) - nu(alpha)) / e
+        assert abs(left - right) < 1e-5 * max(1.0, abs(left))
+        assert abs(nu(alpha + e) - nu(alpha - e)) < 1e-5
+
+
+def test_nominal_and_extrapolation():
+    h0, lo, hi = np.array([10.0, 4.0]), np.array([7.0, 5.0]), np.array([14.5, 3.0])
+    m = B.BinnedModel(2, [0], [h0], [True, True], [B.Modifier(0, B.HISTOSYS, 0, h_lo=lo, h_hi=hi),
+                                                   B.Modifier(0, B.NORMSYS, 1, 0.8, 1.3)])
+    assert np.array_equal(m.expected([0.0, 0.0])[0], h0)
+    # linear beyond +-1 sigma: at alpha = 2 the histosys gives h + 3 (h_hi - h) - (h_hi - h_lo) ... i.e.
+    # delta(2) = a 2 + b 3 with a, b from the +-1 sigma points
+    a, b = 0.5 * (hi - lo), 0.5 * (hi + lo) - h0
+    assert np.allclose(m.expected([2.0, 0.0])[0], h0 + 2 * a + 3 * b, rtol=1e-15)
+    # exponential beyond +-1 in log: eta(-2) = exp(-2 a + 3 b)
+    an, bn = 0.5 * (np.log(1.3) - np.log(0.8)), 0.5 * (np.log(1.3) + np.log(0.8))
+    assert np.allclose(m.expected([0.0, -2.0])[0], h0 * np.exp(-2 * an + 3 * bn), rtol=1e-15)
 
 
 def test_nonpositive_expectation_is_infinite():
