@@ -586,13 +586,15 @@ def run_binned(args, api, torch, dist, rank, world, local):
     e2e_s = (time.perf_counter() - t0) / k
     if rank != 0:
         return None
-    # batched fits of the 4096 datasets from the nominal point
+    # batched fits of 256 of the datasets from the nominal point (each
+    # fit's BFGS state holds a 256 x 256 inverse Hessian on the host)
+    n_fit = 256
     lo = np.array([0.01] * 3 + [-5.0] * (P - 3))
     hi = np.array([5.0] * 3 + [5.0] * (P - 3))
     start = np.concatenate([[1.0, 1.0, 1.0], np.zeros(P - 3)])
-    m.fit(hc[:64], start, lo, hi, want_cov=False)
+    m.fit(hc[:8], start, lo, hi, want_cov=False)
     t0 = time.perf_counter()
-    r = m.fit(hc, start, lo, hi, want_cov=False)
+    r = m.fit(hc[:n_fit], start, lo, hi, want_cov=False)
     fit_s = time.perf_counter() - t0
     fl = binned_flops(spec)
     fp64 = api.probe(0)
@@ -609,7 +611,7 @@ def run_binned(args, api, torch, dist, rank, world, local):
         "e2e": {"value": world * S / e2e_s, "unit": "datasets/s", "h2d_bytes_per_step": S * (Bn + P) * 8,
                 "d2h_bytes_per_step": S * (1 + P) * 8 + S * 4},
         "gpu_launches": args.steps, "clocks": clk.summary(),
-        "fits": {"toy_fits_per_s": S / fit_s, "mean_evals": float(r["n_evals"].mean()),
+        "fits": {"datasets": n_fit, "fits_per_s": n_fit / fit_s, "mean_evals": float(r["n_evals"].mean()),
                  "max_evals": int(r["n_evals"].max()), "converged_frac": float((r["status"] == 0).mean()),
                  "tol_edm": 1e-7, "start": "nominal (normfactors 1, nuisances 0)"},
     }

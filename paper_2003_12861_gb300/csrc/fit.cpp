@@ -88,8 +88,9 @@ class Pool {
     for (std::thread& t : workers_) t.join();
   }
   int size() const { return 1 + (int)workers_.size(); }
-  void run(int64_t n, const std::function<void(int64_t)>& f) {
-    if (workers_.empty() || n < 1024) {
+  // min_n: the smallest n worth splitting (the dispatch costs ~10 us)
+  void run(int64_t n, const std::function<void(int64_t)>& f, int64_t min_n = 1024) {
+    if (workers_.empty() || n < min_n) {
       for (int64_t i = 0; i < n; ++i) f(i);
       return;
     }
@@ -97,6 +98,7 @@ class Pool {
       std::lock_guard<std::mutex> lk(mu_);
       job_ = &f;
       n_ = n;
+      chunk_ = std::max<int64_t>(1, std::min<int64_t>(64, n / (4 * size())));
       next_.store(0);
       busy_ = (int)workers_.size();
       ++gen_;
@@ -109,12 +111,12 @@ class Pool {
   }
 
  private:
-  static constexpr int64_t kChunk = 64;
+  int64_t chunk_ = 64;
   void work(const std::function<void(int64_t)>& f, int64_t n) {
     while (true) {
-      const int64_t i0 = next_.fetch_add(kChunk);
+      const int64_t i0 = next_.fetch_add(chunk_);
       if (i0 >= n) return;
-      const int64_t i1 = std::min(n, i0 + kChunk);
+      const int64_t i1 = std::min(n, i0 + chunk_);
       for (int64_t i = i0; i < i1; ++i) f(i);
     }
   }
@@ -190,6 +192,7 @@ struct SetFit {
   std::vector<double> g_lo;
   int trials = 0;
   std::vector<double> trial;  // point to evaluate next (internal)
+  std::vector<double> w_s, w_y, w_hy, w_ga;  // scratch of the update and the round (P each)
 
   void set_trial(double a) {
     a_cur = a;
@@ -236,7 +239,8 @@ struct SetFit {
 
   // Accept the step to alpha with value fa and gradient ga.
   void accept(double a, double fa, const double* ga, double tol, int max_evals) {
-    double s[kMaxFree], y[kMaxFree];
+    double* s = w_s.data();
+    double* y = w_y.data();
     for (int k = 0; k < P; ++k) {
       s[k] = a * p[k];
       y[k] = ga[k] - g[k];
@@ -249,7 +253,8 @@ struct SetFit {
     first_step = false;
     if (sy > 1e-300) {
       const double rho = 1.0 / sy;
-      double Hy[kMaxFree] = {0.0};
+      double* Hy = w_hy.data();
+      std::fill(w_hy.begin(), w_hy.end(), 0.0);
       for (int i = 0; i < P; ++i)
         for (int j = 0; j < P; ++j) Hy[i] += H[i * P + j] * y[j];
       const double yHy = dot(y, Hy, P);
@@ -512,12 +517,19 @@ rf_status fit_batch(int S, int P, const double* lo, const double* hi, const doub
     F.p.assign(P, 0.0);
     F.trial.assign(P, 0.0);
     F.g_lo.assign(P, 0.0);
+    F.w_s.assign(P, 0.0);
+    F.w_y.assign(P, 0.0);
+    F.w_hy.assign(P, 0.0);
+    F.w_ga.assign(P, 0.0);
     F.H.assign(P * P, 0.0);
     for (int k = 0; k < P; ++k) F.H[k * P + k] = 1.0;
     co.to_internal(start + (size_t)s * P, F.trial.data());
     F.phase = INIT;
   }
-  Pool pool(S >= 1024 ? pool_threads() : 1);
+  // The per-set update is O(P^2): with many parameters even a few sets are
+  // worth spreading over threads.
+  const int64_t min_n = P >= 32 ? 2 : 1024;
+  Pool pool(S >= min_n ? pool_threads() : 1);
   std::vector<int32_t> active;
   std::vector<double> jc((size_t)S * std::max(P, 1));
   while (true) {
@@ -528,15 +540,15 @@ rf_status fit_batch(int S, int P, const double* lo, const double* hi, const doub
     pool.run((int64_t)active.size(), [&](int64_t i) {
       const int s = active[i];
       co.to_theta_jac(fits[s].trial.data(), &th[(size_t)s * P], &jc[(size_t)s * P]);
-    });
+    }, min_n);
     const rf_status st = eval(active, th, nll, grad);
     if (st != RF_OK) return st;
     pool.run((int64_t)active.size(), [&](int64_t i) {
       const int s = active[i];
-      double ga[kMaxFree];
+      double* ga = fits[s].w_ga.data();
       for (int k = 0; k < P; ++k) ga[k] = grad[(size_t)s * P + k] * jc[(size_t)s * P + k];
       fits[s].deliver(nll[s], ga, tol, max_evals);
-    });
+    }, min_n);
   }
   for (int s = 0; s < S; ++s) {
     co.to_theta(fits[s].x.data(), theta_hat + (size_t)s * P);
