@@ -187,6 +187,33 @@ __device__ __forceinline__ ff ff_log(const FFTables& T, ff a, bool& ok) {
   return fast_two_sum(out.hi, out.lo);
 }
 
+// ------------------------------------------------------- log of a product
+// A running product m 2^e of positive float-float factors, m kept in
+// [1, 2) by exact power-of-two scaling: sum_i log p_i = log(prod_i p_i)
+// costs one logarithm per product instead of one per factor.
+struct LogProd {
+  ff m;
+  int e;
+};
+__device__ __forceinline__ LogProd logprod_init() { return {{1.0f, 0.0f}, 0}; }
+// p in [2^-100, 2^100] (the caller checks).
+__device__ __forceinline__ void logprod_mul(LogProd& L, ff p) {
+  const ff m = ff_mul(L.m, p);
+  const int ex = ((__float_as_int(m.hi) >> 23) & 0xff) - 127;
+  const float sc = __int_as_float((127 - ex) << 23);  // 2^-ex, exact
+  L.m = {__fmul_rn(m.hi, sc), __fmul_rn(m.lo, sc)};
+  L.e += ex;
+}
+// log(m 2^e) = log(m) + e ln2, |e| < 2^12.
+__device__ __forceinline__ ff logprod_log(const FFTables& T, const LogProd& L, bool& ok) {
+  const ff lm = ff_log(T, L.m, ok);
+  const float ef = (float)L.e;
+  const ff e2 = two_prod(ef, kLn2e_2);
+  ff s = two_sum(__fmul_rn(ef, kLn2e_1), e2.hi);  // e ln2_1 exact (12-bit constant)
+  s.lo = __fadd_rn(s.lo, __fmaf_rn(ef, kLn2e_3, e2.lo));
+  return ff_add(fast_two_sum(s.hi, s.lo), lm);
+}
+
 // ---------------------------------------------------------------- rcp
 __device__ __forceinline__ ff ff_rcp(ff a) {
   float y0;

@@ -890,6 +890,7 @@ __global__ void __launch_bounds__(kLanes, ff_min_blocks(kShape)) events_ff(const
     ff acc[NP];
 #pragma unroll
     for (int j = 0; j < NP; ++j) acc[j] = {0.0f, 0.0f};
+    LogProd lpd = logprod_init();
     int qs = 0;
     unsigned myfb = 0u;
     const int k0 = part * kPartK;
@@ -902,7 +903,7 @@ __global__ void __launch_bounds__(kLanes, ff_min_blocks(kShape)) events_ff(const
       const FFIn<kShape> cur = ff_split_in<kShape>(cols, col, nxt);
       if (k + 1 < k0 + kPartK && e + kLanes < s_end) nxt = ff_load_raw<kShape>(cols, col, e + kLanes);
       int st = 0;
-      if (e < s_end) st = ff_event<kShape, kGrad, false>(T, kc, cur, acc);
+      if (e < s_end) st = ff_event<kShape, kGrad, false>(T, kc, cur, acc, lpd);
       const unsigned bs = __ballot_sync(0xffffffffu, st == 1);
       if (st == 1) sm.queue[warp][qs + __popc(bs & lt)] = (short)(e - base);
       if (st == 2) myfb |= 1u << k;
@@ -914,7 +915,7 @@ __global__ void __launch_bounds__(kLanes, ff_min_blocks(kShape)) events_ff(const
       const int j = j0 + lane;
       if (j < qs) {
         const int off = sm.queue[warp][j];
-        if (ff_event<kShape, kGrad, true>(T, kc, ff_load<kShape>(cols, col, base + off), acc) == 2)
+        if (ff_event<kShape, kGrad, true>(T, kc, ff_load<kShape>(cols, col, base + off), acc, lpd) == 2)
           atomicOr(&fbmask[off % kLanes], 1u << (off / kLanes));  // owner lane, event bit
       }
     }
@@ -941,7 +942,12 @@ __global__ void __launch_bounds__(kLanes, ff_min_blocks(kShape)) events_ff(const
         eval_generic<true, kGrad>(P, sm.C, x, acc64, &bad);
       }
     }
-    // the part's moments: reduce-scatter butterfly, then the warps in order
+    // sum log p of the lane's events from their product, then the part's
+    // moments: reduce-scatter butterfly, then the warps in order
+    {
+      bool lok = true;
+      acc[0] = logprod_log(T, lpd, lok);  // m in [1, 2): always in range
+    }
     warp_ff_reduce<NP>(acc, lane);
     if (ff_lane_writes<NP>(lane)) wacc[warp][ff_lane_index<NP>(lane)] = acc[0];
     if (any_fb) {

@@ -338,8 +338,11 @@ __device__ __forceinline__ FFIn<kShape> ff_load(const Columns& cols, const int* 
   return ff_split_in<kShape>(cols, col, ff_load_raw<kShape>(cols, col, e));
 }
 
+// p_i goes into the lane's running product L (its log is taken once per
+// part: sum log p_i = log prod p_i); the moments into acc[1..].
 template <int kShape, bool kGrad, bool kSlow>
-__device__ __forceinline__ int ff_event(const FFTables& T, const float* k, const FFIn<kShape>& in, ff* acc) {
+__device__ __forceinline__ int ff_event(const FFTables& T, const float* k, const FFIn<kShape>& in, ff* acc,
+                                        LogProd& L) {
   bool ok = in.ok, dropped = false;
   if constexpr (kShape == SHAPE_SUM_GAUSSEXP_CHEB2) {
     const ff t = in.x[0];
@@ -348,9 +351,9 @@ __device__ __forceinline__ int ff_event(const FFTables& T, const float* k, const
     const ff vs = decay_shape<kSlow>(T, k, t, &R, &u, ok, dropped);
     const ff pb = ff_add(ff_mul(ff_add(ff_mul(ldc(k, 10), t), ldc(k, 8)), t), ldc(k, 6));
     const ff p = ff_add(ff_mul(ldc(k, 4), vs), pb);
-    const ff lp = ff_log(T, p, ok);
+    ok = ok && p.hi > 7.9e-31f && p.hi < 1.2e30f;  // 2^-100 .. 2^100
     if (!ok || (dropped && p.hi < 1e-14f)) return 2;
-    ff_acc(acc[0], lp);
+    logprod_mul(L, p);
     if constexpr (kGrad) {
       const ff ip = ff_rcp(p);
       const ff E = ff_mul(vs, ip);
@@ -372,9 +375,9 @@ __device__ __forceinline__ int ff_event(const FFTables& T, const float* k, const
     const ff u = ff_mul(ff_sub(x, ldc(k, 0)), ldc(k, 2));
     const ff g = ff_exp0(T, ff_add(ff_scale(ff_sqr(u), -0.5f), ldc(k, 14)), ok, dropped);
     const ff p = ff_add(ff_mul(ldc(k, 4), g), ff_add(ff_mul(ldc(k, 8), x), ldc(k, 6)));
-    const ff lp = ff_log(T, p, ok);
+    ok = ok && p.hi > 7.9e-31f && p.hi < 1.2e30f;
     if (!ok || (dropped && p.hi < 1e-14f)) return 2;
-    ff_acc(acc[0], lp);
+    logprod_mul(L, p);
     if constexpr (kGrad) {
       const ff ip = ff_rcp(p);
       const ff G = ff_mul(g, ip);
@@ -402,9 +405,10 @@ __device__ __forceinline__ int ff_event(const FFTables& T, const float* k, const
     const ff pt = ff_add(ff_mul(ldc(kd, 4), vs),
                          ff_add(ff_mul(ff_add(ff_mul(ldc(kd, 10), t), ldc(kd, 8)), t), ldc(kd, 6)));
     const ff pa = ff_add(ff_mul(ff_add(ff_mul(ldc(k, 42), c), ldc(k, 40)), c), ldc(k, 38));
-    const ff lp = ff_log(T, ff_mul(ff_mul(pm, pt), pa), ok);
+    const ff p = ff_mul(ff_mul(pm, pt), pa);
+    ok = ok && p.hi > 7.9e-31f && p.hi < 1.2e30f;
     if (!ok || (dm && pm.hi < 1e-14f) || (dropped && pt.hi < 1e-14f)) return 2;
-    ff_acc(acc[0], lp);
+    logprod_mul(L, p);
     if constexpr (kGrad) {
       const ff ipm = ff_rcp(pm), ipt = ff_rcp(pt), ipa = ff_rcp(pa);
       const ff G = ff_mul(g, ipm);
