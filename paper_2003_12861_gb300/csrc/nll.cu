@@ -396,13 +396,41 @@ __device__ __forceinline__ Pair merge(Pair a, Pair b) {
   return {s, (a.c + b.c) + e};
 }
 
+// A lane's running product for sum_i log p_i = log(m) + e ln2: m multiplies
+// the mantissas of the p_i (in [1, 2), split from the bits exactly), e sums
+// their binary exponents.  One FP64 multiply per event instead of a log; a
+// lane takes at most 64 factors per chunk, so m < 2^64.
+struct LogProd64 {
+  double m;
+  int e;
+};
+
+__device__ __forceinline__ LogProd64 logprod64_init() { return {1.0, 0}; }
+
+// p > 0 and finite
+__device__ __forceinline__ void logprod64_mul(LogProd64& L, double p) {
+  int hi = __double2hiint(p), sh = 0;
+  if (hi < 0x00100000) {  // subnormal: scale by 2^64 (exact)
+    p *= 18446744073709551616.0;
+    hi = __double2hiint(p);
+    sh = 64;
+  }
+  L.e += (hi >> 20) - 1023 - sh;
+  L.m *= __hiloint2double((hi & 0x000fffff) | 0x3ff00000, __double2loint(p));
+}
+
+__device__ __forceinline__ double logprod64_log(const LogProd64& L) {
+  return log(L.m) + (double)L.e * 0.69314718055994530942;
+}
+
 // Generic graph interpreter for one event.  kFull = false: the fast path,
 // which returns false (and adds nothing) when some node needs its slow path.
-// Adds log p to acc[0] and the slot gradients to acc[1..]; counts events
-// with p <= 0 or not finite in *bad instead.
+// Multiplies p into the lane's running product L (the log p term) and adds
+// the slot gradients to acc[1..]; counts events with p <= 0 or not finite in
+// *bad instead.
 template <bool kFull, bool kGrad>
 __device__ bool eval_generic(const Program& P, const double* __restrict__ C, const double* x, double* acc,
-                             int* bad) {
+                             LogProd64& L, int* bad) {
   double v[kMaxPdf];
   const int N = P.n_pdf;
   for (int n = 0; n < N; ++n) {
@@ -475,7 +503,7 @@ __device__ bool eval_generic(const Program& P, const double* __restrict__ C, con
     ++*bad;
     return true;
   }
-  acc[0] += log(p);
+  logprod64_mul(L, p);
   if constexpr (!kGrad) {
     return true;
   } else {
@@ -758,13 +786,14 @@ __global__ void __launch_bounds__(kLanes) events_generic(const __grid_constant__
     double acc[kQMax];
     for (int q = 0; q < kQMax; ++q) acc[q] = 0.0;
     int bad = 0, qcnt = 0;
+    LogProd64 L = logprod64_init();
     double x[kMaxObs];
     for (int k = 0; k < kPerLane; ++k) {
       const int64_t e = base + tid + (int64_t)k * kLanes;
       bool slow = false;
       if (e < s_end) {
         for (int c = 0; c < P.n_obs; ++c) x[c] = load_col(cols, c, e);
-        slow = !eval_generic<false, kGrad>(P, sm.C, x, acc, &bad);
+        slow = !eval_generic<false, kGrad>(P, sm.C, x, acc, L, &bad);
       }
       if (P.has_slow) {
         const unsigned b = __ballot_sync(0xffffffffu, slow);
@@ -777,8 +806,9 @@ __global__ void __launch_bounds__(kLanes) events_generic(const __grid_constant__
     for (int j = lane; j < qcnt; j += 32) {
       const int64_t e = base + sm.queue[warp][j];
       for (int c = 0; c < P.n_obs; ++c) x[c] = load_col(cols, c, e);
-      eval_generic<true, kGrad>(P, sm.C, x, acc, &bad);
+      eval_generic<true, kGrad>(P, sm.C, x, acc, L, &bad);
     }
+    acc[0] += logprod64_log(L);
     (void)Q;
     finish_chunk(P, pass, sm, acc, bad, set, chunk, s_end - s_begin);
     __syncthreads();
@@ -934,13 +964,15 @@ __global__ void __launch_bounds__(kLanes, ff_min_blocks(kShape)) events_ff(const
       __syncthreads();
       for (int q = 0; q < kQMax; ++q) acc64[q] = 0.0;
       double x[kMaxObs];
+      LogProd64 L64 = logprod64_init();
       while (myfb) {
         const int k = __ffs(myfb) - 1;
         myfb &= myfb - 1u;
         const int64_t e = base + tid + (int64_t)k * kLanes;
         for (int c = 0; c < P.n_obs; ++c) x[c] = load_col(cols, c, e);
-        eval_generic<true, kGrad>(P, sm.C, x, acc64, &bad);
+        eval_generic<true, kGrad>(P, sm.C, x, acc64, L64, &bad);
       }
+      acc64[0] += logprod64_log(L64);
     }
     // sum log p of the lane's events from their product, then the part's
     // moments: reduce-scatter butterfly, then the warps in order
