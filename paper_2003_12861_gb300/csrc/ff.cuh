@@ -98,6 +98,16 @@ __device__ __forceinline__ ff ff_mul_f(ff a, float b) {
   p.lo = __fmaf_rn(a.lo, b, p.lo);
   return fast_two_sum(p.hi, p.lo);
 }
+// a b + c with one renormalisation: the product's error terms join the
+// sum's low word (the accuracy of ff_add(ff_mul(a, b), c), three fewer
+// operations).
+__device__ __forceinline__ ff ff_fma(ff a, ff b, ff c) {
+  const ff p = two_prod(a.hi, b.hi);
+  const ff s = two_sum(p.hi, c.hi);
+  float lo = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, p.lo));
+  lo = __fadd_rn(lo, __fadd_rn(c.lo, s.lo));
+  return fast_two_sum(s.hi, lo);
+}
 __device__ __forceinline__ ff ff_sqr(ff a) {
   ff p = two_prod(a.hi, a.hi);
   p.lo = __fmaf_rn(__fmul_rn(2.0f, a.hi), a.lo, p.lo);
@@ -246,7 +256,7 @@ __device__ __forceinline__ ff ff_erfcx(const FFTables& T, ff y, bool& ok) {
   float s = c[2 * 16];
   for (int k = 15; k >= kf; --k) s = __fmaf_rn(s, x.hi, c[2 * k]);
   ff acc = {s, 0.0f};
-  for (int k = kf - 1; k >= 0; --k) acc = ff_add(ff_mul(acc, x), ff{c[2 * k], c[2 * k + 1]});
+  for (int k = kf - 1; k >= 0; --k) acc = ff_fma(acc, x, ff{c[2 * k], c[2 * k + 1]});
   return piece >= 3 ? ff_mul(acc, v) : acc;
 }
 

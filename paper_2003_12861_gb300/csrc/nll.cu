@@ -610,6 +610,7 @@ struct SmemT {
   double wsum[kWarps][kQMax];
   int wbad[kWarps];
   QT queue[kWarps][kQueue];
+  int qn[kWarps];
   int item;
   int last;
 };
@@ -866,7 +867,8 @@ __host__ __device__ constexpr int pow2_at_least(int n) { return n <= 1 ? 1 : n <
 // work item u / 4 (a quarter of a 4096-event chunk, 8 events per lane), so
 // the last round of units is short.  Per lane the shape's moments are summed
 // in float-float; events in the decay resolution region are queued per warp
-// (ballot order) and evaluated after the fast pass; events outside the
+// (ballot order) and evaluated after the fast pass by all the block's
+// threads; events outside the
 // float-float range take the FP64 interpreter (FP64 sums).  At the end of a
 // part the warps' moments are merged in fixed order and stored as the part's
 // record; the block that completes the chunk's last part (arrival ticket)
@@ -939,15 +941,18 @@ __global__ void __launch_bounds__(kLanes, ff_min_blocks(kShape)) events_ff(const
       if (st == 2) myfb |= 1u << k;
       qs += __popc(bs);
     }
-    __syncwarp();
-    if (lane == 0 && qs > 0 && pass.slow) atomicAdd(pass.slow, (unsigned long long)qs);
-    for (int j0 = 0; j0 < qs; j0 += 32) {
-      const int j = j0 + lane;
-      if (j < qs) {
-        const int off = sm.queue[warp][j];
-        if (ff_event<kShape, kGrad, true>(T, kc, ff_load<kShape>(cols, col, base + off), acc, lpd) == 2)
-          atomicOr(&fbmask[off % kLanes], 1u << (off / kLanes));  // owner lane, event bit
-      }
+    // The block's queued events, in warp then ballot order, are shared out
+    // over all its threads (entry j to thread j mod 128), so only the last
+    // round of the block's queue leaves lanes idle.
+    if (lane == 0) sm.qn[warp] = qs;
+    __syncthreads();
+    const int q1 = sm.qn[0], q2 = q1 + sm.qn[1], q3 = q2 + sm.qn[2], qt = q3 + sm.qn[3];
+    if (tid == 0 && qt > 0 && pass.slow) atomicAdd(pass.slow, (unsigned long long)qt);
+    for (int j = tid; j < qt; j += kLanes) {
+      const int w = (j >= q1) + (j >= q2) + (j >= q3);
+      const int off = sm.queue[w][j - (w == 0 ? 0 : w == 1 ? q1 : w == 2 ? q2 : q3)];
+      if (ff_event<kShape, kGrad, true>(T, kc, ff_load<kShape>(cols, col, base + off), acc, lpd) == 2)
+        atomicOr(&fbmask[off % kLanes], 1u << (off / kLanes));  // owner lane, event bit
     }
     __syncthreads();
     myfb |= fbmask[tid];

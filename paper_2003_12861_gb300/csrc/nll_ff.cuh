@@ -263,7 +263,7 @@ __device__ __forceinline__ ff ff_exp0(const FFTables& T, ff x, bool& ok, bool& d
 template <bool kSlow>
 __device__ __forceinline__ ff decay_shape(const FFTables& T, const float* k, ff t, ff* R, ff* uo, bool& ok,
                                           bool& dropped) {
-  const ff logv = ff_sub(ldc(k, 0), ff_mul(t, ldc(k, 2)));
+  const ff logv = ff_fma(ff_neg(t), ldc(k, 2), ldc(k, 0));
   if (!kSlow) {
     *R = {0.0f, 0.0f};
     return ff_exp0(T, logv, ok, dropped);
@@ -274,7 +274,7 @@ __device__ __forceinline__ ff decay_shape(const FFTables& T, const float* k, ff 
   const bool neg = z.hi < 0.0f;
   const ff y = neg ? ff_neg(z) : z;
   const ff ex = ff_erfcx(T, y, ok);
-  const ff G = ff_exp0(T, ff_add(ff_scale(ff_sqr(u), -0.5f), ldc(k, 20)), ok, dropped);
+  const ff G = ff_exp0(T, ff_fma(ff_scale(u, -0.5f), u, ldc(k, 20)), ok, dropped);
   const ff half_g_ex = ff_scale(ff_mul(G, ex), 0.5f);
   const ff two_over_sqrtpi = {kTwoInvSqrtPi_hi, kTwoInvSqrtPi_lo};
   if (!neg) {
@@ -349,8 +349,8 @@ __device__ __forceinline__ int ff_event(const FFTables& T, const float* k, const
     if (!kSlow && __fmaf_rn(-t.hi, k[13], k[12]) >= kSlowZf) return ok ? 1 : 2;
     ff R, u;
     const ff vs = decay_shape<kSlow>(T, k, t, &R, &u, ok, dropped);
-    const ff pb = ff_add(ff_mul(ff_add(ff_mul(ldc(k, 10), t), ldc(k, 8)), t), ldc(k, 6));
-    const ff p = ff_add(ff_mul(ldc(k, 4), vs), pb);
+    const ff pb = ff_fma(ff_fma(ldc(k, 10), t, ldc(k, 8)), t, ldc(k, 6));
+    const ff p = ff_fma(ldc(k, 4), vs, pb);
     ok = ok && p.hi > 7.9e-31f && p.hi < 1.2e30f;  // 2^-100 .. 2^100
     if (!ok || (dropped && p.hi < 1e-14f)) return 2;
     logprod_mul(L, p);
@@ -373,8 +373,8 @@ __device__ __forceinline__ int ff_event(const FFTables& T, const float* k, const
   } else if constexpr (kShape == SHAPE_SUM_GAUSS_POLY1) {
     const ff x = in.x[0];
     const ff u = ff_mul(ff_sub(x, ldc(k, 0)), ldc(k, 2));
-    const ff g = ff_exp0(T, ff_add(ff_scale(ff_sqr(u), -0.5f), ldc(k, 14)), ok, dropped);
-    const ff p = ff_add(ff_mul(ldc(k, 4), g), ff_add(ff_mul(ldc(k, 8), x), ldc(k, 6)));
+    const ff g = ff_exp0(T, ff_fma(ff_scale(u, -0.5f), u, ldc(k, 14)), ok, dropped);
+    const ff p = ff_fma(ldc(k, 4), g, ff_fma(ldc(k, 8), x, ldc(k, 6)));
     ok = ok && p.hi > 7.9e-31f && p.hi < 1.2e30f;
     if (!ok || (dropped && p.hi < 1e-14f)) return 2;
     logprod_mul(L, p);
@@ -397,14 +397,13 @@ __device__ __forceinline__ int ff_event(const FFTables& T, const float* k, const
     const ff c = in.x[2];
     const ff um = ff_mul(ff_sub(m, ldc(k, 0)), ldc(k, 2));
     bool dm = false;
-    const ff g = ff_exp0(T, ff_add(ff_scale(ff_sqr(um), -0.5f), ldc(k, 14)), ok, dm);
-    const ff ym = ff_sub(ff_mul(m, ldc(k, 10)), ldc(k, 12));
-    const ff pm = ff_add(ff_mul(ldc(k, 4), g), ff_add(ff_mul(ldc(k, 8), ym), ldc(k, 6)));
+    const ff g = ff_exp0(T, ff_fma(ff_scale(um, -0.5f), um, ldc(k, 14)), ok, dm);
+    const ff ym = ff_fma(m, ldc(k, 10), ff_neg(ldc(k, 12)));
+    const ff pm = ff_fma(ldc(k, 4), g, ff_fma(ldc(k, 8), ym, ldc(k, 6)));
     ff R, u;
     const ff vs = decay_shape<kSlow>(T, kd, t, &R, &u, ok, dropped);
-    const ff pt = ff_add(ff_mul(ldc(kd, 4), vs),
-                         ff_add(ff_mul(ff_add(ff_mul(ldc(kd, 10), t), ldc(kd, 8)), t), ldc(kd, 6)));
-    const ff pa = ff_add(ff_mul(ff_add(ff_mul(ldc(k, 42), c), ldc(k, 40)), c), ldc(k, 38));
+    const ff pt = ff_fma(ldc(kd, 4), vs, ff_fma(ff_fma(ldc(kd, 10), t, ldc(kd, 8)), t, ldc(kd, 6)));
+    const ff pa = ff_fma(ff_fma(ldc(k, 42), c, ldc(k, 40)), c, ldc(k, 38));
     const ff p = ff_mul(ff_mul(pm, pt), pa);
     ok = ok && p.hi > 7.9e-31f && p.hi < 1.2e30f;
     if (!ok || (dm && pm.hi < 1e-14f) || (dropped && pt.hi < 1e-14f)) return 2;
