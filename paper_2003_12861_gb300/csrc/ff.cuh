@@ -93,6 +93,14 @@ __device__ __forceinline__ ff ff_mul(ff a, ff b) {
   p.lo = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, p.lo));
   return fast_two_sum(p.hi, p.lo);
 }
+// The product without the final renormalisation: |lo| may reach 2^-22 |hi|
+// instead of 2^-24.  Such a pair is as accurate as an operand of ff_mul,
+// ff_acc and ff_acc_mul; other functions take normalised pairs.
+__device__ __forceinline__ ff ff_mul_u(ff a, ff b) {
+  ff p = two_prod(a.hi, b.hi);
+  p.lo = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, p.lo));
+  return p;
+}
 __device__ __forceinline__ ff ff_mul_f(ff a, float b) {
   ff p = two_prod(a.hi, b);
   p.lo = __fmaf_rn(a.lo, b, p.lo);
@@ -120,6 +128,16 @@ __device__ __forceinline__ ff ff_scale(ff a, float pow2) { return {__fmul_rn(a.h
 __device__ __forceinline__ void ff_acc(ff& acc, ff x) {
   const ff s = two_sum(acc.hi, x.hi);
   acc.lo = __fadd_rn(acc.lo, __fadd_rn(s.lo, x.lo));
+  acc.hi = s.hi;
+}
+
+// acc += a b: the product's hi word through the exact two-sum, its error
+// terms into the low word.
+__device__ __forceinline__ void ff_acc_mul(ff& acc, ff a, ff b) {
+  const ff p = two_prod(a.hi, b.hi);
+  const ff s = two_sum(acc.hi, p.hi);
+  const float e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, p.lo));
+  acc.lo = __fadd_rn(acc.lo, __fadd_rn(s.lo, e));
   acc.hi = s.hi;
 }
 
@@ -206,9 +224,9 @@ struct LogProd {
   int e;
 };
 __device__ __forceinline__ LogProd logprod_init() { return {{1.0f, 0.0f}, 0}; }
-// p in [2^-100, 2^100] (the caller checks).
+// p in [2^-100, 2^100] (the caller checks); m is kept unnormalised.
 __device__ __forceinline__ void logprod_mul(LogProd& L, ff p) {
-  const ff m = ff_mul(L.m, p);
+  const ff m = ff_mul_u(L.m, p);
   const int ex = ((__float_as_int(m.hi) >> 23) & 0xff) - 127;
   const float sc = __int_as_float((127 - ex) << 23);  // 2^-ex, exact
   L.m = {__fmul_rn(m.hi, sc), __fmul_rn(m.lo, sc)};
@@ -216,7 +234,7 @@ __device__ __forceinline__ void logprod_mul(LogProd& L, ff p) {
 }
 // log(m 2^e) = log(m) + e ln2, |e| < 2^12.
 __device__ __forceinline__ ff logprod_log(const FFTables& T, const LogProd& L, bool& ok) {
-  const ff lm = ff_log(T, L.m, ok);
+  const ff lm = ff_log(T, fast_two_sum(L.m.hi, L.m.lo), ok);
   const float ef = (float)L.e;
   const ff e2 = two_prod(ef, kLn2e_2);
   ff s = two_sum(__fmul_rn(ef, kLn2e_1), e2.hi);  // e ln2_1 exact (12-bit constant)
@@ -225,14 +243,19 @@ __device__ __forceinline__ ff logprod_log(const FFTables& T, const LogProd& L, b
 }
 
 // ---------------------------------------------------------------- rcp
-__device__ __forceinline__ ff ff_rcp(ff a) {
+// y0 (1 + e) with e = 1 - a y0, unnormalised (see ff_mul_u)
+__device__ __forceinline__ ff ff_rcp_u(ff a) {
   float y0;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y0) : "f"(a.hi));
   const ff p = two_prod(a.hi, y0);
   float e = __fsub_rn(1.0f, p.hi);
   e = __fsub_rn(e, p.lo);
   e = __fmaf_rn(-a.lo, y0, e);
-  return fast_two_sum(y0, __fmul_rn(y0, e));
+  return {y0, __fmul_rn(y0, e)};
+}
+__device__ __forceinline__ ff ff_rcp(ff a) {
+  const ff r = ff_rcp_u(a);
+  return fast_two_sum(r.hi, r.lo);
 }
 
 // -------------------------------------------------------------- erfcx

@@ -84,7 +84,7 @@ __global__ void probe_trans_ff(double* out, int events, int n_exp, int n_erfc, i
     for (int k = 0; k < n_exp; ++k) ff_acc(acc, ff_exp(T, ff_mul_f(x, -(1.0f + 0.25f * k)), ok));
     for (int k = 0; k < n_erfc; ++k) ff_acc(acc, ff_erfcx(T, ff_add_f(ff_mul_f(x, 1.0f + 0.25f * k), 0.3f), ok));
     for (int k = 0; k < n_log; ++k) ff_acc(acc, ff_log(T, ff_add_f(x, (float)k), ok));
-    for (int k = 0; k < n_rcp; ++k) ff_acc(acc, ff_rcp(ff_add_f(x, (float)k)));
+    for (int k = 0; k < n_rcp; ++k) ff_acc(acc, ff_rcp_u(ff_add_f(x, (float)k)));
     x = ff_add(x, step);
   }
   out[blockIdx.x * blockDim.x + threadIdx.x] = ok ? ff_to_double(acc) : -1.0;

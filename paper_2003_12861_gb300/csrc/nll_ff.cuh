@@ -275,15 +275,15 @@ __device__ __forceinline__ ff decay_shape(const FFTables& T, const float* k, ff 
   const ff y = neg ? ff_neg(z) : z;
   const ff ex = ff_erfcx(T, y, ok);
   const ff G = ff_exp0(T, ff_fma(ff_scale(u, -0.5f), u, ldc(k, 20)), ok, dropped);
-  const ff half_g_ex = ff_scale(ff_mul(G, ex), 0.5f);
+  const ff half_g_ex = ff_scale(ff_mul_u(G, ex), 0.5f);
   const ff two_over_sqrtpi = {kTwoInvSqrtPi_hi, kTwoInvSqrtPi_lo};
   if (!neg) {
-    *R = ff_mul(two_over_sqrtpi, ff_rcp(ex));
+    *R = ff_mul_u(two_over_sqrtpi, ff_rcp_u(ex));
     return half_g_ex;
   }
   bool dq = false;  // exp(-z^2) only scales R
   const ff q = ff_exp0(T, ff_neg(ff_sqr(z)), ok, dq);
-  *R = ff_mul(ff_mul(two_over_sqrtpi, q), ff_rcp(ff_sub(ff{2.0f, 0.0f}, ff_mul(q, ex))));
+  *R = ff_mul_u(ff_mul_u(two_over_sqrtpi, q), ff_rcp_u(ff_fma(ff_neg(q), ex, ff{2.0f, 0.0f})));
   return ff_sub(ff_exp0(T, logv, ok, dropped), half_g_ex);
 }
 
@@ -355,18 +355,18 @@ __device__ __forceinline__ int ff_event(const FFTables& T, const float* k, const
     if (!ok || (dropped && p.hi < 1e-14f)) return 2;
     logprod_mul(L, p);
     if constexpr (kGrad) {
-      const ff ip = ff_rcp(p);
-      const ff E = ff_mul(vs, ip);
-      const ff ipt = ff_mul(ip, t);
+      const ff ip = ff_rcp_u(p);
+      const ff E = ff_mul_u(vs, ip);
+      const ff ipt = ff_mul_u(ip, t);
       ff_acc(acc[1], E);
-      ff_acc(acc[2], ff_mul(E, t));
+      ff_acc_mul(acc[2], E, t);
       ff_acc(acc[3], ip);
       ff_acc(acc[4], ipt);
-      ff_acc(acc[5], ff_mul(ipt, t));
+      ff_acc_mul(acc[5], ipt, t);
       if (kSlow) {
-        const ff ER = ff_mul(E, R);
+        const ff ER = ff_mul_u(E, R);
         ff_acc(acc[6], ER);
-        ff_acc(acc[7], ff_mul(ER, u));
+        ff_acc_mul(acc[7], ER, u);
       }
     }
     return 0;
@@ -379,14 +379,14 @@ __device__ __forceinline__ int ff_event(const FFTables& T, const float* k, const
     if (!ok || (dropped && p.hi < 1e-14f)) return 2;
     logprod_mul(L, p);
     if constexpr (kGrad) {
-      const ff ip = ff_rcp(p);
-      const ff G = ff_mul(g, ip);
-      const ff Gu = ff_mul(G, u);
+      const ff ip = ff_rcp_u(p);
+      const ff G = ff_mul_u(g, ip);
+      const ff Gu = ff_mul_u(G, u);
       ff_acc(acc[1], G);
       ff_acc(acc[2], Gu);
-      ff_acc(acc[3], ff_mul(Gu, u));
+      ff_acc_mul(acc[3], Gu, u);
       ff_acc(acc[4], ip);
-      ff_acc(acc[5], ff_mul(ip, x));
+      ff_acc_mul(acc[5], ip, x);
     }
     return 0;
   } else {  // PROD3
@@ -409,30 +409,30 @@ __device__ __forceinline__ int ff_event(const FFTables& T, const float* k, const
     if (!ok || (dm && pm.hi < 1e-14f) || (dropped && pt.hi < 1e-14f)) return 2;
     logprod_mul(L, p);
     if constexpr (kGrad) {
-      const ff ipm = ff_rcp(pm), ipt = ff_rcp(pt), ipa = ff_rcp(pa);
-      const ff G = ff_mul(g, ipm);
-      const ff Gu = ff_mul(G, um);
+      const ff ipm = ff_rcp_u(pm), ipt = ff_rcp_u(pt), ipa = ff_rcp_u(pa);
+      const ff G = ff_mul_u(g, ipm);
+      const ff Gu = ff_mul_u(G, um);
       ff_acc(acc[1], G);
       ff_acc(acc[2], Gu);
-      ff_acc(acc[3], ff_mul(Gu, um));
+      ff_acc_mul(acc[3], Gu, um);
       ff_acc(acc[4], ipm);
-      ff_acc(acc[5], ff_mul(ipm, ym));
-      const ff E = ff_mul(vs, ipt);
-      const ff it_ = ff_mul(ipt, t);
+      ff_acc_mul(acc[5], ipm, ym);
+      const ff E = ff_mul_u(vs, ipt);
+      const ff it_ = ff_mul_u(ipt, t);
       ff_acc(acc[6], E);
-      ff_acc(acc[7], ff_mul(E, t));
+      ff_acc_mul(acc[7], E, t);
       ff_acc(acc[8], ipt);
       ff_acc(acc[9], it_);
-      ff_acc(acc[10], ff_mul(it_, t));
+      ff_acc_mul(acc[10], it_, t);
       if (kSlow) {
-        const ff ER = ff_mul(E, R);
+        const ff ER = ff_mul_u(E, R);
         ff_acc(acc[11], ER);
-        ff_acc(acc[12], ff_mul(ER, u));
+        ff_acc_mul(acc[12], ER, u);
       }
-      const ff iac = ff_mul(ipa, c);
+      const ff iac = ff_mul_u(ipa, c);
       ff_acc(acc[13], ipa);
       ff_acc(acc[14], iac);
-      ff_acc(acc[15], ff_mul(iac, c));
+      ff_acc_mul(acc[15], iac, c);
     }
     return 0;
   }
