@@ -74,9 +74,23 @@ bool cuda_ok(cudaError_t e, const char* what);
 // indexed by set).  cov (S x P x P) may be null.
 using BatchEval = std::function<rf_status(const std::vector<int32_t>&, std::vector<double>&, std::vector<double>&,
                                           std::vector<double>&)>;
+// Optional split evaluation for pipelined rounds: the sets [0, split) and
+// [split, S) are evaluated as separate passes, launch queueing one and wait
+// finishing it, so the host updates one half while the other is evaluated;
+// events(sets) counts events, and the driver returns to whole-batch rounds
+// once the active events fall below min_events.
+struct SplitEval {
+  int64_t split = 0, min_events = 0;
+  std::function<rf_status(int, const std::vector<int32_t>&, const std::vector<double>&)> launch;
+  std::function<rf_status(int, std::vector<double>&, std::vector<double>&)> wait;
+  std::function<int64_t(const std::vector<int32_t>&)> events;
+};
+// Below this many active events a pass is short enough that the launch
+// latency of two half passes costs more than the host work they hide.
+constexpr int64_t kPipelineMinEvents = int64_t(1) << 21;
 rf_status fit_batch(int S, int P, const double* lo, const double* hi, const double* start, double tol, int max_evals,
-                    bool want_cov, const BatchEval& eval, double* theta_hat, double* nll_min, double* cov,
-                    int32_t* n_evals, int32_t* fit_status);
+                    bool want_cov, const BatchEval& eval, const SplitEval* split, double* theta_hat,
+                    double* nll_min, double* cov, int32_t* n_evals, int32_t* fit_status);
 int sm_count();
 int64_t tree_nodes(int64_t chunks);
 

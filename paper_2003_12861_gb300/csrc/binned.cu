@@ -579,7 +579,7 @@ rf_status rf_binned_fit(rf_binned* m, int32_t n_sets, const double* counts, cons
     }
     return RF_OK;
   };
-  return fit_batch(S, P, lo, hi, theta0, tol, max_evals, want_cov, eval, theta_hat, nll_min,
+  return fit_batch(S, P, lo, hi, theta0, tol, max_evals, want_cov, eval, nullptr, theta_hat, nll_min,
                    want_cov ? cov : nullptr, n_evals, fit_status);
 }
 

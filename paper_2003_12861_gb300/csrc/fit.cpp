@@ -63,7 +63,8 @@ struct Coords {
         jc[k] = 1.0;
         continue;
       }
-      const double sn = std::sin(x[k]), cs = std::cos(x[k]);
+      double sn, cs;
+      sincos(x[k], &sn, &cs);
       th[k] = lo[k] + (hi[k] - lo[k]) * (sn + 1.0) * 0.5;
       jc[k] = (hi[k] - lo[k]) * 0.5 * cs;
     }
@@ -399,26 +400,38 @@ bool invert(std::vector<double> A, int n, double* inv) {
 
 }  // namespace
 
-// One device pass over the sets in `active` at their trial points (theta),
-// results into nll/grad (indexed by set).  The pass (parameter upload, the
-// two kernels, result download) is captured once per work plan as a CUDA
-// graph and replayed.  The plan covers a superset of the active sets and is
-// rebuilt only when the events of still-active sets fall below 3/4 of the
-// planned events (finished sets are re-evaluated at their last point and
-// their results ignored) or a set outside the plan becomes active.
+// Device passes over active sets at their trial points (theta), results
+// into nll/grad (indexed by set).  A pass (parameter upload, the two
+// kernels, result download) is captured once per work plan as a CUDA graph
+// and replayed.  A plan covers a superset of the active sets and is rebuilt
+// only when the events of still-active sets fall below 3/4 of the planned
+// events (finished sets are re-evaluated at their last point and their
+// results ignored) or a set outside the plan becomes active.  Groups 0 and 1
+// serve the two halves of a pipelined fit (launch, then wait: while one
+// half's pass runs, the host updates the other half), group 2 whole-batch
+// passes (run).  All passes go to one stream, so they never overlap on the
+// device; only the planned sets' range of theta and results is copied.
 struct Evaluator {
+  struct Group {
+    Plan plan;
+    std::vector<int32_t> planned;
+    int64_t planned_events = 0;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t done = nullptr;
+  };
   const rf_model* m;
   rf_data* d;
-  Plan plan;
-  std::vector<int32_t> planned;
-  int64_t planned_events = 0;
   cudaStream_t st = nullptr;
-  cudaGraphExec_t exec = nullptr;
   bool use_graph = true;
+  Group grp[3];
 
   Evaluator(const rf_model* mm, rf_data* dd, bool graph) : m(mm), d(dd), use_graph(graph) {}
   ~Evaluator() {
-    if (exec) cudaGraphExecDestroy(exec);
+    if (st) cudaStreamSynchronize(st);
+    for (Group& G : grp) {
+      if (G.exec) cudaGraphExecDestroy(G.exec);
+      if (G.done) cudaEventDestroy(G.done);
+    }
     if (st) cudaStreamDestroy(st);
   }
 
@@ -428,65 +441,96 @@ struct Evaluator {
     return n;
   }
 
-  rf_status capture() {
-    if (exec) {
-      cudaGraphExecDestroy(exec);
-      exec = nullptr;
-    }
-    Workspace& w = d->ws;
-    const int P = m->m.prog.n_free, S = d->n_sets;
-    cudaGraph_t graph = nullptr;
-    if (!cuda_ok(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "graph capture")) return RF_E_CUDA;
-    cudaMemcpyAsync(w.theta.p, w.h_theta.p, sizeof(double) * S * P, cudaMemcpyHostToDevice, st);
-    launch_pass(m, d, plan, (const double*)w.theta.p, (double*)w.out.p, (int32_t*)w.flags.p, true, st);
-    cudaMemcpyAsync(w.h_out.p, w.out.p, sizeof(double) * S * (1 + P), cudaMemcpyDeviceToHost, st);
-    cudaMemcpyAsync(w.h_flags.p, w.flags.p, sizeof(int32_t) * S, cudaMemcpyDeviceToHost, st);
-    if (!cuda_ok(cudaStreamEndCapture(st, &graph), "graph capture")) return RF_E_CUDA;
-    const bool ok = cuda_ok(cudaGraphInstantiate(&exec, graph, 0), "graph instantiate");
-    cudaGraphDestroy(graph);
-    return ok ? RF_OK : RF_E_CUDA;
-  }
-
-  rf_status run(const std::vector<int32_t>& active, const std::vector<double>& theta, std::vector<double>& nll,
-                std::vector<double>& grad) {
-    bool covered = !planned.empty();
+  // Keeps or rebuilds G's plan for `active`; *rebuilt tells which.
+  bool replan(Group& G, const std::vector<int32_t>& active, bool* rebuilt) {
+    bool covered = !G.planned.empty();
     if (covered) {
       size_t j = 0;  // active and planned are both increasing
       for (int32_t s : active) {
-        while (j < planned.size() && planned[j] < s) ++j;
-        if (j == planned.size() || planned[j] != s) {
+        while (j < G.planned.size() && G.planned[j] < s) ++j;
+        if (j == G.planned.size() || G.planned[j] != s) {
           covered = false;
           break;
         }
       }
     }
     const int64_t need = events_of(active);
-    const bool rebuild = !covered || 4 * need < 3 * planned_events;
-    if (rebuild) {
-      if (!build_plan(d, active, &plan)) return RF_E_OOM;
-      planned = active;
-      planned_events = need;
+    *rebuilt = !covered || 4 * need < 3 * G.planned_events;
+    if (*rebuilt) {
+      if (!build_plan(d, active, &G.plan)) return false;
+      G.planned = active;
+      G.planned_events = need;
     }
-    if (!use_graph) {
-      const rf_status s = eval_host(m, d, plan, theta.data(), nll.data(), grad.data(), nullptr);
-      return s == RF_E_DOMAIN ? RF_OK : s;
+    return true;
+  }
+
+  rf_status capture(Group& G) {
+    if (G.exec) {
+      cudaGraphExecDestroy(G.exec);
+      G.exec = nullptr;
     }
+    Workspace& w = d->ws;
+    const int P = m->m.prog.n_free;
+    const size_t s0 = G.planned.front(), ns = (size_t)G.planned.back() + 1 - s0;
+    cudaGraph_t graph = nullptr;
+    if (!cuda_ok(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "graph capture")) return RF_E_CUDA;
+    cudaMemcpyAsync((double*)w.theta.p + s0 * P, (const double*)w.h_theta.p + s0 * P, sizeof(double) * ns * P,
+                    cudaMemcpyHostToDevice, st);
+    launch_pass(m, d, G.plan, (const double*)w.theta.p, (double*)w.out.p, (int32_t*)w.flags.p, true, st);
+    cudaMemcpyAsync((double*)w.h_out.p + s0 * (1 + P), (const double*)w.out.p + s0 * (1 + P),
+                    sizeof(double) * ns * (1 + P), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync((int32_t*)w.h_flags.p + s0, (const int32_t*)w.flags.p + s0, sizeof(int32_t) * ns,
+                    cudaMemcpyDeviceToHost, st);
+    if (!cuda_ok(cudaStreamEndCapture(st, &graph), "graph capture")) return RF_E_CUDA;
+    const bool ok = cuda_ok(cudaGraphInstantiate(&G.exec, graph, 0), "graph instantiate");
+    cudaGraphDestroy(graph);
+    return ok ? RF_OK : RF_E_CUDA;
+  }
+
+  // Queues group g's pass over `active` (non-empty, within the group's sets).
+  rf_status launch(int g, const std::vector<int32_t>& active, const std::vector<double>& theta) {
+    Group& G = grp[g];
+    bool rebuilt = false;
+    if (!replan(G, active, &rebuilt)) return RF_E_OOM;
     if (!st && !cuda_ok(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking), "stream")) return RF_E_CUDA;
-    if (rebuild || !exec) {
-      const rf_status s = capture();
+    if (!G.done && !cuda_ok(cudaEventCreateWithFlags(&G.done, cudaEventDisableTiming), "event")) return RF_E_CUDA;
+    if (rebuilt || !G.exec) {
+      const rf_status s = capture(G);
       if (s != RF_OK) return s;
     }
     Workspace& w = d->ws;
-    const int P = m->m.prog.n_free, S = d->n_sets;
-    std::memcpy(w.h_theta.p, theta.data(), sizeof(double) * S * P);
-    if (!cuda_ok(cudaGraphLaunch(exec, st), "graph launch") || !cuda_ok(cudaStreamSynchronize(st), "graph sync"))
+    const int P = m->m.prog.n_free;
+    const size_t s0 = G.planned.front(), ns = (size_t)G.planned.back() + 1 - s0;
+    std::memcpy((double*)w.h_theta.p + s0 * P, theta.data() + s0 * P, sizeof(double) * ns * P);
+    if (!cuda_ok(cudaGraphLaunch(G.exec, st), "graph launch") || !cuda_ok(cudaEventRecord(G.done, st), "event"))
       return RF_E_CUDA;
-    const double* o = (const double*)w.h_out.p;
-    for (int32_t s : planned) {
+    return RF_OK;
+  }
+
+  // Waits for group g's pass and reads its results.
+  rf_status wait(int g, std::vector<double>& nll, std::vector<double>& grad) {
+    Group& G = grp[g];
+    if (!cuda_ok(cudaEventSynchronize(G.done), "graph sync")) return RF_E_CUDA;
+    const int P = m->m.prog.n_free;
+    const double* o = (const double*)d->ws.h_out.p;
+    for (int32_t s : G.planned) {
       nll[s] = o[(size_t)s * (1 + P)];
       for (int k = 0; k < P; ++k) grad[(size_t)s * P + k] = o[(size_t)s * (1 + P) + 1 + k];
     }
     return RF_OK;
+  }
+
+  // One synchronous whole-batch pass.
+  rf_status run(const std::vector<int32_t>& active, const std::vector<double>& theta, std::vector<double>& nll,
+                std::vector<double>& grad) {
+    if (!use_graph) {
+      bool rebuilt = false;
+      if (!replan(grp[2], active, &rebuilt)) return RF_E_OOM;
+      const rf_status s = eval_host(m, d, grp[2].plan, theta.data(), nll.data(), grad.data(), nullptr);
+      return s == RF_E_DOMAIN ? RF_OK : s;
+    }
+    const rf_status s = launch(2, active, theta);
+    return s != RF_OK ? s : wait(2, nll, grad);
   }
 };
 
@@ -496,8 +540,8 @@ struct Evaluator {
 // them with one call of `eval` (active sets, theta S x P in, nll S and
 // gradient S x P out, indexed by set).  cov (S x P x P) may be null.
 rf_status fit_batch(int S, int P, const double* lo, const double* hi, const double* start, double tol, int max_evals,
-                    bool want_cov, const BatchEval& eval, double* theta_hat, double* nll_min, double* cov,
-                    int32_t* n_evals, int32_t* fit_status) {
+                    bool want_cov, const BatchEval& eval, const SplitEval* split, double* theta_hat,
+                    double* nll_min, double* cov, int32_t* n_evals, int32_t* fit_status) {
   (void)want_cov;
   Coords co;
   co.P = P;
@@ -532,23 +576,64 @@ rf_status fit_batch(int S, int P, const double* lo, const double* hi, const doub
   Pool pool(S >= min_n ? pool_threads() : 1);
   std::vector<int32_t> active;
   std::vector<double> jc((size_t)S * std::max(P, 1));
+  // One host pass per round: a set's result is delivered and its next trial
+  // point mapped to theta (and the Jacobian) in the same task.
+  pool.run(S, [&](int64_t s) { co.to_theta_jac(fits[s].trial.data(), &th[(size_t)s * P], &jc[(size_t)s * P]); },
+           min_n);
+  auto deliver = [&](const std::vector<int32_t>& sets) {
+    pool.run((int64_t)sets.size(), [&](int64_t i) {
+      const int s = sets[i];
+      double* ga = fits[s].w_ga.data();
+      for (int k = 0; k < P; ++k) ga[k] = grad[(size_t)s * P + k] * jc[(size_t)s * P + k];
+      fits[s].deliver(nll[s], ga, tol, max_evals);
+      if (fits[s].phase != DONE) co.to_theta_jac(fits[s].trial.data(), &th[(size_t)s * P], &jc[(size_t)s * P]);
+    }, min_n);
+  };
+  if (split && split->split > 0 && split->split < S) {
+    // Pipelined rounds over the halves [0, split) and [split, S): while one
+    // half's pass runs on the device the host updates the other half.  Each
+    // set's sequence of trial points is the same as in the plain loop below,
+    // which takes over once the active events fall below split->min_events.
+    std::vector<int32_t> act[2];
+    bool busy[2] = {false, false};
+    auto collect = [&](int g) {
+      act[g].clear();
+      const int a = g ? (int)split->split : 0, b = g ? S : (int)split->split;
+      for (int s = a; s < b; ++s)
+        if (fits[s].phase != DONE) act[g].push_back(s);
+    };
+    auto drain = [&](rf_status st) {
+      for (int g = 0; g < 2; ++g)
+        if (busy[g]) split->wait(g, nll, grad);
+      return st;
+    };
+    rf_status st = RF_OK;
+    for (int g = 0; g < 2 && st == RF_OK; ++g) {
+      collect(g);
+      if (!act[g].empty() && (st = split->launch(g, act[g], th)) == RF_OK) busy[g] = true;
+    }
+    if (st != RF_OK) return drain(st);
+    while (busy[0] || busy[1]) {
+      for (int g = 0; g < 2; ++g) {
+        if (!busy[g]) continue;
+        busy[g] = false;
+        if ((st = split->wait(g, nll, grad)) != RF_OK) return drain(st);
+        deliver(act[g]);
+        collect(g);
+        if (act[g].empty() || split->events(act[0]) + split->events(act[1]) < split->min_events) continue;
+        if ((st = split->launch(g, act[g], th)) != RF_OK) return drain(st);
+        busy[g] = true;
+      }
+    }
+  }
   while (true) {
     active.clear();
     for (int s = 0; s < S; ++s)
       if (fits[s].phase != DONE) active.push_back(s);
     if (active.empty()) break;
-    pool.run((int64_t)active.size(), [&](int64_t i) {
-      const int s = active[i];
-      co.to_theta_jac(fits[s].trial.data(), &th[(size_t)s * P], &jc[(size_t)s * P]);
-    }, min_n);
     const rf_status st = eval(active, th, nll, grad);
     if (st != RF_OK) return st;
-    pool.run((int64_t)active.size(), [&](int64_t i) {
-      const int s = active[i];
-      double* ga = fits[s].w_ga.data();
-      for (int k = 0; k < P; ++k) ga[k] = grad[(size_t)s * P + k] * jc[(size_t)s * P + k];
-      fits[s].deliver(nll[s], ga, tol, max_evals);
-    }, min_n);
+    deliver(active);
   }
   for (int s = 0; s < S; ++s) {
     co.to_theta(fits[s].x.data(), theta_hat + (size_t)s * P);
@@ -635,8 +720,22 @@ extern "C" rf_status rf_fit(const rf_model* m, const rf_data* d, const double* t
   for (int s = 0; s < S; ++s)
     for (int k = 0; k < P; ++k) start[(size_t)s * P + k] = theta0 ? theta0[(size_t)s * P + k] : m->m.theta_default[k];
   Evaluator ev(m, dd, !(opts && opts->no_graph == 1));
+  // the halves of a pipelined fit split the events evenly
+  SplitEval split;
+  split.split = 0;
+  if (ev.use_graph && S >= 2) {
+    const int64_t total = d->offsets[S] - d->offsets[0];
+    int s = 1;
+    while (s < S - 1 && 2 * (d->offsets[s] - d->offsets[0]) < total) ++s;
+    split.split = s;
+  }
+  split.min_events = kPipelineMinEvents;
+  split.launch = [&](int g, const std::vector<int32_t>& a, const std::vector<double>& th) { return ev.launch(g, a, th); };
+  split.wait = [&](int g, std::vector<double>& nll, std::vector<double>& grad) { return ev.wait(g, nll, grad); };
+  split.events = [&](const std::vector<int32_t>& a) { return ev.events_of(a); };
   return fit_batch(S, P, m->m.lo.data(), m->m.hi.data(), start.data(), tol, max_evals, want_cov,
                    [&](const std::vector<int32_t>& active, std::vector<double>& th, std::vector<double>& nll,
                        std::vector<double>& grad) { return ev.run(active, th, nll, grad); },
+                   split.split > 0 ? &split : nullptr,
                    theta_hat, nll_min, want_cov ? cov : nullptr, n_evals, fit_status);
 }
