@@ -29,28 +29,38 @@ struct ff {
   float hi, lo;
 };
 
-// Shared-memory copies of the tables (filled by ff_load_tables).
-struct FFTables {
+// Shared-memory copy of the tables (filled by ff_load_tables), the layout
+// of kFFTablesFlat: 514-entry tables padded to 516, the six erfcx pieces'
+// per-piece values to 8.
+struct __align__(16) FFTables {
   float exp_tab[512];
-  float log_tab[514];
-  float invf_tab[514];
+  float log_tab[516];
+  float invf_tab[516];
   float erfcx[6 * 17 * 2];
-  float erfcx_mid[6], erfcx_ihalf[6];
-  int erfcx_kf[6];
+  float erfcx_mid[8], erfcx_ihalf[8];
+  float erfcx_kf[8];  // small integers
 };
+static_assert(sizeof(FFTables) == sizeof(kFFTablesFlat), "table layout");
 
+// Every 16-byte load is issued before the first store, so staging costs one
+// memory round trip (blocks of at least 111 threads; smaller ones loop).
 __device__ __forceinline__ void ff_load_tables(FFTables& t) {
-  for (int i = threadIdx.x; i < 512; i += blockDim.x) t.exp_tab[i] = kExpTab[i];
-  for (int i = threadIdx.x; i < 514; i += blockDim.x) {
-    t.log_tab[i] = kLogTab[i];
-    t.invf_tab[i] = kInvFTab[i];
+  constexpr int kN4 = (int)(sizeof(FFTables) / 16), kPer = 4;
+  const uint4* src = reinterpret_cast<const uint4*>(kFFTablesFlat);
+  uint4* dst = reinterpret_cast<uint4*>(&t);
+  const int nt = blockDim.x;
+  uint4 r[kPer];
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    const int i = threadIdx.x + j * nt;
+    if (i < kN4) r[j] = __ldg(src + i);
   }
-  for (int i = threadIdx.x; i < 6 * 17 * 2; i += blockDim.x) t.erfcx[i] = kErfcxCoef[i];
-  for (int i = threadIdx.x; i < 6; i += blockDim.x) {
-    t.erfcx_mid[i] = kErfcxMid[i];
-    t.erfcx_ihalf[i] = kErfcxInvHalf[i];
-    t.erfcx_kf[i] = kErfcxFF[i];
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    const int i = threadIdx.x + j * nt;
+    if (i < kN4) dst[i] = r[j];
   }
+  for (int i = threadIdx.x + kPer * nt; i < kN4; i += nt) dst[i] = __ldg(src + i);
 }
 
 __device__ __forceinline__ ff ff_from_double(double d) {
@@ -275,7 +285,7 @@ __device__ __forceinline__ ff ff_erfcx(const FFTables& T, ff y, bool& ok) {
   // x = (v - mid) / half, exact scaling by a power of two
   const ff x = ff_scale(ff_add_f(v, -T.erfcx_mid[piece]), T.erfcx_ihalf[piece]);
   const float* c = T.erfcx + piece * 34;
-  const int kf = T.erfcx_kf[piece];  // 1 <= kf <= 16: tail a_16..a_kf in float
+  const int kf = (int)T.erfcx_kf[piece];  // 1 <= kf <= 16: tail a_16..a_kf in float
   float s = c[2 * 16];
   for (int k = 15; k >= kf; --k) s = __fmaf_rn(s, x.hi, c[2 * k]);
   ff acc = {s, 0.0f};

@@ -13,6 +13,7 @@
 #include <cmath>
 #include <cstdio>
 
+#include "k1_ff.cuh"
 #include "nll_ff.cuh"
 #include "nll_kernels.cuh"
 
@@ -289,19 +290,53 @@ __device__ void finish_param_point(const Program& P, const Pass& pass, int s, bo
   }
 }
 
+// The decay shape's float-float K1 path (k1_ff.cuh) applies to its plain
+// (not extended) form; the event kernel then reads the float-float block.
+__device__ __forceinline__ bool decay_ff_eligible(const Program& P, const Pass& pass) {
+  return pass.ff_shape == SHAPE_SUM_GAUSSEXP_CHEB2 && pass.ffc && !P.ext;
+}
+
+// One thread's float-float parameter point of a decay set: the CHEB2 and
+// SUM constants in FP64, the decay node, its per-event constants and K in
+// float-float.  False (nothing usable written): take the FP64 path.
+__device__ bool decay_set_ff(const FFTables& T, const Program& P, const double* th, double* C, float* out) {
+  const PNode &qg = P.node[0], &qc = P.node[1], &qs = P.node[2];
+  if (!node_consts(qc, th, C + qc.cofs, nullptr) || !node_consts(qs, th, C + qs.cofs, nullptr)) return false;
+  const DecayFF d = decay_setup(qg, param_of(qg, 0, th), param_of(qg, 1, th), param_of(qg, 2, th));
+  if (!d.ok) return false;
+  bool ok = true;
+  EndFF A, B;
+  decay_end_ff(T, d, d.al, A, ok);
+  decay_end_ff(T, d, d.be, B, ok);
+  ff ge[8];
+  if (!ok || !decay_point_ff(T, d, A, B, C + qc.cofs, C + qs.cofs, ge, out)) return false;
+  for (int k = 0; k < 8; ++k) C[qg.cofs + k] = ff_to_double(ge[k]);
+  return true;
+}
+
 // K1, one thread per active set (many sets: toy fits).  Also resets the
 // event kernel's work counter.
 __global__ void param_point_kernel(const __grid_constant__ Program P, Pass pass) {
+  __shared__ FFTables T;
   pdl_launch_dependents();
   const int a = blockIdx.x * blockDim.x + threadIdx.x;
   if (a == 0) {
     for (int i = 0; i < (pass.n_counters > 1 ? pass.n_counters : 1); ++i) pass.counter[i] = 0;
     if (pass.slow) *pass.slow = 0ull;
   }
+  const bool try_ff = decay_ff_eligible(P, pass);
+  if (try_ff) {
+    ff_load_tables(T);
+    __syncthreads();
+  }
   if (a >= pass.n_active) return;
   const int s = pass.sets[a];
   const double* th = pass.theta + (size_t)s * P.n_free;
   double* C = pass.consts + (size_t)s * P.n_const;
+  if (try_ff && decay_set_ff(T, P, th, C, pass.ffc + (size_t)s * kFFConst)) {
+    finish_param_point(P, pass, s, false, C, true);
+    return;
+  }
   bool bad = false;
   for (int n = 0; n < P.n_pdf; ++n) bad |= !node_consts(P.node[n], th, C + P.node[n].cofs, nullptr);
   finish_param_point(P, pass, s, bad, C);
@@ -321,17 +356,66 @@ __global__ void __launch_bounds__(kK1Warps * 32) param_point_block_kernel(const 
   __shared__ double Ks[13 * 16];
   __shared__ double Cs[kMaxConst];  // the set's constant block, copied out at the end
   __shared__ int sbad;
-  pdl_launch_dependents();
+  __shared__ FFTables T;
+  __shared__ EndFF endff[2];
+  __shared__ ff geff[8];
+  __shared__ int ffok;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (blockIdx.x == 0 && tid == 0) {
     for (int i = 0; i < (pass.n_counters > 1 ? pass.n_counters : 1); ++i) pass.counter[i] = 0;
     if (pass.slow) *pass.slow = 0ull;
   }
-  if (tid == 0) sbad = 0;
+  // The event kernel may launch once this kernel has started (FP64 path) or
+  // once the float-float chain is done: its waiting blocks would otherwise
+  // share the issue slots that the chain's single warp depends on.
+  const bool try_ff = decay_ff_eligible(P, pass);
+  if (!try_ff) pdl_launch_dependents();
+  if (tid == 0) {
+    sbad = 0;
+    ffok = 1;
+  }
+  if (try_ff) ff_load_tables(T);
   __syncthreads();
   const int s = pass.sets[blockIdx.x];
   const double* th = pass.theta + (size_t)s * P.n_free;
   double* C = pass.consts + (size_t)s * P.n_const;
+  if (try_ff) {
+    // float-float path (k1_ff.cuh): the two range ends of the decay node on
+    // lanes 0 and 1 while warps 1 and 2 take the CHEB2 and SUM constants
+    const PNode &qg = P.node[0], &qc = P.node[1], &qs = P.node[2];
+    if (warp == 0 && lane < 2) {
+      const DecayFF d = decay_setup(qg, param_of(qg, 0, th), param_of(qg, 1, th), param_of(qg, 2, th));
+      bool ok = d.ok;
+      if (ok) decay_end_ff(T, d, lane ? d.be : d.al, endff[lane], ok);
+      if (!ok) atomicAnd(&ffok, 0);
+    } else if ((warp == 1 || warp == 2) && lane == 0) {
+      const PNode& q = warp == 1 ? qc : qs;
+      if (!node_consts(q, th, Cs + q.cofs, nullptr)) atomicOr(&sbad, 1);
+    }
+    __syncthreads();
+    if (ffok && !sbad && tid == 0) {
+      const DecayFF d = decay_setup(qg, param_of(qg, 0, th), param_of(qg, 1, th), param_of(qg, 2, th));
+      ff ge[8];
+      if (decay_point_ff(T, d, endff[0], endff[1], Cs + qc.cofs, Cs + qs.cofs, ge,
+                         pass.ffc + (size_t)s * kFFConst)) {
+        for (int k = 0; k < 8; ++k) geff[k] = ge[k];
+      } else {
+        ffok = 0;
+      }
+    }
+    __syncthreads();
+    pdl_launch_dependents();
+    if (ffok && !sbad) {
+      if (tid < 8) Cs[qg.cofs + tid] = ff_to_double(geff[tid]);
+      __syncthreads();
+      for (int i = tid; i < P.n_const; i += blockDim.x) C[i] = Cs[i];
+      if (tid == 0) finish_param_point(P, pass, s, false, Cs, true);
+      return;
+    }
+    // otherwise the FP64 path below recomputes the set
+    if (tid == 0) sbad = 0;
+    __syncthreads();
+  }
   // jobs: (node, end, part), numbered in node order
   if (lane == 0) {
     int j = 0;
