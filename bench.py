@@ -1,7 +1,7 @@
 """Benchmark of the batched unbinned-likelihood hot path on GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload decay_1e7|prod3_1e8_f32|decay_toys_4096|gauss_poly1_1e4]
+                    [--workload decay_1e7|decay_generic_1e7|prod3_1e8_f32|decay_toys_4096|...]
 
 Default workload (the configuration the headline metric is quoted on):
 events/s of one NLL + gradient pass over the decay-time model, 1e7 events,
@@ -14,7 +14,8 @@ the C ABI with host buffers: host->device copy of the event columns from
 pinned memory, rf_nll_grad with host parameters, device->host read of the
 NLL and gradient.
 
-Other workloads: prod3_1e8_f32 (3-observable product, 1e8 events, FP32
+Other workloads: decay_generic_1e7 (the same model and events on the
+generic FP64 interpreter); prod3_1e8_f32 (3-observable product, 1e8 events, FP32
 columns, 12 parameters); decay_toys_4096 (toy fits/s of 4096 ragged toys of
 the decay model fitted together, graph-replayed evaluation step, autotuned
 tile shape); gauss_poly1_1e4 (1e4 events, latency-bound).
@@ -46,13 +47,14 @@ METRIC = "events/s of NLL+grad eval; toy fits/s learned-start vs plain at |ΔNLL
 WORKLOADS = {
     # name: model constructor, generating theta, events per dataset, FP32 columns, bytes/event
     "decay_1e7": ("decay_model", W.DECAY_TRUE, 10_000_000, False, 8),
+    "decay_generic_1e7": ("decay_generic_model", W.DECAY_GENERIC_TRUE, 10_000_000, False, 8),
     "prod3_1e8_f32": ("prod3_model", W.PROD3_TRUE, 100_000_000, True, 12),
     "gauss_poly1_1e4": ("gauss_poly1_model", W.GAUSS_POLY1_TRUE, 10_000, False, 8),
     "decay_toys_4096": ("decay_model", W.DECAY_TRUE, 0, False, 8),
     "learned_start": ("decay_model", W.DECAY_TRUE, 0, False, 8),
     "binned_4096": ("binned_model", None, 0, False, 8),
 }
-DEFAULT_STEPS = {"decay_1e7": 400, "prod3_1e8_f32": 40, "gauss_poly1_1e4": 2000, "decay_toys_4096": 3,
+DEFAULT_STEPS = {"decay_1e7": 400, "decay_generic_1e7": 40, "prod3_1e8_f32": 40, "gauss_poly1_1e4": 2000, "decay_toys_4096": 3,
                  "learned_start": 1, "binned_4096": 100}
 
 

@@ -138,6 +138,26 @@ def decay_model() -> ModelSpec:
     return b.spec(_decay_part(b, t, DECAY_START))
 
 
+def decay_generic_model() -> ModelSpec:
+    """The decay model with the SUM operands in the other order (background
+    first, f_bkg = 1 - f_sig): the same density, matched by no float-float
+    program, so it runs on the generic FP64 interpreter.  Defaults are the
+    generating values of DECAY_GENERIC_TRUE."""
+    b = _Builder()
+    t = b.obs(0.0, 10.0)
+    tau = b.param("tau", DECAY_TRUE[0], 0.1, 10.0)
+    mur = b.param("mu_r", DECAY_TRUE[1], -0.5, 0.5)
+    sgr = b.param("sigma_r", DECAY_TRUE[2], 0.005, 1.0)
+    c1 = b.param("c1", DECAY_TRUE[3], -1.0, 1.0)
+    c2 = b.param("c2", DECAY_TRUE[4], -1.0, 1.0)
+    fb = b.param("f_bkg", 1.0 - DECAY_TRUE[5], 0.0, 1.0)
+    sig = b.pdf("gaussexp", t, tau, mur, sgr)
+    bkg = b.pdf("cheb", t, c1, c2)
+    return b.spec(b.pdf("sum", bkg, sig, fb))
+
+
+DECAY_GENERIC_TRUE = np.array([*DECAY_TRUE[:5], 1.0 - DECAY_TRUE[5]])
+
 PROD3_TRUE = np.array([5.28, 0.015, 0.4, -0.3, *DECAY_TRUE, 0.1, 0.3])
 
 
