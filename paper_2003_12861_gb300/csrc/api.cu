@@ -602,9 +602,13 @@ extern "C" rf_status rf_nll_grad_stream(const rf_model* m, rf_data* d, const voi
     for (int k = 0; k < K; ++k) wc[k + 1] = (wsum += (K >= 3 && k == K - 1) ? 1 : (K >= 3 && k == K - 2) ? 2 : 4);
     for (int k = 0; k <= K; ++k) bound[k] = n_items * wc[k] / wsum;
   }
-  // theta, then K1, on `stream`; the copy stream starts after everything
-  // already queued there (a previous pass may still read the columns); the
-  // compute streams start after K1.
+  // The copy stream starts after everything already queued on `stream` (a
+  // previous pass may still read the columns), alongside the theta upload;
+  // then K1 on `stream`; the compute streams start after K1.
+  cudaEvent_t ev_start = w.seg_ev[kMaxSegments], ev_k1 = w.seg_ev[kMaxSegments + 1];
+  if (!cuda_ok(cudaEventRecord(ev_start, st), "rf_nll_grad_stream") ||
+      !cuda_ok(cudaStreamWaitEvent(w.copy_stream, ev_start, 0), "rf_nll_grad_stream"))
+    return RF_E_CUDA;
   std::memcpy(w.h_theta.p, theta, sizeof(double) * S * P);
   if (P > 0 && !cuda_ok(cudaMemcpyAsync(w.theta.p, w.h_theta.p, sizeof(double) * S * P, cudaMemcpyHostToDevice, st),
                         "theta upload"))
@@ -612,10 +616,6 @@ extern "C" rf_status rf_nll_grad_stream(const rf_model* m, rf_data* d, const voi
   Pass pass = make_pass(m, d, plan, (const double*)w.theta.p, (double*)w.out.p, (int32_t*)w.flags.p, true);
   pass.counter = (int32_t*)w.seg_counters.p;
   pass.n_counters = K;
-  cudaEvent_t ev_start = w.seg_ev[kMaxSegments], ev_k1 = w.seg_ev[kMaxSegments + 1];
-  if (!cuda_ok(cudaEventRecord(ev_start, st), "rf_nll_grad_stream") ||
-      !cuda_ok(cudaStreamWaitEvent(w.copy_stream, ev_start, 0), "rf_nll_grad_stream"))
-    return RF_E_CUDA;
   launch_param_point(m->m.prog, pass, st);
   if (!cuda_ok(cudaEventRecord(ev_k1, st), "rf_nll_grad_stream")) return RF_E_CUDA;
   const int n_comp = std::min(K, kCompStreams);
