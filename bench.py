@@ -344,6 +344,7 @@ def run_events(args, api, torch, dist, rank, world, local):
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+    n_launch0 = api.launch_count()
     with ClockSampler(local) as clk:
         with torch.cuda.stream(stream):
             for i in range(args.steps):
@@ -352,6 +353,7 @@ def run_events(args, api, torch, dist, rank, world, local):
                 step()
                 ends[i].record(stream)
         torch.cuda.synchronize()
+    n_launches = api.launch_count() - n_launch0
     if dist:
         dist.barrier()
     total_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
@@ -404,7 +406,7 @@ def run_events(args, api, torch, dist, rank, world, local):
                                    "free_parameters": P, "l2": "flushed between steps (256 MiB write)",
                                    "tile": {"threads_per_block": tune[0], "blocks_per_sm": tune[1]}},
         "roofline": roofline(api, model, spec, data, kern_ms, kern_n, n, bpe, peaks, peak_kind, workload=wl),
-        "e2e": e2e, "gpu_launches": 2 * args.steps, "clocks": clk.summary(),
+        "e2e": e2e, "gpu_launches": int(n_launches), "clocks": clk.summary(),
         "nll_check": float(out[0].item()),
     }
     if wl == "gauss_poly1_1e4":
@@ -454,6 +456,7 @@ def run_toys(args, api, torch, dist, rank, world, local):
     torch.cuda.synchronize()
     evals, conv = [], []
     with ClockSampler(local) as clk:
+        n_launch0 = api.launch_count()
         t0 = time.perf_counter()
         for _ in range(args.steps):
             r = api.fit(model, data, want_cov=False)
@@ -461,6 +464,7 @@ def run_toys(args, api, torch, dist, rank, world, local):
             conv.append(r["status"] == 0)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
+        n_launches = api.launch_count() - n_launch0
     if dist:
         t = torch.tensor([dt], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -489,7 +493,7 @@ def run_toys(args, api, torch, dist, rank, world, local):
         "roofline": rl,
         "e2e": {"value": world * S / e2e_s, "unit": "toy fits/s", "h2d_bytes_per_step": int(n_events) * 8,
                 "d2h_bytes_per_step": S * (P + 3) * 8},
-        "gpu_launches": int(2 * rounds * args.steps),
+        "gpu_launches": int(n_launches),
         "clocks": clk.summary(),
         "fits": {"mean_evals": float(ev.mean()), "max_evals": int(ev.max()),
                  "converged_frac": float(np.concatenate(conv).mean())},
@@ -527,7 +531,7 @@ def run_learned(args, api, torch, dist, rank, world, local):
         "e2e": {"value": r["learned"]["toy_fits_per_s"] * world, "unit": "toy fits/s",
                 "h2d_bytes_per_step": 8 * 10_000 * 6, "d2h_bytes_per_step": 10_000 * 9 * 8,
                 "note": "histogram, network, fits and fallback through the public API, host results"},
-        "gpu_launches": None, "clocks": clk.summary(),
+        "gpu_launches": r["learned"]["gpu_launches"], "clocks": clk.summary(),
     }
 
 
@@ -572,6 +576,7 @@ def run_binned(args, api, torch, dist, rank, world, local):
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+    n_launch0 = api.launch_count()
     with ClockSampler(local) as clk:
         with torch.cuda.stream(stream):
             for i in range(args.steps):
@@ -580,6 +585,7 @@ def run_binned(args, api, torch, dist, rank, world, local):
                 m.nll_grad_async(counts, th, out, flags, stream=stream)
                 ends[i].record(stream)
         torch.cuda.synchronize()
+    n_launches = api.launch_count() - n_launch0
     total_ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
     if dist:
         t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
@@ -620,7 +626,7 @@ def run_binned(args, api, torch, dist, rank, world, local):
                      "peak_basis": f"FP64 FMA rate measured in-run; {fl} algorithmic FP64 flops per dataset"},
         "e2e": {"value": world * S / e2e_s, "unit": "datasets/s", "h2d_bytes_per_step": S * (Bn + P) * 8,
                 "d2h_bytes_per_step": S * (1 + P) * 8 + S * 4},
-        "gpu_launches": args.steps, "clocks": clk.summary(),
+        "gpu_launches": int(n_launches), "clocks": clk.summary(),
         "fits": {"datasets": n_fit, "fits_per_s": n_fit / fit_s, "mean_evals": float(r["n_evals"].mean()),
                  "max_evals": int(r["n_evals"].max()), "converged_frac": float((r["status"] == 0).mean()),
                  "tol_edm": 1e-7, "start": "nominal (normfactors 1, nuisances 0)"},

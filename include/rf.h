@@ -348,6 +348,13 @@ rf_status rf_data_refill(rf_data* d, const void* const* cols, void* stream);
 rf_status rf_kernel_timing(int32_t enable);
 rf_status rf_kernel_time(double* total_ms, int64_t* launches, int32_t reset);
 
+/* Number of the library's kernels launched so far in this process (every
+ * kernel of the likelihood, fit, generation, histogram and network paths;
+ * a replayed evaluation graph counts its kernels; launches recorded into a
+ * stream capture are not counted; the roofline probes are not counted).
+ * Read it before and after a region to count that region's launches. */
+rf_status rf_launch_count(int64_t* n);
+
 /* Events that took the slow path (the decay-resolution convolution near the
  * resolution region) in the last pass over `d`, summed over sets. */
 rf_status rf_slow_events(const rf_data* d, int64_t* count);

@@ -59,6 +59,7 @@ SIGNATURES = {
     "rf_data_refill": (C.c_int, [_vp, C.POINTER(_vp), _vp]),
     "rf_kernel_timing": (C.c_int, [C.c_int32]),
     "rf_kernel_time": (C.c_int, [_dp, _i64p, C.c_int32]),
+    "rf_launch_count": (C.c_int, [_i64p]),
     "rf_slow_events": (C.c_int, [_vp, _i64p]),
     "rf_probe": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, _dp]),
     "rf_nll_grad_noalloc": (C.c_int, [_vp, C.POINTER(_vp), _ip, C.c_int64, _vp, _vp, _vp, _vp]),

@@ -343,6 +343,13 @@ def kernel_time(reset: bool = True):
     return ms.value, n.value
 
 
+def launch_count() -> int:
+    """The library's kernel launches so far in this process (rf_launch_count)."""
+    n = C.c_int64()
+    L.check(L.load().rf_launch_count(C.byref(n)))
+    return n.value
+
+
 def slow_events(data: Data) -> int:
     n = C.c_int64()
     L.check(L.load().rf_slow_events(data._h, C.byref(n)))

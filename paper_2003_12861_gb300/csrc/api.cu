@@ -1,4 +1,5 @@
 // C ABI: models, datasets, likelihood entry points.
+#include <atomic>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -109,6 +110,16 @@ bool build_plan(const rf_data* d, const std::vector<int32_t>& sets, Plan* plan) 
   if (!items.empty() && !cuda_ok(cudaMemcpy(plan->items.p, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice), "plan upload"))
     return false;
   return true;
+}
+
+namespace {
+std::atomic<long long> g_launches{0};
+}  // namespace
+
+void note_launches(int n, cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (st && cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) return;
+  g_launches.fetch_add(n, std::memory_order_relaxed);
 }
 
 bool ensure_workspace(const rf_model* m, rf_data* d) {
@@ -653,4 +664,13 @@ extern "C" rf_status rf_nll_grad_stream(const rf_model* m, rf_data* d, const voi
       return RF_E_CUDA;
   if (!cuda_ok(cudaGetLastError(), "kernel launch")) return RF_E_CUDA;
   return finish_host(m, d, plan, nll, grad, st);
+}
+
+extern "C" rf_status rf_launch_count(int64_t* n) {
+  if (!n) {
+    set_error("rf_launch_count: NULL output");
+    return RF_E_INVALID;
+  }
+  *n = g_launches.load(std::memory_order_relaxed);
+  return RF_OK;
 }

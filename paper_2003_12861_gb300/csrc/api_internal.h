@@ -92,6 +92,9 @@ rf_status fit_batch(int S, int P, const double* lo, const double* hi, const doub
                     bool want_cov, const BatchEval& eval, const SplitEval* split, double* theta_hat,
                     double* nll_min, double* cov, int32_t* n_evals, int32_t* fit_status);
 int sm_count();
+// Counts n kernel launches on st for rf_launch_count (not while st is being
+// captured into a graph).
+void note_launches(int n, cudaStream_t st);
 int64_t tree_nodes(int64_t chunks);
 
 }  // namespace rf

@@ -266,6 +266,7 @@ rf_status launch_binned(rf_binned* m, int32_t n_sets, const double* d_counts, co
                         int32_t* d_flags, cudaStream_t st, const int32_t* d_sets = nullptr) {
   if (n_sets == 0) return RF_OK;
   const int grid = std::min(n_sets, m->grid);
+  note_launches(1, st);
   binned_kernel<<<grid, kBinnedThreads, m->smem, st>>>(m->dev, n_sets, d_sets, d_counts, d_theta, d_out, d_flags,
                                                         (double*)m->scratch.p);
   return cuda_ok(cudaGetLastError(), "binned launch") ? RF_OK : RF_E_CUDA;
@@ -523,6 +524,7 @@ rf_status rf_binned_expected(rf_binned* m, int32_t n_sets, const double* d_theta
     return RF_E_INVALID;
   }
   if (n_sets == 0) return RF_OK;
+  note_launches(1, (cudaStream_t)stream);
   binned_expected_kernel<<<std::min(n_sets, m->grid), kBinnedThreads, m->smem, (cudaStream_t)stream>>>(
       m->dev, n_sets, d_theta, d_nu, (double*)m->scratch.p);
   return cuda_ok(cudaGetLastError(), "binned launch") ? RF_OK : RF_E_CUDA;

@@ -504,6 +504,7 @@ struct Evaluator {
     std::memcpy((double*)w.h_theta.p + s0 * P, theta.data() + s0 * P, sizeof(double) * ns * P);
     if (!cuda_ok(cudaGraphLaunch(G.exec, st), "graph launch") || !cuda_ok(cudaEventRecord(G.done, st), "event"))
       return RF_E_CUDA;
+    note_launches(2, st);  // the graph's K1 and event kernel
     return RF_OK;
   }
 

@@ -221,6 +221,7 @@ void gemm_bf16(const float* A, int lda, bool tA, const float* B, int ldb, bool t
                int K, const float* bias, float* Z, bool gelu, cudaStream_t st) {
   GemmArgs g{A, B, C, bias, Z, M, N, K, lda, ldb, ldc, tA ? 1 : 0, tB ? 1 : 0, gelu ? 1 : 0};
   dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
+  note_launches(1, st);
   gemm_bf16_kernel<<<grid, 128, 0, st>>>(g);
 }
 
@@ -302,10 +303,12 @@ void mlp_backward(rf_mlp* n, int batch, cudaStream_t st) {
     const int ni = n->dims[l], no = n->dims[l + 1];
     if (l < L - 1) {
       const int64_t cnt = (int64_t)batch * no;
+      note_launches(1, st);
       gelu_backward_kernel<<<blocks_for(cnt, 256), 256, 0, st>>>(d, zs + zo[l], cnt);
     }
     // dW = a_in^T dZ  (ni x no), db = column sums of dZ
     gemm_bf16(acts + ao[l], ni, true, d, no, false, G + n->w_off[l], no, ni, no, batch, nullptr, nullptr, false, st);
+    note_launches(1, st);
     colsum_kernel<<<blocks_for(no, 128), 128, 0, st>>>(d, batch, no, G + n->b_off[l]);
     if (l > 0) {
       // dA_in = dZ W^T  (batch x ni)
@@ -319,6 +322,7 @@ void mlp_backward(rf_mlp* n, int batch, cudaStream_t st) {
 rf_status mlp_loss_grad(rf_mlp* n, const float* x, const float* t, int batch, cudaStream_t st) {
   mlp_forward(n, x, batch, st);
   const int64_t cnt = (int64_t)batch * n->dims.back();
+  note_launches(1, st);
   mse_kernel<<<1, 256, 0, st>>>((const float*)n->y.p, t, cnt, (float*)n->dbuf.p, (float*)n->loss.p);
   mlp_backward(n, batch, st);
   return cuda_ok(cudaGetLastError(), "mlp launch") ? RF_OK : RF_E_CUDA;
@@ -328,6 +332,7 @@ void mlp_adam(rf_mlp* n, float lr, cudaStream_t st) {
   ++n->step;
   const float b1 = 0.9f, b2 = 0.999f;
   const float c1 = 1.f - powf(b1, (float)n->step), c2 = 1.f - powf(b2, (float)n->step);
+  note_launches(1, st);
   adam_kernel<<<blocks_for(n->n_params, 256), 256, 0, st>>>((float*)n->params.p, (const float*)n->grads.p,
                                                              (float*)n->m.p, (float*)n->v.p, n->n_params, lr, b1, b2,
                                                              1e-8f, c1, c2);
@@ -408,10 +413,12 @@ rf_status rf_mlp_forward(rf_mlp* n, const float* d_x, int32_t batch, float* d_y,
   cudaStream_t st = (cudaStream_t)stream;
   mlp_forward(n, d_x, batch, st);
   const int no = n->dims.back();
-  if (n->has_affine)
+  if (n->has_affine) {
+    note_launches(1, st);
     affine_cols_kernel<<<blocks_for((int64_t)batch * no, 256), 256, 0, st>>>((float*)n->y.p, batch, no,
                                                                             (const float*)n->scale.p,
                                                                             (const float*)n->shift.p);
+  }
   cudaMemcpyAsync(d_y, n->y.p, sizeof(float) * (size_t)batch * no, cudaMemcpyDeviceToDevice, st);
   return cuda_ok(cudaGetLastError(), "rf_mlp_forward") ? RF_OK : RF_E_CUDA;
 }
@@ -451,7 +458,9 @@ rf_status rf_mlp_train(rf_mlp* n, const float* d_x, const float* d_t, int32_t ro
   const float* targets = d_t;
   if (standardise) {
     if (!tstd.ensure(sizeof(float) * (size_t)rows * no)) return RF_E_OOM;
+    note_launches(1, nullptr);
     col_stats_kernel<<<1, 128>>>(d_t, rows, no, (float*)n->mean.p, (float*)n->sd.p);
+    note_launches(1, nullptr);
     standardise_kernel<<<blocks_for((int64_t)rows * no, 256), 256>>>(d_t, rows, no, (const float*)n->mean.p,
                                                                     (const float*)n->sd.p, (float*)tstd.p);
     targets = (const float*)tstd.p;
@@ -476,7 +485,9 @@ rf_status rf_mlp_train(rf_mlp* n, const float* d_x, const float* d_t, int32_t ro
     double sum = 0.0;
     for (int s = 0; s < steps_per_epoch; ++s, ++it) {
       const int32_t* ids = (const int32_t*)dperm.p + (size_t)s * batch;
+      note_launches(1, nullptr);
       gather_rows_kernel<<<blocks_for((int64_t)batch * ni, 256), 256>>>(d_x, ids, batch, ni, (float*)n->xb.p);
+      note_launches(1, nullptr);
       gather_rows_kernel<<<blocks_for((int64_t)batch * no, 256), 256>>>(targets, ids, batch, no, (float*)n->tb.p);
       rf_status st = mlp_loss_grad(n, (const float*)n->xb.p, (const float*)n->tb.p, batch, 0);
       if (st != RF_OK) return st;

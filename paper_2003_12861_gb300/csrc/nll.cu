@@ -1141,6 +1141,7 @@ __global__ void __launch_bounds__(kLanes, ff_min_blocks(kShape)) events_ff(const
 }  // namespace
 
 void launch_param_point(const Program& P, const Pass& pass, cudaStream_t st) {
+  note_launches(1, st);
   if (pass.n_active > 0 && pass.n_active <= kBlockK1MaxSets) {
     param_point_block_kernel<<<pass.n_active, kK1Warps * 32, 0, st>>>(P, pass);
     return;
@@ -1205,6 +1206,7 @@ void launch_events(const Program& P, Shape shape, const Columns& cols, const Pas
   const Shape sh = (pass.ff_shape != SHAPE_GENERIC && pass.ffc) ? shape : SHAPE_GENERIC;
   const int64_t units = sh == SHAPE_GENERIC ? (int64_t)pass.n_items : (int64_t)pass.n_items * kParts;
   if (grid > units) grid = (int)units;
+  note_launches(1, st);
   timing_begin(st);
   switch (sh) {
     case SHAPE_SUM_GAUSSEXP_CHEB2:

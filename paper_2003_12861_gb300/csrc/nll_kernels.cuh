@@ -56,6 +56,7 @@ constexpr int kPartFloats = 32;
 constexpr int32_t kThetaBad = 1 << 30;
 
 void launch_param_point(const Program& P, const Pass& pass, cudaStream_t st);
+void note_launches(int n, cudaStream_t st);  // the library's launch count (api.cu)
 // Kernel timing hooks (measure.cu): bracket a launch with CUDA events.
 void timing_begin(cudaStream_t st);
 void timing_end(cudaStream_t st);

@@ -141,6 +141,7 @@ extern "C" rf_status rf_nll_grad_noalloc(const rf_model* m, const void* const* d
   const int64_t work = chunks > nodes ? chunks : nodes;
   const int blocks = (int)((work + 255) / 256) > 0 ? (int)((work + 255) / 256) : 1;
   noalloc_setup<<<blocks < 1024 ? blocks : 1024, 256, 0, st>>>(base, L, n_events, chunks, nodes);
+  note_launches(1, st);
   Pass pass{};
   pass.counter = (int32_t*)(base + 0);
   pass.slow = (unsigned long long*)(base + 8);

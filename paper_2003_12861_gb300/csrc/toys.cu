@@ -354,8 +354,10 @@ rf_status rf_generate_toys(const rf_model* m, const double* theta, int32_t theta
       set_error("rf_generate_toys: generating parameters outside the pdf's domain");
       return RF_E_DOMAIN;
     }
+  note_launches(1, nullptr);
   bounds_kernel<<<n_sets * g.n_factors, 256>>>(P, g, (const double*)d_consts.p, (const int32_t*)d_sets.p,
                                                (double*)d_bounds.p);
+  note_launches(1, nullptr);
   sizes_kernel<<<(n_sets + 127) / 128, 128>>>((const double*)d_mean.p, n_sets, poisson, k0, k1,
                                               (int64_t*)d_sizes.p);
   std::vector<int64_t> sizes(n_sets);
@@ -400,6 +402,7 @@ rf_status rf_generate_toys(const rf_model* m, const double* theta, int32_t theta
   }
   if (d->n_events > 0) {
     const int64_t blocks = (d->n_events + 127) / 128;
+    note_launches(1, nullptr);
     events_kernel<<<(unsigned)blocks, 128>>>(P, g, (const double*)d_consts.p, (const double*)d_bounds.p,
                                              (const int64_t*)d->offsets_dev.p, n_sets, d->n_events, k0, k1, outc,
                                              (int32_t*)d_err.p);
@@ -430,6 +433,7 @@ rf_status rf_hist64(const rf_model* m, const rf_data* d, int32_t col, float* d_o
     c.is_f32[i] = d->dtype[i] == RF_F32;
   }
   const double lo = m->m.obs_lo[col], hi = m->m.obs_hi[col];
+  note_launches(1, (cudaStream_t)stream);
   hist64_kernel<<<d->n_sets, 256, 0, (cudaStream_t)stream>>>(c, col, (const int64_t*)d->offsets_dev.p, lo,
                                                             64.0 / (hi - lo), d_out);
   return cuda_ok(cudaGetLastError(), "rf_hist64 launch") ? RF_OK : RF_E_CUDA;

@@ -81,9 +81,11 @@ def compare(net, model, n_toys: int, seed: int, tol_edm: float = 1e-7, n_lo: flo
     mean = W.toy_mean_sizes(n_toys, seed, n_lo, n_hi)
     data = api.generate_toys(model, th, seed, mean, poisson=True)
     torch.cuda.synchronize()
+    n0 = api.launch_count()
     t0 = time.perf_counter()
     plain = api.fit(model, data, tol_edm=tol_edm, want_cov=False)
     t_plain = time.perf_counter() - t0
+    n1 = api.launch_count()
     t0 = time.perf_counter()
     start = predict_starts(net, model, data)
     learned = api.fit(model, data, theta0=start, tol_edm=tol_edm, want_cov=False)
@@ -103,16 +105,18 @@ def compare(net, model, n_toys: int, seed: int, tol_edm: float = 1e-7, n_lo: flo
             learned["status"][s] = rb["status"][j]
             learned["n_evals"][s] += rb["n_evals"][j]
     t_learned = time.perf_counter() - t0
+    n2 = api.launch_count()
     both = (plain["status"] == 0) & (learned["status"] == 0)
     d = learned["nll"][both] - plain["nll"][both]
     return {
         "toys": n_toys, "events": int(data.n_events),
         "plain": {"wall_s": t_plain, "toy_fits_per_s": n_toys / t_plain,
                   "mean_evals": float(plain["n_evals"].mean()), "max_evals": int(plain["n_evals"].max()),
-                  "converged": float((plain["status"] == 0).mean())},
+                  "converged": float((plain["status"] == 0).mean()), "gpu_launches": n1 - n0},
         "learned": {"wall_s": t_learned, "toy_fits_per_s": n_toys / t_learned,
                     "mean_evals": float(learned["n_evals"].mean()), "max_evals": int(learned["n_evals"].max()),
-                    "converged": float((learned["status"] == 0).mean()), "fallbacks": int(len(bad))},
+                    "converged": float((learned["status"] == 0).mean()), "fallbacks": int(len(bad)),
+                    "gpu_launches": n2 - n1},
         "same_minimum_frac": float(np.mean(np.abs(d) < 1e-6)) if d.size else 0.0,
         "learned_lower_nll_frac": float(np.mean(d <= -1e-6)) if d.size else 0.0,
         "learned_higher_nll_frac": float(np.mean(d >= 1e-6)) if d.size else 0.0,

@@ -190,3 +190,21 @@ def test_device_resident_async_pass(oracle_mod):
     o = out.cpu().numpy()
     check_nll(o[0], o[1:], om.nll(TRUE["decay_model"], cols))
     assert int(flags.item()) == 0
+
+
+def test_launch_count(oracle_mod):
+    """rf_launch_count: one pass is K1 + the event kernel; a batched fit's
+    graph replays count their two kernels each."""
+    spec = W.decay_model()
+    m = api.Model.from_spec(spec)
+    d = api.generate_toys(m, W.DECAY_TRUE, 3, [20000.0], poisson=False)
+    api.nll_grad(m, d, W.DECAY_TRUE)
+    n0 = api.launch_count()
+    api.nll_grad(m, d, W.DECAY_TRUE)
+    assert api.launch_count() - n0 == 2
+    sets = api.generate_toys(m, np.tile(W.DECAY_TRUE, (8, 1)), 4, np.full(8, 3000.0))
+    api.fit(m, sets, want_cov=False)  # first fit captures its graphs
+    n1 = api.launch_count()
+    r = api.fit(m, sets, want_cov=False)
+    n = api.launch_count() - n1
+    assert n % 2 == 0 and int(r["n_evals"].max()) <= n // 2 <= 2 * int(r["n_evals"].max()) + 2
