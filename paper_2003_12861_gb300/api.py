@@ -522,3 +522,61 @@ class BinnedModel:
     def expected(self, d_theta, d_nu, stream=None):
         L.check(L.load().rf_binned_expected(self._h, d_theta.shape[0], C.c_void_p(d_theta.data_ptr()),
                                             C.c_void_p(d_nu.data_ptr()), _stream(stream)))
+
+
+# --------------------------------------------------------------- autograd
+
+_RFNLL = None
+
+
+def _rfnll():
+    global _RFNLL
+    if _RFNLL is None:
+        import torch
+
+        class RfNLL(torch.autograd.Function):
+            """NLL(theta) as a torch function.  forward runs one device-resident
+            pass (rf_nll_grad_async) on the current stream and saves the
+            gradient; backward returns grad_out * grad without a second pass.
+            theta: (n_free,) for one set or shared by all sets, or
+            (n_sets, n_free); the result is a scalar or (n_sets,) NLLs."""
+
+            @staticmethod
+            def forward(ctx, theta, model, data):
+                S, P = data.n_sets, model.n_free
+                th = theta.detach().to(device="cuda", dtype=torch.float64).contiguous().reshape(-1)
+                shared = theta.dim() == 1 and S > 1
+                if shared:
+                    th = th.repeat(S)
+                if th.numel() != S * P:
+                    raise ValueError("theta must hold n_free or n_sets x n_free values")
+                out = torch.empty(S * (1 + P), dtype=torch.float64, device="cuda")
+                flags = torch.zeros(S, dtype=torch.int32, device="cuda")
+                nll_grad_async(model, data, th, out, flags, stream=torch.cuda.current_stream())
+                o = out.view(S, 1 + P)
+                ctx.save_for_backward(o[:, 1:].clone())
+                ctx.shared = shared
+                ctx.single = theta.dim() == 1 and S == 1
+                ctx.dtype = theta.dtype
+                nll = o[:, 0].clone()
+                return nll.reshape(()) if ctx.single else nll
+
+            @staticmethod
+            def backward(ctx, grad_out):
+                (g,) = ctx.saved_tensors
+                if ctx.single:
+                    d = grad_out * g[0]
+                elif ctx.shared:
+                    d = (grad_out[:, None] * g).sum(0)
+                else:
+                    d = grad_out[:, None] * g
+                return d.to(ctx.dtype), None, None
+
+        _RFNLL = RfNLL
+    return _RFNLL
+
+
+def __getattr__(name):
+    if name == "RfNLL":  # torch is imported on first use only
+        return _rfnll()
+    raise AttributeError(name)
