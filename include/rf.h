@@ -258,6 +258,13 @@ rf_status rf_mlp_adam(rf_mlp* n, float lr, void* stream);
 rf_status rf_mlp_train(rf_mlp* n, const float* d_x, const float* d_t, int32_t rows, int32_t batch, int32_t epochs,
                        float lr, uint64_t seed, int32_t standardise, float* final_loss);
 /* Checkpoint: dimensions, step, master weights, Adam moments, output map. */
+/* The learned fit start (the network's use): for every set of d, the
+ * 64-bin histogram of observable col (rf_hist64), the network's forward
+ * pass (with the output de-standardisation of rf_mlp_train), and the
+ * prediction in theta0 (HOST, n_sets x n_free doubles, the model's free
+ * parameters in order; a start for rf_fit).  The network must map 64 inputs
+ * to the model's n_free outputs (RF_E_INVALID otherwise).  Synchronous. */
+rf_status rf_mlp_predict(rf_mlp* n, const rf_model* m, const rf_data* d, int32_t col, double* theta0);
 rf_status rf_mlp_save(const rf_mlp* n, const char* path);
 rf_status rf_mlp_load(const char* path, rf_mlp** out);
 

@@ -81,6 +81,7 @@ SIGNATURES = {
     "rf_mlp_get_params": (C.c_int, [_vp, C.POINTER(C.c_float)]),
     "rf_mlp_set_params": (C.c_int, [_vp, C.POINTER(C.c_float)]),
     "rf_mlp_forward": (C.c_int, [_vp, _vp, C.c_int32, _vp, _vp]),
+    "rf_mlp_predict": (C.c_int, [_vp, _vp, _vp, C.c_int32, _dp]),
     "rf_mlp_grad": (C.c_int, [_vp, _vp, _vp, C.c_int32, C.POINTER(C.c_float), _vp, _vp]),
     "rf_mlp_adam": (C.c_int, [_vp, C.c_float, _vp]),
     "rf_mlp_train": (C.c_int, [_vp, _vp, _vp, C.c_int32, C.c_int32, C.c_int32, C.c_float, C.c_uint64, C.c_int32,

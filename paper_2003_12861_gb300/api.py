@@ -413,6 +413,12 @@ class MLP:
         L.check(L.load().rf_mlp_forward(self._h, C.c_void_p(d_x.data_ptr()), d_x.shape[0],
                                         C.c_void_p(d_y.data_ptr()), _stream(stream)))
 
+    def predict(self, model: Model, data: Data, col: int = 0) -> np.ndarray:
+        """Learned fit starts (rf_mlp_predict): n_sets x n_free, host."""
+        out = np.zeros(data.n_sets * model.n_free)
+        L.check(L.load().rf_mlp_predict(self._h, model._h, data._h, col, _dp(out)))
+        return out.reshape(data.n_sets, model.n_free)
+
     def grad(self, d_x, d_t, d_grad=None, stream=None):
         loss = C.c_float()
         L.check(L.load().rf_mlp_grad(self._h, C.c_void_p(d_x.data_ptr()), C.c_void_p(d_t.data_ptr()),

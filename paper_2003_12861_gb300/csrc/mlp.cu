@@ -235,6 +235,7 @@ struct rf_mlp {
   std::vector<int64_t> w_off, b_off;
   DevBuf params, grads, m, v;
   DevBuf acts, zs, dbuf, dbuf2, y, t_std, loss, idx, xb, tb, mean, sd, scale, shift;
+  DevBuf pred_h, pred_y;  // rf_mlp_predict: histograms and outputs of the sets
   int cap = 0;  // batch capacity of the activation buffers
   int64_t step = 0;
   bool has_affine = false;
@@ -581,3 +582,27 @@ rf_status rf_mlp_load(const char* path, rf_mlp** out) {
 }
 
 }  // extern "C"
+
+extern "C" rf_status rf_mlp_predict(rf_mlp* n, const rf_model* m, const rf_data* d, int32_t col, double* theta0) {
+  if (!n || !m || !d || !theta0) {
+    set_error("rf_mlp_predict: bad argument (NULL)");
+    return RF_E_INVALID;
+  }
+  const int S = rf_data_n_sets(d), no = n->dims.back();
+  if (n->dims.front() != 64 || no != rf_model_n_free(m)) {
+    set_error("rf_mlp_predict: the network must map 64 histogram bins to the model's free parameters");
+    return RF_E_INVALID;
+  }
+  if (S == 0) return RF_OK;
+  if (!n->pred_h.ensure(sizeof(float) * (size_t)S * 64) || !n->pred_y.ensure(sizeof(float) * (size_t)S * no))
+    return RF_E_OOM;
+  rf_status st = rf_hist64(m, d, col, (float*)n->pred_h.p, nullptr);
+  if (st != RF_OK) return st;
+  st = rf_mlp_forward(n, (const float*)n->pred_h.p, S, (float*)n->pred_y.p, nullptr);
+  if (st != RF_OK) return st;
+  std::vector<float> y((size_t)S * no);
+  if (!cuda_ok(cudaMemcpy(y.data(), n->pred_y.p, sizeof(float) * y.size(), cudaMemcpyDeviceToHost), "rf_mlp_predict"))
+    return RF_E_CUDA;
+  for (size_t i = 0; i < y.size(); ++i) theta0[i] = (double)y[i];
+  return RF_OK;
+}

@@ -64,13 +64,7 @@ def train(X, Y, epochs: int = 30, batch: int = 1024, lr: float = 1e-3, seed: int
 
 
 def predict_starts(net, model, data):
-    import torch
-
-    h = _hist(model, data, torch)
-    y = torch.zeros(data.n_sets, 6, dtype=torch.float32, device="cuda")
-    net.forward(h, y)
-    torch.cuda.synchronize()
-    return y.cpu().numpy().astype(np.float64)
+    return net.predict(model, data, 0)
 
 
 def compare(net, model, n_toys: int, seed: int, tol_edm: float = 1e-7, n_lo: float = 1e3, n_hi: float = 1e5):

@@ -103,3 +103,25 @@ def test_training_learns_and_checkpoints(tmp_path):
     n1.train(dx, dt, batch=256, epochs=2, seed=4)
     n2.train(dx, dt, batch=256, epochs=2, seed=4)
     assert np.array_equal(n1.get_params(), n2.get_params())
+
+
+def test_predict_is_histogram_then_forward():
+    """rf_mlp_predict: per set the 64-bin histogram, the forward pass and the
+    prediction on the host -- the same values as the two calls by hand."""
+    from paper_2003_12861_gb300 import workloads as W
+
+    m = api.Model.from_spec(W.decay_model())
+    S = 7
+    d = api.generate_toys(m, np.tile(W.DECAY_TRUE, (S, 1)), 31, np.full(S, 2500.0))
+    net = api.MLP(seed=5)
+    got = net.predict(m, d)
+    assert got.shape == (S, m.n_free)
+    h = torch.zeros(S * 64, dtype=torch.float32, device="cuda")
+    api.hist64(m, d, 0, h)
+    y = torch.zeros(S, 6, dtype=torch.float32, device="cuda")
+    net.forward(h.view(S, 64), y)
+    torch.cuda.synchronize()
+    assert np.array_equal(got, y.cpu().numpy().astype(np.float64))
+    bad = api.MLP(n_in=64, n_hidden=16, n_hidden_layers=1, n_out=4, seed=1)
+    with pytest.raises(RuntimeError):
+        bad.predict(m, d)
