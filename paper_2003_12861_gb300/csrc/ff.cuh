@@ -152,11 +152,9 @@ __device__ __forceinline__ void ff_acc_mul(ff& acc, ff a, ff b) {
 }
 
 // ---------------------------------------------------------------- exp
-__device__ __forceinline__ ff ff_exp(const FFTables& T, ff x, bool& ok) {
-  const float kf = rintf(__fmul_rn(x.hi, kExpK));
-  ok = ok && fabsf(x.hi) < 80.0f;
-  const int k = ok ? (int)kf : 0;
-  const float kk = ok ? kf : 0.0f;
+// The reduction and reconstruction for an integer kk = k = rint(x 256/ln2)
+// whose 2^(k >> 8) scale is a normal float.
+__device__ __forceinline__ ff ff_exp_k(const FFTables& T, ff x, int k, float kk) {
   // r = x - k ln2/256, the large cancellation exact
   const float t1 = __fmaf_rn(-kk, kLn2_256_1, x.hi);
   const ff p2 = two_prod(kk, kLn2_256_2);
@@ -180,9 +178,22 @@ __device__ __forceinline__ ff ff_exp(const FFTables& T, ff x, bool& ok) {
   ff res = fast_two_sum(t.hi, tp.hi);
   res.lo = __fadd_rn(res.lo, __fadd_rn(t.lo, tp.lo));
   res = fast_two_sum(res.hi, res.lo);
-  ok = ok && m >= -100 && m <= 100;
-  const float sc = __int_as_float(((ok ? m : 0) + 127) << 23);
-  return ff_scale(res, sc);
+  return ff_scale(res, __int_as_float((m + 127) << 23));
+}
+
+__device__ __forceinline__ ff ff_exp(const FFTables& T, ff x, bool& ok) {
+  const float kf = rintf(__fmul_rn(x.hi, kExpK));
+  ok = ok && fabsf(x.hi) < 80.0f;
+  const int k = ok ? (int)kf : 0;
+  ok = ok && (k >> 8) >= -100 && (k >> 8) <= 100;
+  return ff_exp_k(T, x, ok ? k : 0, ok ? kf : 0.0f);
+}
+
+// exp for |x.hi| <= 69, which the caller has checked: |k| <= 25484, so
+// 2^(k >> 8) is within 2^+-100 and no further range test is needed.
+__device__ __forceinline__ ff ff_exp_in_range(const FFTables& T, ff x) {
+  const float kf = rintf(__fmul_rn(x.hi, kExpK));
+  return ff_exp_k(T, x, (int)kf, kf);
 }
 
 // ---------------------------------------------------------------- log

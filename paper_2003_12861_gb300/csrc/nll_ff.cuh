@@ -245,13 +245,18 @@ __device__ __forceinline__ ff ldc(const float* k, int i) { return {k[i], k[i + 1
 
 // exp, with arguments below -69 giving 0 and setting `dropped`: such a term
 // (a normalised density below 1e-30) is negligible when the event's total
-// density is at least 1e-14, which the caller then checks.
+// density is at least 1e-14, which the caller then checks.  Arguments above
+// 69 (or NaN) clear ok.
 __device__ __forceinline__ ff ff_exp0(const FFTables& T, ff x, bool& ok, bool& dropped) {
   if (x.hi < -69.0f) {
     dropped = true;
     return {0.0f, 0.0f};
   }
-  return ff_exp(T, x, ok);
+  if (!(x.hi <= 69.0f)) {
+    ok = false;
+    return {1.0f, 0.0f};
+  }
+  return ff_exp_in_range(T, x);
 }
 
 // Normalised decay signal density v and the derivative ratio R at t (the
