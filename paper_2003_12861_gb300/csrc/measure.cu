@@ -81,7 +81,7 @@ __global__ void probe_trans_ff(double* out, int events, int n_exp, int n_erfc, i
   ff x = ff_from_double(0.5 + (blockIdx.x * blockDim.x + threadIdx.x) * 1e-9);
   const ff step = {1e-6f, 0.f};
   for (int i = 0; i < events; ++i) {
-    for (int k = 0; k < n_exp; ++k) ff_acc(acc, ff_exp(T, ff_mul_f(x, -(1.0f + 0.25f * k)), ok));
+    for (int k = 0; k < n_exp; ++k) ff_acc(acc, ff_exp_in_range(T, ff_mul_f(x, -(1.0f + 0.25f * k))));
     for (int k = 0; k < n_erfc; ++k) ff_acc(acc, ff_erfcx(T, ff_add_f(ff_mul_f(x, 1.0f + 0.25f * k), 0.3f), ok));
     for (int k = 0; k < n_log; ++k) ff_acc(acc, ff_log(T, ff_add_f(x, (float)k), ok));
     for (int k = 0; k < n_rcp; ++k) ff_acc(acc, ff_rcp_u(ff_add_f(x, (float)k)));
