@@ -286,10 +286,19 @@ __device__ __forceinline__ ff decay_shape(const FFTables& T, const float* k, ff 
     *R = ff_mul_u(two_over_sqrtpi, ff_rcp_u(ex));
     return half_g_ex;
   }
-  bool dq = false;  // exp(-z^2) only scales R
-  const ff q = ff_exp0(T, ff_neg(ff_sqr(z)), ok, dq);
+  const ff ev = ff_exp0(T, logv, ok, dropped);
+  // q = exp(-z^2) = G / exp(logv): both exponents carry log(1/I), and
+  // A - z^2 = -u^2/2 (one reciprocal instead of an exponential; q only
+  // scales R)
+  ff q;
+  if (G.hi > 0.0f && ev.hi > 0.0f) {
+    q = ff_mul_u(G, ff_rcp_u(ev));
+  } else {
+    bool dq = false;
+    q = ff_exp0(T, ff_neg(ff_sqr(z)), ok, dq);
+  }
   *R = ff_mul_u(ff_mul_u(two_over_sqrtpi, q), ff_rcp_u(ff_fma(ff_neg(q), ex, ff{2.0f, 0.0f})));
-  return ff_sub(ff_exp0(T, logv, ok, dropped), half_g_ex);
+  return ff_sub(ev, half_g_ex);
 }
 
 // Per-shape event programs.  Each adds the event's moments to acc and
