@@ -8,7 +8,7 @@ evaluated by its kernels (rf_mlp_*); PyTorch holds the device buffers.
 Training labels are the plain fits' minima (theta-hat) of each training toy,
 whose generating parameters are drawn uniformly within +-30 % of the decay
 model's values; the plain fit from the default start is also the fallback
-and the judge: a learned start that fails (outside the domain, or no
+and the yardstick: a learned start that fails (outside the domain, or no
 convergence) is refitted from the default start, and a learned fit that ends
 in a different minimum (|delta NLL| >= 1e-6) is counted and reported.
 """
