@@ -1010,18 +1010,20 @@ __global__ void __launch_bounds__(kLanes, ff_min_blocks(kShape)) events_ff(const
     int qs = 0;
     unsigned myfb = 0u;
     const int k0 = part * kPartK;
-    // the next event's observables are loaded one iteration ahead
-    int64_t e = base + tid + (int64_t)k0 * kLanes;
+    // events of the chunk present (32-bit offsets within the chunk); the
+    // next event's observables are loaded one iteration ahead
+    const int rem = (int)(s_end - base < (int64_t)kChunk ? s_end - base : (int64_t)kChunk);
+    int off = tid + k0 * kLanes;
     FFRaw<kShape> nxt;
-    if (e < s_end) nxt = ff_load_raw<kShape>(cols, col, e);
+    if (off < rem) nxt = ff_load_raw<kShape>(cols, col, base + off);
 #pragma unroll 1
-    for (int k = k0; k < k0 + kPartK; ++k, e += kLanes) {
+    for (int k = k0; k < k0 + kPartK; ++k, off += kLanes) {
       const FFIn<kShape> cur = ff_split_in<kShape>(cols, col, nxt);
-      if (k + 1 < k0 + kPartK && e + kLanes < s_end) nxt = ff_load_raw<kShape>(cols, col, e + kLanes);
+      if (k + 1 < k0 + kPartK && off + kLanes < rem) nxt = ff_load_raw<kShape>(cols, col, base + off + kLanes);
       int st = 0;
-      if (e < s_end) st = ff_event<kShape, kGrad, false>(T, kc, cur, acc, lpd);
+      if (off < rem) st = ff_event<kShape, kGrad, false>(T, kc, cur, acc, lpd);
       const unsigned bs = __ballot_sync(0xffffffffu, st == 1);
-      if (st == 1) sm.queue[warp][qs + __popc(bs & lt)] = (short)(e - base);
+      if (st == 1) sm.queue[warp][qs + __popc(bs & lt)] = (short)off;
       if (st == 2) myfb |= 1u << k;
       qs += __popc(bs);
     }
