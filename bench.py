@@ -302,6 +302,9 @@ def roofline(api, model, spec, data, kern_ms, kern_n, n_events, bpe, peaks, peak
     ff = "kernel=ff_" in model.describe()
     alu, hbm, basis = transcendental_ceiling(api, spec, slow_frac, n_events, bpe, peaks, peak_kind, ff)
     alu0, _, _ = transcendental_ceiling(api, spec, slow_frac, n_events, bpe, peaks, peak_kind, ff, n_log=0)
+    # the fixed per-event count (every event charged the resolution region's
+    # full set, whether or not its region needs it)
+    alu_fixed, _, _ = transcendental_ceiling(api, spec, 1.0, n_events, bpe, peaks, peak_kind, ff)
     ceiling = min(alu, hbm)
     avg = kern_ms / max(1, kern_n)
     achieved = n_events / (avg * 1e-3)
@@ -313,6 +316,7 @@ def roofline(api, model, spec, data, kern_ms, kern_n, n_events, bpe, peaks, peak
         "fp64_fma_tflops_measured": api.probe(0) / 1e12,
         "hbm_frac": achieved * bpe / (peaks["hbm_gbs"] * 1e9),
         "peak_without_log": min(alu0, hbm) / 1e9, "frac_without_log": achieved / min(alu0, hbm),
+        "peak_fixed_count": min(alu_fixed, hbm) / 1e9, "frac_fixed_count": achieved / min(alu_fixed, hbm),
     }
 
 
