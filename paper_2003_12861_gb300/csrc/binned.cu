@@ -14,10 +14,15 @@
 // parameter k: a normfactor or normsys on sample s contributes dlog(factor)
 // / dtheta_k sum_i w nu_s[i], a histosys F_s sum_i w (a_i + b_i g').
 //
-// One block per dataset (persistent over datasets), FP64 throughout, every
-// sum in a fixed order (each thread's bins / samples / modifiers in index
-// order, a fixed tree across threads), so results do not depend on the
-// launch.
+// One block per dataset (persistent over datasets), every sum in a fixed
+// order (each thread's bins / samples / modifiers in index order, a fixed
+// tree across threads), so results do not depend on the launch.  The two
+// loops that carry nearly all the multiply-adds -- the entries' histosys
+// sums and the histosys modifiers' weighted coefficient sums -- and the
+// samples' weighted sums run in float-float on the FP32 pipe (ff.cuh: FP64
+// issues at 1/58 of the FP32 rate); the sample factors, the bins' Poisson
+// terms and weights, the gradient's assembly and the expected counts stay
+// in FP64.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -26,6 +31,7 @@
 #include <vector>
 
 #include "api_internal.h"
+#include "ff.cuh"
 
 namespace rf {
 
@@ -34,10 +40,11 @@ namespace {
 constexpr int kBinnedThreads = 256;
 constexpr int kMaxBinnedBins = 8192, kMaxBinnedSamples = 2048;
 
-// Dynamic shared memory of the kernels: theta, F and Ssum per sample, W per
-// bin, one partial sum per thread, g and g' per parameter.
+// Dynamic shared memory of the kernels (8-byte slots): theta, F and Ssum per
+// sample, W per bin (a float pair), one partial sum per thread, g and g' per
+// parameter, then theta, g and F as float pairs.
 size_t binned_smem(int n_params, int n_samples, int n_bins) {
-  return sizeof(double) * (3 * (size_t)n_params + 2 * (size_t)n_samples + (size_t)n_bins + kBinnedThreads);
+  return sizeof(double) * (5 * (size_t)n_params + 3 * (size_t)n_samples + (size_t)n_bins + kBinnedThreads);
 }
 
 enum ModKind : int32_t { MOD_NORMFACTOR = 0, MOD_NORMSYS = 1, MOD_HISTOSYS = 2 };
@@ -70,6 +77,14 @@ struct BinnedDev {
   const int32_t* g_sample;    // per position in shs: its sample
   const double* coef_a;
   const double* coef_b;
+  // The nominal rates and the histosys coefficients again as float pairs
+  // (same indexing), for the float-float loops.
+  const float2* nominal_f;
+  const float2* coef_f;
+  const int32_t* shs_k;       // per position in shs: the histosys's parameter and
+  const int64_t* shs_ofs;     //   coefficient offset (one load level instead of two)
+  const float2* coef_af;
+  const float2* coef_bf;
   const int32_t* bin_start;   // per bin: its entries (CSR, sample order)
   const int32_t* bin_entry;
   const int32_t* pmod_start;  // per parameter: its modifiers (CSR, modifier order)
@@ -119,6 +134,30 @@ __device__ __forceinline__ void entry_rates(const BinnedDev& m, const double* th
   }
 }
 
+__device__ __forceinline__ ff ld_pair(const float2* p) {
+  const float2 v = __ldg(p);
+  return {v.x, v.y};
+}
+__device__ __forceinline__ ff as_ff(double v) { return ff_from_double(v); }
+
+// The same rates in float-float from the pairs' copies of the constants:
+// thf, gkf, Ff = theta, g, F as pairs.
+__device__ __forceinline__ void entry_rates_ff(const BinnedDev& m, const ff* thf, const ff* gkf, const ff* Ff,
+                                               ff* nu_e) {
+  for (int e = threadIdx.x; e < m.n_entries; e += kBinnedThreads) {
+    const int s = m.esample[e], i = e - m.eofs[s], n = m.nb[s];
+    ff shape = ld_pair(m.nominal_f + e);
+    const int j1 = m.shs_start[s + 1];
+#pragma unroll 4
+    for (int j = m.shs_start[s]; j < j1; ++j) {
+      const int k = __ldg(m.shs_k + j);
+      const float2* c = m.coef_f + __ldg(m.shs_ofs + j) + i;
+      shape = ff_fma(ld_pair(c + n), gkf[k], ff_fma(ld_pair(c), thf[k], shape));
+    }
+    nu_e[e] = ff_mul(Ff[s], shape);
+  }
+}
+
 // out[set]: NLL then gradient (1 + n_params); flags[set]: 1 if some bin has
 // nu <= 0 (NLL +inf).  scratch: per block n_entries (entry rates) +
 // n_hs (histosys sums) doubles.
@@ -130,55 +169,71 @@ __global__ void __launch_bounds__(kBinnedThreads) binned_kernel(const BinnedDev 
   double* th = smem;
   double* F = th + m.n_params;
   double* Ssum = F + m.n_samples;
-  double* W = Ssum + m.n_samples;
-  double* part = W + m.n_bins;
+  ff* W = reinterpret_cast<ff*>(Ssum + m.n_samples);
+  double* part = reinterpret_cast<double*>(W + m.n_bins);
   double* gk = part + kBinnedThreads;
   double* dgk = gk + m.n_params;
+  ff* thf = reinterpret_cast<ff*>(dgk + m.n_params);
+  ff* gkf = thf + m.n_params;
+  ff* Ff = gkf + m.n_params;
   __shared__ int bad;
   const int tid = threadIdx.x;
-  double* nu_e = scratch + (size_t)blockIdx.x * (m.n_entries + m.n_hs);
-  double* T = nu_e + m.n_entries;
+  ff* nu_e = reinterpret_cast<ff*>(scratch + (size_t)blockIdx.x * (m.n_entries + m.n_hs));
+  double* T = reinterpret_cast<double*>(nu_e + m.n_entries);
   for (int set = blockIdx.x; set < n_sets; set += gridDim.x) {
     const double* n = counts + (size_t)(sets ? sets[set] : set) * m.n_bins;
     if (tid == 0) bad = 0;
     sample_factors(m, theta + (size_t)set * m.n_params, th, gk, dgk, F);
-    entry_rates(m, th, gk, F, nu_e);
+    for (int k = tid; k < m.n_params; k += kBinnedThreads) {
+      thf[k] = as_ff(th[k]);
+      gkf[k] = as_ff(gk[k]);
+    }
+    for (int s = tid; s < m.n_samples; s += kBinnedThreads) Ff[s] = as_ff(F[s]);
+    __syncthreads();
+    entry_rates_ff(m, thf, gkf, Ff, nu_e);
     __syncthreads();
     // bins: expected count, weight 1 - n/nu, the Poisson term
     double acc = 0.0;
     for (int b = tid; b < m.n_bins; b += kBinnedThreads) {
-      double nu = 0.0;
-      for (int j = m.bin_start[b]; j < m.bin_start[b + 1]; ++j) nu += nu_e[m.bin_entry[j]];
+      ff nf = {0.0f, 0.0f};
+      const int j1 = m.bin_start[b + 1];
+#pragma unroll 4
+      for (int j = m.bin_start[b]; j < j1; ++j) nf = ff_add(nf, nu_e[__ldg(m.bin_entry + j)]);
+      const double nu = ff_to_double(nf);
       if (!(nu > 0.0) || !isfinite(nu)) {
         bad = 1;
-        W[b] = 0.0;
+        W[b] = {0.0f, 0.0f};
         continue;
       }
-      W[b] = 1.0 - n[b] / nu;
+      W[b] = as_ff(1.0 - n[b] / nu);
       acc += nu - (n[b] != 0.0 ? n[b] * log(nu) : 0.0);
     }
     part[tid] = acc;
     __syncthreads();
     // per sample sum_i w nu_s[i]; per histosys sum_i w (a_i + b_i g')
     for (int s = tid; s < m.n_samples; s += kBinnedThreads) {
-      double a = 0.0;
-      for (int i = 0; i < m.nb[s]; ++i) a += W[m.bin0[s] + i] * nu_e[m.eofs[s] + i];
-      Ssum[s] = a;
+      ff a = {0.0f, 0.0f};
+      const int nbs = m.nb[s], b0 = m.bin0[s], e0 = m.eofs[s];
+#pragma unroll 4
+      for (int i = 0; i < nbs; ++i) ff_acc_mul(a, W[b0 + i], nu_e[e0 + i]);
+      Ssum[s] = ff_to_double(a);
     }
     // (a thread each, bins in order; consecutive threads read consecutive
     // coefficients of the transposed layout)
     for (int g = tid; g < m.n_hs; g += kBinnedThreads) {
       const int s = m.g_sample[g], h = m.shs[g];
       const int nh = m.shs_start[s + 1] - m.shs_start[s], j = g - m.shs_start[s];
-      const double* ca = m.coef_a + m.tbase[s] + j;
-      const double* cb = m.coef_b + m.tbase[s] + j;
-      const double* w = W + m.bin0[s];
-      double ta = 0.0, tb = 0.0;
-      for (int i = 0; i < m.nb[s]; ++i) {
-        ta = fma(w[i], ca[(size_t)i * nh], ta);
-        tb = fma(w[i], cb[(size_t)i * nh], tb);
+      const float2* ca = m.coef_af + m.tbase[s] + j;
+      const float2* cb = m.coef_bf + m.tbase[s] + j;
+      const ff* w = W + m.bin0[s];
+      ff ta = {0.0f, 0.0f}, tb = {0.0f, 0.0f};
+      const int nbs = m.nb[s];
+#pragma unroll 4
+      for (int i = 0; i < nbs; ++i) {
+        ff_acc_mul(ta, w[i], ld_pair(ca + (size_t)i * nh));
+        ff_acc_mul(tb, w[i], ld_pair(cb + (size_t)i * nh));
       }
-      T[h] = fma(dgk[m.hs_param[h]], tb, ta);
+      T[h] = fma(dgk[m.hs_param[h]], ff_to_double(tb), ff_to_double(ta));
     }
     // NLL: the threads' partial sums by a fixed tree
     for (int o = kBinnedThreads / 2; o > 0; o >>= 1) {
@@ -244,7 +299,7 @@ struct rf_binned {
   int32_t n_bins = 0, n_samples = 0, n_params = 0, n_mods = 0, n_entries = 0, n_hs = 0;
   rf::DevBuf bin0, nb, eofs, esample, nominal, smod_start, smod, shs_start, shs, kind, param, msample, mhs, ns_a,
       ns_b, hs_param, hs_sample, hs_ofs, coef, tbase, g_sample, coef_a, coef_b, bin_start, bin_entry, pmod_start, pmod,
-      constrained;
+      constrained, nominal_f, coef_f, coef_af, coef_bf, shs_k, shs_ofs;
   rf::DevBuf scratch, counts, theta, out, flags, sets;
   rf::HostBuf h_out, h_flags, h_theta, h_sets;
   rf::BinnedDev dev{};
@@ -399,7 +454,25 @@ rf_status rf_binned_create(int32_t n_bins, int32_t n_samples, const int32_t* bin
   const std::vector<double> vnom(nominal, nominal + total);
   std::vector<int32_t> vcon(n_params);
   for (int k = 0; k < n_params; ++k) vcon[k] = constrained[k] ? 1 : 0;
-  const bool ok = upload(m->bin0, vb0) && upload(m->nb, vnb) && upload(m->eofs, eofs) && upload(m->esample, esample) &&
+  std::vector<int32_t> shs_k(shs.size());
+  std::vector<int64_t> shs_ofs(shs.size());
+  for (size_t j = 0; j < shs.size(); ++j) {
+    shs_k[j] = hs_param[shs[j]];
+    shs_ofs[j] = hs_ofs[shs[j]];
+  }
+  // float-pair copies: hi = the float nearest v, lo = the float nearest v - hi
+  auto pairs = [](const std::vector<double>& v) {
+    std::vector<float2> f(v.size());
+    for (size_t i = 0; i < v.size(); ++i) {
+      const float h = (float)v[i];
+      f[i] = make_float2(h, (float)(v[i] - (double)h));
+    }
+    return f;
+  };
+  const bool ok = upload(m->shs_k, shs_k) && upload(m->shs_ofs, shs_ofs) &&
+                  upload(m->nominal_f, pairs(vnom)) && upload(m->coef_f, pairs(coef)) &&
+                  upload(m->coef_af, pairs(coef_a)) && upload(m->coef_bf, pairs(coef_b)) &&
+                  upload(m->bin0, vb0) && upload(m->nb, vnb) && upload(m->eofs, eofs) && upload(m->esample, esample) &&
                   upload(m->nominal, vnom) && upload(m->smod_start, smod_start) && upload(m->smod, smod) &&
                   upload(m->shs_start, shs_start) && upload(m->shs, shs) && upload(m->kind, kind) &&
                   upload(m->param, param) && upload(m->msample, msample) && upload(m->mhs, mhs) &&
@@ -460,6 +533,12 @@ rf_status rf_binned_create(int32_t n_bins, int32_t n_samples, const int32_t* bin
   D.g_sample = (const int32_t*)m->g_sample.p;
   D.coef_a = (const double*)m->coef_a.p;
   D.coef_b = (const double*)m->coef_b.p;
+  D.nominal_f = (const float2*)m->nominal_f.p;
+  D.shs_k = (const int32_t*)m->shs_k.p;
+  D.shs_ofs = (const int64_t*)m->shs_ofs.p;
+  D.coef_f = (const float2*)m->coef_f.p;
+  D.coef_af = (const float2*)m->coef_af.p;
+  D.coef_bf = (const float2*)m->coef_bf.p;
   D.bin_start = (const int32_t*)m->bin_start.p;
   D.bin_entry = (const int32_t*)m->bin_entry.p;
   D.pmod_start = (const int32_t*)m->pmod_start.p;
