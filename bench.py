@@ -618,6 +618,7 @@ def run_binned(args, api, torch, dist, rank, world, local):
     fit_s = time.perf_counter() - t0
     fl = binned_flops(spec)
     fp64 = api.probe(0)
+    fffma = 2.0 * api.probe(6)  # float-float multiply-adds, counted as 2 flops each
     achieved = S * fl / (ms * 1e-3)
     return {
         "value": world * S / (ms * 1e-3), "unit": "datasets/s", "ms_per_step": ms, "dtype": "f64",
@@ -625,9 +626,11 @@ def run_binned(args, api, torch, dist, rank, world, local):
                    "parameters": P, "modifiers": len(spec["modifiers"]),
                    "histograms": len(spec["nominal"]) + 2 * sum(1 for md in spec["modifiers"] if md[1] == 2),
                    "l2": "flushed between steps (256 MiB write); the model's histograms (3.6 MB) are re-read from L2"},
-        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": fp64 / 1e12, "unit": "TFLOP/s",
-                     "frac": achieved / fp64, "traffic": None,
-                     "peak_basis": f"FP64 FMA rate measured in-run; {fl} algorithmic FP64 flops per dataset"},
+        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": fffma / 1e12, "unit": "TFLOP/s",
+                     "frac": achieved / fffma, "traffic": None,
+                     "peak_basis": f"float-float multiply-add rate measured in-run (the kernel's multiply-add "
+                                   f"loops run in float-float); {fl} algorithmic flops per dataset",
+                     "fp64_fma_tflops_measured": fp64 / 1e12, "frac_of_fp64_fma": achieved / fp64},
         "e2e": {"value": world * S / e2e_s, "unit": "datasets/s", "h2d_bytes_per_step": S * (Bn + P) * 8,
                 "d2h_bytes_per_step": S * (1 + P) * 8 + S * 4},
         "gpu_launches": int(n_launches), "clocks": clk.summary(),

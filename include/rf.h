@@ -378,6 +378,8 @@ rf_status rf_slow_events(const rf_data* d, int64_t* count);
  *           (exp, erfcx for erfc, log, reciprocal)  -> *rate in events/s
  *   kind 5: streaming read of pinned host memory by the SMs, in place over
  *           the host link                           -> *rate in bytes/s
+ *   kind 6: float-float multiply-add rate (a b + c on float pairs, the
+ *           library's ff_fma)                       -> *rate in multiply-adds/s
  * Each probe allocates and frees its own scratch. */
 rf_status rf_probe(int32_t kind, int32_t n_exp, int32_t n_erfc, int32_t n_log, int32_t n_rcp, double* rate);
 

@@ -56,6 +56,20 @@ __global__ void probe_ffma(double* out, int iters, float a, float b) {
   out[blockIdx.x * blockDim.x + threadIdx.x] = (double)(x0 + x1 + x2 + x3 + x4 + x5 + x6 + x7);
 }
 
+// Float-float multiply-adds (ff_fma: a b + c on float pairs), eight
+// independent chains per thread.
+__global__ void probe_fffma(double* out, int iters, float a, float b) {
+  const ff A = {a, a * 1e-9f}, B = {b, b * 1e-9f};
+  ff x[8];
+  for (int j = 0; j < 8; ++j) x[j] = {threadIdx.x * 1e-3f + j, 0.0f};
+  for (int i = 0; i < iters; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) x[j] = ff_fma(x[j], A, B);
+  double sum = 0.0;
+  for (int j = 0; j < 8; ++j) sum += ff_to_double(x[j]);
+  out[blockIdx.x * blockDim.x + threadIdx.x] = sum;
+}
+
 // Per "event": the requested numbers of exp, erfc, log and reciprocal calls on
 // arguments that change every event (so nothing is hoisted), summed.
 __global__ void probe_trans(double* out, int events, int n_exp, int n_erfc, int n_log, int n_rcp) {
@@ -213,7 +227,7 @@ rf_status rf_data_refill(rf_data* d, const void* const* cols, void* stream) {
 }
 
 rf_status rf_probe(int32_t kind, int32_t n_exp, int32_t n_erfc, int32_t n_log, int32_t n_rcp, double* rate) {
-  if (!rate || kind < 0 || kind > 5 || n_exp < 0 || n_erfc < 0 || n_log < 0 || n_rcp < 0) {
+  if (!rate || kind < 0 || kind > 6 || n_exp < 0 || n_erfc < 0 || n_log < 0 || n_rcp < 0) {
     set_error("rf_probe: bad argument");
     return RF_E_INVALID;
   }
@@ -260,6 +274,10 @@ rf_status rf_probe(int32_t kind, int32_t n_exp, int32_t n_erfc, int32_t n_log, i
       const int ev = 512;
       probe_trans_ff<<<blocks, threads>>>((double*)out.p, ev, n_exp, n_erfc, n_log, n_rcp);
       work = (double)ev * threads * blocks;
+    } else if (kind == 6) {
+      const int it = 2048;
+      probe_fffma<<<blocks, threads>>>((double*)out.p, it, 0.999999f, 1e-7f);
+      work = 8.0 * it * (double)threads * blocks;  // multiply-adds
     } else {
       probe_read<<<nsm * 4, 512>>>(src, n2, (double*)out.p);
       work = (double)n2 * sizeof(double2);
