@@ -1,0 +1,81 @@
+"""Write oracle_nll.json: the CPU oracle's NLL and gradient on seeded datasets
+drawn by the oracle's own counter-based generator.
+
+Only the oracle and the input recipe (model node lists, parameter values,
+seeds) are used; nothing here touches the CUDA library.  Each case stores the
+generating recipe, a SHA-256 of the event columns (float64, little-endian,
+column after column) so that a reader can confirm it holds the same events,
+and the oracle's NLL = -sum log p_i, gradient, sum |log p_i| and
+sum |dlog p_i/dtheta_k| (the scales of the parity tolerances).
+
+    python tests/golden/make_oracle_golden.py
+"""
+import hashlib
+import json
+import os
+import sys
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(os.path.dirname(HERE))
+sys.path.insert(0, ROOT)
+
+import oracle  # noqa: E402
+from paper_2003_12861_gb300 import workloads as W  # noqa: E402
+
+OUT = os.path.join(HERE, "oracle_nll.json")
+
+
+def cases():
+    """(model constructor, generating theta, seed, events, evaluation points)."""
+    gp_true = W.GAUSS_POLY1_TRUE
+    gp_start = np.array([4.5, 1.0, 0.5, 0.0])
+    d_true = W.DECAY_TRUE
+    d_start = W.DECAY_START
+    d_off = d_true + np.array([0.1, 0.01, -0.01, 0.05, -0.02, 0.03])
+    g_true = W.DECAY_GENERIC_TRUE
+    g_off = g_true + np.array([-0.1, -0.01, 0.02, -0.05, 0.02, -0.03])
+    p_true = W.PROD3_TRUE
+    p_off = p_true + np.array([0.002, 0.001, -0.05, 0.1, 0.1, 0.01, -0.01, 0.05, -0.02, 0.03, -0.05, 0.05])
+    return [
+        ("gauss_poly1_model", gp_true, W.SEED_BASE + 0, 10_000, [gp_true, gp_start]),
+        ("decay_model", d_true, W.SEED_BASE + 1, 20_000, [d_true, d_start, d_off]),
+        ("decay_generic_model", g_true, W.SEED_BASE + 1, 20_000, [g_true, g_off]),
+        ("prod3_model", p_true, W.SEED_BASE + 3, 12_345, [p_true, p_off]),
+    ]
+
+
+def columns_sha256(cols):
+    h = hashlib.sha256()
+    for c in cols:
+        h.update(np.ascontiguousarray(c, dtype="<f8").tobytes())
+    return h.hexdigest()
+
+
+def main():
+    oracle.build()
+    out = []
+    for which, gen_theta, seed, n, points in cases():
+        spec = W.model_for(which)
+        om = oracle.Model(spec.nodes, spec.root)
+        cols = om.generate(gen_theta, seed, 0, 0, n)
+        evals = []
+        for th in points:
+            nll, g, al, ag, rc = om.nll(th, cols)
+            if rc != 0:
+                raise RuntimeError(f"{which}: oracle status {rc}")
+            evals.append({"theta": [float(v) for v in th], "nll": nll, "grad": [float(v) for v in g],
+                          "sum_abs_logp": al, "sum_abs_grad": [float(v) for v in ag]})
+        out.append({"model": which, "generate_theta": [float(v) for v in gen_theta], "seed": seed, "set": 0,
+                    "events": n, "columns_sha256": columns_sha256(cols), "evaluations": evals})
+    doc = {"source": "written by tests/golden/make_oracle_golden.py from the CPU oracle alone",
+           "cases": out}
+    with open(OUT, "w") as f:
+        json.dump(doc, f, indent=1)
+        f.write("\n")
+    print(f"wrote {OUT}: {len(out)} datasets")
+
+
+if __name__ == "__main__":
+    main()

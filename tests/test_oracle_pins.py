@@ -5,6 +5,7 @@ differences, special cases of SUM/PROD and published Philox vectors.
 
 None of these re-types the oracle's closed forms."""
 import math
+import os
 
 import mpmath as mp
 import numpy as np
@@ -261,14 +262,19 @@ def test_invalid_models_rejected(oracle_mod):
         oracle_mod.Model(base + [Node("gauss", (0, 3, 2))], 4)
 
 
-# Known-answer vectors of Philox4x32-10 published with the Random123 library
-# (Salmon et al., SC'11): (counter, key) -> output.
-PHILOX_KAT = [
-    ([0, 0, 0, 0], [0, 0], [0x6627E8D5, 0xE169C58D, 0xBC57AC4C, 0x9B00DBD8]),
-    ([0xFFFFFFFF] * 4, [0xFFFFFFFF] * 2, [0x408F276D, 0x41C83B0E, 0xA20BC7C6, 0x6D5451FD]),
-    ([0x243F6A88, 0x85A308D3, 0x13198A2E, 0x03707344], [0xA4093822, 0x299F31D0],
-     [0xD16CFE09, 0x94FDCCEB, 0x5001E420, 0x24126EA1]),
-]
+def _philox_kat():
+    """Known-answer vectors from tests/golden/philox4x32_10_kat.txt (cited there)."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "philox4x32_10_kat.txt")
+    rows = []
+    with open(path) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                v = [int(w, 16) for w in line.split()]
+                rows.append((v[0:4], v[4:6], v[6:10]))
+    return rows
+
+
+PHILOX_KAT = _philox_kat()
 
 
 @pytest.mark.parametrize("ctr,key,out", PHILOX_KAT)
