@@ -77,7 +77,7 @@ using BatchEval = std::function<rf_status(const std::vector<int32_t>&, std::vect
 // Optional split evaluation for pipelined rounds: the sets [0, split) and
 // [split, S) are evaluated as separate passes, launch queueing one and wait
 // finishing it, so the host updates one half while the other is evaluated;
-// events(sets) counts events, and the driver returns to whole-batch rounds
+// events(sets) counts events, and fit_batch returns to whole-batch rounds
 // once the active events fall below min_events.
 struct SplitEval {
   int64_t split = 0, min_events = 0;
