@@ -140,6 +140,36 @@ def oracle_events_per_s(wl: str, seconds: float, n_sample: int):
     return reps * n_sample / dt, f"{reps} oracle NLL+gradient passes over {n_sample} events of the {ctor}, {dt:.1f} s"
 
 
+def oracle_events_all_cores(wl: str, seconds: float, n_per_thread: int):
+    """The same oracle pass split over every host core: contiguous event
+    slices, one thread each (the oracle's C entry point runs without the
+    interpreter lock), per-slice NLL and gradient summed in slice order."""
+    import oracle
+    from concurrent.futures import ThreadPoolExecutor
+
+    ctor, theta, _, f32, _ = WORKLOADS[wl]
+    spec = W.model_for(ctor)
+    om = oracle.Model(spec.nodes, spec.root)
+    T = os.cpu_count() or 1
+    cols = om.generate(theta, W.SEED_BASE + 1, 0, 0, n_per_thread * T)
+    if f32:
+        cols = [c.astype(np.float32).astype(np.float64) for c in cols]
+    slices = [[c[t * n_per_thread:(t + 1) * n_per_thread] for c in cols] for t in range(T)]
+    with ThreadPoolExecutor(T) as pool:
+        reps, t0 = 0, time.perf_counter()
+        while True:
+            parts = list(pool.map(lambda sl: om.nll(theta, sl), slices))
+            nll = sum(p[0] for p in parts)
+            grad = np.sum([p[1] for p in parts], axis=0)
+            reps += 1
+            if time.perf_counter() - t0 >= seconds:
+                break
+        dt = time.perf_counter() - t0
+    assert np.isfinite(nll) and np.all(np.isfinite(grad))
+    return (reps * n_per_thread * T / dt, T,
+            f"{reps} oracle passes over {T} threads x {n_per_thread} events of the {ctor}, {dt:.1f} s")
+
+
 def oracle_toy_fits_per_s(seconds: float):
     """The oracle's own fitter on the toy workload's first toys (same seeds,
     sizes and generating parameters), one at a time, single-threaded."""
@@ -187,7 +217,11 @@ def cpu_baseline(wl: str):
         v, s = oracle_toy_fits_per_s(15.0)
         return {"value": v, "unit": "toy fits/s", "cores": 1, "kind": "oracle", "sample": s}
     v, s = oracle_events_per_s(wl, 12.0, 400_000 if wl != "gauss_poly1_1e4" else 10_000)
-    return {"value": v, "unit": "events/s", "cores": 1, "kind": "oracle", "sample": s}
+    out = {"value": v, "unit": "events/s", "cores": 1, "kind": "oracle", "sample": s}
+    if wl != "gauss_poly1_1e4":
+        va, cores, sa = oracle_events_all_cores(wl, 6.0, 100_000)
+        out["all_cores"] = {"value": va, "unit": "events/s", "cores": cores, "sample": sa}
+    return out
 
 
 def run_reference(args):
