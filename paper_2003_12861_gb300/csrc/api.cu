@@ -136,6 +136,8 @@ bool ensure_workspace(const rf_model* m, rf_data* d) {
             w.tree_bad.ensure(sizeof(int32_t) * std::max<int64_t>(1, d->total_nodes)) &&
             w.tickets.ensure(sizeof(int32_t) * std::max<int64_t>(1, d->total_nodes)) &&
             w.counter.ensure(sizeof(int32_t)) && w.slow.ensure(sizeof(unsigned long long)) &&
+            w.slot_counter.ensure(sizeof(int32_t) * kPassSlots) &&
+            w.slot_slow.ensure(sizeof(unsigned long long) * kPassSlots) &&
             (m->m.shape == SHAPE_GENERIC ||
              (w.ffc.ensure(sizeof(float) * S * kFFConst) &&
               w.part_m.ensure(sizeof(float) * nodes * kParts * kPartFloats) &&
@@ -199,8 +201,12 @@ Columns make_columns(const rf_data* d) {
 }
 
 bool launch_pass(const rf_model* m, rf_data* d, const Plan& plan, const double* d_theta, double* d_out,
-                 int32_t* d_flags, bool grad, cudaStream_t st) {
-  const Pass pass = make_pass(m, d, plan, d_theta, d_out, d_flags, grad);
+                 int32_t* d_flags, bool grad, cudaStream_t st, int slot) {
+  Pass pass = make_pass(m, d, plan, d_theta, d_out, d_flags, grad);
+  if (slot >= 0 && slot < kPassSlots) {
+    pass.counter = (int32_t*)d->ws.slot_counter.p + slot;
+    pass.slow = (unsigned long long*)d->ws.slot_slow.p + slot;
+  }
   launch_param_point(m->m.prog, pass, st);
   launch_events(m->m.prog, m->m.shape, make_columns(d), pass, m->m.threads_per_block, m->m.blocks_per_sm,
                 sm_count(), st);

@@ -51,6 +51,9 @@ struct Workspace {
   bool ready = false;
   int n_const = -1, n_free = -1, Q = -1;
   DevBuf consts, theta, out, flags, tree, tree_bad, tickets, counter, slow, ffc, part_m, part_fb, part_info;
+  // work and slow-event counters of passes that may run concurrently on
+  // other streams (launch_pass with slot >= 0)
+  DevBuf slot_counter, slot_slow;
   HostBuf h_theta, h_out, h_flags;
   // rf_nll_grad_stream: its copy stream, compute streams and events
   // (created on first use)
@@ -122,8 +125,12 @@ namespace rf {
 rf_status finish_data(rf_data* d);
 bool build_plan(const rf_data* d, const std::vector<int32_t>& sets, Plan* plan);
 bool ensure_workspace(const rf_model* m, rf_data* d);
+// Queues K1 and the event kernel for the plan's sets.  slot >= 0 (below
+// kPassSlots) gives the pass its own work and slow-event counters, for
+// passes over disjoint sets that run at the same time on different streams.
+constexpr int kPassSlots = 4;
 bool launch_pass(const rf_model* m, rf_data* d, const Plan& plan, const double* d_theta, double* d_out,
-                 int32_t* d_flags, bool grad, cudaStream_t st);
+                 int32_t* d_flags, bool grad, cudaStream_t st, int slot = -1);
 rf_status eval_host(const rf_model* m, rf_data* d, const Plan& plan, const double* theta, double* nll,
                     double* grad, cudaStream_t st);
 }  // namespace rf

@@ -409,8 +409,12 @@ bool invert(std::vector<double> A, int n, double* inv) {
 // results ignored) or a set outside the plan becomes active.  Groups 0 and 1
 // serve the two halves of a pipelined fit (launch, then wait: while one
 // half's pass runs, the host updates the other half), group 2 whole-batch
-// passes (run).  All passes go to one stream, so they never overlap on the
-// device; only the planned sets' range of theta and results is copied.
+// passes (run).  The halves run on streams of their own with their own work
+// counters (their sets, constants, trees and result ranges are disjoint), so
+// one half's parameter point and the start of its event pass overlap the
+// end of the other half's event pass; group 2 shares group 0's stream and
+// runs only when neither half has a pass in flight.  Only the planned sets'
+// range of theta and results is copied.
 struct Evaluator {
   struct Group {
     Plan plan;
@@ -421,19 +425,23 @@ struct Evaluator {
   };
   const rf_model* m;
   rf_data* d;
-  cudaStream_t st = nullptr;
+  cudaStream_t st[2] = {nullptr, nullptr};
   bool use_graph = true;
   Group grp[3];
 
   Evaluator(const rf_model* mm, rf_data* dd, bool graph) : m(mm), d(dd), use_graph(graph) {}
   ~Evaluator() {
-    if (st) cudaStreamSynchronize(st);
+    for (cudaStream_t s : st)
+      if (s) cudaStreamSynchronize(s);
     for (Group& G : grp) {
       if (G.exec) cudaGraphExecDestroy(G.exec);
       if (G.done) cudaEventDestroy(G.done);
     }
-    if (st) cudaStreamDestroy(st);
+    for (cudaStream_t s : st)
+      if (s) cudaStreamDestroy(s);
   }
+
+  static int stream_of(int g) { return g == 1 ? 1 : 0; }
 
   int64_t events_of(const std::vector<int32_t>& sets) const {
     int64_t n = 0;
@@ -464,7 +472,9 @@ struct Evaluator {
     return true;
   }
 
-  rf_status capture(Group& G) {
+  rf_status capture(int g) {
+    Group& G = grp[g];
+    cudaStream_t st = this->st[stream_of(g)];
     if (G.exec) {
       cudaGraphExecDestroy(G.exec);
       G.exec = nullptr;
@@ -476,7 +486,7 @@ struct Evaluator {
     if (!cuda_ok(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "graph capture")) return RF_E_CUDA;
     cudaMemcpyAsync((double*)w.theta.p + s0 * P, (const double*)w.h_theta.p + s0 * P, sizeof(double) * ns * P,
                     cudaMemcpyHostToDevice, st);
-    launch_pass(m, d, G.plan, (const double*)w.theta.p, (double*)w.out.p, (int32_t*)w.flags.p, true, st);
+    launch_pass(m, d, G.plan, (const double*)w.theta.p, (double*)w.out.p, (int32_t*)w.flags.p, true, st, g);
     cudaMemcpyAsync((double*)w.h_out.p + s0 * (1 + P), (const double*)w.out.p + s0 * (1 + P),
                     sizeof(double) * ns * (1 + P), cudaMemcpyDeviceToHost, st);
     cudaMemcpyAsync((int32_t*)w.h_flags.p + s0, (const int32_t*)w.flags.p + s0, sizeof(int32_t) * ns,
@@ -492,10 +502,11 @@ struct Evaluator {
     Group& G = grp[g];
     bool rebuilt = false;
     if (!replan(G, active, &rebuilt)) return RF_E_OOM;
+    cudaStream_t& st = this->st[stream_of(g)];
     if (!st && !cuda_ok(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking), "stream")) return RF_E_CUDA;
     if (!G.done && !cuda_ok(cudaEventCreateWithFlags(&G.done, cudaEventDisableTiming), "event")) return RF_E_CUDA;
     if (rebuilt || !G.exec) {
-      const rf_status s = capture(G);
+      const rf_status s = capture(g);
       if (s != RF_OK) return s;
     }
     Workspace& w = d->ws;

@@ -1148,7 +1148,10 @@ void launch_param_point(const Program& P, const Pass& pass, cudaStream_t st) {
     param_point_block_kernel<<<pass.n_active, kK1Warps * 32, 0, st>>>(P, pass);
     return;
   }
-  const int threads = 128;
+  // two-warp blocks: one fits in the registers that an SM full of event
+  // kernel blocks leaves free, so the K1 of a pass on another stream runs
+  // beside an event pass instead of waiting for its blocks to drain
+  const int threads = 64;
   const int blocks = (pass.n_active + threads - 1) / threads;
   param_point_kernel<<<blocks > 0 ? blocks : 1, threads, 0, st>>>(P, pass);
 }
