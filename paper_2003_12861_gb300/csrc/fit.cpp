@@ -404,7 +404,7 @@ bool invert(std::vector<double> A, int n, double* inv) {
 // into nll/grad (indexed by set).  A pass (parameter upload, the two
 // kernels, result download) is captured once per work plan as a CUDA graph
 // and replayed.  A plan covers a superset of the active sets and is rebuilt
-// only when the events of still-active sets fall below 3/4 of the planned
+// only when the events of still-active sets fall below 15/16 of the planned
 // events (finished sets are re-evaluated at their last point and their
 // results ignored) or a set outside the plan becomes active.  Groups 0 and 1
 // serve the two halves of a pipelined fit (launch, then wait: while one
@@ -463,7 +463,7 @@ struct Evaluator {
       }
     }
     const int64_t need = events_of(active);
-    *rebuilt = !covered || 4 * need < 3 * G.planned_events;
+    *rebuilt = !covered || 16 * need < 15 * G.planned_events;
     if (*rebuilt) {
       if (!build_plan(d, active, &G.plan)) return false;
       G.planned = active;
