@@ -1,5 +1,7 @@
 """Write oracle_nll.json: the CPU oracle's NLL and gradient on seeded datasets
-drawn by the oracle's own counter-based generator.
+drawn by the oracle's own counter-based generator; and oracle_binned.json:
+the binned oracle's NLL and sampled gradient on datasets of the binned
+workload's model.
 
 Only the oracle and the input recipe (model node lists, parameter values,
 seeds) are used; nothing here touches the CUDA library.  Each case stores the
@@ -53,8 +55,45 @@ def columns_sha256(cols):
     return h.hexdigest()
 
 
+BINNED_OUT = os.path.join(HERE, "oracle_binned.json")
+BINNED_GRAD_K = [0, 1, 2] + list(range(3, 256, 23))
+
+
+def binned_cases():
+    """The binned workload's model (28 channels x 50 bins, 256 parameters):
+    two datasets with counts Poisson-drawn at their parameter points
+    (numpy PCG64 draws of the oracle's expected counts, stored as such),
+    each evaluated at its point and at the point shifted by +0.1; the NLL,
+    a sample of gradient components and the tolerance scales."""
+    from oracle import binned as OB
+
+    spec = W.binned_model()
+    om = OB.from_spec(spec)
+    P = spec["n_params"]
+    seed = W.SEED_BASE + 7
+    th = W.binned_toy_thetas(2, seed, P)
+    rng = np.random.Generator(np.random.PCG64(seed + 1))
+    out = []
+    for t in range(2):
+        counts = rng.poisson(om.expected(th[t])[0]).astype(np.int64)
+        evals = []
+        for shift in (0.0, 0.1):
+            x = th[t] + shift
+            nll, g, scale = om.nll(x, counts)
+            evals.append({"shift": shift, "nll": float(nll), "nll_scale": float(scale),
+                          "grad": {str(k): float(g[k]) for k in BINNED_GRAD_K},
+                          "grad_scale": float(np.abs(g).sum() + np.abs(counts).sum() + 1.0)})
+        out.append({"theta_recipe": f"workloads.binned_toy_thetas(2, {seed}, {P})[{t}] + shift",
+                    "counts": " ".join(str(int(c)) for c in counts), "evaluations": evals})
+    return {"source": "written by tests/golden/make_oracle_golden.py from the CPU oracle alone",
+            "model": "workloads.binned_model()", "theta_seed": seed, "cases": out}
+
+
 def main():
     oracle.build()
+    with open(BINNED_OUT, "w") as f:
+        json.dump(binned_cases(), f)
+        f.write("\n")
     out = []
     for which, gen_theta, seed, n, points in cases():
         spec = W.model_for(which)

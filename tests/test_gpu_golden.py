@@ -32,3 +32,15 @@ def test_cuda_matches_stored_oracle_values(case):
         for k in range(len(g)):
             assert abs(g[k] - ev["grad"][k]) <= GRAD_RTOL * ev["sum_abs_grad"][k], (k, g[k], ev["grad"][k])
     d.close()
+
+
+def test_cuda_binned_matches_stored_oracle_values():
+    _, cases = G.binned()
+    m = api.BinnedModel(W.binned_model())
+    for counts, evals in cases:
+        th = np.array([theta for theta, _ in evals])
+        nll, g = m.nll_grad(np.tile(counts, (len(evals), 1)), th)
+        for i, (_, ev) in enumerate(evals):
+            assert abs(nll[i] - ev["nll"]) <= NLL_RTOL * ev["nll_scale"], (nll[i], ev["nll"])
+            for k, v in ev["grad"].items():
+                assert abs(g[i, int(k)] - v) <= GRAD_RTOL * ev["grad_scale"], (k, g[i, int(k)], v)

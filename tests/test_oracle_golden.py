@@ -26,3 +26,16 @@ def test_oracle_reproduces_stored_values(oracle_mod, case):
         assert abs(nll - ev["nll"]) <= 1e-14 * ev["sum_abs_logp"]
         for k in range(len(g)):
             assert abs(g[k] - ev["grad"][k]) <= 1e-14 * ev["sum_abs_grad"][k], k
+
+
+def test_binned_oracle_reproduces_stored_values():
+    from oracle import binned as OB
+
+    _, cases = G.binned()
+    om = OB.from_spec(W.binned_model())
+    for counts, evals in cases:
+        for theta, ev in evals:
+            nll, g, scale = om.nll(theta, counts)
+            assert abs(nll - ev["nll"]) <= 1e-14 * ev["nll_scale"]
+            for k, v in ev["grad"].items():
+                assert abs(g[int(k)] - v) <= 1e-14 * ev["grad_scale"], k
