@@ -183,6 +183,33 @@ def prod3_model() -> ModelSpec:
     return b.spec(b.pdf("prod", mass, decay, ang))
 
 
+def decay_extended_model() -> ModelSpec:
+    """The decay model under an extended root: + nu - N log nu with a free
+    yield nu (start 5000), the decay parameters first, nu last."""
+    spec = decay_model()
+    nodes = list(spec.nodes) + [Node("param", (), 5000.0, 1.0, 1e8, True)]
+    nodes.append(Node("extend", (spec.root, len(nodes) - 1)))
+    return ModelSpec(nodes, len(nodes) - 1, list(spec.names) + ["nu"])
+
+
+DECAY_EXTENDED_TRUE = np.array([*DECAY_TRUE, 5000.0])
+
+
+def poisson_gauss_model() -> ModelSpec:
+    """Poisson(k; lambda) on k in [0, 30) times Gauss(y; mu, sigma) on
+    [-5, 5]: the batched Poisson leaf beside a continuous factor."""
+    b = _Builder()
+    k = b.obs(0.0, 30.0)
+    y = b.obs(-5.0, 5.0)
+    lam = b.param("lambda", 7.0, 0.1, 50.0)
+    mu = b.param("mu", 0.2, -3.0, 3.0)
+    sg = b.param("sigma", 1.1, 0.1, 5.0)
+    return b.spec(b.pdf("prod", b.pdf("poisson", k, lam), b.pdf("gauss", y, mu, sg)))
+
+
+POISSON_GAUSS_TRUE = np.array([7.0, 0.2, 1.1])
+
+
 # ------------------------------------------------------------------ configs
 
 SEED_BASE = 20031286

@@ -40,8 +40,14 @@ def cases():
     g_off = g_true + np.array([-0.1, -0.01, 0.02, -0.05, 0.02, -0.03])
     p_true = W.PROD3_TRUE
     p_off = p_true + np.array([0.002, 0.001, -0.05, 0.1, 0.1, 0.01, -0.01, 0.05, -0.02, 0.03, -0.05, 0.05])
+    e_true = W.DECAY_EXTENDED_TRUE
+    e_off = e_true + np.array([0.05, 0.005, 0.01, -0.03, 0.01, 0.02, -150.0])
+    q_true = W.POISSON_GAUSS_TRUE
+    q_off = q_true + np.array([0.4, -0.05, 0.1])
     return [
         ("gauss_poly1_model", gp_true, W.SEED_BASE + 0, 10_000, [gp_true, gp_start]),
+        ("decay_extended_model", e_true, W.SEED_BASE + 1, 5_000, [e_true, e_off]),
+        ("poisson_gauss_model", q_true, W.SEED_BASE + 8, 9_000, [q_true, q_off]),
         ("decay_model", d_true, W.SEED_BASE + 1, 20_000, [d_true, d_start, d_off]),
         ("decay_generic_model", g_true, W.SEED_BASE + 1, 20_000, [g_true, g_off]),
         ("prod3_model", p_true, W.SEED_BASE + 3, 12_345, [p_true, p_off]),
