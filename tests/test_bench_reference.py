@@ -34,3 +34,21 @@ def test_reference_arm_other_ranks_exit_quietly():
     r = run(["--impl", "reference", "--steps", "1"], {"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
     assert r.returncode == 0, r.stderr
     assert r.stdout.strip() == ""
+
+
+def test_clock_summary_parses_samples_and_reasons():
+    sys.path.insert(0, ROOT)
+    import bench
+
+    c = bench.ClockSampler(0)
+    c.out = "\n".join([
+        "0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "0, 2055, 2070, 1350.0, 0x4, Not Active, Not Active, Not Active, Active",
+        "0, 1980, 2070, 1400.0, 0x4, Active, Not Active, Not Active, Active",
+        "0, [N/A], 2070, [N/A], 0x0, Not Active, Not Active, Not Active, Not Active",
+    ])
+    s = c.summary()
+    assert s["sm_mhz"] == 2055.0 and s["sm_max_mhz"] == 2070.0 and s["samples"] == 4
+    assert s["reasons"] == ["hw_slowdown", "sw_power_cap"]
+    c.out = None
+    assert c.summary()["reasons"] == ["nvidia-smi unavailable"]
