@@ -449,6 +449,11 @@ rf_status rf_combine_partials(const double* pairs, const int32_t* flags, int32_t
  * that device current; make it before any stream capture. */
 rf_status rf_nll_grad_noalloc(const rf_model* m, const void* const* d_cols, const int32_t* dtype, int64_t n_events,
                               const double* d_theta, double* d_out, int32_t* d_flags, void* stream);
+/* The largest n_events that rf_nll_grad_noalloc accepts for model m (its
+ * scratch grows with the number of 4096-event chunks and with the model's
+ * gradient slots); larger datasets are rejected.  Host only: touches no
+ * device. */
+rf_status rf_nll_grad_noalloc_max_events(const rf_model* m, int64_t* max_events);
 
 /* -------------------------------------------------------------- messages */
 

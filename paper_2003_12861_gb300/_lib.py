@@ -63,6 +63,7 @@ SIGNATURES = {
     "rf_slow_events": (C.c_int, [_vp, _i64p]),
     "rf_probe": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, _dp]),
     "rf_nll_grad_noalloc": (C.c_int, [_vp, C.POINTER(_vp), _ip, C.c_int64, _vp, _vp, _vp, _vp]),
+    "rf_nll_grad_noalloc_max_events": (C.c_int, [_vp, _i64p]),
     "rf_nll_grad_stream": (C.c_int, [_vp, _vp, C.POINTER(_vp), _dp, _dp, _dp, _vp]),
     "rf_binned_create": (C.c_int, [C.c_int32, C.c_int32, _ip, _ip, _dp, C.c_int32, _ip, C.c_int32, _vp, _dp,
                                    C.POINTER(_vp)]),

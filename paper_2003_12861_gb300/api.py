@@ -362,16 +362,56 @@ def probe(kind: int, n_exp: int = 0, n_erfc: int = 0, n_log: int = 0, n_rcp: int
     return r.value
 
 
+def _check_noalloc_args(model: Model, cols, d_theta, d_out, d_flags):
+    """Argument checks of nll_grad_noalloc, before anything reaches the
+    library: every buffer the pass reads or writes must be a contiguous CUDA
+    tensor of the type and size the C entry point assumes, because it only
+    receives their addresses."""
+    import torch
+
+    if len(cols) != model.n_obs:
+        raise ValueError(f"expected {model.n_obs} columns, got {len(cols)}")
+    n = None
+    for c in cols:
+        if not getattr(c, "is_cuda", False) or not c.is_contiguous():
+            raise ValueError("columns must be contiguous CUDA tensors")
+        if c.dtype not in (torch.float32, torch.float64):
+            raise ValueError("columns must be float32 or float64")
+        if n is None:
+            n = c.numel()
+        elif c.numel() != n:
+            raise ValueError("columns must hold the same number of events")
+    for name, t, dt, need in (("d_theta", d_theta, torch.float64, model.n_free),
+                              ("d_out", d_out, torch.float64, 1 + model.n_free),
+                              ("d_flags", d_flags, torch.int32, 1)):
+        if not getattr(t, "is_cuda", False) or not t.is_contiguous() or t.dtype != dt:
+            raise ValueError(f"{name} must be a contiguous CUDA {dt} tensor")
+        if t.numel() < need or (name == "d_theta" and t.numel() != need):
+            raise ValueError(f"{name} must hold {'exactly' if name == 'd_theta' else 'at least'} {need} values")
+    return n or 0
+
+
+def noalloc_max_events(model: Model) -> int:
+    """Largest dataset nll_grad_noalloc accepts for this model (host only)."""
+    n = C.c_int64()
+    L.check(L.load().rf_nll_grad_noalloc_max_events(model._h, C.byref(n)))
+    return n.value
+
+
 def nll_grad_noalloc(model: Model, cols, d_theta, d_out, d_flags, stream=None):
     """NLL + gradient of one dataset held in caller-owned CUDA tensors, with no
     device allocation by the library (its scratch is a static device array).
     For callers that cannot allocate device memory while they run.  Launches
-    only; overlapping calls on one GPU must be serialised by the caller."""
+    only, on `stream` (default: torch's current stream, so that the pass is
+    ordered after the producers of the tensors); overlapping calls on one GPU
+    must be serialised by the caller."""
     import torch
 
+    n = _check_noalloc_args(model, cols, d_theta, d_out, d_flags)
+    if stream is None:
+        stream = torch.cuda.current_stream(cols[0].device if cols else d_out.device)
     ptrs = (C.c_void_p * max(1, len(cols)))(*[c.data_ptr() for c in cols])
     dt = (C.c_int32 * max(1, len(cols)))(*[L.RF_F32 if c.dtype == torch.float32 else L.RF_F64 for c in cols])
-    n = cols[0].numel() if cols else 0
     L.check(L.load().rf_nll_grad_noalloc(model._h, ptrs, dt, n, C.c_void_p(d_theta.data_ptr()),
                                          C.c_void_p(d_out.data_ptr()), C.c_void_p(d_flags.data_ptr()),
                                          _stream(stream)))

@@ -82,11 +82,35 @@ __global__ void noalloc_setup(unsigned char* base, Layout L, int64_t n_events, i
   }
 }
 
+// Scratch bytes of a pass over n_events events of model m.
+size_t scratch_bytes(const rf_model* m, int64_t n_events) {
+  const Program& P = m->m.prog;
+  const int64_t chunks = (n_events + kChunk - 1) / kChunk;
+  return layout_for(chunks, tree_nodes(chunks), P.n_const, 1 + P.n_slots, m->m.shape != SHAPE_GENERIC).total;
+}
+
 }  // namespace
 
 }  // namespace rf
 
 using namespace rf;
+
+extern "C" rf_status rf_nll_grad_noalloc_max_events(const rf_model* m, int64_t* max_events) {
+  if (!m || !max_events) {
+    set_error("rf_nll_grad_noalloc_max_events: bad argument");
+    return RF_E_INVALID;
+  }
+  // the scratch grows with the chunk count: bisect on whole chunks, then
+  // every event count up to the last fitting chunk's end fits too
+  int64_t lo = 0, hi = int64_t(1) << 31;  // chunks; 2^31 chunks never fit 16 MiB
+  while (hi - lo > 1) {
+    const int64_t mid = lo + (hi - lo) / 2;
+    if (scratch_bytes(m, mid * kChunk) <= kScratchBytes) lo = mid;
+    else hi = mid;
+  }
+  *max_events = lo * kChunk;
+  return RF_OK;
+}
 
 extern "C" rf_status rf_nll_grad_noalloc(const rf_model* m, const void* const* d_cols, const int32_t* dtype,
                                          int64_t n_events, const double* d_theta, double* d_out, int32_t* d_flags,

@@ -87,3 +87,84 @@ def test_null_arguments_are_errors_not_crashes():
     h = C.c_void_p()
     assert lib.rf_model_create(None, 3, 0, C.byref(h)) == L.RF_E_INVALID
     assert lib.rf_last_error()
+
+
+# ----------------------------------------------- allocation-free pass: host side
+
+# The documented limits of rf_nll_grad_noalloc's 16 MiB static scratch
+# (include/rf.h): about 7.5e7 events for the float-float shapes with 6
+# gradient slots, 5.7e7 with 12, about 5e8 for the generic kernel.
+@pytest.mark.parametrize("which,lo,hi", [("decay_model", 7.0e7, 8.0e7), ("prod3_model", 5.2e7, 6.2e7),
+                                         ("decay_generic_model", 4.5e8, 5.5e8)])
+def test_noalloc_limit_matches_documented_figures(which, lo, hi):
+    m = api.Model.from_spec(W.model_for(which))
+    n_max = api.noalloc_max_events(m)
+    assert lo <= n_max <= hi, n_max
+    assert n_max % 4096 == 0
+
+
+@pytest.mark.parametrize("which", ["decay_model", "prod3_model", "decay_generic_model"])
+def test_noalloc_rejects_one_chunk_beyond_the_limit(which):
+    # Through the C ABI; the size is checked before any device call, so
+    # nothing is read from the (dummy) column pointers.
+    m = api.Model.from_spec(W.model_for(which))
+    n_max = api.noalloc_max_events(m)
+    lib = L.load()
+    ptrs = (C.c_void_p * m.n_obs)(*([0x1000] * m.n_obs))
+    st = lib.rf_nll_grad_noalloc(m._h, ptrs, None, n_max + 1, C.c_void_p(0x1000), C.c_void_p(0x1000),
+                                 C.c_void_p(0x1000), None)
+    assert st == L.RF_E_INVALID
+    assert b"static array" in lib.rf_last_error()
+
+
+class _FakeTensor:
+    """Duck-typed stand-in for a tensor: enough for the argument checks of
+    nll_grad_noalloc, which must reject it before the C call."""
+
+    def __init__(self, dtype, numel, is_cuda=True, contiguous=True):
+        self.dtype, self._n, self.is_cuda, self._c = dtype, numel, is_cuda, contiguous
+
+    def numel(self):
+        return self._n
+
+    def is_contiguous(self):
+        return self._c
+
+    def data_ptr(self):  # never reached: the checks fail first
+        raise AssertionError("the C entry point must not be called")
+
+
+def test_noalloc_wrapper_rejects_bad_buffers_on_the_host():
+    import torch
+
+    m = api.Model.from_spec(W.decay_model())
+    P = m.n_free
+    good = dict(cols=[_FakeTensor(torch.float64, 100)], d_theta=_FakeTensor(torch.float64, P),
+                d_out=_FakeTensor(torch.float64, 1 + P), d_flags=_FakeTensor(torch.int32, 1))
+    bad_cases = [
+        dict(cols=[]),                                                       # column count
+        dict(cols=[_FakeTensor(torch.float64, 100)] * 2),
+        dict(cols=[_FakeTensor(torch.float64, 100, is_cuda=False)]),         # host tensor
+        dict(cols=[_FakeTensor(torch.float64, 100, contiguous=False)]),
+        dict(cols=[_FakeTensor(torch.float16, 100)]),                        # dtype
+        dict(cols=[_FakeTensor(torch.int32, 100)]),
+        dict(d_theta=_FakeTensor(torch.float32, P)),
+        dict(d_theta=_FakeTensor(torch.float64, P - 1)),
+        dict(d_theta=_FakeTensor(torch.float64, P + 1)),
+        dict(d_out=_FakeTensor(torch.float64, P)),
+        dict(d_out=_FakeTensor(torch.float32, 1 + P)),
+        dict(d_flags=_FakeTensor(torch.int64, 1)),
+        dict(d_flags=_FakeTensor(torch.int32, 0)),
+        dict(d_flags=_FakeTensor(torch.int32, 1, is_cuda=False)),
+    ]
+    for case in bad_cases:
+        args = dict(good, **case)
+        with pytest.raises(ValueError):
+            api.nll_grad_noalloc(m, args["cols"], args["d_theta"], args["d_out"], args["d_flags"])
+    # columns of unequal length (a two-observable model)
+    m3 = api.Model.from_spec(W.prod3_model())
+    P3 = m3.n_free
+    with pytest.raises(ValueError):
+        api.nll_grad_noalloc(m3, [_FakeTensor(torch.float32, 10), _FakeTensor(torch.float32, 10),
+                                  _FakeTensor(torch.float32, 11)], _FakeTensor(torch.float64, P3),
+                             _FakeTensor(torch.float64, 1 + P3), _FakeTensor(torch.int32, 1))
