@@ -332,3 +332,95 @@ def test_hist64_matches_numpy(oracle_mod):
     ref, _ = np.histogram(x, np.linspace(0, 10, 65))
     assert np.allclose(h, ref / len(x), rtol=0, atol=2e-5)
     assert abs(h.sum() - 1) < 1e-6
+
+
+# ------------------------------------------- generation under a PROD root
+
+def _factor_density(m, theta, root_inputs, f, n_obs, col):
+    """Normalised density of PROD factor f in its own observable (column
+    col), the other observables held at fixed in-range values."""
+    def dens(x):
+        cols = [np.array([0.5 * (lo + hi)]) for lo, hi in _RANGES[n_obs]]
+        cols[col] = np.array([x])
+        return m.pdf(theta, cols, node=f)[0]
+    return dens
+
+
+_RANGES = {3: [(5.2, 5.4), (0.0, 10.0), (-1.0, 1.0)], 2: [(0.0, 30.0), (-5.0, 5.0)]}
+
+
+def _chi2_p(cnt, exp_):
+    keep = exp_ > 0
+    chi2 = ((cnt[keep] - exp_[keep]) ** 2 / exp_[keep]).sum()
+    return stats.chi2.sf(chi2, keep.sum() - 1)
+
+
+@pytest.mark.parametrize("which", ["prod3_model", "poisson_gauss_model"])
+def test_prod_root_generation_follows_each_factor(oracle_mod, which):
+    """Events of a product model are drawn factor by factor (each factor's
+    observable by accept-reject against its own bound): every column's
+    histogram must follow that factor's normalised density, and the columns
+    must be independent (the joint density is the product, paper Sec. 1: a
+    PROD node multiplies PDFs of disjoint observables)."""
+    spec = W.model_for(which)
+    theta = W.PROD3_TRUE if which == "prod3_model" else W.POISSON_GAUSS_TRUE
+    m, cols = _events(spec, theta, 80000, 31337, oracle_mod)
+    root = spec.nodes[spec.root]
+    n_obs = len(cols)
+    N = len(cols[0])
+    probs = []
+    for col, f in enumerate(root.inputs):
+        lo, hi = _RANGES[n_obs][col]
+        x = cols[col]
+        assert x.min() >= lo and x.max() < hi
+        if spec.nodes[f].kind == "poisson":
+            # a step density of unit steps: k = floor(x) follows the pmf
+            # renormalised on lo .. hi-1, and x - k is uniform on [0, 1)
+            k = np.arange(int(lo), int(hi))
+            fr = x - np.floor(x)
+            fc, _ = np.histogram(fr, np.linspace(0, 1, 21))
+            assert _chi2_p(fc.astype(float), np.full(20, N / 20)) > 1e-4
+            cnt = np.bincount(np.floor(x).astype(int) - int(lo), minlength=len(k))[: len(k)].astype(float)
+            pmf = stats.poisson.pmf(k, theta[0])
+            prob = pmf / pmf.sum()
+            edges = np.concatenate([k, [hi]]).astype(float)
+        else:
+            dens = _factor_density(m, theta, root.inputs, f, n_obs, col)
+            edges = np.linspace(lo, hi, 41)
+            cnt, _ = np.histogram(x, edges)
+            prob = np.array([integrate.quad(dens, a, b, epsrel=1e-10, limit=200)[0]
+                             for a, b in zip(edges[:-1], edges[1:])])
+        assert abs(prob.sum() - 1.0) < 1e-8
+        assert _chi2_p(cnt.astype(float), N * prob) > 1e-4, (which, col)
+        probs.append((edges, prob))
+    # independence: each pair of columns against the product of the marginals
+    for c1 in range(n_obs):
+        for c2 in range(c1 + 1, n_obs):
+            e1, p1 = _coarse(*probs[c1])
+            e2, p2 = _coarse(*probs[c2])
+            joint, _, _ = np.histogram2d(cols[c1], cols[c2], [e1, e2])
+            assert _chi2_p(joint.ravel(), N * np.outer(p1, p2).ravel()) > 1e-4, (which, c1, c2)
+
+
+def _coarse(edges, prob, n=8):
+    """Merge adjacent bins into about n groups of similar probability."""
+    cum = np.concatenate([[0.0], np.cumsum(prob)])
+    cut = sorted({int(np.searchsorted(cum, q)) for q in np.linspace(0, 1, n + 1)[1:-1]} - {0, len(prob)})
+    idx = [0] + cut + [len(prob)]
+    return edges[idx], np.array([prob[a:b].sum() for a, b in zip(idx[:-1], idx[1:])])
+
+
+def test_prod_generation_detects_a_planted_dependence(oracle_mod):
+    """The independence check above has power: pairing each mass value with
+    a decay time sorted by the mass (a perfect rank correlation, both
+    marginals unchanged) fails it."""
+    spec = W.prod3_model()
+    m, cols = _events(spec, W.PROD3_TRUE, 80000, 31337, oracle_mod)
+    order = np.argsort(cols[0])
+    t_sorted = np.sort(cols[1])
+    planted = [cols[0][order], t_sorted, cols[2]]
+    e1 = np.quantile(planted[0], np.linspace(0, 1, 9))
+    e2 = np.quantile(planted[1], np.linspace(0, 1, 9))
+    joint, _, _ = np.histogram2d(planted[0], planted[1], [e1, e2])
+    p = np.full(8, 1 / 8)
+    assert _chi2_p(joint.ravel(), len(planted[0]) * np.outer(p, p).ravel()) < 1e-10
