@@ -1,29 +1,35 @@
 """Benchmark of the batched unbinned-likelihood hot path on GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload decay_1e7|decay_generic_1e7|prod3_1e8_f32|decay_toys_4096|...]
+                    [--workload prod3_1e8_f32|decay_1e7|decay_generic_1e7|decay_toys_4096|...]
+                    [--no-extras] [--no-cpu-baseline]
 
-Default workload (the configuration the headline metric is quoted on):
-events/s of one NLL + gradient pass over the decay-time model, 1e7 events,
-t in [0, 10], f*[exp(-t/tau) (x) Gauss] + (1-f)*Chebychev2, 6 free parameters,
-FP64 column.  One step = one pass of the whole path over the dataset: the
-parameter-point kernel and the fused event/adjoint/reduction kernel.  The
-device-resident value times K steps with CUDA events (inputs already in HBM,
-L2 flushed between steps).  The end-to-end number runs the same step through
-the C ABI with host buffers: host->device copy of the event columns from
-pinned memory, rf_nll_grad with host parameters, device->host read of the
-NLL and gradient.
+Default workload (the headline: NLL + gradient over 1e8 events): events/s
+of one NLL + gradient pass over the 3-observable product model
+[mass: Gauss + Chebychev1] x [decay time: exp(-t/tau) (x) Gauss + Chebychev2]
+x [cos theta: Poly2], 12 free parameters, 1e8 events in three FP32 columns.
+One step = one pass of the whole path over the dataset: the parameter-point
+kernel and the fused event/adjoint/reduction kernel.  The device-resident
+value times K steps with CUDA events (inputs already in HBM, 1.2 GB of
+columns, L2 flushed between steps).  The end-to-end number runs the same
+step through the C ABI with host buffers: host->device copy of the event
+columns from pinned memory, rf_nll_grad with host parameters,
+device->host read of the NLL and gradient.  Beside it the same line
+reports the FP64 interpreter on the same events (`fp64_interpreter`) and,
+under `extras`, the rest of the metric measured in the same run: the decay
+model at 1e7 FP64 events (events/s and its 6-parameter fit), 4096 ragged
+toys fitted together (toy fits/s), and learned-start against plain-start
+fits of 1e4 fresh toys after training on 1e6 (toy fits/s, evaluations,
+identical minima).
 
-Other workloads: decay_generic_1e7 (the same model and events on the
-generic FP64 interpreter); prod3_1e8_f32 (3-observable product, 1e8 events, FP32
-columns, 12 parameters); decay_toys_4096 (toy fits/s of 4096 ragged toys of
-the decay model fitted together, graph-replayed evaluation step, autotuned
-tile shape); gauss_poly1_1e4 (1e4 events, latency-bound).
+Other workloads, one line each: decay_1e7; decay_generic_1e7 (the FP64
+interpreter); decay_toys_4096; learned_start; gauss_poly1_1e4 (1e4 events,
+latency-bound); binned_4096.
 
 Multi-GPU (torchrun): every rank evaluates its own dataset (weak scaling, no
-collective on the data path); rank 0 prints one JSON line.  --impl reference
-times the CPU oracle (single thread, the machine's host cores) on a bounded sample
-of the same workload, with the same metric.
+collective on the data path); rank 0 prints one JSON line (no extras).
+--impl reference times the CPU oracle (single thread, the machine's host cores)
+on a bounded sample of the same workload, with the same metric.
 """
 from __future__ import annotations
 
@@ -54,7 +60,7 @@ WORKLOADS = {
     "learned_start": ("decay_model", W.DECAY_TRUE, 0, False, 8),
     "binned_4096": ("binned_model", None, 0, False, 8),
 }
-DEFAULT_STEPS = {"decay_1e7": 400, "decay_generic_1e7": 40, "prod3_1e8_f32": 40, "gauss_poly1_1e4": 2000, "decay_toys_4096": 3,
+DEFAULT_STEPS = {"decay_1e7": 400, "decay_generic_1e7": 40, "prod3_1e8_f32": 20, "gauss_poly1_1e4": 2000, "decay_toys_4096": 3,
                  "learned_start": 1, "binned_4096": 100}
 
 
@@ -179,11 +185,10 @@ def oracle_toy_fits_per_s(seconds: float):
     om = oracle.Model(spec.nodes, spec.root)
     seed = W.SEED_BASE + 2
     mean = W.toy_mean_sizes(4096, seed)
-    th = W.toy_thetas(4096, seed)
     fits, dt = 0, 0.0
     while dt < seconds and fits < 4096:
         n = oracle.poisson(seed, fits, mean[fits])
-        cols = om.generate(th[fits], seed, fits, 0, n)
+        cols = om.generate(W.DECAY_TRUE, seed, fits, 0, n)
         t1 = time.perf_counter()
         om.fit(cols, tol_edm=1e-7, cov=False)
         dt += time.perf_counter() - t1
@@ -203,11 +208,10 @@ def oracle_toy_fits_all_cores(seconds: float):
     om = oracle.Model(spec.nodes, spec.root)
     seed = W.SEED_BASE + 2
     mean = W.toy_mean_sizes(4096, seed)
-    th = W.toy_thetas(4096, seed)
     T = os.cpu_count() or 1
     n_toys = min(4096, 32 * T)
     with ThreadPoolExecutor(T) as pool:
-        cols = list(pool.map(lambda s: om.generate(th[s], seed, s, 0, oracle.poisson(seed, s, mean[s])),
+        cols = list(pool.map(lambda s: om.generate(W.DECAY_TRUE, seed, s, 0, oracle.poisson(seed, s, mean[s])),
                              range(n_toys)))
         t0 = time.perf_counter()
 
@@ -387,8 +391,62 @@ def roofline(api, model, spec, data, kern_ms, kern_n, n_events, bpe, peaks, peak
     }
 
 
-def run_events(args, api, torch, dist, rank, world, local):
-    wl = args.workload
+def path_dtype(model, f32: bool) -> str:
+    """What the pass computes in: the float-float event programs keep every
+    per-event quantity as a pair of floats (~48 significant bits) on the FP32
+    pipe and merge chunks in an FP64 two-sum tree; the generic interpreter is
+    FP64 throughout."""
+    cols = "f32 columns" if f32 else "f64 columns"
+    if "kernel=ff_" in model.describe():
+        return f"float-float (~48-bit) per event on the FP32 pipe, f64 reduction tree; {cols}"
+    return f"f64 per event (FP64 interpreter), f64 reduction tree; {cols}"
+
+
+def fp64_interpreter_figure(api, torch, model, spec, data, theta, out, flags, stream, flush, n, bpe, peaks,
+                            peak_kind, steps=10):
+    """The same model and events through the FP64 graph interpreter (every
+    node in double precision, CUDA's FP64 exp/erfc/log): events/s of a
+    device-resident pass and its kernel's fraction of the FP64 ceiling."""
+    model.set_fp64(True)
+    try:
+        def step():
+            api.nll_grad_async(model, data, theta, out, flags, stream=stream)
+
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                step()
+        stream.synchronize()
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        with torch.cuda.stream(stream):
+            for i in range(steps):
+                flush.zero_()
+                starts[i].record(stream)
+                step()
+                ends[i].record(stream)
+        torch.cuda.synchronize()
+        total_ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
+        api.kernel_time(reset=True)
+        api.kernel_timing(True)
+        with torch.cuda.stream(stream):
+            for _ in range(steps):
+                flush.zero_()
+                step()
+        torch.cuda.synchronize()
+        api.kernel_timing(False)
+        kern_ms, kern_n = api.kernel_time(reset=True)
+        rl = roofline(api, model, spec, data, kern_ms, kern_n, n, bpe, peaks, peak_kind)
+        return {"value": n * steps / (total_ms * 1e-3), "unit": "events/s", "ms_per_step": total_ms / steps,
+                "dtype": "f64 (every node, CUDA FP64 functions)", "nll_check": float(out[0].item()),
+                "roofline": {k: rl[k] for k in ("bound", "achieved", "peak", "unit", "frac", "kernel",
+                                                 "kernel_avg_ms", "peak_basis", "frac_fixed_count")}}
+    finally:
+        model.set_fp64(False)
+
+
+def run_events(args, api, torch, dist, rank, world, local, wl=None, steps=None, fp64_figure=False, fit_figure=False):
+    wl = wl or args.workload
+    steps = steps or args.steps
     ctor, theta_true, n, f32, bpe = WORKLOADS[wl]
     spec = W.model_for(ctor)
     model = api.Model.from_spec(spec)
@@ -410,15 +468,15 @@ def run_events(args, api, torch, dist, rank, world, local):
         for _ in range(args.warmup):
             step()
     stream.synchronize()
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     n_launch0 = api.launch_count()
     with ClockSampler(local) as clk:
         with torch.cuda.stream(stream):
-            for i in range(args.steps):
+            for i in range(steps):
                 flush.zero_()
                 starts[i].record(stream)
                 step()
@@ -433,7 +491,7 @@ def run_events(args, api, torch, dist, rank, world, local):
     api.kernel_time(reset=True)
     api.kernel_timing(True)
     with torch.cuda.stream(stream):
-        for i in range(min(args.steps, 50)):
+        for i in range(min(steps, 50)):
             flush.zero_()
             step()
     torch.cuda.synchronize()
@@ -443,7 +501,7 @@ def run_events(args, api, torch, dist, rank, world, local):
         t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
-    value = world * n * args.steps / (total_ms * 1e-3)
+    value = world * n * steps / (total_ms * 1e-3)
 
     # End to end through the C ABI with host buffers (pinned columns).
     host_cols = []
@@ -455,7 +513,7 @@ def run_events(args, api, torch, dist, rank, world, local):
     th_host = theta.cpu().numpy()
     for _ in range(2):
         api.nll_grad_stream(model, e2e_data, host_cols, th_host)
-    k_e2e = max(3, args.steps // 4)
+    k_e2e = max(3, steps // 4)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(k_e2e):
@@ -471,8 +529,8 @@ def run_events(args, api, torch, dist, rank, world, local):
         return None
     peaks, peak_kind = measured_peaks()
     line = {
-        "value": value, "unit": "events/s", "ms_per_step": total_ms / args.steps,
-        "dtype": "f64", "config": {"workload": wl, "n_events_per_gpu": n,
+        "value": value, "unit": "events/s", "ms_per_step": total_ms / steps,
+        "dtype": path_dtype(model, f32), "config": {"workload": wl, "n_events_per_gpu": n,
                                    "columns": f"{spec.n_obs} x {'f32' if f32 else 'f64'}",
                                    "free_parameters": P, "l2": "flushed between steps (256 MiB write)",
                                    "tile": {"threads_per_block": tune[0], "blocks_per_sm": tune[1]}},
@@ -480,6 +538,22 @@ def run_events(args, api, torch, dist, rank, world, local):
         "e2e": e2e, "gpu_launches": int(n_launches), "clocks": clk.summary(),
         "nll_check": float(out[0].item()),
     }
+    if fp64_figure:
+        line["fp64_interpreter"] = fp64_interpreter_figure(api, torch, model, spec, data, theta, out, flags, stream,
+                                                           flush, n, bpe, peaks, peak_kind)
+    if fit_figure:
+        # the configuration's 6-parameter quasi-Newton fit from the default
+        # start over the resident dataset: every evaluation is one pass
+        api.fit(model, data, want_cov=False, max_evals=3)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = api.fit(model, data, want_cov=True)
+        wall = time.perf_counter() - t0
+        ne = int(r["n_evals"][0])
+        line["fit"] = {"wall_ms": 1e3 * wall, "n_evals": ne, "status": int(r["status"][0]),
+                       "events_per_s_in_fit": ne * n / wall, "start": "plain default start", "tol_edm": 1e-7,
+                       "theta": r["theta"][0].tolist(), "nll": float(r["nll"][0]),
+                       "note": "wall time of rf_fit: host BFGS + one device pass per evaluation + covariance"}
     if wl == "gauss_poly1_1e4":
         # the configuration's full fit from its stated start, end to end
         host = api.Data.upload(model, [data.read(0)])
@@ -487,18 +561,21 @@ def run_events(args, api, torch, dist, rank, world, local):
         r = api.fit(model, host, want_cov=True)
         line["fit"] = {"wall_ms": 1e3 * (time.perf_counter() - t0), "n_evals": int(r["n_evals"][0]),
                        "status": int(r["status"][0]), "theta": r["theta"][0].tolist()}
-        line["us_per_eval"] = 1e3 * total_ms / args.steps
+        line["us_per_eval"] = 1e3 * total_ms / steps
     return line
 
 
-def run_toys(args, api, torch, dist, rank, world, local):
+def run_toys(args, api, torch, dist, rank, world, local, steps=None, warmup=None):
+    """4096 ragged toys of the decay model, every toy drawn at its generating
+    values (the configuration of the batched fit), fitted together."""
+    steps = steps or steps
+    warmup = warmup if warmup is not None else warmup
     spec = W.decay_model()
     model = api.Model.from_spec(spec)
     S = 4096
     seed = W.SEED_BASE + 2
     mean = W.toy_mean_sizes(S, seed)
-    th = W.toy_thetas(S, seed)
-    data = api.generate_toys(model, th, seed + 1000 * rank, mean, poisson=True)
+    data = api.generate_toys(model, W.DECAY_TRUE, seed + 1000 * rank, mean, poisson=True)
     n_events = data.n_events
     tune = api.autotune(model, data, passes=2)
     P = model.n_free
@@ -520,7 +597,7 @@ def run_toys(args, api, torch, dist, rank, world, local):
     kern_ms, kern_n = api.kernel_time(reset=True)
     slow_frac = api.slow_events(data) / n_events
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         api.fit(model, data, want_cov=False)
     if dist:
         dist.barrier()
@@ -529,7 +606,7 @@ def run_toys(args, api, torch, dist, rank, world, local):
     with ClockSampler(local) as clk:
         n_launch0 = api.launch_count()
         t0 = time.perf_counter()
-        for _ in range(args.steps):
+        for _ in range(steps):
             r = api.fit(model, data, want_cov=False)
             evals.append(r["n_evals"])
             conv.append(r["status"] == 0)
@@ -540,7 +617,7 @@ def run_toys(args, api, torch, dist, rank, world, local):
         t = torch.tensor([dt], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         dt = float(t.item())
-    value = world * S * args.steps / dt
+    value = world * S * steps / dt
     ev = np.concatenate(evals)
     # end to end: host columns uploaded, fitted, results read back
     cols = [data.read(0)]
@@ -556,9 +633,10 @@ def run_toys(args, api, torch, dist, rank, world, local):
     rounds = int(ev.max())
     rl["toy_fits_per_s_ceiling"] = rl["peak"] * 1e9 / (n_events * float(ev.mean())) * S
     return {
-        "value": value, "unit": "toy fits/s", "ms_per_step": 1e3 * dt / args.steps, "dtype": "f64",
+        "value": value, "unit": "toy fits/s", "ms_per_step": 1e3 * dt / steps, "dtype": "f64",
         "config": {"workload": "decay_toys_4096", "toys": S, "events": int(n_events),
-                   "sizes": "Poisson(N), N log-uniform in [1e3, 1e5]", "start": "plain default start",
+                   "sizes": "Poisson(N), N log-uniform in [1e3, 1e5]", "theta": "the decay model's values for every toy",
+                   "start": "plain default start",
                    "tol_edm": 1e-7, "tile": {"threads_per_block": tune[0], "blocks_per_sm": tune[1]},
                    "eval_step": "CUDA graph replay, one ragged persistent launch per round"},
         "roofline": rl,
@@ -571,7 +649,7 @@ def run_toys(args, api, torch, dist, rank, world, local):
     }
 
 
-def run_learned(args, api, torch, dist, rank, world, local):
+def run_learned(args, api, torch, dist, rank, world, local, steps=None):
     """Learned start: train on plain-fitted toys (setup, untimed), then time
     the 1e4 fresh evaluation toys fitted from the network's start (with the
     plain fit as fallback) next to the same toys fitted from the plain start."""
@@ -586,7 +664,7 @@ def run_learned(args, api, torch, dist, rank, world, local):
     del warm
     with ClockSampler(local) as clk:
         r = None
-        for _ in range(args.steps):
+        for _ in range(steps or args.steps):
             r = learned.compare(net, model, 10_000, seed + 777)
     if rank != 0:
         return None
@@ -707,6 +785,27 @@ def run_binned(args, api, torch, dist, rank, world, local):
     }
 
 
+def headline_extras(args, api, torch, local):
+    """The rest of the metric beside the headline's events/s, each measured
+    in this run on its own configuration: the decay model at 1e7 events
+    (events/s and its 6-parameter fit), 4096 batched toy fits (toy fits/s)
+    and learned-start against plain-start fits (toy fits/s, evaluations,
+    identical minima)."""
+    ex = {}
+    t0 = time.perf_counter()
+    d = run_events(args, api, torch, None, 0, 1, local, wl="decay_1e7", steps=100, fit_figure=True)
+    ex["decay_1e7"] = {k: d[k] for k in ("value", "unit", "ms_per_step", "dtype", "config", "roofline", "e2e",
+                                         "gpu_launches", "clocks", "fit")}
+    ex["decay_1e7"]["cpu_baseline"] = {"kind": "oracle", "note": "see --workload decay_1e7"}
+    t = run_toys(args, api, torch, None, 0, 1, local, steps=3, warmup=3)
+    v, smp = oracle_toy_fits_per_s(8.0)
+    t["cpu_baseline"] = {"value": v, "unit": "toy fits/s", "cores": 1, "kind": "oracle", "sample": smp}
+    ex["toy_fits_4096"] = t
+    ex["learned_vs_plain"] = run_learned(args, api, torch, None, 0, 1, local, steps=1)
+    ex["seconds"] = time.perf_counter() - t0
+    return ex
+
+
 def run_ours(args):
     import torch
 
@@ -721,6 +820,7 @@ def run_ours(args):
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     L.load()
+    headline = args.workload == "prod3_1e8_f32"
     if args.workload == "decay_toys_4096":
         line = run_toys(args, api, torch, dist, rank, world, local)
     elif args.workload == "learned_start":
@@ -728,7 +828,10 @@ def run_ours(args):
     elif args.workload == "binned_4096":
         line = run_binned(args, api, torch, dist, rank, world, local)
     else:
-        line = run_events(args, api, torch, dist, rank, world, local)
+        line = run_events(args, api, torch, dist, rank, world, local, fp64_figure=headline and rank == 0,
+                          fit_figure=args.workload == "decay_1e7")
+    if headline and world == 1 and not args.no_extras:
+        line["extras"] = headline_extras(args, api, torch, local)
     if rank == 0:
         full = {"metric": METRIC, "value": line.pop("value"), "unit": line.pop("unit"), "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": line.pop("ms_per_step"),
@@ -749,8 +852,10 @@ def main():
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="decay_1e7", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="prod3_1e8_f32", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default workload: skip the decay, toy-fit and learned-start figures")
     ap.add_argument("--train-toys", type=int, default=1_000_000, help="learned_start: training toys")
     ap.add_argument("--epochs", type=int, default=20, help="learned_start: training epochs")
     args = ap.parse_args()

@@ -106,6 +106,12 @@ rf_status rf_model_create(const rf_node* nodes, int32_t n, int32_t root, rf_mode
 void rf_model_destroy(rf_model* m);
 int32_t rf_model_n_free(const rf_model* m);
 int32_t rf_model_n_obs(const rf_model* m);
+/* on = 1: evaluate every event of this model with the FP64 graph interpreter
+ * (Sec. 4: the likelihood in double precision, node by node per event)
+ * instead of the float-float event program of a recognised graph shape;
+ * on = 0 (the default) restores the specialised program.  Results agree
+ * within the library's stated tolerances either way. */
+rf_status rf_model_set_fp64(rf_model* m, int32_t on);
 /* Writes a short description of the compiled event program (which fused
  * kernel it runs on) into buf (NUL-terminated, at most cap bytes). */
 rf_status rf_model_describe(const rf_model* m, char* buf, int32_t cap);

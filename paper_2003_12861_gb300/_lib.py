@@ -51,6 +51,7 @@ SIGNATURES = {
     "rf_nll_grad": (C.c_int, [_vp, _vp, _dp, _dp, _dp, _vp]),
     "rf_nll_grad_async": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "rf_nll_chunks": (C.c_int, [_vp, _vp, _dp, C.c_int32, _dp, C.c_int32, _ip]),
+    "rf_model_set_fp64": (C.c_int, [_vp, C.c_int32]),
     "rf_set_launch": (C.c_int, [_vp, C.c_int32, C.c_int32]),
     "rf_autotune": (C.c_int, [_vp, _vp, C.c_int32, _ip, _ip, _dp]),
     "rf_fit": (C.c_int, [_vp, _vp, _dp, C.POINTER(rf_fit_opts), _dp, _dp, _dp, _ip, _ip]),

@@ -65,6 +65,10 @@ class Model:
         L.check(L.load().rf_model_describe(self._h, buf, 512))
         return buf.value.decode()
 
+    def set_fp64(self, on: bool = True):
+        """Run every event through the FP64 graph interpreter (rf_model_set_fp64)."""
+        L.check(L.load().rf_model_set_fp64(self._h, 1 if on else 0))
+
     def set_launch(self, threads_per_block: int = 0, blocks_per_sm: int = 0):
         L.check(L.load().rf_set_launch(self._h, threads_per_block, blocks_per_sm))
 

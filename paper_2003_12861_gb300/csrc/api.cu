@@ -126,7 +126,9 @@ bool ensure_workspace(const rf_model* m, rf_data* d) {
   Workspace& w = d->ws;
   const Program& P = m->m.prog;
   const int Q = 1 + P.n_slots;
-  if (w.ready && w.n_const == P.n_const && w.n_free == P.n_free && w.Q == Q) return true;
+  if (w.ready && w.n_const == P.n_const && w.n_free == P.n_free && w.Q == Q &&
+      (m->m.shape == SHAPE_GENERIC || w.ffc.p))
+    return true;
   const size_t S = d->n_sets;
   const size_t nodes = (size_t)std::max<int64_t>(1, d->total_nodes);
   bool ok = w.consts.ensure(sizeof(double) * S * std::max(1, P.n_const)) &&
@@ -279,6 +281,12 @@ rf_status rf_model_describe(const rf_model* m, char* buf, int32_t cap) {
   static const char* shapes[] = {"generic_fp64", "ff_sum_gauss_poly1", "ff_sum_gaussexp_cheb2", "ff_prod3"};
   std::snprintf(buf, cap, "%s kernel=%s pdf_nodes=%d free=%d slots=%d consts=%d", m->m.signature.c_str(),
                 shapes[m->m.shape], m->m.prog.n_pdf, m->m.prog.n_free, m->m.prog.n_slots, m->m.prog.n_const);
+  return RF_OK;
+}
+
+rf_status rf_model_set_fp64(rf_model* m, int32_t on) {
+  if (!m || (on != 0 && on != 1)) { set_error("rf_model_set_fp64: bad argument"); return RF_E_INVALID; }
+  m->m.shape = on ? SHAPE_GENERIC : m->m.detected_shape;
   return RF_OK;
 }
 

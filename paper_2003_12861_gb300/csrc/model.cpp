@@ -227,6 +227,7 @@ rf_status compile_model(const rf_node* nodes, int n, int root, Model* m) {
   if (m->signature == "SUM(GAUSS,POLY1)") m->shape = SHAPE_SUM_GAUSS_POLY1;
   if (m->signature == "SUM(GAUSSEXP,CHEB2)") m->shape = SHAPE_SUM_GAUSSEXP_CHEB2;
   if (m->signature == "PROD(SUM(GAUSS,CHEB1),SUM(GAUSSEXP,CHEB2),POLY2)") m->shape = SHAPE_PROD3;
+  m->detected_shape = m->shape;
 
   // Generation factors: the root, or the factors of (nested) PRODs at the root.
   std::function<void(int)> factors = [&](int i) {

@@ -97,6 +97,7 @@ enum Shape : int32_t {
 struct Model {
   Program prog;
   Shape shape = SHAPE_GENERIC;
+  Shape detected_shape = SHAPE_GENERIC;  // the recognised shape (shape may be forced generic)
   std::vector<rf_node> nodes;
   std::vector<int> free_node;        // free index -> node index
   std::vector<double> theta_default; // free parameter defaults

@@ -168,3 +168,13 @@ def test_noalloc_wrapper_rejects_bad_buffers_on_the_host():
         api.nll_grad_noalloc(m3, [_FakeTensor(torch.float32, 10), _FakeTensor(torch.float32, 10),
                                   _FakeTensor(torch.float32, 11)], _FakeTensor(torch.float64, P3),
                              _FakeTensor(torch.float64, 1 + P3), _FakeTensor(torch.int32, 1))
+
+
+def test_fp64_switch_selects_the_interpreter():
+    m = api.Model.from_spec(W.prod3_model())
+    assert "kernel=ff_prod3" in m.describe()
+    m.set_fp64(True)
+    assert "kernel=generic_fp64" in m.describe()
+    m.set_fp64(False)
+    assert "kernel=ff_prod3" in m.describe()
+    assert L.load().rf_model_set_fp64(m._h, 2) == L.RF_E_INVALID

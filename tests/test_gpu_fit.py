@@ -73,27 +73,31 @@ def test_batched_ragged_toy_fits(oracle_mod):
     d = api.Data.upload(m, [np.concatenate(cols)], offsets=off)
     r = api.fit(m, d, tol_edm=TOL_EDM)
     assert (r["status"] == L.RF_OK).mean() >= 0.9, r["status"]
-    # Parity is defined at one minimum, where it is interior: a toy whose
-    # minimum sits on a parameter bound (where the sin transform flattens the
-    # NLL) or whose covariance is not positive definite has no 1e-3 sigma.
-    # Small toys of this model have several local minima, and two correct
-    # fitters may stop in different ones from the same start; then the oracle
-    # is restarted at the GPU's point, which must be a minimum of its NLL.
+    # Every toy against the oracle's fitter from the same (default) start.
+    # Parity at 1e-3 sigma is defined at an interior minimum with a positive
+    # definite covariance; a fit that ends on a parameter bound (where the
+    # sin transform flattens the NLL) is compared on NLL and parameters.
+    # Small toys of this model can have several local minima: a toy whose
+    # two fits end in different ones is counted, not refitted.
     lo, hi = spec.bounds().T
-    compared = 0
-    for s in np.argsort(-np.diff(off))[:16]:
-        if r["status"][s] != L.RF_OK:
-            continue
+    same_sigma = boundary = different = 0
+    for s in range(S):
         o = om.fit([cols[s]], tol_edm=TOL_EDM)
-        if abs(o["nll"] - r["nll"][s]) > 1e-6:
-            o = om.fit([cols[s]], theta0=r["theta"][s], tol_edm=TOL_EDM)
-        interior = np.all(np.minimum(o["theta"] - lo, hi - o["theta"]) > 1e-3 * (hi - lo))
-        if o["status"] != 0 or not interior or not np.all(np.isfinite(o["cov"])) \
-                or not np.all(np.linalg.eigvalsh(o["cov"]) > 0):
+        if r["status"][s] != L.RF_OK or o["status"] != 0:
+            assert r["status"][s] == L.RF_OK or o["status"] != 0, (s, r["status"][s], o["status"])
             continue
-        compare_fit({"theta": r["theta"][s], "nll": r["nll"][s], "cov": r["cov"][s]}, o, f"toy {s}")
-        compared += 1
-    assert compared >= 4
+        if abs(o["nll"] - r["nll"][s]) > 1e-6:
+            different += 1
+            continue
+        interior = np.all(np.minimum(o["theta"] - lo, hi - o["theta"]) > 1e-3 * (hi - lo))
+        if interior and np.all(np.isfinite(o["cov"])) and np.all(np.linalg.eigvalsh(o["cov"]) > 0):
+            compare_fit({"theta": r["theta"][s], "nll": r["nll"][s], "cov": r["cov"][s]}, o, f"toy {s}")
+            same_sigma += 1
+        else:
+            assert np.all(np.abs(r["theta"][s] - o["theta"]) <= 1e-4 * (hi - lo)), s
+            boundary += 1
+    print(f"{S} toys: {same_sigma} within 1e-3 sigma, {boundary} on a bound, {different} in different minima")
+    assert different <= 2 and same_sigma >= 36, (same_sigma, boundary, different)
     # a batch of one set reproduces the batched result for that set
     d0 = api.Data.upload(m, [cols[7]])
     r0 = api.fit(m, d0, tol_edm=TOL_EDM)

@@ -59,37 +59,53 @@ def test_prod3_1e8_sampled_chunks(oracle_mod):
         assert np.all(np.abs(parts[c, 1:] + ref_g) <= GRAD_RTOL * ag), c
 
 
-def test_toys_4096_sampled_fits(oracle_mod):
+def test_toys_4096_fits_match_the_oracle_fitter(oracle_mod):
+    """The batched fit of the 4096-toy workload (every toy drawn at the
+    decay model's generating values, Poisson sizes, log-uniform means)
+    against the oracle's own fitter on 64 toys spread over the batch, both
+    from the model's default start with the same stopping rule: the fitted
+    parameters agree within 1e-3 of the oracle's sigma, the minima within
+    1e-6 in NLL.  A toy whose two fits end in different minima is counted
+    and reported, not refitted; a fit that ends on a parameter bound (no
+    interior covariance) is compared on its NLL and parameters only."""
+    from concurrent.futures import ThreadPoolExecutor
+
     spec = W.decay_model()
     m = api.Model.from_spec(spec)
     om = oracle_mod.Model(spec.nodes, spec.root)
     S = 4096
     seed = W.SEED_BASE + 2
     mean = W.toy_mean_sizes(S, seed)
-    th = W.toy_thetas(S, seed)
-    d = api.generate_toys(m, th, seed, mean, poisson=True)
+    d = api.generate_toys(m, TRUE["decay_model"], seed, mean, poisson=True)
     api.autotune(m, d, passes=1)
     r = api.fit(m, d, tol_edm=1e-10)
-    assert (r["status"] == L.RF_OK).mean() > 0.9
+    assert (r["status"] == L.RF_OK).mean() > 0.95
     off = d.offsets()
     lo, hi = spec.bounds().T
-    compared = 0
-    for s in [5, 100, 1000, 2047, 3000, 4095, 17, 333, 2500, 3900]:
+    picks = list(range(0, S, 64))
+
+    def oracle_fit(s):
         n = int(off[s + 1] - off[s])
         assert n == oracle_mod.poisson(seed, s, mean[s])
-        cols = om.generate(th[s], seed, s, 0, n)
+        cols = om.generate(TRUE["decay_model"], seed, s, 0, n)
         assert np.array_equal(d.read(0, off[s], off[s + 1]), cols[0]), s
-        if r["status"][s] != L.RF_OK or compared >= 3:
-            continue
-        o = om.fit(cols, tol_edm=1e-10)
+        return om.fit(cols, tol_edm=1e-10)
+
+    with ThreadPoolExecutor(8) as pool:
+        fits = list(pool.map(oracle_fit, picks))
+    same_sigma = boundary = different = 0
+    for s, o in zip(picks, fits):
+        assert r["status"][s] == L.RF_OK and o["status"] == 0, (s, r["status"][s], o["status"])
         if abs(o["nll"] - r["nll"][s]) > 1e-6:
-            o = om.fit(cols, theta0=r["theta"][s], tol_edm=1e-10)
-        interior = np.all(np.minimum(o["theta"] - lo, hi - o["theta"]) > 1e-3 * (hi - lo))
-        if o["status"] != 0 or not interior or not np.all(np.isfinite(o["cov"])) \
-                or not np.all(np.linalg.eigvalsh(o["cov"]) > 0):
+            different += 1
             continue
-        sig = np.sqrt(np.diag(o["cov"]))
-        assert np.all(np.abs(r["theta"][s] - o["theta"]) <= 1e-3 * sig), s
-        assert abs(r["nll"][s] - o["nll"]) <= 1e-7 * abs(o["nll"]), s
-        compared += 1
-    assert compared >= 2
+        interior = np.all(np.minimum(o["theta"] - lo, hi - o["theta"]) > 1e-3 * (hi - lo))
+        if interior and np.all(np.isfinite(o["cov"])) and np.all(np.linalg.eigvalsh(o["cov"]) > 0):
+            sig = np.sqrt(np.diag(o["cov"]))
+            assert np.all(np.abs(r["theta"][s] - o["theta"]) <= 1e-3 * sig), (s, r["theta"][s], o["theta"], sig)
+            same_sigma += 1
+        else:
+            assert np.all(np.abs(r["theta"][s] - o["theta"]) <= 1e-4 * (hi - lo)), s
+            boundary += 1
+    print(f"64 toys: {same_sigma} within 1e-3 sigma, {boundary} on a bound, {different} in different minima")
+    assert different <= 1 and same_sigma >= 56, (same_sigma, boundary, different)
