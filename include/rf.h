@@ -441,9 +441,10 @@ rf_status rf_combine_partials(const double* pairs, const int32_t* flags, int32_t
  * allocation mid-run has unbounded latency and may fail).  Its scratch lives
  * in a static 16 MiB device array inside the library (held by every GPU that
  * loads it, until exit); a dataset whose scratch would not fit -- for the
- * float-float shapes beyond about 7.5e7 events with 6 gradient slots, 5.7e7
+ * float-float shapes beyond about 2e8 events with 6 gradient slots, 1.4e8
  * with 12; for the generic kernel about 5e8 and 3e8 -- is rejected with
- * RF_E_INVALID and a message giving the limit.
+ * RF_E_INVALID and a message giving the limit
+ * (rf_nll_grad_noalloc_max_events).
  *   d_cols : n_obs DEVICE column pointers (host array of pointers), dtype per
  *            column (NULL = all RF_F64), n_events events each.
  *   d_theta: DEVICE n_free parameters; d_out: DEVICE 1 + n_free doubles (NLL,

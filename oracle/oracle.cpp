@@ -862,11 +862,16 @@ double dot(const std::vector<double>& a, const std::vector<double>& b) {
 }
 
 // Strong-Wolfe line search along p from x (Nocedal & Wright Alg. 3.5 with the
-// zoom of Alg. 3.6, bisection as the interpolation).  Returns the accepted
-// step, or 0 when none is found.
+// zoom of Alg. 3.6, bisection as the interpolation), first trial step a1.
+// Returns the accepted step, or 0 when none is found.
+// A trial point is also accepted under the approximate Wolfe conditions of
+// Hager & Zhang (SIAM J. Optim. 16, 2005): phi'(a) within [c2, 2 c1 - 1]
+// times phi'(0) and phi(a) <= phi(0) + 1e-12 |phi(0)|, which still hold when
+// the decrease near a minimum is below the NLL's rounding.
 double line_search(Problem& pr, const std::vector<double>& x, double f0, const std::vector<double>& g0,
-                   const std::vector<double>& p, double* f_out, std::vector<double>* g_out, int max_evals) {
-  const double c1 = 1e-4, c2 = 0.9;
+                   const std::vector<double>& p, double* f_out, std::vector<double>* g_out, int max_evals,
+                   double a1) {
+  const double c1 = 1e-4, c2 = 0.9, eps_f = 1e-12;
   const int P = pr.P;
   const double d0 = dot(g0, p);
   std::vector<double> xt(P), gt(P);
@@ -876,11 +881,15 @@ double line_search(Problem& pr, const std::vector<double>& x, double f0, const s
     *d = dot(gt, p);
     return v;
   };
+  auto approx_wolfe = [&](double fa, double d) {
+    return std::isfinite(fa) && fa <= f0 + eps_f * std::fabs(f0) && d >= c2 * d0 && d <= (2.0 * c1 - 1.0) * d0;
+  };
   auto zoom = [&](double alo, double flo, double ahi) -> double {
     for (int it = 0; it < max_evals; ++it) {
       const double a = 0.5 * (alo + ahi);
       double d;
       const double fa = phi(a, &d);
+      if (approx_wolfe(fa, d)) { *f_out = fa; *g_out = gt; return a; }
       if (fa > f0 + c1 * a * d0 || fa >= flo) {
         ahi = a;
       } else {
@@ -898,10 +907,11 @@ double line_search(Problem& pr, const std::vector<double>& x, double f0, const s
     }
     return 0.0;
   };
-  double a_prev = 0.0, f_prev = f0, a = 1.0;
+  double a_prev = 0.0, f_prev = f0, a = a1;
   for (int it = 0; it < max_evals; ++it) {
     double d;
     const double fa = phi(a, &d);
+    if (approx_wolfe(fa, d)) { *f_out = fa; *g_out = gt; return a; }
     if (fa > f0 + c1 * a * d0 || (it > 0 && fa >= f_prev)) return zoom(a_prev, f_prev, a);
     if (std::fabs(d) <= -c2 * d0) { *f_out = fa; *g_out = gt; return a; }
     if (d >= 0) return zoom(a, fa, a_prev);
@@ -983,10 +993,22 @@ int orc_fit(const orc_model* h, const double* const* cols, int64_t N, const doub
     if (dot(p, g) >= 0) {  // not a descent direction: restart from steepest descent
       std::fill(H.begin(), H.end(), 0.0);
       for (int k = 0; k < P; ++k) { H[k * P + k] = 1.0; p[k] = -g[k]; }
+      first = true;
+    }
+    // N&W Sec. 3.5 leave the first trial step to the implementation; with a
+    // fresh (identity) H the step -g carries the gradient's units, so its
+    // first trial is limited to 0.2 in every internal coordinate (the sin
+    // transform makes a bounded coordinate periodic: a longer step can land
+    // anywhere in the parameter's range).  Later steps try 1 first (Alg. 6.1).
+    double a1 = 1.0;
+    if (first) {
+      double pm = 0.0;
+      for (int k = 0; k < P; ++k) pm = std::max(pm, std::fabs(p[k]));
+      if (pm > 0.0) a1 = std::min(1.0, 0.2 / pm);
     }
     double fn;
     std::vector<double> gn(P);
-    const double a = line_search(pr, x, f, g, p, &fn, &gn, 30);
+    const double a = line_search(pr, x, f, g, p, &fn, &gn, 30, a1);
     if (a == 0.0) { status = 2; break; }
     std::vector<double> s(P), y(P);
     for (int k = 0; k < P; ++k) { s[k] = a * p[k]; y[k] = gn[k] - g[k]; }

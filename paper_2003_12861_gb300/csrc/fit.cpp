@@ -32,6 +32,13 @@ namespace rf {
 namespace {
 
 constexpr double kC1 = 1e-4, kC2 = 0.9;
+// Near a minimum the decrease a step can make falls below the precision of
+// the NLL itself (float-float event sums: ~1e-14 of sum |log p|), and the
+// sufficient-decrease test turns into noise.  A step is then also accepted
+// under the approximate Wolfe conditions of Hager & Zhang (SIAM J. Optim.
+// 16, 2005): the curvature condition on the directional derivative, and a
+// value no more than kEpsF |f| above the start.
+constexpr double kEpsF = 1e-12;
 constexpr int kMaxLineTrials = 25;
 const double kInf = std::numeric_limits<double>::infinity();
 
@@ -311,6 +318,10 @@ struct SetFit {
     const double da = std::isfinite(fa) ? dot(ga, p.data(), P) : std::numeric_limits<double>::quiet_NaN();
     ++trials;
     const bool too_many = trials >= kMaxLineTrials || evals >= max_evals;
+    if (approx_wolfe(fa, da)) {
+      accept(a, fa, ga, tol, max_evals);
+      return;
+    }
     if (phase == BRACKET) {
       if (!(fa <= f + kC1 * a * d0) || (trials > 1 && fa >= f_prev)) {
         a_lo = a_prev; f_lo = f_prev; d_lo = d_prev;
@@ -353,6 +364,12 @@ struct SetFit {
       return;
     }
     set_trial(std::isfinite(f_hi) ? cubic_step(a_lo, f_lo, d_lo, a_hi, f_hi, d_hi) : 0.5 * (a_lo + a_hi));
+  }
+
+  // Hager-Zhang's approximate Wolfe conditions at a trial point (d0 < 0).
+  bool approx_wolfe(double fa, double da) const {
+    return std::isfinite(fa) && std::isfinite(da) && fa <= f + kEpsF * std::fabs(f) && da >= kC2 * d0 &&
+           da <= (2.0 * kC1 - 1.0) * d0;
   }
 
   bool edm_identity_small(double tol) {

@@ -512,12 +512,16 @@ __device__ __forceinline__ double logprod64_log(const LogProd64& L) {
 // Multiplies p into the lane's running product L (the log p term) and adds
 // the slot gradients to acc[1..]; counts events with p <= 0 or not finite in
 // *bad instead.
+// Nodes [n0, n1) with n1 - 1 as the root: the whole program by default, or
+// one factor's sub-program (a PROD factor's nodes are contiguous in program
+// order and refer only to each other), whose log p and slot gradients are
+// then those of that factor alone.
 template <bool kFull, bool kGrad>
 __device__ bool eval_generic(const Program& P, const double* __restrict__ C, const double* x, double* acc,
-                             LogProd64& L, int* bad) {
+                             LogProd64& L, int* bad, int n0 = 0, int n1 = -1) {
   double v[kMaxPdf];
-  const int N = P.n_pdf;
-  for (int n = 0; n < N; ++n) {
+  const int N = n1 < 0 ? P.n_pdf : n1;
+  for (int n = n0; n < N; ++n) {
     const PNode& q = P.node[n];
     const double* c = C + q.cofs;
     switch (q.kind) {
@@ -592,10 +596,10 @@ __device__ bool eval_generic(const Program& P, const double* __restrict__ C, con
     return true;
   } else {
   double ad[kMaxPdf];
-  for (int n = 0; n < N; ++n) ad[n] = 0.0;
+  for (int n = n0; n < N; ++n) ad[n] = 0.0;
   ad[N - 1] = 1.0 / p;
   double* g = acc + 1;
-  for (int n = N - 1; n >= 0; --n) {
+  for (int n = N - 1; n >= n0; --n) {
     const PNode& q = P.node[n];
     const double* c = C + q.cofs;
     const double a = ad[n];
@@ -959,18 +963,22 @@ __host__ __device__ constexpr int pow2_at_least(int n) { return n <= 1 ? 1 : n <
 // merges the four records in part order, maps the moments to (sum log p,
 // slot gradients) with the set's matrix K and climbs the reduction tree.
 // Every sum has a fixed order, so the result does not depend on the launch.
-template <int kShape, bool kGrad>
+template <int kShape, bool kGrad, bool kF32>
 __global__ void __launch_bounds__(kLanes, ff_min_blocks(kShape)) events_ff(const __grid_constant__ Program P,
                                                                   const __grid_constant__ Columns cols, Pass pass) {
   constexpr int NA = kGrad ? ff_nacc(kShape) : 1;
   constexpr int NP = pow2_at_least(NA);
   constexpr int NAK = ff_nacc(kShape);
-  constexpr int kPartK = kPerLane / kParts;
-  __shared__ SmemT<short, kPartK * 32> sm;
+  const int parts = pass.parts;
+  const int kPartK = kPerLane / parts;
+  __shared__ SmemT<short, kPerLane * 32> sm;
   __shared__ FFTables T;
   __shared__ float kc[kFFConst];
   __shared__ ff wacc[kWarps][16];
   __shared__ unsigned fbmask[kLanes];  // per lane: its events (bit k) that need the FP64 path
+  // PROD3: events whose decay factor alone needs the FP64 path (their mass
+  // and angle factors were summed in the fast pass)
+  __shared__ unsigned fbmask_f[kShape == SHAPE_PROD3 ? kLanes : 1];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int Q = pass.Q;
   ff_load_tables(T);
@@ -981,7 +989,7 @@ __global__ void __launch_bounds__(kLanes, ff_min_blocks(kShape)) events_ff(const
     col[0] = col[1] = col[2] = P.node[0].col;
   }
   const unsigned lt = (1u << lane) - 1u;
-  const int n_units = pass.n_items * kParts;
+  const int n_units = pass.n_items * parts;
   int kc_set = -1, c_set = -1;  // sets whose constants the block holds (block-uniform)
   pdl_wait();  // K1 has reset the counter and written the constants
   // One unit of lookahead: thread 0 claims the next unit while the block
@@ -993,7 +1001,7 @@ __global__ void __launch_bounds__(kLanes, ff_min_blocks(kShape)) events_ff(const
     const int u = sm.item;
     if (u >= n_units) break;
     if (tid == 0) next_u = atomicAdd(pass.counter, 1);
-    const int it = u / kParts, part = u % kParts;
+    const int it = u / parts, part = u % parts;
     const int set = pass.items[it].x, chunk = pass.items[it].y;
     const int64_t s_begin = pass.offsets[set], s_end = pass.offsets[set + 1];
     const int64_t base = s_begin + (int64_t)chunk * kChunk;
@@ -1002,6 +1010,7 @@ __global__ void __launch_bounds__(kLanes, ff_min_blocks(kShape)) events_ff(const
       kc_set = set;
     }
     fbmask[tid] = 0u;
+    if (kShape == SHAPE_PROD3) fbmask_f[tid] = 0u;
     __syncthreads();
     ff acc[NP];
 #pragma unroll
@@ -1015,11 +1024,12 @@ __global__ void __launch_bounds__(kLanes, ff_min_blocks(kShape)) events_ff(const
     const int rem = (int)(s_end - base < (int64_t)kChunk ? s_end - base : (int64_t)kChunk);
     int off = tid + k0 * kLanes;
     FFRaw<kShape> nxt;
-    if (off < rem) nxt = ff_load_raw<kShape>(cols, col, base + off);
+    if (off < rem) nxt = ff_load_raw<kShape, kF32>(cols, col, base + off);
 #pragma unroll 1
     for (int k = k0; k < k0 + kPartK; ++k, off += kLanes) {
-      const FFIn<kShape> cur = ff_split_in<kShape>(cols, col, nxt);
-      if (k + 1 < k0 + kPartK && off + kLanes < rem) nxt = ff_load_raw<kShape>(cols, col, base + off + kLanes);
+      const FFIn<kShape> cur = ff_split_in<kShape, kF32>(cols, col, nxt);
+      if (k + 1 < k0 + kPartK && off + kLanes < rem)
+        nxt = ff_load_raw<kShape, kF32>(cols, col, base + off + kLanes);
       int st = 0;
       if (off < rem) st = ff_event<kShape, kGrad, false>(T, kc, cur, acc, lpd);
       const unsigned bs = __ballot_sync(0xffffffffu, st == 1);
@@ -1037,16 +1047,18 @@ __global__ void __launch_bounds__(kLanes, ff_min_blocks(kShape)) events_ff(const
     for (int j = tid; j < qt; j += kLanes) {
       const int w = (j >= q1) + (j >= q2) + (j >= q3);
       const int off = sm.queue[w][j - (w == 0 ? 0 : w == 1 ? q1 : w == 2 ? q2 : q3)];
-      if (ff_event<kShape, kGrad, true>(T, kc, ff_load<kShape>(cols, col, base + off), acc, lpd) == 2)
-        atomicOr(&fbmask[off % kLanes], 1u << (off / kLanes));  // owner lane, event bit
+      if (ff_event<kShape, kGrad, true>(T, kc, ff_load<kShape, kF32>(cols, col, base + off), acc, lpd) == 2)
+        atomicOr(kShape == SHAPE_PROD3 ? &fbmask_f[off % kLanes] : &fbmask[off % kLanes],
+                 1u << (off / kLanes));  // owner lane, event bit
     }
     __syncthreads();
     myfb |= fbmask[tid];
+    unsigned myfb_f = kShape == SHAPE_PROD3 ? fbmask_f[tid] : 0u;
     // FP64 fallback for events outside the float-float range: each lane
     // evaluates its own flagged events in event order.
     double acc64[kQMax];
     int bad = 0;
-    const bool any_fb = __syncthreads_or(myfb != 0u);
+    const bool any_fb = __syncthreads_or((myfb | myfb_f) != 0u);
     if (any_fb) {
       if (set != c_set) {
         for (int i = tid; i < P.n_const; i += kLanes) sm.C[i] = pass.consts[(size_t)set * P.n_const + i];
@@ -1062,6 +1074,13 @@ __global__ void __launch_bounds__(kLanes, ff_min_blocks(kShape)) events_ff(const
         const int64_t e = base + tid + (int64_t)k * kLanes;
         for (int c = 0; c < P.n_obs; ++c) x[c] = load_col(cols, c, e);
         eval_generic<true, kGrad>(P, sm.C, x, acc64, L64, &bad);
+      }
+      while (myfb_f) {  // PROD3: the decay factor's sub-program, program nodes 3..5
+        const int k = __ffs(myfb_f) - 1;
+        myfb_f &= myfb_f - 1u;
+        const int64_t e = base + tid + (int64_t)k * kLanes;
+        for (int c = 0; c < P.n_obs; ++c) x[c] = load_col(cols, c, e);
+        eval_generic<true, kGrad>(P, sm.C, x, acc64, L64, &bad, 3, 6);
       }
       acc64[0] += logprod64_log(L64);
     }
@@ -1083,7 +1102,7 @@ __global__ void __launch_bounds__(kLanes, ff_min_blocks(kShape)) events_ff(const
     }
     __syncthreads();
     const int64_t leaf = pass.tree_base[set] + chunk;
-    const int64_t rec = leaf * kParts + part;
+    const int64_t rec = leaf * parts + part;
     if (tid < NA) {
       const ff M = ff_add(ff_add(wacc[0][tid], wacc[1][tid]), ff_add(wacc[2][tid], wacc[3][tid]));
       pass.part_m[rec * kPartFloats + 2 * tid] = M.hi;
@@ -1101,7 +1120,7 @@ __global__ void __launch_bounds__(kLanes, ff_min_blocks(kShape)) events_ff(const
     __syncthreads();
     if (tid == 0) {
       const int t = atomicAdd(&pass.tickets[leaf], 1);
-      sm.last = (t == kParts - 1);
+      sm.last = (t == parts - 1);
       if (sm.last) pass.tickets[leaf] = 0;
     }
     __syncthreads();
@@ -1109,29 +1128,28 @@ __global__ void __launch_bounds__(kLanes, ff_min_blocks(kShape)) events_ff(const
     __threadfence();
     // The chunk: parts merged in part order, out_q = sum_j K[q][j] M_j.
     double v = 0.0;
-    int info[kParts];
+    int info[kMaxParts];
 #pragma unroll
-    for (int p = 0; p < kParts; ++p) info[p] = __ldcg(pass.part_info + leaf * kParts + p);
+    for (int p = 0; p < kMaxParts; ++p) info[p] = p < parts ? __ldcg(pass.part_info + leaf * parts + p) : 0;
     if (tid < Q) {
       const float* K = kc + ff_koff(kShape);
-      const float* pm = pass.part_m + leaf * kParts * kPartFloats;
+      const float* pm = pass.part_m + leaf * parts * kPartFloats;
       ff out = {0.0f, 0.0f};
 #pragma unroll
       for (int j = 0; j < NA; ++j) {
         ff Mj = {__ldcg(pm + 2 * j), __ldcg(pm + 2 * j + 1)};
-#pragma unroll
-        for (int p = 1; p < kParts; ++p)
+        for (int p = 1; p < parts; ++p)
           Mj = ff_add(Mj, ff{__ldcg(pm + p * kPartFloats + 2 * j), __ldcg(pm + p * kPartFloats + 2 * j + 1)});
         out = ff_add(out, ff_mul(ff{K[2 * (tid * NAK + j)], K[2 * (tid * NAK + j) + 1]}, Mj));
       }
       v = ff_to_double(out);
 #pragma unroll
-      for (int p = 0; p < kParts; ++p)
-        if (info[p] & 1) v += __ldcg(pass.part_fb + (leaf * kParts + p) * Q + tid);
+      for (int p = 0; p < kMaxParts; ++p)
+        if (info[p] & 1) v += __ldcg(pass.part_fb + (leaf * parts + p) * Q + tid);
     }
     int bad_all = 0;
 #pragma unroll
-    for (int p = 0; p < kParts; ++p) bad_all += info[p] >> 1;
+    for (int p = 0; p < kMaxParts; ++p) bad_all += info[p] >> 1;
     __syncthreads();
     if (tid < Q) sm.wsum[0][tid] = v;
     __syncthreads();
@@ -1163,7 +1181,7 @@ bool launch_supports_threads(Shape shape, int threads) {
 
 template <int kShape>
 const void* ff_kernel(bool grad) {
-  return grad ? (const void*)events_ff<kShape, true> : (const void*)events_ff<kShape, false>;
+  return grad ? (const void*)events_ff<kShape, true, false> : (const void*)events_ff<kShape, false, false>;
 }
 
 const void* event_kernel(Shape shape, bool grad) {
@@ -1202,6 +1220,17 @@ void launch_dependent(void (*kernel)(Args...), int grid, cudaStream_t st, const 
   cudaLaunchKernelEx(&cfg, kernel, P, cols, pass);
 }
 
+// The float-float kernel of a shape, with or without the gradient, for
+// datasets whose columns are all FP32 or not.
+template <int kShape>
+void launch_ff(bool grad, bool all_f32, int grid, cudaStream_t st, const Program& P, const Columns& cols,
+               const Pass& pass) {
+  if (grad && all_f32) launch_dependent(events_ff<kShape, true, true>, grid, st, P, cols, pass);
+  else if (grad) launch_dependent(events_ff<kShape, true, false>, grid, st, P, cols, pass);
+  else if (all_f32) launch_dependent(events_ff<kShape, false, true>, grid, st, P, cols, pass);
+  else launch_dependent(events_ff<kShape, false, false>, grid, st, P, cols, pass);
+}
+
 void launch_events(const Program& P, Shape shape, const Columns& cols, const Pass& pass, int threads,
                    int blocks_per_sm, int n_sm, cudaStream_t st) {
   (void)threads;
@@ -1209,23 +1238,16 @@ void launch_events(const Program& P, Shape shape, const Columns& cols, const Pas
   const int bps = blocks_per_sm > 0 ? blocks_per_sm : 8;
   int grid = n_sm * bps;
   const Shape sh = (pass.ff_shape != SHAPE_GENERIC && pass.ffc) ? shape : SHAPE_GENERIC;
-  const int64_t units = sh == SHAPE_GENERIC ? (int64_t)pass.n_items : (int64_t)pass.n_items * kParts;
+  const int64_t units = sh == SHAPE_GENERIC ? (int64_t)pass.n_items : (int64_t)pass.n_items * pass.parts;
   if (grid > units) grid = (int)units;
   note_launches(1, st);
   timing_begin(st);
+  bool all_f32 = true;
+  for (int c = 0; c < P.n_obs; ++c) all_f32 = all_f32 && cols.is_f32[c];
   switch (sh) {
-    case SHAPE_SUM_GAUSSEXP_CHEB2:
-      if (pass.want_grad) launch_dependent(events_ff<SHAPE_SUM_GAUSSEXP_CHEB2, true>, grid, st, P, cols, pass);
-      else launch_dependent(events_ff<SHAPE_SUM_GAUSSEXP_CHEB2, false>, grid, st, P, cols, pass);
-      break;
-    case SHAPE_SUM_GAUSS_POLY1:
-      if (pass.want_grad) launch_dependent(events_ff<SHAPE_SUM_GAUSS_POLY1, true>, grid, st, P, cols, pass);
-      else launch_dependent(events_ff<SHAPE_SUM_GAUSS_POLY1, false>, grid, st, P, cols, pass);
-      break;
-    case SHAPE_PROD3:
-      if (pass.want_grad) launch_dependent(events_ff<SHAPE_PROD3, true>, grid, st, P, cols, pass);
-      else launch_dependent(events_ff<SHAPE_PROD3, false>, grid, st, P, cols, pass);
-      break;
+    case SHAPE_SUM_GAUSSEXP_CHEB2: launch_ff<SHAPE_SUM_GAUSSEXP_CHEB2>(pass.want_grad, all_f32, grid, st, P, cols, pass); break;
+    case SHAPE_SUM_GAUSS_POLY1: launch_ff<SHAPE_SUM_GAUSS_POLY1>(pass.want_grad, all_f32, grid, st, P, cols, pass); break;
+    case SHAPE_PROD3: launch_ff<SHAPE_PROD3>(pass.want_grad, all_f32, grid, st, P, cols, pass); break;
     default:
       if (pass.want_grad) launch_dependent(events_generic<true>, grid, st, P, cols, pass);
       else launch_dependent(events_generic<false>, grid, st, P, cols, pass);

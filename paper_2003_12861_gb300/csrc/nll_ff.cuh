@@ -313,43 +313,47 @@ struct FFIn {
 };
 // The raw bits of an event's observables (a double, or a float in the low
 // word), loaded ahead of use; ff_split_in converts them when needed, so a
-// prefetch does not make the warp wait for its load early.
+// prefetch does not make the warp wait for its load early.  kF32: every
+// column of the dataset is FP32 (known at compile time: no per-event dtype
+// test, and the observables' low words are zero).
 template <int kShape>
 struct FFRaw {
   unsigned long long b[kShape == SHAPE_PROD3 ? 3 : 1];
 };
+template <bool kF32>
 __device__ __forceinline__ unsigned long long ld_raw(const Columns& cols, int c, int64_t e) {
-  if (cols.is_f32[c]) return (unsigned long long)__float_as_uint(__ldg((const float*)cols.ptr[c] + e));
+  if (kF32 || cols.is_f32[c]) return (unsigned long long)__float_as_uint(__ldg((const float*)cols.ptr[c] + e));
   return (unsigned long long)__double_as_longlong(__ldg((const double*)cols.ptr[c] + e));
 }
+template <bool kF32>
 __device__ __forceinline__ ff split_raw(const Columns& cols, int c, unsigned long long b, bool& ok) {
-  if (cols.is_f32[c]) return {__uint_as_float((unsigned)b), 0.0f};
+  if (kF32 || cols.is_f32[c]) return {__uint_as_float((unsigned)b), 0.0f};
   return ff_split(__longlong_as_double((long long)b), ok);
 }
-template <int kShape>
+template <int kShape, bool kF32>
 __device__ __forceinline__ FFRaw<kShape> ff_load_raw(const Columns& cols, const int* col, int64_t e) {
   FFRaw<kShape> r;
-  r.b[0] = ld_raw(cols, col[0], e);
+  r.b[0] = ld_raw<kF32>(cols, col[0], e);
   if constexpr (kShape == SHAPE_PROD3) {
-    r.b[1] = ld_raw(cols, col[1], e);
-    r.b[2] = ld_raw(cols, col[2], e);
+    r.b[1] = ld_raw<kF32>(cols, col[1], e);
+    r.b[2] = ld_raw<kF32>(cols, col[2], e);
   }
   return r;
 }
-template <int kShape>
+template <int kShape, bool kF32>
 __device__ __forceinline__ FFIn<kShape> ff_split_in(const Columns& cols, const int* col, const FFRaw<kShape>& r) {
   FFIn<kShape> in;
   in.ok = true;
-  in.x[0] = split_raw(cols, col[0], r.b[0], in.ok);
+  in.x[0] = split_raw<kF32>(cols, col[0], r.b[0], in.ok);
   if constexpr (kShape == SHAPE_PROD3) {
-    in.x[1] = split_raw(cols, col[1], r.b[1], in.ok);
-    in.x[2] = split_raw(cols, col[2], r.b[2], in.ok);
+    in.x[1] = split_raw<kF32>(cols, col[1], r.b[1], in.ok);
+    in.x[2] = split_raw<kF32>(cols, col[2], r.b[2], in.ok);
   }
   return in;
 }
-template <int kShape>
+template <int kShape, bool kF32>
 __device__ __forceinline__ FFIn<kShape> ff_load(const Columns& cols, const int* col, int64_t e) {
-  return ff_split_in<kShape>(cols, col, ff_load_raw<kShape>(cols, col, e));
+  return ff_split_in<kShape, kF32>(cols, col, ff_load_raw<kShape, kF32>(cols, col, e));
 }
 
 // p_i goes into the lane's running product L (its log is taken once per
@@ -404,51 +408,86 @@ __device__ __forceinline__ int ff_event(const FFTables& T, const float* k, const
     }
     return 0;
   } else {  // PROD3
+    // The factors are over disjoint observables, so log p = log p_m + log
+    // p_t + log p_c and each factor's moments depend on its own density
+    // only.  The fast pass (kSlow = false) takes the mass and angle factors
+    // of every event, and the decay factor of the events outside its
+    // resolution region; an event in the region returns 1 after its mass and
+    // angle terms are summed, and the slow pass (kSlow = true) then adds its
+    // decay factor alone.  2 in the fast pass: nothing of the event was
+    // summed, the whole event takes the FP64 path; 2 in the slow pass: the
+    // decay factor alone takes it.
     const ff t = in.x[1];
     const float* kd = k + 16;
-    if (!kSlow && __fmaf_rn(-t.hi, kd[13], kd[12]) >= kSlowZf) return ok ? 1 : 2;
-    const ff m = in.x[0];
-    const ff c = in.x[2];
-    const ff um = ff_mul(ff_sub(m, ldc(k, 0)), ldc(k, 2));
-    bool dm = false;
-    const ff g = ff_exp0(T, ff_fma(ff_scale(um, -0.5f), um, ldc(k, 14)), ok, dm);
-    const ff ym = ff_fma(m, ldc(k, 10), ff_neg(ldc(k, 12)));
-    const ff pm = ff_fma(ldc(k, 4), g, ff_fma(ldc(k, 8), ym, ldc(k, 6)));
-    ff R, u;
-    const ff vs = decay_shape<kSlow>(T, kd, t, &R, &u, ok, dropped);
-    const ff pt = ff_fma(ldc(kd, 4), vs, ff_fma(ff_fma(ldc(kd, 10), t, ldc(kd, 8)), t, ldc(kd, 6)));
-    const ff pa = ff_fma(ff_fma(ldc(k, 42), c, ldc(k, 40)), c, ldc(k, 38));
-    const ff p = ff_mul(ff_mul(pm, pt), pa);
-    ok = ok && p.hi > 7.9e-31f && p.hi < 1.2e30f;
-    if (!ok || (dm && pm.hi < 1e-14f) || (dropped && pt.hi < 1e-14f)) return 2;
-    logprod_mul(L, p);
-    if constexpr (kGrad) {
-      const ff ipm = ff_rcp_u(pm), ipt = ff_rcp_u(pt), ipa = ff_rcp_u(pa);
-      const ff G = ff_mul_u(g, ipm);
-      const ff Gu = ff_mul_u(G, um);
-      ff_acc(acc[1], G);
-      ff_acc(acc[2], Gu);
-      ff_acc_mul(acc[3], Gu, um);
-      ff_acc(acc[4], ipm);
-      ff_acc_mul(acc[5], ipm, ym);
-      const ff E = ff_mul_u(vs, ipt);
-      const ff it_ = ff_mul_u(ipt, t);
-      ff_acc(acc[6], E);
-      ff_acc_mul(acc[7], E, t);
-      ff_acc(acc[8], ipt);
-      ff_acc(acc[9], it_);
-      ff_acc_mul(acc[10], it_, t);
-      if (kSlow) {
+    if constexpr (!kSlow) {
+      const ff m = in.x[0];
+      const ff c = in.x[2];
+      const ff um = ff_mul(ff_sub(m, ldc(k, 0)), ldc(k, 2));
+      bool dm = false;
+      const ff g = ff_exp0(T, ff_fma(ff_scale(um, -0.5f), um, ldc(k, 14)), ok, dm);
+      const ff ym = ff_fma(m, ldc(k, 10), ff_neg(ldc(k, 12)));
+      const ff pm = ff_fma(ldc(k, 4), g, ff_fma(ldc(k, 8), ym, ldc(k, 6)));
+      const ff pa = ff_fma(ff_fma(ldc(k, 42), c, ldc(k, 40)), c, ldc(k, 38));
+      const bool slow = __fmaf_rn(-t.hi, kd[13], kd[12]) >= kSlowZf;
+      // the decay's fast formula for every lane, used where not slow
+      ff R, u;
+      bool okd = true;
+      const ff vsf = decay_shape<false>(T, kd, t, &R, &u, okd, dropped);
+      const ff ptf = ff_fma(ldc(kd, 4), vsf, ff_fma(ff_fma(ldc(kd, 10), t, ldc(kd, 8)), t, ldc(kd, 6)));
+      const ff vs = slow ? ff{0.0f, 0.0f} : vsf;
+      const ff pt = slow ? ff{1.0f, 0.0f} : ptf;
+      okd = slow || (okd && !(dropped && pt.hi < 1e-14f));
+      const ff p = ff_mul(ff_mul(pm, pt), pa);
+      ok = ok && okd && p.hi > 7.9e-31f && p.hi < 1.2e30f && pm.hi > 7.9e-31f && pa.hi > 7.9e-31f &&
+           pm.hi < 1.2e30f && pa.hi < 1.2e30f && pt.hi < 1.2e30f;
+      if (!ok || (dm && pm.hi < 1e-14f)) return 2;
+      logprod_mul(L, p);
+      if constexpr (kGrad) {
+        const ff ipm = ff_rcp_u(pm), ipa = ff_rcp_u(pa);
+        const ff iptf = ff_rcp_u(pt);
+        const ff ipt = slow ? ff{0.0f, 0.0f} : iptf;
+        const ff G = ff_mul_u(g, ipm);
+        const ff Gu = ff_mul_u(G, um);
+        ff_acc(acc[1], G);
+        ff_acc(acc[2], Gu);
+        ff_acc_mul(acc[3], Gu, um);
+        ff_acc(acc[4], ipm);
+        ff_acc_mul(acc[5], ipm, ym);
+        const ff E = ff_mul_u(vs, ipt);
+        const ff it_ = ff_mul_u(ipt, t);
+        ff_acc(acc[6], E);
+        ff_acc_mul(acc[7], E, t);
+        ff_acc(acc[8], ipt);
+        ff_acc(acc[9], it_);
+        ff_acc_mul(acc[10], it_, t);
+        const ff iac = ff_mul_u(ipa, c);
+        ff_acc(acc[13], ipa);
+        ff_acc(acc[14], iac);
+        ff_acc_mul(acc[15], iac, c);
+      }
+      return slow ? 1 : 0;
+    } else {
+      ff R, u;
+      const ff vs = decay_shape<true>(T, kd, t, &R, &u, ok, dropped);
+      const ff pt = ff_fma(ldc(kd, 4), vs, ff_fma(ff_fma(ldc(kd, 10), t, ldc(kd, 8)), t, ldc(kd, 6)));
+      ok = ok && pt.hi > 7.9e-31f && pt.hi < 1.2e30f;
+      if (!ok || (dropped && pt.hi < 1e-14f)) return 2;
+      logprod_mul(L, pt);
+      if constexpr (kGrad) {
+        const ff ipt = ff_rcp_u(pt);
+        const ff E = ff_mul_u(vs, ipt);
+        const ff it_ = ff_mul_u(ipt, t);
+        ff_acc(acc[6], E);
+        ff_acc_mul(acc[7], E, t);
+        ff_acc(acc[8], ipt);
+        ff_acc(acc[9], it_);
+        ff_acc_mul(acc[10], it_, t);
         const ff ER = ff_mul_u(E, R);
         ff_acc(acc[11], ER);
         ff_acc_mul(acc[12], ER, u);
       }
-      const ff iac = ff_mul_u(ipa, c);
-      ff_acc(acc[13], ipa);
-      ff_acc(acc[14], iac);
-      ff_acc_mul(acc[15], iac, c);
+      return 0;
     }
-    return 0;
   }
 }
 

@@ -36,8 +36,9 @@ struct Pass {
   int32_t want_grad;
   int32_t ff_shape;         // specialised float-float event program (Shape), 0 = generic
   float* ffc;               // n_sets x 512 floats of its parameter-point constants, or null
-  // Float-float kernels: per chunk, kParts part records (indexed by the
-  // chunk's level-0 tree node x kParts + part).
+  // Float-float kernels: per chunk, `parts` part records (indexed by the
+  // chunk's level-0 tree node x parts + part; room for kMaxParts).
+  int32_t parts;            // work units per chunk (1 or 4), fixed per dataset
   float* part_m;            // 32 floats per part: its moment sums (float-float pairs)
   double* part_fb;          // Q doubles per part: its FP64 fallback sums (valid if info bit 0)
   int32_t* part_info;       // per part: bit 0 = fallback sums present, bits 1.. = bad events
@@ -47,10 +48,16 @@ struct Pass {
   double* pairs;
 };
 
-// Work units per chunk of the float-float kernels: part p of a chunk covers
-// its events [1024 p, 1024 (p + 1)), i.e. lane l's events l + 128 k for
-// k in [8 p, 8 p + 8).
-constexpr int kParts = 4;
+// Work units per chunk of the float-float kernels (Pass::parts, 1 or 4):
+// with P parts, part p of a chunk covers lane l's events l + 128 k for k in
+// [32 p / P, 32 (p + 1) / P).  Quarter chunks shorten the last round of units
+// when a dataset has few chunks; whole chunks spread the per-unit work (the
+// lane log, the warp reduction, the record) over 4x more events.  The count
+// is a property of the dataset (its total chunk count), never of the
+// launch, so a dataset's results do not depend on how it is launched.
+constexpr int kMaxParts = 4;
+constexpr int64_t kWholeChunkMin = 1024;  // datasets with at least this many chunks use whole chunks
+inline int parts_for_chunks(int64_t total_chunks) { return total_chunks >= kWholeChunkMin ? 1 : kMaxParts; }
 constexpr int kPartFloats = 32;
 
 constexpr int32_t kThetaBad = 1 << 30;

@@ -45,6 +45,7 @@ struct Layout {
 // Header (first 256 bytes): int32 counter @0, u64 slow-event count @8,
 // int64 offsets[2] @16, int64 tree base @32, int32 active set @40.
 Layout layout_for(int64_t chunks, int64_t nodes, int n_const, int Q, bool parts) {
+  const size_t np = (size_t)parts_for_chunks(chunks);
   Layout L{};
   L.consts = 256;
   L.ffc = L.consts + up256(sizeof(double) * (size_t)(n_const > 0 ? n_const : 1));
@@ -55,9 +56,9 @@ Layout layout_for(int64_t chunks, int64_t nodes, int n_const, int Q, bool parts)
   // float-float kernels only: the part records of every chunk
   const size_t nn = parts ? (size_t)(nodes > 0 ? nodes : 1) : 0;
   L.part_m = L.tree + up256(sizeof(double) * 2 * (size_t)Q * (size_t)(nodes > 0 ? nodes : 1));
-  L.part_fb = L.part_m + up256(sizeof(float) * kParts * kPartFloats * nn);
-  L.part_info = L.part_fb + up256(sizeof(double) * kParts * (size_t)Q * nn);
-  L.total = L.part_info + sizeof(int32_t) * kParts * nn;
+  L.part_fb = L.part_m + up256(sizeof(float) * np * kPartFloats * nn);
+  L.part_info = L.part_fb + up256(sizeof(double) * np * (size_t)Q * nn);
+  L.total = L.part_info + sizeof(int32_t) * np * nn;
   return L;
 }
 
@@ -189,6 +190,7 @@ extern "C" rf_status rf_nll_grad_noalloc(const rf_model* m, const void* const* d
   pass.part_m = (float*)(base + L.part_m);
   pass.part_fb = (double*)(base + L.part_fb);
   pass.part_info = (int32_t*)(base + L.part_info);
+  pass.parts = parts_for_chunks(chunks);
   launch_param_point(P, pass, st);
   launch_events(P, m->m.shape, cols, pass, m->m.threads_per_block, m->m.blocks_per_sm, sm_count(), st);
   return cuda_ok(cudaGetLastError(), "rf_nll_grad_noalloc launch") ? RF_OK : RF_E_CUDA;

@@ -61,9 +61,13 @@ def test_noalloc_at_its_largest_size_matches_the_allocating_pass():
     spec = W.prod3_model()
     m = api.Model.from_spec(spec)
     n = api.noalloc_max_events(m)
-    gen = api.generate_toys(m, W.PROD3_TRUE, 777, [float(n)], poisson=False, f32=[True] * 3)
-    dcols = [torch.from_numpy(gen.read(c).astype(np.float32)).cuda() for c in range(3)]
-    del gen
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(777)
+    # uniform events on each observable's range (any in-range data will do)
+    dcols = [lo + (hi - lo) * torch.rand(n, generator=gen, dtype=torch.float32, device="cuda")
+             for lo, hi in ((5.2, 5.4), (0.0, 10.0), (-1.0, 1.0))]
+    for c, (lo, hi) in zip(dcols, ((5.2, 5.4), (0.0, 10.0), (-1.0, 1.0))):
+        c.clamp_(lo, np.nextafter(np.float32(hi), np.float32(lo)).item())
     d = api.Data.from_torch(m, dcols)
     P = m.n_free
     th = torch.tensor(W.PROD3_TRUE * (1 + 0.01 * np.cos(np.arange(P))), dtype=torch.float64, device="cuda")
