@@ -5,7 +5,8 @@ may import this package.  It loads ``liboracle.so`` built from ``oracle.cpp``
 (plain single-threaded C++17, compiled with ``-ffp-contract=off``) and the
 numpy MLP reference in ``mlp.py``.  It imports nothing from the CUDA package;
 models arrive as plain node lists (objects with ``kind``, ``inputs``, ``value``,
-``lo``, ``hi``, ``free`` attributes) and data as numpy arrays.
+``lo``, ``hi``, ``free`` attributes; an ``expr`` node also carries ``prog`` and
+``consts``, its postfix program) and data as numpy arrays.
 """
 from __future__ import annotations
 
@@ -21,7 +22,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 
 # The oracle's own numbering of node kinds (independent of the CUDA library's).
 _KIND = {"obs": 0, "param": 1, "gauss": 2, "exp": 3, "gaussexp": 4, "cheb": 5, "poly": 6, "sum": 7, "prod": 8,
-         "poisson": 9, "extend": 10}
+         "poisson": 9, "extend": 10, "expr": 11}
 
 
 def build(force: bool = False) -> str:
@@ -45,6 +46,7 @@ def lib():
         L.orc_model_new.restype = vp
         L.orc_model_new.argtypes = [C.c_int, ip, ip, ip, dp, dp, dp, ip, C.c_int]
         L.orc_model_free.argtypes = [vp]
+        L.orc_model_set_expr.argtypes = [vp, C.c_int, C.c_int, ip, C.c_int, dp]
         L.orc_n_free.argtypes = [vp]
         L.orc_n_obs.argtypes = [vp]
         L.orc_last_error.restype = C.c_char_p
@@ -95,6 +97,13 @@ class Model:
         if not h:
             raise ValueError("oracle rejected the model: " + L.orc_last_error().decode())
         self._h = h
+        for i, nd in enumerate(nodes):
+            if nd.kind == "expr":
+                ops = np.ascontiguousarray(getattr(nd, "prog", ()), dtype=np.int32)
+                cst = np.ascontiguousarray(getattr(nd, "consts", ()), dtype=np.float64)
+                if L.orc_model_set_expr(h, i, len(ops), ops.ctypes.data_as(ip), len(cst),
+                                        _dp(cst) if len(cst) else None) != 0:
+                    raise ValueError("oracle rejected the program: " + L.orc_last_error().decode())
         self.nodes = list(nodes)
         self.root = root
         self.n_free = L.orc_n_free(h)

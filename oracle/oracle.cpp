@@ -31,6 +31,12 @@
 //            count k as a step density of unit-width steps; its integral is
 //            the Poisson mass of k = a .. b-1 (Sec. 4.1 lists the batched
 //            Poisson PDF)
+//   EXPR     a density written as a short postfix program over the
+//            observable, the node's parameters and constants (+ - * /,
+//            neg, exp, log, pow), normalised by adaptive Gauss-Legendre
+//            quadrature of the program and of its parameter derivatives
+//            (Sec. 5: a fall-back evaluation for PDFs without specialised
+//            batch code)
 //   EXTEND   root only: the pdf below it, and the NLL gains the extended
 //            term nu - N log nu for N events and expected count nu (the
 //            Poisson probability of observing N, up to the constant log N!)
@@ -64,7 +70,12 @@ constexpr double kSqrtPi = 1.77245385090551602730;
 constexpr double kSqrt2Pi = 2.50662827463100050242;
 
 enum Kind { OBS = 0, PARAM = 1, GAUSS = 2, EXPO = 3, GAUSSEXP = 4, CHEB = 5, POLY = 6, SUM = 7, PROD = 8,
-            POISSON = 9, EXTEND = 10 };
+            POISSON = 9, EXTEND = 10, EXPR = 11 };
+
+// EXPR programs: one int per operation, code | (argument << 8).
+enum ExprCode { EX_X = 0, EX_PAR = 1, EX_CONST = 2, EX_ADD = 3, EX_SUB = 4, EX_MUL = 5, EX_DIV = 6, EX_NEG = 7,
+                EX_EXP = 8, EX_LOG = 9, EX_POW = 10 };
+constexpr int kExprMaxOps = 64, kExprMaxStack = 16, kExprMaxConsts = 16;
 
 struct Node {
   int kind = 0;
@@ -74,6 +85,8 @@ struct Node {
   int free_index = -1;  // PARAM: index into theta, or -1 if fixed
   int column = -1;      // OBS: column index (order of OBS nodes)
   std::vector<int> obs; // PDFs: sorted observable columns this node depends on
+  std::vector<int> prog;       // EXPR: the program
+  std::vector<double> consts;  // EXPR: its constants
 };
 
 struct Model {
@@ -87,7 +100,9 @@ struct Model {
 
 thread_local std::string g_err;
 
-bool is_leaf_pdf(int k) { return k == GAUSS || k == EXPO || k == GAUSSEXP || k == CHEB || k == POLY || k == POISSON; }
+bool is_leaf_pdf(int k) {
+  return k == GAUSS || k == EXPO || k == GAUSSEXP || k == CHEB || k == POLY || k == POISSON || k == EXPR;
+}
 bool is_pdf(int k) { return is_leaf_pdf(k) || k == SUM || k == PROD || k == EXTEND; }
 
 // A dual number: value and derivatives in the n free parameters.
@@ -172,6 +187,166 @@ void gaussexp_shape(double t, double tau, double mu, double sigma, double* f, do
   for (int k = 0; k < 3; ++k) df[k] = val * dA[k] - g / kSqrtPi * dz[k];
 }
 
+// ------------------------------------------------------------ EXPR leaves
+
+// The program's value at x with its derivatives in the node's np local
+// parameters q (forward mode: every stack entry carries its np tangents).
+// False when an operation leaves its domain (log or pow of a value <= 0,
+// division by 0) or the result is not finite.
+bool expr_eval(const Node& n, const double* q, int np, double x, double* f, double* df) {
+  struct T {
+    double v, d[8];
+  };
+  T st[kExprMaxStack];
+  int sp = 0;
+  if (n.prog.empty()) return false;  // no program attached (orc_model_set_expr)
+  for (int op : n.prog) {
+    const int code = op & 0xff, arg = op >> 8;
+    if (code <= EX_CONST) {
+      T& t = st[sp++];
+      t.v = code == EX_X ? x : code == EX_PAR ? q[arg] : n.consts[arg];
+      for (int k = 0; k < np; ++k) t.d[k] = (code == EX_PAR && k == arg) ? 1.0 : 0.0;
+      continue;
+    }
+    if (code == EX_NEG || code == EX_EXP || code == EX_LOG) {
+      T& a = st[sp - 1];
+      if (code == EX_NEG) {
+        a.v = -a.v;
+        for (int k = 0; k < np; ++k) a.d[k] = -a.d[k];
+      } else if (code == EX_EXP) {
+        a.v = std::exp(a.v);
+        for (int k = 0; k < np; ++k) a.d[k] *= a.v;
+      } else {
+        if (!(a.v > 0)) return false;
+        for (int k = 0; k < np; ++k) a.d[k] /= a.v;
+        a.v = std::log(a.v);
+      }
+      continue;
+    }
+    const T b = st[--sp];
+    T& a = st[sp - 1];
+    switch (code) {
+      case EX_ADD:
+        a.v += b.v;
+        for (int k = 0; k < np; ++k) a.d[k] += b.d[k];
+        break;
+      case EX_SUB:
+        a.v -= b.v;
+        for (int k = 0; k < np; ++k) a.d[k] -= b.d[k];
+        break;
+      case EX_MUL:
+        for (int k = 0; k < np; ++k) a.d[k] = a.d[k] * b.v + a.v * b.d[k];
+        a.v *= b.v;
+        break;
+      case EX_DIV: {
+        if (b.v == 0.0) return false;
+        const double v = a.v / b.v;
+        for (int k = 0; k < np; ++k) a.d[k] = (a.d[k] - v * b.d[k]) / b.v;
+        a.v = v;
+        break;
+      }
+      case EX_POW: {  // a^b = exp(b log a), a > 0
+        if (!(a.v > 0)) return false;
+        const double la = std::log(a.v), v = std::exp(b.v * la);
+        for (int k = 0; k < np; ++k) a.d[k] = v * (b.d[k] * la + b.v * a.d[k] / a.v);
+        a.v = v;
+        break;
+      }
+    }
+  }
+  *f = st[0].v;
+  for (int k = 0; k < np; ++k) df[k] = st[0].d[k];
+  if (!std::isfinite(*f)) return false;
+  for (int k = 0; k < np; ++k)
+    if (!std::isfinite(df[k])) return false;
+  return true;
+}
+
+// Gauss-Legendre rule of order n on [-1, 1]: the nodes are the roots of the
+// Legendre polynomial P_n, found by Newton's method from the estimates
+// cos(pi (i + 3/4) / (n + 1/2)), with P_n and P_n' from the three-term
+// recurrence; the weights are 2 / ((1 - x^2) P_n'(x)^2).
+struct GLRule {
+  std::vector<double> x, w;
+  explicit GLRule(int n) : x(n), w(n) {
+    for (int i = 0; i < n; ++i) {
+      double z = std::cos(M_PI * (i + 0.75) / (n + 0.5)), dp = 0.0;
+      for (int it = 0; it < 100; ++it) {
+        double p0 = 1.0, p1 = z;
+        for (int k = 2; k <= n; ++k) {
+          const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+          p0 = p1;
+          p1 = p2;
+        }
+        dp = n * (z * p1 - p0) / (z * z - 1.0);
+        const double dz = p1 / dp;
+        z -= dz;
+        if (std::fabs(dz) < 1e-17) break;
+      }
+      x[i] = z;
+      w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+  }
+};
+const GLRule& gl20() {
+  static const GLRule r(20);
+  return r;
+}
+
+// The 20-point rule on [a, b] for the program and its np derivatives
+// (out[0] = value, out[1 + k] = derivative k).
+bool gl_panel(const Node& n, const double* q, int np, double a, double b, double* out) {
+  const GLRule& r = gl20();
+  const double h = 0.5 * (b - a), c = 0.5 * (a + b);
+  for (int k = 0; k <= np; ++k) out[k] = 0.0;
+  for (size_t i = 0; i < r.x.size(); ++i) {
+    double f, df[8];
+    if (!expr_eval(n, q, np, c + h * r.x[i], &f, df)) return false;
+    out[0] += r.w[i] * f;
+    for (int k = 0; k < np; ++k) out[1 + k] += r.w[i] * df[k];
+  }
+  for (int k = 0; k <= np; ++k) out[k] *= h;
+  return true;
+}
+
+// Adaptive bisection: a panel is split until its two halves agree with it
+// within tol (absolute, halved per split, so the panels' errors add up to
+// at most the first panel's tol) or its depth reaches 30; the halves' sums
+// are returned.  tol is kept well above the panels' rounding (1e-14 of the
+// integral), so the recursion ends.
+bool gl_adapt(const Node& n, const double* q, int np, double a, double b, const double* whole, double tol,
+              int depth, double* out) {
+  double L[9], R[9];
+  const double m = 0.5 * (a + b);
+  if (!gl_panel(n, q, np, a, m, L) || !gl_panel(n, q, np, m, b, R)) return false;
+  if (std::fabs(L[0] + R[0] - whole[0]) <= tol || depth >= 30) {
+    for (int k = 0; k <= np; ++k) out[k] += L[k] + R[k];
+    return true;
+  }
+  return gl_adapt(n, q, np, a, m, L, 0.5 * tol, depth + 1, out) &&
+         gl_adapt(n, q, np, m, b, R, 0.5 * tol, depth + 1, out);
+}
+
+// Integral of an EXPR leaf over [a, b] to ~1e-14 of itself, with its
+// derivatives; false outside the program's domain or for I <= 0.
+bool expr_norm(const Node& n, const double* q, int np, double a, double b, double* I, double* dI) {
+  // a first estimate from 16 panels sets the absolute tolerance
+  double est = 0.0, P[9];
+  for (int j = 0; j < 16; ++j) {
+    if (!gl_panel(n, q, np, a + (b - a) * j / 16.0, a + (b - a) * (j + 1) / 16.0, P)) return false;
+    est += std::fabs(P[0]);
+  }
+  double out[9] = {0};
+  const double tol = 1e-14 * est / 16.0;
+  for (int j = 0; j < 16; ++j) {
+    const double pa = a + (b - a) * j / 16.0, pb = a + (b - a) * (j + 1) / 16.0;
+    if (!gl_panel(n, q, np, pa, pb, P) || !gl_adapt(n, q, np, pa, pb, P, tol, 0, out)) return false;
+  }
+  *I = out[0];
+  for (int k = 0; k < np; ++k) dI[k] = out[1 + k];
+  return *I > 0.0 && std::isfinite(*I);
+}
+
 // Normalisation integral of a leaf pdf over its observable range, with its
 // derivatives in the leaf's parameters (local order = the leaf's inputs 1..n).
 // Returns false on a parameter outside the pdf's domain.
@@ -238,6 +413,8 @@ bool leaf_norm(const Model& m, const Node& n, const double* theta, double* I, do
       *I = s;
       return true;
     }
+    case EXPR:
+      return expr_norm(n, q.data(), np, a, b, I, dI);
     case POISSON: {
       // I = sum_{k=a}^{b-1} P(k), dI/dlambda = sum P(k) (k/lambda - 1), summed term by term.
       const double lam = q[0];
@@ -293,6 +470,13 @@ void leaf_shape(const Model& m, const Node& n, const double* theta, double x, do
       double s = 1.0, xk = 1.0;
       for (int k = 1; k <= np; ++k) { xk *= x; s += q[k - 1] * xk; df[k - 1] = xk; }
       *f = s;
+      return;
+    }
+    case EXPR: {
+      if (!expr_eval(n, q, np, x, f, df)) {
+        *f = std::numeric_limits<double>::quiet_NaN();
+        for (int k = 0; k < np; ++k) df[k] = 0.0;
+      }
       return;
     }
     case POISSON: {
@@ -617,6 +801,40 @@ orc_model* orc_model_new(int n, const int* kinds, const int* n_in, const int* in
 }
 
 void orc_model_free(orc_model* h) { delete reinterpret_cast<Model*>(h); }
+
+// Attach the program of EXPR node `node` (ops: n_ops codes, code | arg << 8;
+// consts: n_consts values).  The program is checked as a whole: every
+// argument in range, the stack never underflows nor exceeds its depth, and
+// exactly one value is left.  Returns 0, or -1 with the reason in
+// orc_last_error.
+int orc_model_set_expr(orc_model* h, int node, int n_ops, const int* ops, int n_consts, const double* consts) {
+  Model& m = *reinterpret_cast<Model*>(h);
+  auto fail = [](const char* why) {
+    g_err = why;
+    return -1;
+  };
+  if (node < 0 || node >= (int)m.nodes.size() || m.nodes[node].kind != EXPR) return fail("not an EXPR node");
+  if (n_ops < 1 || n_ops > kExprMaxOps) return fail("program length must be 1..64");
+  if (n_consts < 0 || n_consts > kExprMaxConsts) return fail("at most 16 constants");
+  Node& nd = m.nodes[node];
+  const int np = (int)nd.in.size() - 1;
+  int depth = 0;
+  for (int i = 0; i < n_ops; ++i) {
+    const int code = ops[i] & 0xff, arg = ops[i] >> 8;
+    if (code < EX_X || code > EX_POW) return fail("unknown operation");
+    if (code == EX_PAR && (arg < 0 || arg >= np)) return fail("parameter index out of range");
+    if (code == EX_CONST && (arg < 0 || arg >= n_consts)) return fail("constant index out of range");
+    if (code > EX_CONST && arg != 0) return fail("operation with an argument");
+    if (code <= EX_CONST) ++depth;
+    else if (code == EX_NEG || code == EX_EXP || code == EX_LOG) { if (depth < 1) return fail("stack underflow"); }
+    else { if (depth < 2) return fail("stack underflow"); --depth; }
+    if (depth > kExprMaxStack) return fail("stack deeper than 16");
+  }
+  if (depth != 1) return fail("the program must leave exactly one value");
+  nd.prog.assign(ops, ops + n_ops);
+  nd.consts.assign(consts, consts + n_consts);
+  return 0;
+}
 int orc_n_free(const orc_model* h) { return reinterpret_cast<const Model*>(h)->n_free; }
 int orc_n_obs(const orc_model* h) { return reinterpret_cast<const Model*>(h)->n_obs; }
 

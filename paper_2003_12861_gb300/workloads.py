@@ -23,6 +23,8 @@ sum        [pdf_1..pdf_n, f_1..f_{n-1}]   (last fraction = 1 - sum f)
 prod       [pdf_1..pdf_n]                 (disjoint observables)
 poisson    [obs, lambda]                  (count k = floor(x); integer range)
 extend     [pdf, nu]                      (root only: extended likelihood)
+expr       [obs, p_1, ..., p_n]           (a density given as a postfix program,
+                                           ``prog`` / ``consts``; see expr_program)
 =========  ==========================================================
 
 The five workloads (sizes, true values and ranges) are the ones the
@@ -33,11 +35,11 @@ fixed here once.
 from __future__ import annotations
 
 from dataclasses import dataclass, field
-from typing import List, Sequence
+from typing import List, Sequence, Tuple
 
 import numpy as np
 
-KINDS = ("obs", "param", "gauss", "exp", "gaussexp", "cheb", "poly", "sum", "prod", "poisson", "extend")
+KINDS = ("obs", "param", "gauss", "exp", "gaussexp", "cheb", "poly", "sum", "prod", "poisson", "extend", "expr")
 
 
 @dataclass(frozen=True)
@@ -48,6 +50,26 @@ class Node:
     lo: float = 0.0
     hi: float = 0.0
     free: bool = False
+    prog: Tuple[int, ...] = ()       # expr: the program's operations
+    consts: Tuple[float, ...] = ()   # expr: its constants
+
+
+# The program format of an expr node: one int per operation, code | (arg <<
+# 8), evaluated on a stack.  x pushes the observable, p<j> the node's j-th
+# parameter (input 1 + j), c<j> constant j; + - * / and pow pop two values
+# (a then b, pushing a op b, pow = a^b with a > 0), neg, exp and log pop one.
+EXPR_CODES = {"x": 0, "p": 1, "c": 2, "+": 3, "-": 4, "*": 5, "/": 6, "neg": 7, "exp": 8, "log": 9, "pow": 10}
+
+
+def expr_program(text: str) -> Tuple[int, ...]:
+    """Encode a whitespace-separated postfix program, e.g. "x p0 - p1 /"."""
+    ops = []
+    for tok in text.split():
+        if tok[0] in "pc" and tok[1:].isdigit():
+            ops.append(EXPR_CODES[tok[0]] | (int(tok[1:]) << 8))
+        else:
+            ops.append(EXPR_CODES[tok])
+    return tuple(ops)
 
 
 @dataclass
@@ -90,6 +112,9 @@ class _Builder:
 
     def pdf(self, kind, *inputs):
         return self.add(Node(kind, tuple(inputs)))
+
+    def expr(self, text, consts, *inputs):
+        return self.add(Node("expr", tuple(inputs), prog=expr_program(text), consts=tuple(consts)))
 
     def spec(self, root):
         return ModelSpec(self.nodes, root, self.names)
@@ -208,6 +233,45 @@ def poisson_gauss_model() -> ModelSpec:
 
 
 POISSON_GAUSS_TRUE = np.array([7.0, 0.2, 1.1])
+
+
+def expr_gauss_poly1_model() -> ModelSpec:
+    """gauss_poly1_model with its Gaussian written as an expr node,
+    exp(-((x - mu)/sigma)^2 / 2): the same density through the generic
+    program path and a numerical normalisation."""
+    b = _Builder()
+    x = b.obs(0.0, 10.0)
+    mu = b.param("mu", 4.5, 0.0, 10.0)
+    sg = b.param("sigma", 1.0, 0.01, 10.0)
+    f = b.param("f", 0.5, 0.0, 1.0)
+    a1 = b.param("a1", 0.0, -0.1, 1.0)
+    g = b.expr("x p0 - p1 / x p0 - p1 / * c0 * exp", (-0.5,), x, mu, sg)
+    p = b.pdf("poly", x, a1)
+    return b.spec(b.pdf("sum", g, p, f))
+
+
+def expr_mix_model() -> ModelSpec:
+    """Programs beside built-in nodes: [mass m in [5.2, 5.4]: f * Cauchy(m;
+    m0, gamma) + (1 - f) * Chebychev1] x [t in [0.2, 5]: t^a exp(-b t)], the
+    Cauchy line shape 1/((m - m0)^2 + gamma^2) and the gamma-like t density
+    as expr nodes.  6 free parameters; defaults are the generating values."""
+    b = _Builder()
+    m = b.obs(5.2, 5.4)
+    t = b.obs(0.2, 5.0)
+    m0 = b.param("m0", 5.28, 5.2, 5.4)
+    gam = b.param("gamma", 0.012, 0.001, 0.1)
+    fm = b.param("f_m", 0.45, 0.0, 1.0)
+    cm = b.param("c_m", -0.2, -1.0, 1.0)
+    a = b.param("a", 1.5, 0.0, 5.0)
+    bb = b.param("b", 1.2, 0.1, 5.0)
+    line = b.expr("c0 x p0 - x p0 - * p1 p1 * + /", (1.0,), m, m0, gam)
+    bkg = b.pdf("cheb", m, cm)
+    mass = b.pdf("sum", line, bkg, fm)
+    tt = b.expr("x p0 pow x p1 * neg exp *", (), t, a, bb)
+    return b.spec(b.pdf("prod", mass, tt))
+
+
+EXPR_MIX_TRUE = np.array([5.28, 0.012, 0.45, -0.2, 1.5, 1.2])
 
 
 # ------------------------------------------------------------------ configs

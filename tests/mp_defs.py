@@ -59,6 +59,32 @@ def shape(kind, x, q, a, b):
     raise ValueError(kind)
 
 
+def expr_value(prog, consts, x, q):
+    """The postfix program of an expr node at x, in mpmath (its own
+    interpreter: code | arg << 8; x, parameter, constant pushes; + - * /
+    pow pop two; neg exp log pop one)."""
+    st = []
+    for op in prog:
+        code, arg = op & 0xFF, op >> 8
+        if code == 0:
+            st.append(mp.mpf(x))
+        elif code == 1:
+            st.append(q[arg])
+        elif code == 2:
+            st.append(mp.mpf(consts[arg]))
+        elif code == 7:
+            st.append(-st.pop())
+        elif code == 8:
+            st.append(mp.exp(st.pop()))
+        elif code == 9:
+            st.append(mp.log(st.pop()))
+        else:
+            bv, av = st.pop(), st.pop()
+            st.append({3: av + bv, 4: av - bv, 5: av * bv, 6: av / bv, 10: av ** bv}[code])
+    assert len(st) == 1
+    return st[0]
+
+
 def norm(kind, q, a, b):
     a, b = mp.mpf(a), mp.mpf(b)
     if kind == "gaussexp":
@@ -78,6 +104,20 @@ def norm(kind, q, a, b):
 def pdf(nodes, node, theta, x, _cache=None):
     """Normalised probability of `node` at event x (tuple over columns)."""
     n = nodes[node]
+    if n.kind == "expr":
+        ob = nodes[n.inputs[0]]
+        q = _params(nodes, node, theta)
+        key = (node, tuple(q))
+        if _cache is not None and key in _cache:
+            I = _cache[key]
+        else:
+            f = lambda t: expr_value(n.prog, n.consts, t, q)
+            # split the range at 32 points so a narrow peak is resolved
+            pts = [mp.mpf(ob.lo) + (mp.mpf(ob.hi) - mp.mpf(ob.lo)) * k / 32 for k in range(33)]
+            I = mp.quad(f, pts)
+            if _cache is not None:
+                _cache[key] = I
+        return expr_value(n.prog, n.consts, x[_obs_column(nodes, n.inputs[0])], q) / I
     if n.kind in ("gauss", "exp", "gaussexp", "cheb", "poly"):
         ob = nodes[n.inputs[0]]
         q = _params(nodes, node, theta)
