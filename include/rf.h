@@ -70,11 +70,34 @@ typedef enum {
                       an observable range with integer bounds 0 <= lo < hi <=
                       lo + 1e5; normalised by the Poisson mass of k = lo..hi-1
                       (Sec. 4.1 lists the batched Poisson PDF)                        */
-  RF_EXTEND = 10   /* root only, in = [pdf, nu]: extended likelihood, the NLL of a
+  RF_EXTEND = 10,  /* root only, in = [pdf, nu]: extended likelihood, the NLL of a
                       dataset of N events gains nu - N log nu (the Poisson
                       probability of N given the expected count nu, without the
                       constant log N!); nu <= 0 is outside the domain              */
+  RF_EXPR = 11     /* in = [obs, p_1..p_n], n <= 7: a density given as a short
+                      postfix program over x, p_j and constants (rf_expr, passed
+                      to rf_model_create_expr), for PDFs that have no built-in
+                      kind (Sec. 5: a fall-back implementation for PDFs that
+                      have not been given batch code).  Evaluated per event by
+                      the FP64 graph interpreter with its parameter derivatives
+                      by forward mode; normalised per parameter point by
+                      adaptive 15-point Gauss-Kronrod quadrature on the device
+                      (to ~1e-14 of the integral, at most 256 panels per
+                      refinement level).  The program must be positive and
+                      finite on the range; where it is not, that event (or,
+                      in the normalisation, the parameter point) is outside
+                      the domain                                               */
 } rf_kind;
+
+/* Operations of an RF_EXPR program: one int32 per operation, code | (arg <<
+ * 8).  RF_EX_X pushes the observable, RF_EX_PAR pushes the node's parameter
+ * arg (input 1 + arg), RF_EX_CONST pushes constant arg; ADD SUB MUL DIV POW
+ * pop b then a and push a op b (POW: a^b, a > 0); NEG EXP LOG pop a and push
+ * -a, exp(a), log(a) (a > 0). */
+typedef enum {
+  RF_EX_X = 0, RF_EX_PAR = 1, RF_EX_CONST = 2, RF_EX_ADD = 3, RF_EX_SUB = 4, RF_EX_MUL = 5, RF_EX_DIV = 6,
+  RF_EX_NEG = 7, RF_EX_EXP = 8, RF_EX_LOG = 9, RF_EX_POW = 10
+} rf_expr_code;
 
 typedef enum { RF_F64 = 0, RF_F32 = 1 } rf_dtype;
 
@@ -103,6 +126,24 @@ typedef struct rf_mlp rf_mlp;
  * the library cannot evaluate (cycle, PROD factors sharing an observable, SUM
  * components over different observables, wrong arity, limits). */
 rf_status rf_model_create(const rf_node* nodes, int32_t n, int32_t root, rf_model** out);
+
+/* The program of one RF_EXPR node: n_ops operations (1..64), n_consts
+ * constants (0..16).  A program is checked as a whole: every argument in
+ * range, the stack (depth <= 16) never underflows, exactly one value left.
+ * Per model at most 128 operations and 32 constants over all its programs. */
+typedef struct {
+  int32_t node;          /* index of the RF_EXPR node in the node list */
+  int32_t n_ops;
+  const int32_t* ops;    /* rf_expr_code | (arg << 8) */
+  int32_t n_consts;
+  const double* consts;
+} rf_expr;
+/* rf_model_create for a node list with RF_EXPR nodes: exprs[0..n_exprs)
+ * gives every RF_EXPR node its program (host arrays, copied).  RF_E_INVALID
+ * for an RF_EXPR node without a program, a program given twice or for a
+ * node of another kind, or an invalid program. */
+rf_status rf_model_create_expr(const rf_node* nodes, int32_t n, int32_t root, const rf_expr* exprs,
+                               int32_t n_exprs, rf_model** out);
 void rf_model_destroy(rf_model* m);
 int32_t rf_model_n_free(const rf_model* m);
 int32_t rf_model_n_obs(const rf_model* m);

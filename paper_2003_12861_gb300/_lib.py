@@ -14,7 +14,7 @@ RF_OK, RF_E_INVALID, RF_E_OOM, RF_E_CUDA, RF_E_DOMAIN, RF_E_NOT_CONVERGED, RF_E_
 STATUS_NAMES = {0: "RF_OK", 1: "RF_E_INVALID", 2: "RF_E_OOM", 3: "RF_E_CUDA", 4: "RF_E_DOMAIN",
                 5: "RF_E_NOT_CONVERGED", 6: "RF_E_TIMEOUT"}
 KIND = {"obs": 0, "param": 1, "gauss": 2, "exp": 3, "gaussexp": 4, "cheb": 5, "poly": 6, "sum": 7, "prod": 8,
-        "poisson": 9, "extend": 10}
+        "poisson": 9, "extend": 10, "expr": 11}
 RF_F64, RF_F32 = 0, 1
 
 
@@ -28,6 +28,11 @@ class rf_node(C.Structure):
                 ("lo", C.c_double), ("hi", C.c_double), ("is_free", C.c_int32)]
 
 
+class rf_expr(C.Structure):
+    _fields_ = [("node", C.c_int32), ("n_ops", C.c_int32), ("ops", C.POINTER(C.c_int32)), ("n_consts", C.c_int32),
+                ("consts", C.POINTER(C.c_double))]
+
+
 class rf_fit_opts(C.Structure):
     _fields_ = [("tol_edm", C.c_double), ("max_evals", C.c_int32), ("want_cov", C.c_int32),
                 ("no_graph", C.c_int32), ("reserved", C.c_int32)]
@@ -37,6 +42,8 @@ class rf_fit_opts(C.Structure):
 _vp, _dp, _ip, _i64p = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int32), C.POINTER(C.c_int64)
 SIGNATURES = {
     "rf_model_create": (C.c_int, [C.POINTER(rf_node), C.c_int32, C.c_int32, C.POINTER(_vp)]),
+    "rf_model_create_expr": (C.c_int, [C.POINTER(rf_node), C.c_int32, C.c_int32, C.POINTER(rf_expr), C.c_int32,
+                                       C.POINTER(_vp)]),
     "rf_model_destroy": (None, [_vp]),
     "rf_model_n_free": (C.c_int32, [_vp]),
     "rf_model_n_obs": (C.c_int32, [_vp]),

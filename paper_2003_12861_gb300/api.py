@@ -49,7 +49,19 @@ class Model:
         lib = L.load()
         arr = make_nodes(nodes)
         h = C.c_void_p()
-        L.check(lib.rf_model_create(arr, len(nodes), root, C.byref(h)))
+        exprs = [(i, nd) for i, nd in enumerate(nodes) if nd.kind == "expr"]
+        if exprs:
+            keep = []
+            ex = (L.rf_expr * len(exprs))()
+            for j, (i, nd) in enumerate(exprs):
+                ops = (C.c_int32 * max(1, len(nd.prog)))(*nd.prog)
+                cst = (C.c_double * max(1, len(nd.consts)))(*nd.consts)
+                keep += [ops, cst]
+                ex[j].node, ex[j].n_ops, ex[j].ops = i, len(nd.prog), ops
+                ex[j].n_consts, ex[j].consts = len(nd.consts), cst
+            L.check(lib.rf_model_create_expr(arr, len(nodes), root, ex, len(exprs), C.byref(h)))
+        else:
+            L.check(lib.rf_model_create(arr, len(nodes), root, C.byref(h)))
         self._h = h
         self.nodes = list(nodes)
         self.root = root

@@ -273,6 +273,18 @@ rf_status rf_model_create(const rf_node* nodes, int32_t n, int32_t root, rf_mode
   return RF_OK;
 }
 
+rf_status rf_model_create_expr(const rf_node* nodes, int32_t n, int32_t root, const rf_expr* exprs,
+                               int32_t n_exprs, rf_model** out) {
+  if (!out || n_exprs < 0 || (n_exprs > 0 && !exprs)) { set_error("rf_model_create_expr: bad argument"); return RF_E_INVALID; }
+  *out = nullptr;
+  rf_model* m = new (std::nothrow) rf_model();
+  if (!m) return RF_E_OOM;
+  const rf_status s = compile_model(nodes, n, root, &m->m, exprs, n_exprs);
+  if (s != RF_OK) { delete m; return s; }
+  *out = m;
+  return RF_OK;
+}
+
 void rf_model_destroy(rf_model* m) { delete m; }
 int32_t rf_model_n_free(const rf_model* m) { return m ? m->m.prog.n_free : 0; }
 int32_t rf_model_n_obs(const rf_model* m) { return m ? m->m.prog.n_obs : 0; }

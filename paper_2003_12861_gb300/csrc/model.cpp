@@ -21,18 +21,46 @@ namespace rf {
 
 namespace {
 
-bool is_leaf(int k) { return k == GAUSS || k == EXPO || k == GAUSSEXP || k == CHEB || k == POLY || k == POISSON; }
+bool is_leaf(int k) {
+  return k == GAUSS || k == EXPO || k == GAUSSEXP || k == CHEB || k == POLY || k == POISSON || k == EXPR;
+}
 bool is_pdf(int k) { return is_leaf(k) || k == SUM || k == PROD; }  // EXTEND: only as the root
 
 std::string kind_name(int k) {
   static const char* names[] = {"OBS", "PARAM", "GAUSS", "EXP", "GAUSSEXP", "CHEB", "POLY", "SUM", "PROD",
-                                "POISSON", "EXTEND"};
-  return (k >= 0 && k <= 10) ? names[k] : "?";
+                                "POISSON", "EXTEND", "EXPR"};
+  return (k >= 0 && k <= 11) ? names[k] : "?";
+}
+
+// An RF_EXPR program as a whole: known operations, arguments in range
+// (n_par parameters, n_consts constants), a stack that never underflows nor
+// holds more than kExprStack values, and exactly one value at the end.
+const char* check_expr(const rf_expr& e, int n_par) {
+  if (e.n_ops < 1 || e.n_ops > kExprMaxOps || !e.ops) return "program length must be 1..64";
+  if (e.n_consts < 0 || e.n_consts > kExprMaxConsts || (e.n_consts > 0 && !e.consts)) return "at most 16 constants";
+  int depth = 0;
+  for (int i = 0; i < e.n_ops; ++i) {
+    const int code = e.ops[i] & 0xff, arg = e.ops[i] >> 8;
+    if (code < RF_EX_X || code > RF_EX_POW) return "unknown operation";
+    if (code == RF_EX_PAR && (arg < 0 || arg >= n_par)) return "parameter index out of range";
+    if (code == RF_EX_CONST && (arg < 0 || arg >= e.n_consts)) return "constant index out of range";
+    if (code > RF_EX_CONST && arg != 0) return "operation with an argument";
+    if (code <= RF_EX_CONST) {
+      ++depth;
+    } else if (code >= RF_EX_NEG && code <= RF_EX_LOG) {
+      if (depth < 1) return "stack underflow";
+    } else {
+      if (depth < 2) return "stack underflow";
+      --depth;
+    }
+    if (depth > kExprStack) return "stack deeper than 16";
+  }
+  return depth == 1 ? nullptr : "the program must leave exactly one value";
 }
 
 }  // namespace
 
-rf_status compile_model(const rf_node* nodes, int n, int root, Model* m) {
+rf_status compile_model(const rf_node* nodes, int n, int root, Model* m, const rf_expr* exprs, int n_exprs) {
   char buf[256];
   auto fail = [&](const char* why, int i) {
     std::snprintf(buf, sizeof buf, "rf_model_create: node %d: %s", i, why);
@@ -47,7 +75,7 @@ rf_status compile_model(const rf_node* nodes, int n, int root, Model* m) {
   int n_obs = 0, n_free = 0;
   for (int i = 0; i < n; ++i) {
     const rf_node& nd = nodes[i];
-    if (nd.kind < 0 || nd.kind > 10) return fail("unknown kind", i);
+    if (nd.kind < 0 || nd.kind > 11) return fail("unknown kind", i);
     if (nd.n_in < 0 || nd.n_in > 8) return fail("n_in must be 0..8", i);
     for (int j = 0; j < nd.n_in; ++j)
       if (nd.in[j] < 0 || nd.in[j] >= n || nd.in[j] == i) return fail("input index out of range", i);
@@ -69,7 +97,8 @@ rf_status compile_model(const rf_node* nodes, int n, int root, Model* m) {
     } else if (is_leaf(nd.kind)) {
       const int want = nd.kind == GAUSS ? 3 : nd.kind == EXPO || nd.kind == POISSON ? 2 : nd.kind == GAUSSEXP ? 4 : -1;
       if (want > 0 && nd.n_in != want) return fail("wrong number of inputs for this pdf", i);
-      if (want < 0 && (nd.n_in < 1 || nd.n_in > 1 + kMaxPar)) return fail("CHEB/POLY take an observable and 0..7 coefficients", i);
+      if (want < 0 && (nd.n_in < 1 || nd.n_in > 1 + kMaxPar))
+        return fail("CHEB/POLY/EXPR take an observable and 0..7 parameters", i);
       if (nodes[nd.in[0]].kind != OBS) return fail("input 0 of a pdf must be an OBS node", i);
       for (int j = 1; j < nd.n_in; ++j)
         if (nodes[nd.in[j]].kind != PARAM) return fail("pdf parameters must be PARAM nodes", i);
@@ -207,6 +236,34 @@ rf_status compile_model(const rf_node* nodes, int n, int root, Model* m) {
   if (cofs > kMaxConst) return fail("constant block too large", root);
   P.n_const = cofs;
   P.n_slots = slot;
+
+  // RF_EXPR programs into the model's pools, in the order given.
+  std::vector<int> has_prog(n, 0);
+  int ops_used = 0, consts_used = 0;
+  for (int e = 0; e < n_exprs; ++e) {
+    const rf_expr& ex = exprs[e];
+    if (ex.node < 0 || ex.node >= n || nodes[ex.node].kind != EXPR) return fail("program for a node that is not EXPR", ex.node);
+    if (has_prog[ex.node]) return fail("two programs for one EXPR node", ex.node);
+    has_prog[ex.node] = 1;
+    if (const char* why = check_expr(ex, nodes[ex.node].n_in - 1)) return fail(why, ex.node);
+    if (ops_used + ex.n_ops > kExprPoolOps || consts_used + ex.n_consts > kExprPoolConsts)
+      return fail("programs longer than 128 operations or 32 constants in all", ex.node);
+    if (prog_index[ex.node] >= 0) {
+      PNode& q = P.node[prog_index[ex.node]];
+      q.ex_op0 = (int16_t)ops_used;
+      q.ex_nops = (int16_t)ex.n_ops;
+      q.ex_c0 = (int16_t)consts_used;
+    }
+    for (int k = 0; k < ex.n_ops; ++k) P.ex_ops[ops_used + k] = ex.ops[k];
+    for (int k = 0; k < ex.n_consts; ++k) P.ex_consts[consts_used + k] = ex.consts[k];
+    ops_used += ex.n_ops;
+    consts_used += ex.n_consts;
+  }
+  for (int pi = 0; pi < P.n_pdf; ++pi)
+    if (P.node[pi].kind == EXPR) {
+      if (!has_prog[order[pi]]) return fail("EXPR node without a program (rf_model_create_expr)", order[pi]);
+      P.has_expr = 1;
+    }
 
   // Signature and specialised shape.
   std::function<std::string(int)> sig = [&](int i) -> std::string {

@@ -13,6 +13,7 @@
 #include <cmath>
 #include <cstdio>
 
+#include "expr.cuh"
 #include "k1_ff.cuh"
 #include "nll_ff.cuh"
 #include "nll_kernels.cuh"
@@ -239,6 +240,11 @@ __device__ bool node_consts(const PNode& q, const double* th, double* c, const E
       for (int k = 0; k < np; ++k) c[1 + k] /= I;
       break;
     }
+    case EXPR:
+      // computed by the whole block of the parameter-point kernel
+      // (expr_consts_block); a single thread never takes this node
+      bad = true;
+      break;
     case SUM: {
       double fs = 0.0;
       for (int j = 0; j < q.n_par; ++j) {
@@ -350,6 +356,8 @@ __global__ void param_point_kernel(const __grid_constant__ Program P, Pass pass)
 // decay node also the convolution at each end (4 jobs); then every node's
 // constants on its own warp; then the float-float constants.
 constexpr int kK1Warps = 8;
+static_assert(kK1Warps * 32 == kQuadPanels, "the EXPR quadrature takes one panel per thread of the block");
+template <bool kExpr>
 __global__ void __launch_bounds__(kK1Warps * 32) param_point_block_kernel(const __grid_constant__ Program P,
                                                                           Pass pass) {
   __shared__ EndVals ends[kMaxPdf][2];
@@ -416,6 +424,31 @@ __global__ void __launch_bounds__(kK1Warps * 32) param_point_block_kernel(const 
     if (tid == 0) sbad = 0;
     __syncthreads();
   }
+  // EXPR nodes: normalisation integral and its derivatives by the whole
+  // block, constants [1/I, dlogI/dp_1..n, p_1..n]
+  if constexpr (kExpr) {
+    __shared__ QuadSmem quad[1];
+    for (int n = 0; n < P.n_pdf; ++n) {
+      const PNode& q = P.node[n];
+      if (q.kind != EXPR) continue;
+      double par[kMaxPar], I[1 + kMaxPar];
+      for (int j = 0; j < q.n_par; ++j) par[j] = param_of(q, j, th);
+      const bool ok = expr_integrate_block(P, q, par, quad[0], I);
+      if (tid == 0) {
+        if (!ok) {
+          sbad = 1;
+        } else {
+          double* c = Cs + q.cofs;
+          c[0] = 1.0 / I[0];
+          for (int j = 0; j < q.n_par; ++j) {
+            c[1 + j] = I[1 + j] / I[0];
+            c[1 + q.n_par + j] = par[j];
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
   // jobs: (node, end, part), numbered in node order
   if (lane == 0) {
     int j = 0;
@@ -441,6 +474,7 @@ __global__ void __launch_bounds__(kK1Warps * 32) param_point_block_kernel(const 
     bool bad = false;
     for (int n = warp; n < P.n_pdf; n += kK1Warps) {
       const PNode& q = P.node[n];
+      if (q.kind == EXPR) continue;  // done above
       const bool split = q.kind == GAUSS || q.kind == GAUSSEXP;
       bad |= !node_consts(q, th, Cs + q.cofs, split ? ends[n] : nullptr);
     }
@@ -516,7 +550,7 @@ __device__ __forceinline__ double logprod64_log(const LogProd64& L) {
 // one factor's sub-program (a PROD factor's nodes are contiguous in program
 // order and refer only to each other), whose log p and slot gradients are
 // then those of that factor alone.
-template <bool kFull, bool kGrad>
+template <bool kFull, bool kGrad, bool kExpr = false>
 __device__ bool eval_generic(const Program& P, const double* __restrict__ C, const double* x, double* acc,
                              LogProd64& L, int* bad, int n0 = 0, int n1 = -1) {
   double v[kMaxPdf];
@@ -571,6 +605,11 @@ __device__ bool eval_generic(const Program& P, const double* __restrict__ C, con
         v[n] = exp(k * c[1] - c[0] - lgamma(k + 1.0)) * c[3];
         break;
       }
+      case EXPR: {
+        double f;
+        if constexpr (kExpr) v[n] = expr_eval(P, q, c + 1 + q.n_par, x[q.col], 0, &f, nullptr) ? f * c[0] : NAN;
+        break;
+      }
       case SUM: {
         double r = 0.0;
         for (int j = 0; j < q.n_child; ++j) r += c[j] * v[q.child[j]];
@@ -619,6 +658,15 @@ __device__ bool eval_generic(const Program& P, const double* __restrict__ C, con
       case POISSON: {
         const double k = fmin(floor(x[q.col]), q.hi - 1.0);
         g[s0] += a * v[n] * (k * c[2] - 1.0 - c[4]);
+        break;
+      }
+      case EXPR: {  // dv/dp_j = (df/dp_j - f dlogI/dp_j) / I, with no division by f (which may underflow)
+        if constexpr (kExpr) {
+          double f, df[kMaxPar];
+          expr_eval(P, q, c + 1 + q.n_par, x[q.col], q.n_par, &f, df);
+          const double w = a * c[0];
+          for (int j = 0; j < q.n_par; ++j) g[s0 + j] += w * (df[j] - f * c[1 + j]);
+        }
         break;
       }
       case GAUSSEXP: {
@@ -855,7 +903,7 @@ __device__ void finish_chunk(const Program& P, const Pass& pass, Smem& sm, doubl
 // chunk in order.  Events that need a node's slow path are queued per warp
 // (ballot order) and evaluated after the fast pass, so the warp stays
 // converged; the lane order of additions is still fixed by the data alone.
-template <bool kGrad>
+template <bool kGrad, bool kExpr>
 __global__ void __launch_bounds__(kLanes) events_generic(const __grid_constant__ Program P,
                                                          const __grid_constant__ Columns cols, Pass pass) {
   __shared__ Smem sm;
@@ -882,7 +930,7 @@ __global__ void __launch_bounds__(kLanes) events_generic(const __grid_constant__
       bool slow = false;
       if (e < s_end) {
         for (int c = 0; c < P.n_obs; ++c) x[c] = load_col(cols, c, e);
-        slow = !eval_generic<false, kGrad>(P, sm.C, x, acc, L, &bad);
+        slow = !eval_generic<false, kGrad, kExpr>(P, sm.C, x, acc, L, &bad);
       }
       if (P.has_slow) {
         const unsigned b = __ballot_sync(0xffffffffu, slow);
@@ -895,7 +943,7 @@ __global__ void __launch_bounds__(kLanes) events_generic(const __grid_constant__
     for (int j = lane; j < qcnt; j += 32) {
       const int64_t e = base + sm.queue[warp][j];
       for (int c = 0; c < P.n_obs; ++c) x[c] = load_col(cols, c, e);
-      eval_generic<true, kGrad>(P, sm.C, x, acc, L, &bad);
+      eval_generic<true, kGrad, kExpr>(P, sm.C, x, acc, L, &bad);
     }
     acc[0] += logprod64_log(L);
     (void)Q;
@@ -1162,8 +1210,12 @@ __global__ void __launch_bounds__(kLanes, ff_min_blocks(kShape)) events_ff(const
 
 void launch_param_point(const Program& P, const Pass& pass, cudaStream_t st) {
   note_launches(1, st);
+  if (pass.n_active > 0 && P.has_expr) {
+    param_point_block_kernel<true><<<pass.n_active, kK1Warps * 32, 0, st>>>(P, pass);
+    return;
+  }
   if (pass.n_active > 0 && pass.n_active <= kBlockK1MaxSets) {
-    param_point_block_kernel<<<pass.n_active, kK1Warps * 32, 0, st>>>(P, pass);
+    param_point_block_kernel<false><<<pass.n_active, kK1Warps * 32, 0, st>>>(P, pass);
     return;
   }
   // two-warp blocks: one fits in the registers that an SM full of event
@@ -1189,7 +1241,7 @@ const void* event_kernel(Shape shape, bool grad) {
     case SHAPE_SUM_GAUSSEXP_CHEB2: return ff_kernel<SHAPE_SUM_GAUSSEXP_CHEB2>(grad);
     case SHAPE_SUM_GAUSS_POLY1: return ff_kernel<SHAPE_SUM_GAUSS_POLY1>(grad);
     case SHAPE_PROD3: return ff_kernel<SHAPE_PROD3>(grad);
-    default: return grad ? (const void*)events_generic<true> : (const void*)events_generic<false>;
+    default: return grad ? (const void*)events_generic<true, false> : (const void*)events_generic<false, false>;
   }
 }
 
@@ -1249,8 +1301,10 @@ void launch_events(const Program& P, Shape shape, const Columns& cols, const Pas
     case SHAPE_SUM_GAUSS_POLY1: launch_ff<SHAPE_SUM_GAUSS_POLY1>(pass.want_grad, all_f32, grid, st, P, cols, pass); break;
     case SHAPE_PROD3: launch_ff<SHAPE_PROD3>(pass.want_grad, all_f32, grid, st, P, cols, pass); break;
     default:
-      if (pass.want_grad) launch_dependent(events_generic<true>, grid, st, P, cols, pass);
-      else launch_dependent(events_generic<false>, grid, st, P, cols, pass);
+      if (P.has_expr && pass.want_grad) launch_dependent(events_generic<true, true>, grid, st, P, cols, pass);
+      else if (P.has_expr) launch_dependent(events_generic<false, true>, grid, st, P, cols, pass);
+      else if (pass.want_grad) launch_dependent(events_generic<true, false>, grid, st, P, cols, pass);
+      else launch_dependent(events_generic<false, false>, grid, st, P, cols, pass);
   }
   timing_end(st);
 }

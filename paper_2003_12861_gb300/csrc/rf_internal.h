@@ -26,8 +26,12 @@ constexpr int kPerLane = kChunk / kLanes;  // 32
 constexpr int kRadix = 32;
 
 enum Kind : int8_t {
-  OBS = 0, PARAM = 1, GAUSS = 2, EXPO = 3, GAUSSEXP = 4, CHEB = 5, POLY = 6, SUM = 7, PROD = 8, POISSON = 9, EXTEND = 10
+  OBS = 0, PARAM = 1, GAUSS = 2, EXPO = 3, GAUSSEXP = 4, CHEB = 5, POLY = 6, SUM = 7, PROD = 8, POISSON = 9, EXTEND = 10,
+  EXPR = 11
 };
+// RF_EXPR programs: per node at most 64 operations and 16 constants, per
+// model 128 and 32 in all; the evaluation stack holds 16 values.
+constexpr int kExprMaxOps = 64, kExprMaxConsts = 16, kExprPoolOps = 128, kExprPoolConsts = 32, kExprStack = 16;
 // Largest observable range (integers) of a POISSON leaf.
 constexpr int kMaxPoissonRange = 100000;
 
@@ -41,6 +45,7 @@ struct PNode {
   int8_t pfree[kMaxPar];     // leaves: free index of local parameter j (-1: fixed); SUM: of fraction j
   int16_t cofs;              // offset of the node's constants in the per-set block
   int16_t slot0;             // first gradient slot of this node
+  int16_t ex_op0, ex_nops, ex_c0;  // EXPR: its program in the model's pools
   double lo, hi;             // leaves: observable range
   double pfixed[kMaxPar];    // leaves/SUM: value of a fixed parameter
 };
@@ -58,7 +63,10 @@ struct Program {
   int32_t ext;               // 1 if extended
   int32_t ext_free;          // nu's free index, or -1 (fixed: ext_fixed)
   double ext_fixed;
+  int32_t has_expr;          // 1 if some node is an EXPR (its K1 needs the block kernel)
   PNode node[kMaxPdf];
+  int32_t ex_ops[kExprPoolOps];      // EXPR programs, back to back
+  double ex_consts[kExprPoolConsts]; // and their constants
 };
 
 // Constant-block layout per node kind (doubles), written by the
@@ -71,6 +79,7 @@ struct Program {
 //   SUM(n)   [f_1..f_{n-1}, 1 - sum f]
 //   PROD     []
 //   POISSON  [lambda, log lambda, 1/lambda, 1/I, dlogI/dlambda]   v = pmf(floor x) / I
+//   EXPR(n)  [1/I, dlogI/dp_1..n, p_1..n]                v = program(x; p) / I
 inline int const_size(int kind, int n_par) {
   switch (kind) {
     case GAUSS: return 5;
@@ -80,6 +89,7 @@ inline int const_size(int kind, int n_par) {
     case POLY: return 1 + 2 * n_par;
     case SUM: return n_par + 1;
     case POISSON: return 5;
+    case EXPR: return 1 + 2 * n_par;
     default: return 0;
   }
 }
@@ -110,6 +120,7 @@ struct Model {
 };
 
 void set_error(const std::string& msg);
-rf_status compile_model(const rf_node* nodes, int n, int root, Model* m);
+rf_status compile_model(const rf_node* nodes, int n, int root, Model* m, const rf_expr* exprs = nullptr,
+                        int n_exprs = 0);
 
 }  // namespace rf

@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "api_internal.h"
+#include "expr.cuh"
 #include "nll_kernels.cuh"
 
 namespace rf {
@@ -97,6 +98,11 @@ __device__ void node_values(const Program& P, const double* __restrict__ C, cons
       case POISSON: {
         const double k = fmin(floor(x[q.col]), q.hi - 1.0);
         v[n] = exp(k * c[1] - c[0] - lgamma(k + 1.0)) * c[3];
+        break;
+      }
+      case EXPR: {
+        double f;
+        v[n] = expr_eval(P, q, c + 1 + q.n_par, x[q.col], 0, &f, nullptr) ? f * c[0] : NAN;
         break;
       }
       case SUM: {

@@ -178,3 +178,28 @@ def test_fp64_switch_selects_the_interpreter():
     m.set_fp64(False)
     assert "kernel=ff_prod3" in m.describe()
     assert L.load().rf_model_set_fp64(m._h, 2) == L.RF_E_INVALID
+
+
+def test_expr_models_compile_and_bad_programs_are_rejected():
+    m = api.Model.from_spec(W.expr_mix_model())
+    assert "EXPR" in m.describe() and "kernel=generic_fp64" in m.describe()
+    lib = L.load()
+    nodes = [Node("obs", (), 0.0, 0.0, 1.0), Node("param", (), 0.5, 0.0, 1.0, True),
+             Node("expr", (0, 1), prog=W.expr_program("x p0 *"))]
+    arr = api.make_nodes(nodes)
+    h = C.c_void_p()
+    # an EXPR node without a program
+    assert lib.rf_model_create(arr, 3, 2, C.byref(h)) == L.RF_E_INVALID
+    bad = ["x +", "x x", "p1", "c0", " ".join(["x"] * 17) + " +" * 16, " ".join(["x exp"] * 33)]
+    for text in bad:
+        ops = W.expr_program(text)
+        o = (C.c_int32 * len(ops))(*ops)
+        ex = (L.rf_expr * 1)()
+        ex[0].node, ex[0].n_ops, ex[0].ops, ex[0].n_consts = 2, len(ops), o, 0
+        assert lib.rf_model_create_expr(arr, 3, 2, ex, 1, C.byref(h)) == L.RF_E_INVALID, text
+    # a program for a node that is not EXPR
+    ops = W.expr_program("x")
+    o = (C.c_int32 * 1)(*ops)
+    ex = (L.rf_expr * 1)()
+    ex[0].node, ex[0].n_ops, ex[0].ops, ex[0].n_consts = 1, 1, o, 0
+    assert lib.rf_model_create_expr(arr, 3, 2, ex, 1, C.byref(h)) == L.RF_E_INVALID
