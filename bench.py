@@ -665,7 +665,7 @@ def run_learned(args, api, torch, dist, rank, world, local, steps=None):
     with ClockSampler(local) as clk:
         r = None
         for _ in range(steps or args.steps):
-            r = learned.compare(net, model, 10_000, seed + 777)
+            r = learned.compare(net, model, 10_000, seed + 777, characterise=True)
     if rank != 0:
         return None
     return {
@@ -674,6 +674,8 @@ def run_learned(args, api, torch, dist, rank, world, local, steps=None):
         "config": {"workload": "learned_start", "train_toys": tinfo["toys"], "train_converged": tinfo["converged"],
                    "eval_toys": 10_000, "sizes": "Poisson(N), N log-uniform in [1e3, 1e5]",
                    "theta": "uniform +-30% around the decay model's values", "network": "64-128-128-128-6 GELU",
+                   "labels": "the deeper of the fits from the default start and from the generating values",
+                   "tol_edm": r["tol_edm"],
                    "epochs": args.epochs},
         "learned_vs_plain": r,
         "training": {"build_s": tinfo["seconds"], "train_s": ninfo["seconds"], "final_loss": ninfo["final_loss"]},

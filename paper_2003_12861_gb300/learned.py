@@ -5,12 +5,17 @@ Orchestration only: toys are generated (rf_generate_toys), histogrammed
 (rf_hist64) and fitted (rf_fit) by the library, the network is trained and
 evaluated by its kernels (rf_mlp_*); PyTorch holds the device buffers.
 
-Training labels are the plain fits' minima (theta-hat) of each training toy,
-whose generating parameters are drawn uniformly within +-30 % of the decay
-model's values; the plain fit from the default start is also the fallback
-and the yardstick: a learned start that fails (outside the domain, or no
+Training toys have generating parameters drawn uniformly within +-30 % of
+the decay model's values.  Each is fitted twice, from the plain default start
+and from its generating parameters, and its label is the fitted point
+(theta-hat) of the lower of the two minima: small toys of this model have
+several local minima (a resolution parameter or the signal fraction on a
+bound against an interior minimum), and the network should point at the
+deeper one.  The plain fit from the default start is also the fallback and
+the yardstick: a learned start that fails (outside the domain, or no
 convergence) is refitted from the default start, and a learned fit that ends
-in a different minimum (|delta NLL| >= 1e-6) is counted and reported.
+in a different minimum (|delta NLL| >= 1e-6) is counted and reported, higher
+and lower separately.
 """
 from __future__ import annotations
 
@@ -30,8 +35,9 @@ def _hist(model, data, torch):
 
 def build_training_set(model, n_toys: int, seed: int, chunk: int = 4096, n_lo: float = 1e3, n_hi: float = 1e5,
                        tol_edm: float = 1e-7):
-    """Generate and plain-fit `n_toys` toys; returns (hist, labels) CUDA
-    tensors of the converged fits and a summary dict."""
+    """Generate `n_toys` toys and fit each from the default start and from
+    its generating parameters; returns (hist, labels) CUDA tensors of the
+    toys with a converged fit (labels: the deeper minimum) and a summary."""
     import torch
 
     xs, ys = [], []
@@ -44,6 +50,13 @@ def build_training_set(model, n_toys: int, seed: int, chunk: int = 4096, n_lo: f
         data = api.generate_toys(model, th, seed + k, mean, poisson=True)
         h = _hist(model, data, torch)
         r = api.fit(model, data, tol_edm=tol_edm, want_cov=False)
+        rt = api.fit(model, data, theta0=th, tol_edm=tol_edm, want_cov=False)
+        # the deeper of the two minima (a fit that did not converge loses)
+        nll_p = np.where(r["status"] == 0, r["nll"], np.inf)
+        nll_t = np.where(rt["status"] == 0, rt["nll"], np.inf)
+        use_t = nll_t < nll_p
+        r["theta"][use_t] = rt["theta"][use_t]
+        r["status"][use_t] = 0
         ok = r["status"] == 0
         fitted += S
         conv += int(ok.sum())
@@ -67,7 +80,8 @@ def predict_starts(net, model, data):
     return net.predict(model, data, 0)
 
 
-def compare(net, model, n_toys: int, seed: int, tol_edm: float = 1e-7, n_lo: float = 1e3, n_hi: float = 1e5):
+def compare(net, model, n_toys: int, seed: int, tol_edm: float = 1e-9, n_lo: float = 1e3, n_hi: float = 1e5,
+            characterise: bool = False):
     """Fit fresh toys from the plain default start and from the learned start."""
     import torch
 
@@ -102,6 +116,7 @@ def compare(net, model, n_toys: int, seed: int, tol_edm: float = 1e-7, n_lo: flo
     n2 = api.launch_count()
     both = (plain["status"] == 0) & (learned["status"] == 0)
     d = learned["nll"][both] - plain["nll"][both]
+    mismatch = _characterise(model, data, plain, learned, both) if characterise else None
     return {
         "toys": n_toys, "events": int(data.n_events),
         "plain": {"wall_s": t_plain, "toy_fits_per_s": n_toys / t_plain,
@@ -115,4 +130,41 @@ def compare(net, model, n_toys: int, seed: int, tol_edm: float = 1e-7, n_lo: flo
         "learned_lower_nll_frac": float(np.mean(d <= -1e-6)) if d.size else 0.0,
         "learned_higher_nll_frac": float(np.mean(d >= 1e-6)) if d.size else 0.0,
         "median_abs_dnll": float(np.median(np.abs(d))) if d.size else None,
+        "tol_edm": tol_edm,
+        "mismatch": mismatch,
     }
+
+
+def _characterise(model, data, plain, learned, both):
+    """The toys whose two fits end in different minima: refitted from each
+    end point with a tight tolerance (EDM < 1e-11), a pair that then agrees
+    was a stop short of one minimum; the others are distinct minima.  Also
+    how many have a parameter within 1e-3 of its range at either end point."""
+    spec_lo = np.array(model_bounds(model)[0])
+    spec_hi = np.array(model_bounds(model)[1])
+    off = data.offsets()
+    col = data.read(0)
+    d = learned["nll"] - plain["nll"]
+    out = {}
+    for name, sel in (("learned_higher", both & (d >= 1e-6)), ("learned_lower", both & (d <= -1e-6))):
+        idx = np.nonzero(sel)[0]
+        if len(idx) == 0:
+            out[name] = {"count": 0}
+            continue
+        parts = [col[off[s]:off[s + 1]] for s in idx]
+        sub = api.Data.upload(model, [np.concatenate(parts)], offsets=np.concatenate([[0], np.cumsum([len(p) for p in parts])]))
+        rl = api.fit(model, sub, theta0=learned["theta"][idx], tol_edm=1e-11, want_cov=False)
+        rp = api.fit(model, sub, theta0=plain["theta"][idx], tol_edm=1e-11, want_cov=False)
+        span = spec_hi - spec_lo
+        near = [np.any(np.minimum(t - spec_lo, spec_hi - t) < 1e-3 * span) or
+                np.any(np.minimum(u - spec_lo, spec_hi - u) < 1e-3 * span)
+                for t, u in zip(learned["theta"][idx], plain["theta"][idx])]
+        out[name] = {"count": int(len(idx)), "resolved_by_tight_refit": float(np.mean(np.abs(rl["nll"] - rp["nll"]) < 1e-6)),
+                     "near_a_bound": float(np.mean(near)), "median_abs_dnll": float(np.median(np.abs(d[idx]))),
+                     "median_events": float(np.median(np.diff(off)[idx]))}
+    return out
+
+
+def model_bounds(model):
+    nodes = [n for n in model.nodes if n.kind == "param" and n.free]
+    return [n.lo for n in nodes], [n.hi for n in nodes]
