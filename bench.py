@@ -28,6 +28,9 @@ latency-bound); binned_4096.
 
 Multi-GPU (torchrun): every rank evaluates its own dataset (weak scaling, no
 collective on the data path); rank 0 prints one JSON line (no extras).
+--shard: strong scaling instead, one 1e8-event dataset split over the ranks
+(rf_shard), each step = every rank's partial pass + one all_gather of the
+(1 + 12) x 2 compensated sums + the rank-ordered exact merge.
 --impl reference times the CPU oracle (single thread, the machine's host cores)
 on a bounded sample of the same workload, with the same metric.
 """
@@ -453,7 +456,9 @@ def run_events(args, api, torch, dist, rank, world, local, wl=None, steps=None, 
     data = api.generate_toys(model, theta_true, W.SEED_BASE + 1 + 1000 * rank, [float(n)], poisson=False,
                              f32=[f32] * spec.n_obs)
     assert data.n_events == n
-    tune = api.autotune(model, data, passes=3)
+    grid = api.autotune_scan(model, data, passes=3)
+    best = min(grid, key=lambda g: g[1])
+    tune = (128, best[0], best[1])
     P = model.n_free
     stream = torch.cuda.Stream()
     theta = torch.tensor(theta_true * (1 + 0.02 * np.cos(np.arange(P))), dtype=torch.float64, device="cuda")
@@ -533,7 +538,8 @@ def run_events(args, api, torch, dist, rank, world, local, wl=None, steps=None, 
         "dtype": path_dtype(model, f32), "config": {"workload": wl, "n_events_per_gpu": n,
                                    "columns": f"{spec.n_obs} x {'f32' if f32 else 'f64'}",
                                    "free_parameters": P, "l2": "flushed between steps (256 MiB write)",
-                                   "tile": {"threads_per_block": tune[0], "blocks_per_sm": tune[1]}},
+                                   "tile": {"threads_per_block": tune[0], "blocks_per_sm": tune[1],
+                                            "grid_ms_per_pass": {str(b): round(t, 4) for b, t in grid}}},
         "roofline": roofline(api, model, spec, data, kern_ms, kern_n, n, bpe, peaks, peak_kind, workload=wl),
         "e2e": e2e, "gpu_launches": int(n_launches), "clocks": clk.summary(),
         "nll_check": float(out[0].item()),
@@ -577,7 +583,9 @@ def run_toys(args, api, torch, dist, rank, world, local, steps=None, warmup=None
     mean = W.toy_mean_sizes(S, seed)
     data = api.generate_toys(model, W.DECAY_TRUE, seed + 1000 * rank, mean, poisson=True)
     n_events = data.n_events
-    tune = api.autotune(model, data, passes=2)
+    grid = api.autotune_scan(model, data, passes=2)
+    best = min(grid, key=lambda g: g[1])
+    tune = (128, best[0], best[1])
     P = model.n_free
     # roofline pass: one ragged persistent launch over all toys
     stream = torch.cuda.Stream()
@@ -637,7 +645,8 @@ def run_toys(args, api, torch, dist, rank, world, local, steps=None, warmup=None
         "config": {"workload": "decay_toys_4096", "toys": S, "events": int(n_events),
                    "sizes": "Poisson(N), N log-uniform in [1e3, 1e5]", "theta": "the decay model's values for every toy",
                    "start": "plain default start",
-                   "tol_edm": 1e-7, "tile": {"threads_per_block": tune[0], "blocks_per_sm": tune[1]},
+                   "tol_edm": 1e-7, "tile": {"threads_per_block": tune[0], "blocks_per_sm": tune[1],
+                                             "grid_ms_per_pass": {str(b): round(t, 4) for b, t in grid}},
                    "eval_step": "CUDA graph replay, one ragged persistent launch per round"},
         "roofline": rl,
         "e2e": {"value": world * S / e2e_s, "unit": "toy fits/s", "h2d_bytes_per_step": int(n_events) * 8,
@@ -787,6 +796,77 @@ def run_binned(args, api, torch, dist, rank, world, local):
     }
 
 
+def exchange_partials(api, pairs, flags, group=None):
+    """The sharded step's one exchange: every rank's compensated partial
+    sums ((n_sets, 1 + P, 2) pairs and n_sets flags, host arrays) gathered
+    in rank order over torch.distributed and merged exactly on every rank
+    (rf_combine_partials).  Returns (NLL and gradient per set, flags)."""
+    allp, allf = api.gather_partials(pairs, flags, group)
+    return api.combine_partials(allp, allf)
+
+
+def run_sharded(args, api, torch, dist, rank, world, local):
+    """Strong scaling of one dataset: the product model's 1e8 events split
+    over the ranks by rf_shard (contiguous 4096-aligned event ranges); per
+    step every rank evaluates its shard's compensated partial sums
+    (rf_nll_grad_partial: parameter point + event pass), the ranks exchange
+    them once (an all_gather of (1 + 12) x 2 doubles per rank) and every rank
+    merges them in rank order.  Each rank's shard is generated on its GPU
+    (any in-range events serve the timing; the combine's correctness against
+    the whole dataset is tested on its own)."""
+    ctor, theta_true, n_total, f32, bpe = WORKLOADS["prod3_1e8_f32"]
+    spec = W.model_for(ctor)
+    model = api.Model.from_spec(spec)
+    lo, hi = api.shard(n_total, 4096, rank, world)
+    data = api.generate_toys(model, theta_true, W.SEED_BASE + 1 + 1000 * rank, [float(hi - lo)], poisson=False,
+                             f32=[f32] * spec.n_obs)
+    api.autotune(model, data, passes=2)
+    P = model.n_free
+    stream = torch.cuda.Stream()
+    th = torch.tensor(theta_true * (1 + 0.02 * np.cos(np.arange(P))), dtype=torch.float64, device="cuda")
+    pairs = torch.zeros((1, 1 + P, 2), dtype=torch.float64, device="cuda")
+    flags = torch.zeros(1, dtype=torch.int32, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def step():
+        api.nll_grad_partial(model, data, th, pairs, flags, stream=stream)
+        stream.synchronize()
+        return exchange_partials(api, pairs.cpu().numpy(), flags.cpu().numpy())
+
+    for _ in range(args.warmup):
+        step()
+    ts = []
+    dist.barrier()
+    torch.cuda.synchronize()
+    n_launch0 = api.launch_count()
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            dist.barrier()
+            t0 = time.perf_counter()
+            out, fo = step()
+            ts.append(time.perf_counter() - t0)
+    n_launches = api.launch_count() - n_launch0
+    t = torch.tensor([sum(ts)], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_s = float(t.item())
+    if rank != 0:
+        return None
+    return {
+        "value": n_total * args.steps / total_s, "unit": "events/s", "ms_per_step": 1e3 * total_s / args.steps,
+        "dtype": path_dtype(model, f32),
+        "config": {"workload": "prod3_1e8_f32", "mode": "one dataset sharded over the ranks (strong scaling)",
+                   "n_events_total": n_total, "shard_events_rank0": hi - lo, "columns": "3 x f32",
+                   "free_parameters": P, "l2": "flushed between steps (256 MiB write)",
+                   "exchange": "one all_gather of (1 + 12) x 2 doubles per rank, rank-ordered exact merge"},
+        "e2e": {"value": n_total * args.steps / total_s, "unit": "events/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": (1 + P) * 16 + 4,
+                "note": "the step ends with the combined NLL and gradient on every rank's host"},
+        "gpu_launches": int(n_launches), "clocks": clk.summary(), "nll_check": float(out[0, 0]), "scaling": "strong",
+    }
+
+
 def headline_extras(args, api, torch, local):
     """The rest of the metric beside the headline's events/s, each measured
     in this run on its own configuration: the decay model at 1e7 events
@@ -822,8 +902,16 @@ def run_ours(args):
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     L.load()
-    headline = args.workload == "prod3_1e8_f32"
-    if args.workload == "decay_toys_4096":
+    headline = args.workload == "prod3_1e8_f32" and not args.shard
+    if args.shard:
+        if dist is None:  # one rank: the same step with a one-rank group
+            import torch.distributed as dist
+
+            os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+            os.environ.setdefault("MASTER_PORT", "29531")
+            dist.init_process_group("gloo", rank=0, world_size=1)
+        line = run_sharded(args, api, torch, dist, rank, world, local)
+    elif args.workload == "decay_toys_4096":
         line = run_toys(args, api, torch, dist, rank, world, local)
     elif args.workload == "learned_start":
         line = run_learned(args, api, torch, dist, rank, world, local)
@@ -837,8 +925,8 @@ def run_ours(args):
     if rank == 0:
         full = {"metric": METRIC, "value": line.pop("value"), "unit": line.pop("unit"), "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": line.pop("ms_per_step"),
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": line.pop("dtype"),
-                "data": "synthetic"}
+                "higher_is_better": True, "scaling": line.pop("scaling", "weak"), "vs_baseline": None,
+                "dtype": line.pop("dtype"), "data": "synthetic"}
         full.update(line)
         if not args.no_cpu_baseline:
             full["cpu_baseline"] = cpu_baseline(args.workload)
@@ -856,13 +944,15 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="prod3_1e8_f32", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--shard", action="store_true",
+                    help="strong scaling: one 1e8-event dataset sharded over the ranks, one exchange per step")
     ap.add_argument("--no-extras", action="store_true",
                     help="default workload: skip the decay, toy-fit and learned-start figures")
     ap.add_argument("--train-toys", type=int, default=1_000_000, help="learned_start: training toys")
     ap.add_argument("--epochs", type=int, default=20, help="learned_start: training epochs")
     args = ap.parse_args()
     if args.steps is None:
-        args.steps = DEFAULT_STEPS[args.workload]
+        args.steps = DEFAULT_STEPS[args.workload] if not args.shard else 20
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

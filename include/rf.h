@@ -212,17 +212,29 @@ rf_status rf_nll_grad_async(const rf_model* m, const rf_data* d, const double* d
 rf_status rf_nll_chunks(const rf_model* m, const rf_data* d, const double* theta, int32_t set, double* out,
                         int32_t max_chunks, int32_t* n_chunks);
 
-/* Tile shape of the fused event kernel: threads per block (128, 256 or 512)
- * and resident blocks per SM for the persistent grid.  0 = library choice.
- * The NLL does not depend on it (bitwise). */
+/* Launch shape of the fused event kernel.  Its block is always 128 threads:
+ * lane l of a block sums events l, l + 128, ... of a chunk, and that fixed
+ * lane-to-event map is what makes the NLL independent of the launch
+ * (bitwise), so threads_per_block accepts 0 or 128 only.  The tunable
+ * dimension is blocks_per_sm, the resident blocks per SM of the persistent
+ * grid (1..32; 0 = library choice).  The work unit (a whole 4096-event chunk,
+ * or a quarter chunk for datasets of fewer than 1024 chunks) is fixed by
+ * the dataset for the same reason. */
 rf_status rf_set_launch(rf_model* m, int32_t threads_per_block, int32_t blocks_per_sm);
 
-/* Autotuner: times `passes` NLL+gradient passes over `d` for every supported
- * tile shape (threads per block x resident blocks per SM), keeps the fastest
- * on the model (as rf_set_launch would) and reports it; *best_ms is the mean
- * pass time of the winner.  Results do not depend on the shape (bitwise). */
+/* Autotuner: times `passes` NLL+gradient passes over `d` for every resident
+ * block count per SM that fits the kernel's registers and shared memory
+ * (from {1..8, 12, 16}), keeps the fastest on the model (as rf_set_launch
+ * would) and reports it: *threads_per_block = 128, *blocks_per_sm, *best_ms
+ * the mean pass time of the winner.  Results do not depend on the choice
+ * (bitwise). */
 rf_status rf_autotune(rf_model* m, rf_data* d, int32_t passes, int32_t* threads_per_block, int32_t* blocks_per_sm,
                       double* best_ms);
+/* The same search, reporting the whole grid: for each candidate i < *n
+ * (at most cap), blocks_per_sm[i] and its mean pass time ms[i]; the winner
+ * is kept on the model. */
+rf_status rf_autotune_scan(rf_model* m, rf_data* d, int32_t passes, int32_t cap, int32_t* blocks_per_sm, double* ms,
+                           int32_t* n);
 
 /* ------------------------------------------------------------------- fits */
 

@@ -174,10 +174,20 @@ def _theta(model: Model, data: Data, theta):
 
 
 def autotune(model: Model, data: Data, passes: int = 5):
-    """Pick the fastest tile shape for (model, data); returns (threads, blocks_per_sm, ms)."""
+    """Pick the fastest launch shape for (model, data); returns (threads, blocks_per_sm, ms)."""
     t, b, ms = C.c_int32(), C.c_int32(), C.c_double()
     L.check(L.load().rf_autotune(model._h, data._h, passes, C.byref(t), C.byref(b), C.byref(ms)))
     return t.value, b.value, ms.value
+
+
+def autotune_scan(model: Model, data: Data, passes: int = 3):
+    """The autotuner's whole grid: [(blocks_per_sm, mean pass ms), ...]; the
+    winner is kept on the model."""
+    bps = (C.c_int32 * 16)()
+    ms = (C.c_double * 16)()
+    n = C.c_int32()
+    L.check(L.load().rf_autotune_scan(model._h, data._h, passes, 16, bps, ms, C.byref(n)))
+    return [(bps[i], ms[i]) for i in range(n.value)]
 
 
 def nll(model: Model, data: Data, theta, stream=None, allow_domain=False):

@@ -305,8 +305,8 @@ rf_status rf_model_set_fp64(rf_model* m, int32_t on) {
 
 rf_status rf_set_launch(rf_model* m, int32_t threads_per_block, int32_t blocks_per_sm) {
   if (!m) { set_error("rf_set_launch: model is NULL"); return RF_E_INVALID; }
-  if (threads_per_block != 0 && threads_per_block != 128 && threads_per_block != 256 && threads_per_block != 512) {
-    set_error("rf_set_launch: threads_per_block must be 0, 128, 256 or 512");
+  if (threads_per_block != 0 && threads_per_block != kLanes) {
+    set_error("rf_set_launch: threads_per_block must be 0 or 128 (the reduction's fixed lane-to-event map)");
     return RF_E_INVALID;
   }
   if (blocks_per_sm < 0 || blocks_per_sm > 32) { set_error("rf_set_launch: blocks_per_sm must be 0..32"); return RF_E_INVALID; }
@@ -525,12 +525,13 @@ rf_status finish_data(rf_data* d) {
 
 }  // namespace rf
 
-extern "C" rf_status rf_autotune(rf_model* m, rf_data* d, int32_t passes, int32_t* threads_per_block,
-                                 int32_t* blocks_per_sm, double* best_ms) {
-  if (!m || !d || passes < 1 || !threads_per_block || !blocks_per_sm || !best_ms) {
+extern "C" rf_status rf_autotune_scan(rf_model* m, rf_data* d, int32_t passes, int32_t cap, int32_t* blocks_per_sm,
+                                      double* ms_out, int32_t* n) {
+  if (!m || !d || passes < 1 || cap < 1 || !blocks_per_sm || !ms_out || !n) {
     set_error("rf_autotune: bad argument");
     return RF_E_INVALID;
   }
+  *n = 0;
   if (d->n_obs != m->m.prog.n_obs) {
     set_error("rf_autotune: data and model have different observable counts");
     return RF_E_INVALID;
@@ -545,43 +546,58 @@ extern "C" rf_status rf_autotune(rf_model* m, rf_data* d, int32_t passes, int32_
     return RF_E_CUDA;
   cudaEvent_t e0, e1;
   if (!cuda_ok(cudaEventCreate(&e0), "autotune") || !cuda_ok(cudaEventCreate(&e1), "autotune")) return RF_E_CUDA;
-  static const int kThreads[] = {128, 256, 512};
   static const int kBps[] = {1, 2, 3, 4, 5, 6, 7, 8, 12, 16};
-  const int save_t = m->m.threads_per_block, save_b = m->m.blocks_per_sm;
+  const int save_b = m->m.blocks_per_sm;
   double best = 1e300;
-  int bt = 0, bb = 0;
-  for (int t : kThreads) {
-    if (!launch_supports_threads(m->m.shape, t)) continue;
-    for (int b : kBps) {
-      if (!launch_fits(m->m.shape, t, b)) continue;
-      m->m.threads_per_block = t;
-      m->m.blocks_per_sm = b;
+  int bb = 0;
+  for (int b : kBps) {
+    if (!launch_fits(m->m.shape, kLanes, b) || *n >= cap) continue;
+    m->m.threads_per_block = kLanes;
+    m->m.blocks_per_sm = b;
+    launch_pass(m, d, d->all_plan, (const double*)w.theta.p, (double*)w.out.p, (int32_t*)w.flags.p, true, 0);
+    cudaEventRecord(e0, 0);
+    for (int i = 0; i < passes; ++i)
       launch_pass(m, d, d->all_plan, (const double*)w.theta.p, (double*)w.out.p, (int32_t*)w.flags.p, true, 0);
-      cudaEventRecord(e0, 0);
-      for (int i = 0; i < passes; ++i)
-        launch_pass(m, d, d->all_plan, (const double*)w.theta.p, (double*)w.out.p, (int32_t*)w.flags.p, true, 0);
-      cudaEventRecord(e1, 0);
-      if (!cuda_ok(cudaEventSynchronize(e1), "autotune")) {
-        m->m.threads_per_block = save_t;
-        m->m.blocks_per_sm = save_b;
-        return RF_E_CUDA;
-      }
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (ms / passes < best) {
-        best = ms / passes;
-        bt = t;
-        bb = b;
-      }
+    cudaEventRecord(e1, 0);
+    if (!cuda_ok(cudaEventSynchronize(e1), "autotune")) {
+      m->m.blocks_per_sm = save_b;
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return RF_E_CUDA;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    blocks_per_sm[*n] = b;
+    ms_out[*n] = ms / passes;
+    ++*n;
+    if (ms / passes < best) {
+      best = ms / passes;
+      bb = b;
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  m->m.threads_per_block = bt;
+  m->m.threads_per_block = kLanes;
   m->m.blocks_per_sm = bb;
-  *threads_per_block = bt;
-  *blocks_per_sm = bb;
-  *best_ms = best;
+  return RF_OK;
+}
+
+extern "C" rf_status rf_autotune(rf_model* m, rf_data* d, int32_t passes, int32_t* threads_per_block,
+                                 int32_t* blocks_per_sm, double* best_ms) {
+  if (!threads_per_block || !blocks_per_sm || !best_ms) {
+    set_error("rf_autotune: bad argument");
+    return RF_E_INVALID;
+  }
+  int32_t bps[16], n = 0;
+  double ms[16];
+  const rf_status s = rf_autotune_scan(m, d, passes, 16, bps, ms, &n);
+  if (s != RF_OK) return s;
+  int best = 0;
+  for (int i = 1; i < n; ++i)
+    if (ms[i] < ms[best]) best = i;
+  *threads_per_block = kLanes;
+  *blocks_per_sm = n > 0 ? bps[best] : 0;
+  *best_ms = n > 0 ? ms[best] : 0.0;
   return RF_OK;
 }
 

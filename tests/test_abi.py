@@ -203,3 +203,14 @@ def test_expr_models_compile_and_bad_programs_are_rejected():
     ex = (L.rf_expr * 1)()
     ex[0].node, ex[0].n_ops, ex[0].ops, ex[0].n_consts = 1, 1, o, 0
     assert lib.rf_model_create_expr(arr, 3, 2, ex, 1, C.byref(h)) == L.RF_E_INVALID
+
+
+def test_launch_shape_is_128_threads_with_tunable_blocks_per_sm():
+    m = api.Model.from_spec(W.decay_model())
+    m.set_launch(128, 4)
+    m.set_launch(0, 0)
+    for t in (64, 256, 512):
+        with pytest.raises(L.RFError):
+            m.set_launch(t, 4)
+    with pytest.raises(L.RFError):
+        m.set_launch(128, 33)

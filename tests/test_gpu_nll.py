@@ -102,6 +102,24 @@ def test_deterministic_across_launch_shapes_and_reruns(oracle_mod):
             assert r[0] == ref[0] and np.array_equal(r[1], ref[1]), bps
 
 
+def test_deterministic_whole_chunk_units_and_autotune_grid():
+    """A dataset of >= 1024 chunks runs whole-chunk work units (three FP32
+    columns: the all-FP32 kernel): its result is bitwise the same for every
+    launch shape the autotuner tries, and the tuner reports its grid."""
+    spec = W.prod3_model()
+    m = api.Model.from_spec(spec)
+    d = api.generate_toys(m, TRUE["prod3_model"], 31, [1100 * 4096 + 77.0], poisson=False, f32=[True] * 3)
+    th = TRUE["prod3_model"] * (1 + 0.01 * np.cos(np.arange(12)))
+    ref = api.nll_grad(m, d, th)
+    grid = api.autotune_scan(m, d, passes=1)
+    assert len(grid) >= 3 and all(t > 0 for _, t in grid)
+    assert {b for b, _ in grid} <= {1, 2, 3, 4, 5, 6, 7, 8, 12, 16}
+    for bps in [b for b, _ in grid] + [0]:
+        m.set_launch(0, bps)
+        r = api.nll_grad(m, d, th)
+        assert r[0] == ref[0] and np.array_equal(r[1], ref[1]), bps
+
+
 def test_domain_errors(oracle_mod):
     # A polynomial that goes negative inside the range: pdf < 0 for some events.
     nodes = [Node("obs", (), 0, 0, 10), Node("param", (), -0.2, -1, 1, True), Node("poly", (0, 1))]
