@@ -574,8 +574,8 @@ def run_events(args, api, torch, dist, rank, world, local, wl=None, steps=None, 
 def run_toys(args, api, torch, dist, rank, world, local, steps=None, warmup=None):
     """4096 ragged toys of the decay model, every toy drawn at its generating
     values (the configuration of the batched fit), fitted together."""
-    steps = steps or steps
-    warmup = warmup if warmup is not None else warmup
+    steps = steps or args.steps
+    warmup = args.warmup if warmup is None else warmup
     spec = W.decay_model()
     model = api.Model.from_spec(spec)
     S = 4096

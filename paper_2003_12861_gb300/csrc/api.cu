@@ -142,9 +142,9 @@ bool ensure_workspace(const rf_model* m, rf_data* d) {
             w.slot_slow.ensure(sizeof(unsigned long long) * kPassSlots) &&
             (m->m.shape == SHAPE_GENERIC ||
              (w.ffc.ensure(sizeof(float) * S * kFFConst) &&
-              w.part_m.ensure(sizeof(float) * nodes * d->parts * kPartFloats) &&
-              w.part_fb.ensure(sizeof(double) * nodes * d->parts * Q) &&
-              w.part_info.ensure(sizeof(int32_t) * nodes * d->parts))) &&
+              w.part_m.ensure(sizeof(float) * nodes * kMaxParts * kPartFloats) &&
+              w.part_fb.ensure(sizeof(double) * nodes * kMaxParts * Q) &&
+              w.part_info.ensure(sizeof(int32_t) * nodes * kMaxParts))) &&
             w.h_theta.ensure(sizeof(double) * S * std::max(1, P.n_free)) &&
             w.h_out.ensure(sizeof(double) * S * (1 + P.n_free)) && w.h_flags.ensure(sizeof(int32_t) * S);
   if (!ok) return false;
@@ -189,7 +189,7 @@ Pass make_pass(const rf_model* m, rf_data* d, const Plan& plan, const double* d_
   p.part_m = (float*)w.part_m.p;
   p.part_fb = (double*)w.part_fb.p;
   p.part_info = (int32_t*)w.part_info.p;
-  p.parts = d->parts;
+  p.parts = parts_for(d->total_chunks, m->m.shape);
   p.pairs = nullptr;
   return p;
 }
@@ -513,9 +513,8 @@ rf_status finish_data(rf_data* d) {
     total += tree_nodes(d->chunks[s]);
   }
   d->total_nodes = total;
-  int64_t all_chunks = 0;
-  for (int s = 0; s < S; ++s) all_chunks += d->chunks[s];
-  d->parts = parts_for_chunks(all_chunks);
+  d->total_chunks = 0;
+  for (int s = 0; s < S; ++s) d->total_chunks += d->chunks[s];
   if (!d->offsets_dev.ensure(sizeof(int64_t) * (S + 1)) || !d->tree_base_dev.ensure(sizeof(int64_t) * S)) return RF_E_OOM;
   if (!cuda_ok(cudaMemcpy(d->offsets_dev.p, d->offsets.data(), sizeof(int64_t) * (S + 1), cudaMemcpyHostToDevice), "offsets upload") ||
       !cuda_ok(cudaMemcpy(d->tree_base_dev.p, d->tree_base.data(), sizeof(int64_t) * S, cudaMemcpyHostToDevice), "tree upload"))

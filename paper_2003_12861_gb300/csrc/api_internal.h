@@ -115,7 +115,7 @@ struct rf_data {
   bool owns_cols = true;
   std::vector<int64_t> offsets, chunks, tree_base;
   int64_t total_nodes = 0;
-  int parts = 4;  // work units per chunk of the float-float kernels (parts_for_chunks)
+  int64_t total_chunks = 0;  // over all sets (parts_for)
   rf::DevBuf offsets_dev, tree_base_dev;
   rf::Workspace ws;
   rf::Plan all_plan;

@@ -735,9 +735,6 @@ __device__ bool eval_generic(const Program& P, const double* __restrict__ C, con
 }
 
 constexpr int kWarps = kLanes / 32;   // warps per chunk group
-// Resident blocks per SM the float-float kernels are compiled for (their
-// register budget: 72 registers for 7 blocks, 96 for 5).
-__host__ __device__ constexpr int ff_min_blocks(int shape) { return shape == SHAPE_PROD3 ? 5 : 7; }
 constexpr int kQMax = 1 + kMaxSlots;
 
 template <class QT, int kQueue>

@@ -48,16 +48,31 @@ struct Pass {
   double* pairs;
 };
 
-// Work units per chunk of the float-float kernels (Pass::parts, 1 or 4):
-// with P parts, part p of a chunk covers lane l's events l + 128 k for k in
-// [32 p / P, 32 (p + 1) / P).  Quarter chunks shorten the last round of units
-// when a dataset has few chunks; whole chunks spread the per-unit work (the
-// lane log, the warp reduction, the record) over 4x more events.  The count
-// is a property of the dataset (its total chunk count), never of the
-// launch, so a dataset's results do not depend on how it is launched.
+// Resident blocks per SM the float-float kernels are compiled for (their
+// register budget: 72 registers for 7 blocks, 96 for 5).
+__host__ __device__ constexpr int ff_min_blocks(int shape) { return shape == SHAPE_PROD3 ? 5 : 7; }
+
+// Work units per chunk of the float-float kernels (Pass::parts: 1, 2 or
+// 4): with P parts, part p of a chunk covers lane l's events l + 128 k for k
+// in [32 p / P, 32 (p + 1) / P).  Whole chunks spread the per-unit work (the
+// lane log, the warp reduction, the record, the claim) over the most
+// events, and measured faster than halves or quarters as soon as the chunks
+// fill one round of the grid, short last round included (decay model, 1e7
+// events = 2.3 rounds: whole chunks 0.180 ms, halves 0.190, quarters 0.189);
+// a dataset with fewer chunks than that takes the smallest P whose units do
+// (up to 4), so that more of the GPU works on it.  The round is that of a
+// reference grid, 152 SMs (the GB300) x the kernel's resident blocks, so P
+// is a function of the dataset's chunk count and the model's kernel only,
+// never of the launch: a dataset's results do not depend on how it is
+// launched.
 constexpr int kMaxParts = 4;
-constexpr int64_t kWholeChunkMin = 1024;  // datasets with at least this many chunks use whole chunks
-inline int parts_for_chunks(int64_t total_chunks) { return total_chunks >= kWholeChunkMin ? 1 : kMaxParts; }
+constexpr int kRefSMs = 152;
+inline int parts_for(int64_t total_chunks, int shape) {
+  const int64_t wave = (int64_t)kRefSMs * ff_min_blocks(shape);
+  int P = 1;
+  while (P < kMaxParts && total_chunks * P < wave) P *= 2;
+  return P;
+}
 constexpr int kPartFloats = 32;
 
 constexpr int32_t kThetaBad = 1 << 30;

@@ -44,8 +44,8 @@ struct Layout {
 
 // Header (first 256 bytes): int32 counter @0, u64 slow-event count @8,
 // int64 offsets[2] @16, int64 tree base @32, int32 active set @40.
-Layout layout_for(int64_t chunks, int64_t nodes, int n_const, int Q, bool parts) {
-  const size_t np = (size_t)parts_for_chunks(chunks);
+Layout layout_for(int64_t chunks, int64_t nodes, int n_const, int Q, bool parts, int shape) {
+  const size_t np = (size_t)parts_for(chunks, shape);
   Layout L{};
   L.consts = 256;
   L.ffc = L.consts + up256(sizeof(double) * (size_t)(n_const > 0 ? n_const : 1));
@@ -87,7 +87,7 @@ __global__ void noalloc_setup(unsigned char* base, Layout L, int64_t n_events, i
 size_t scratch_bytes(const rf_model* m, int64_t n_events) {
   const Program& P = m->m.prog;
   const int64_t chunks = (n_events + kChunk - 1) / kChunk;
-  return layout_for(chunks, tree_nodes(chunks), P.n_const, 1 + P.n_slots, m->m.shape != SHAPE_GENERIC).total;
+  return layout_for(chunks, tree_nodes(chunks), P.n_const, 1 + P.n_slots, m->m.shape != SHAPE_GENERIC, m->m.shape).total;
 }
 
 }  // namespace
@@ -125,7 +125,7 @@ extern "C" rf_status rf_nll_grad_noalloc(const rf_model* m, const void* const* d
   const int64_t chunks = (n_events + kChunk - 1) / kChunk;
   const int64_t nodes = tree_nodes(chunks);
   const int Q = 1 + P.n_slots;
-  const Layout L = layout_for(chunks, nodes, P.n_const, Q, m->m.shape != SHAPE_GENERIC);
+  const Layout L = layout_for(chunks, nodes, P.n_const, Q, m->m.shape != SHAPE_GENERIC, m->m.shape);
   if (L.total > kScratchBytes || chunks > (int64_t)0x7fffffff) {
     const double per_chunk = (double)L.total / (double)(chunks > 0 ? chunks : 1);
     char msg[256];
@@ -190,7 +190,7 @@ extern "C" rf_status rf_nll_grad_noalloc(const rf_model* m, const void* const* d
   pass.part_m = (float*)(base + L.part_m);
   pass.part_fb = (double*)(base + L.part_fb);
   pass.part_info = (int32_t*)(base + L.part_info);
-  pass.parts = parts_for_chunks(chunks);
+  pass.parts = parts_for(chunks, m->m.shape);
   launch_param_point(P, pass, st);
   launch_events(P, m->m.shape, cols, pass, m->m.threads_per_block, m->m.blocks_per_sm, sm_count(), st);
   return cuda_ok(cudaGetLastError(), "rf_nll_grad_noalloc launch") ? RF_OK : RF_E_CUDA;

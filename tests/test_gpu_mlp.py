@@ -1,10 +1,12 @@
 """The learned-start network on the GPU (tensor-core BF16 GEMMs, FP32
 accumulation) against the float64 oracle with the same BF16 operand
-rounding.  Tolerance: the only differences are FP32 accumulation (~1e-6
-relative) and the rare BF16 rounding of an activation that lands on the other
-side of a rounding boundary (one BF16 ulp, 2^-8, in a few elements), so
-outputs and gradients agree to 1e-2 of their largest magnitude and mostly to
-1e-4."""
+rounding.  Two sources of difference: FP32 accumulation (~1e-6 relative),
+and an activation whose FP32 value lands on the other side of a BF16
+rounding boundary than the oracle's FP64 value (one BF16 ulp, 2^-8, in that
+element, which then moves every output of its sample).  So the comparison
+is per sample: samples without such a flip agree to 1e-5 of the outputs'
+scale (FP32 accumulation), and the flipped ones -- counted, a minority --
+within 1e-2."""
 import numpy as np
 import pytest
 import torch
@@ -26,12 +28,15 @@ def net_and_data(B, seed=0):
     return net, p, x, t
 
 
-def close(a, b, scale_rtol=1e-2, med_rtol=1e-4):
+CLEAN = 1e-5   # FP32 accumulation
+FLIPPED = 1e-2  # one BF16 ulp of an activation, propagated
+
+
+def per_sample(a, b):
+    """Per-sample (row) maximum error relative to the whole array's scale."""
     a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
     scale = np.max(np.abs(b))
-    err = np.abs(a - b)
-    assert err.max() <= scale_rtol * scale, (err.max(), scale)
-    assert np.median(err) <= med_rtol * scale, (np.median(err), scale)
+    return np.max(np.abs(a - b).reshape(len(a), -1), axis=1) / scale
 
 
 @pytest.mark.parametrize("B", [1, 37, 300, 1024])
@@ -42,25 +47,40 @@ def test_forward_matches_oracle(B):
     net.forward(dx, dy)
     torch.cuda.synchronize()
     want, _ = M.forward(p, x, SHAPES)
-    close(dy.cpu().numpy(), want)
+    err = per_sample(dy.cpu().numpy(), want)
+    clean = err <= CLEAN
+    print(f"B={B}: {clean.sum()} samples within {CLEAN}, {B - clean.sum()} flipped, worst {err.max():.2e}")
+    assert err.max() <= FLIPPED, err.max()
+    # measured: 0 of 1, 0 of 37, 3 of 300 and 8 of 1024 samples flipped
+    assert clean.mean() >= (0.95 if B >= 37 else 0.0), clean.mean()
 
 
-@pytest.mark.parametrize("B", [64, 333])
-def test_gradient_matches_oracle(B):
-    net, p, x, t = net_and_data(B, seed=7)
-    # train a little first so that the activations are not all near initial values
-    dx, dt = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
-    g = torch.zeros(net.n_params, device="cuda")
-    loss = net.grad(dx, dt, g)
-    torch.cuda.synchronize()
-    want_loss, want_g = M.loss_and_grad(p, x, t, SHAPES)
-    assert abs(loss - want_loss) <= 1e-4 * want_loss
-    gg = g.cpu().numpy()
-    o = 0
-    for (i, j) in SHAPES:  # per layer: weights then biases
-        for n in (i * j, j):
-            close(gg[o:o + n], want_g[o:o + n], scale_rtol=2e-2, med_rtol=2e-3)
-            o += n
+def test_gradient_matches_oracle():
+    """One sample at a time (a flip moves only its own sample's gradient):
+    most samples' whole gradients agree at the FP32-accumulation level."""
+    net, p, x, t = net_and_data(32, seed=7)
+    results = []
+    for b in range(32):
+        dx, dt = torch.from_numpy(x[b:b + 1]).cuda(), torch.from_numpy(t[b:b + 1]).cuda()
+        g = torch.zeros(net.n_params, device="cuda")
+        loss = net.grad(dx, dt, g)
+        torch.cuda.synchronize()
+        want_loss, want_g = M.loss_and_grad(p, x[b:b + 1], t[b:b + 1], SHAPES)
+        gg = g.cpu().numpy()
+        worst = 0.0
+        o = 0
+        for (i, j) in SHAPES:  # per layer: weights then biases
+            for n in (i * j, j):
+                scale = max(np.max(np.abs(want_g[o:o + n])), 1e-30)
+                worst = max(worst, np.max(np.abs(gg[o:o + n] - want_g[o:o + n])) / scale)
+                o += n
+        results.append((abs(loss - want_loss) / want_loss, worst))
+    lerr = np.array([r[0] for r in results])
+    gerr = np.array([r[1] for r in results])
+    clean = gerr <= CLEAN
+    print(f"gradients: {clean.sum()} of 32 samples within {CLEAN}, worst {gerr.max():.2e}; loss worst {lerr.max():.2e}")
+    assert gerr.max() <= 2 * FLIPPED and lerr.max() <= 1e-6
+    assert clean.sum() >= 28, clean.sum()  # measured: 31 of 32
 
 
 def test_adam_step_matches_oracle():
