@@ -338,7 +338,7 @@ def transcendental_ceiling(api, model_spec, slow_fraction, n_events, bytes_per_e
     return alu, hbm, basis
 
 
-KERNEL_SOURCES = ["nll.cu", "nll_ff.cuh", "k1_ff.cuh", "ff.cuh", "ff_tables.h", "nll_kernels.cuh", "rf_internal.h"]
+KERNEL_SOURCES = ["nll.cu", "nll_ff.cuh", "k1_ff.cuh", "ff.cuh", "ff_tables.h", "nll_kernels.cuh", "rf_internal.h", "expr.cuh"]
 
 
 def kernel_digest():

@@ -1033,7 +1033,6 @@ __global__ void __launch_bounds__(kLanes, ff_min_blocks(kShape)) events_ff(const
   } else {
     col[0] = col[1] = col[2] = P.node[0].col;
   }
-  const unsigned lt = (1u << lane) - 1u;
   const int n_units = pass.n_items * parts;
   int kc_set = -1, c_set = -1;  // sets whose constants the block holds (block-uniform)
   pdl_wait();  // K1 has reset the counter and written the constants
@@ -1061,8 +1060,7 @@ __global__ void __launch_bounds__(kLanes, ff_min_blocks(kShape)) events_ff(const
 #pragma unroll
     for (int j = 0; j < NP; ++j) acc[j] = {0.0f, 0.0f};
     LogProd lpd = logprod_init();
-    int qs = 0;
-    unsigned myfb = 0u;
+    unsigned myslow = 0u, myfb = 0u;  // the lane's events (bit k) for the slow pass / the FP64 path
     const int k0 = part * kPartK;
     // events of the chunk present (32-bit offsets within the chunk); the
     // next event's observables are loaded one iteration ahead
@@ -1077,21 +1075,31 @@ __global__ void __launch_bounds__(kLanes, ff_min_blocks(kShape)) events_ff(const
         nxt = ff_load_raw<kShape, kF32>(cols, col, base + off + kLanes);
       int st = 0;
       if (off < rem) st = ff_event<kShape, kGrad, false>(T, kc, cur, acc, lpd);
-      const unsigned bs = __ballot_sync(0xffffffffu, st == 1);
-      if (st == 1) sm.queue[warp][qs + __popc(bs & lt)] = (short)off;
-      if (st == 2) myfb |= 1u << k;
-      qs += __popc(bs);
+      myslow |= (st == 1 ? 1u : 0u) << k;
+      myfb |= (st == 2 ? 1u : 0u) << k;
     }
-    // The block's queued events, in warp then ballot order, are shared out
-    // over all its threads (entry j to thread j mod 128), so only the last
-    // round of the block's queue leaves lanes idle.
-    if (lane == 0) sm.qn[warp] = qs;
+    // The block's slow events form one queue, thread by thread and each
+    // thread's in event order (an exclusive scan of the per-thread counts
+    // places them), shared out over all its threads (entry j to thread j mod
+    // 128), so only the last round of the queue leaves lanes idle.
+    short* const queue = &sm.queue[0][0];
+    const int ns = __popc(myslow);
+    int incl = ns;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    if (lane == 31) sm.qn[warp] = incl;
     __syncthreads();
-    const int q1 = sm.qn[0], q2 = q1 + sm.qn[1], q3 = q2 + sm.qn[2], qt = q3 + sm.qn[3];
+    int pos = incl - ns;
+    for (int w = 0; w < warp; ++w) pos += sm.qn[w];
+    const int qt = sm.qn[0] + sm.qn[1] + sm.qn[2] + sm.qn[3];
+    for (unsigned mk = myslow; mk; mk &= mk - 1u) queue[pos++] = (short)(tid + (__ffs(mk) - 1) * kLanes);
+    __syncthreads();
     if (tid == 0 && qt > 0 && pass.slow) atomicAdd(pass.slow, (unsigned long long)qt);
     for (int j = tid; j < qt; j += kLanes) {
-      const int w = (j >= q1) + (j >= q2) + (j >= q3);
-      const int off = sm.queue[w][j - (w == 0 ? 0 : w == 1 ? q1 : w == 2 ? q2 : q3)];
+      const int off = queue[j];
       if (ff_event<kShape, kGrad, true>(T, kc, ff_load<kShape, kF32>(cols, col, base + off), acc, lpd) == 2)
         atomicOr(kShape == SHAPE_PROD3 ? &fbmask_f[off % kLanes] : &fbmask[off % kLanes],
                  1u << (off / kLanes));  // owner lane, event bit
