@@ -151,6 +151,39 @@ __device__ __forceinline__ void ff_acc_mul(ff& acc, ff a, ff b) {
   acc.hi = s.hi;
 }
 
+// Variants with one operand a plain float (an FP32 observable: its low word
+// is zero, known at compile time).  Each gives the result of the pair
+// variant with {b, 0}, with the product or sum terms of the zero word left
+// out.
+__device__ __forceinline__ float ff_neg(float a) { return -a; }
+__device__ __forceinline__ float ff_hi(float a) { return a; }
+__device__ __forceinline__ float ff_hi(ff a) { return a.hi; }
+__device__ __forceinline__ ff ff_sub(float a, ff b) {
+  ff s = two_sum(a, -b.hi);
+  s.lo = __fsub_rn(s.lo, b.lo);
+  return fast_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ ff ff_mul_u(ff a, float b) {
+  ff p = two_prod(a.hi, b);
+  p.lo = __fmaf_rn(a.lo, b, p.lo);
+  return p;
+}
+__device__ __forceinline__ ff ff_fma(ff a, float b, ff c) {
+  const ff p = two_prod(a.hi, b);
+  const ff s = two_sum(p.hi, c.hi);
+  float lo = __fmaf_rn(a.lo, b, p.lo);
+  lo = __fadd_rn(lo, __fadd_rn(c.lo, s.lo));
+  return fast_two_sum(s.hi, lo);
+}
+__device__ __forceinline__ ff ff_fma(float a, ff b, ff c) { return ff_fma(b, a, c); }
+__device__ __forceinline__ void ff_acc_mul(ff& acc, ff a, float b) {
+  const ff p = two_prod(a.hi, b);
+  const ff s = two_sum(acc.hi, p.hi);
+  const float e = __fmaf_rn(a.lo, b, p.lo);
+  acc.lo = __fadd_rn(acc.lo, __fadd_rn(s.lo, e));
+  acc.hi = s.hi;
+}
+
 // ---------------------------------------------------------------- exp
 // The reduction and reconstruction for an integer kk = k = rint(x 256/ln2)
 // whose 2^(k >> 8) scale is a normal float.

@@ -1074,7 +1074,7 @@ __global__ void __launch_bounds__(kLanes, ff_min_blocks(kShape)) events_ff(const
       if (k + 1 < k0 + kPartK && off + kLanes < rem)
         nxt = ff_load_raw<kShape, kF32>(cols, col, base + off + kLanes);
       int st = 0;
-      if (off < rem) st = ff_event<kShape, kGrad, false>(T, kc, cur, acc, lpd);
+      if (off < rem) st = ff_event<kShape, kGrad, false, kF32>(T, kc, cur, acc, lpd);
       myslow |= (st == 1 ? 1u : 0u) << k;
       myfb |= (st == 2 ? 1u : 0u) << k;
     }
@@ -1100,7 +1100,7 @@ __global__ void __launch_bounds__(kLanes, ff_min_blocks(kShape)) events_ff(const
     if (tid == 0 && qt > 0 && pass.slow) atomicAdd(pass.slow, (unsigned long long)qt);
     for (int j = tid; j < qt; j += kLanes) {
       const int off = queue[j];
-      if (ff_event<kShape, kGrad, true>(T, kc, ff_load<kShape, kF32>(cols, col, base + off), acc, lpd) == 2)
+      if (ff_event<kShape, kGrad, true, kF32>(T, kc, ff_load<kShape, kF32>(cols, col, base + off), acc, lpd) == 2)
         atomicOr(kShape == SHAPE_PROD3 ? &fbmask_f[off % kLanes] : &fbmask[off % kLanes],
                  1u << (off / kLanes));  // owner lane, event bit
     }

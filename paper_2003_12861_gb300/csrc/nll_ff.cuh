@@ -265,8 +265,8 @@ __device__ __forceinline__ ff ff_exp0(const FFTables& T, ff x, bool& ok, bool& d
 // z >= 0: v = exp(-u^2/2) erfcx(z) / (2I), R = 2 / (sqrt(pi) erfcx(z));
 // z < 0:  v = exp(A)/I - exp(-u^2/2) erfcx(|z|) / (2I),
 //         R = 2 q / (sqrt(pi) (2 - q erfcx(|z|))), q = exp(-z^2).
-template <bool kSlow>
-__device__ __forceinline__ ff decay_shape(const FFTables& T, const float* k, ff t, ff* R, ff* uo, bool& ok,
+template <bool kSlow, class OT>
+__device__ __forceinline__ ff decay_shape(const FFTables& T, const float* k, OT t, ff* R, ff* uo, bool& ok,
                                           bool& dropped) {
   const ff logv = ff_fma(ff_neg(t), ldc(k, 2), ldc(k, 0));
   if (!kSlow) {
@@ -356,15 +356,23 @@ __device__ __forceinline__ FFIn<kShape> ff_load(const Columns& cols, const int* 
   return ff_split_in<kShape, kF32>(cols, col, ff_load_raw<kShape, kF32>(cols, col, e));
 }
 
+// An observable as the program uses it: a plain float for an all-FP32
+// dataset (kF32), else the pair.
+template <bool kF32>
+__device__ __forceinline__ auto obs_value(ff x) {
+  if constexpr (kF32) return x.hi;
+  else return x;
+}
+
 // p_i goes into the lane's running product L (its log is taken once per
 // part: sum log p_i = log prod p_i); the moments into acc[1..].
-template <int kShape, bool kGrad, bool kSlow>
+template <int kShape, bool kGrad, bool kSlow, bool kF32 = false>
 __device__ __forceinline__ int ff_event(const FFTables& T, const float* k, const FFIn<kShape>& in, ff* acc,
                                         LogProd& L) {
   bool ok = in.ok, dropped = false;
   if constexpr (kShape == SHAPE_SUM_GAUSSEXP_CHEB2) {
-    const ff t = in.x[0];
-    if (!kSlow && __fmaf_rn(-t.hi, k[13], k[12]) >= kSlowZf) return ok ? 1 : 2;
+    const auto t = obs_value<kF32>(in.x[0]);
+    if (!kSlow && __fmaf_rn(-ff_hi(t), k[13], k[12]) >= kSlowZf) return ok ? 1 : 2;
     ff R, u;
     const ff vs = decay_shape<kSlow>(T, k, t, &R, &u, ok, dropped);
     const ff pb = ff_fma(ff_fma(ldc(k, 10), t, ldc(k, 8)), t, ldc(k, 6));
@@ -389,7 +397,7 @@ __device__ __forceinline__ int ff_event(const FFTables& T, const float* k, const
     }
     return 0;
   } else if constexpr (kShape == SHAPE_SUM_GAUSS_POLY1) {
-    const ff x = in.x[0];
+    const auto x = obs_value<kF32>(in.x[0]);
     const ff u = ff_mul(ff_sub(x, ldc(k, 0)), ldc(k, 2));
     const ff g = ff_exp0(T, ff_fma(ff_scale(u, -0.5f), u, ldc(k, 14)), ok, dropped);
     const ff p = ff_fma(ldc(k, 4), g, ff_fma(ldc(k, 8), x, ldc(k, 6)));
@@ -417,18 +425,18 @@ __device__ __forceinline__ int ff_event(const FFTables& T, const float* k, const
     // decay factor alone.  2 in the fast pass: nothing of the event was
     // summed, the whole event takes the FP64 path; 2 in the slow pass: the
     // decay factor alone takes it.
-    const ff t = in.x[1];
+    const auto t = obs_value<kF32>(in.x[1]);
     const float* kd = k + 16;
     if constexpr (!kSlow) {
-      const ff m = in.x[0];
-      const ff c = in.x[2];
+      const auto m = obs_value<kF32>(in.x[0]);
+      const auto c = obs_value<kF32>(in.x[2]);
       const ff um = ff_mul(ff_sub(m, ldc(k, 0)), ldc(k, 2));
       bool dm = false;
       const ff g = ff_exp0(T, ff_fma(ff_scale(um, -0.5f), um, ldc(k, 14)), ok, dm);
       const ff ym = ff_fma(m, ldc(k, 10), ff_neg(ldc(k, 12)));
       const ff pm = ff_fma(ldc(k, 4), g, ff_fma(ldc(k, 8), ym, ldc(k, 6)));
       const ff pa = ff_fma(ff_fma(ldc(k, 42), c, ldc(k, 40)), c, ldc(k, 38));
-      const bool slow = __fmaf_rn(-t.hi, kd[13], kd[12]) >= kSlowZf;
+      const bool slow = __fmaf_rn(-ff_hi(t), kd[13], kd[12]) >= kSlowZf;
       // the decay's fast formula for every lane, used where not slow
       ff R, u;
       bool okd = true;
