@@ -1078,6 +1078,12 @@ __global__ void __launch_bounds__(kLanes, ff_min_blocks(kShape)) events_ff(const
       myslow |= (st == 1 ? 1u : 0u) << k;
       myfb |= (st == 2 ? 1u : 0u) << k;
     }
+    if constexpr (kShape == SHAPE_PROD3 && kGrad) {
+      // moment 13: the lane's events summed in float-float (those present
+      // in its part, less the ones the FP64 path takes whole)
+      const int nv = min(max((rem - tid + kLanes - 1) / kLanes - k0, 0), kPartK);
+      acc[13] = {(float)(nv - __popc(myfb)), 0.0f};
+    }
     // The block's slow events form one queue, thread by thread and each
     // thread's in event order (an exclusive scan of the per-thread counts
     // places them), shared out over all its threads (entry j to thread j mod

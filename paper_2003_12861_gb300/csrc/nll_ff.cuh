@@ -10,6 +10,7 @@
 // the summed moments to (sum log p, d/dtheta_slot) at the end of each chunk.
 // K and the per-event constants are computed in FP64 once per parameter point.
 //
+// (PROD3's moment 13 is the count of events the pass summed, not a moment.)
 // Shapes (program order = the topological order of rf_model_create):
 //   DECAY     SUM(GAUSSEXP(t; tau,mu,sigma), CHEB2(t; c1,c2); f)      Q = 7
 //   GP1       SUM(GAUSS(x; mu,sigma), POLY1(x; a1); f)                 Q = 5
@@ -209,10 +210,12 @@ static __device__ void prepare_ff_job(const Program& P, int shape, const double*
       case 2: prep_decay_consts(ge, ch, sm, out + 16); break;
       case 3: prep_decay_K(ge, ch, sm, K, nacc, 5, 6); break;
       default:
+        // d log p_c / d a_k = c^k / (I p_c) - dlogI/da_k, and moment 13 is
+        // the count of events (not sum 1/p_c)
         for (int j = 0; j < 3; ++j) put_ff(out + 38 + 2 * j, pa[0] * Sa[j]);
         for (int k = 0; k < 2; ++k) {
-          for (int j = 0; j < 3; ++j) K[(11 + k) * nacc + 13 + j] = -pa[0] * pa[1 + k] * Sa[j];
-          K[(11 + k) * nacc + 13 + 1 + k] += pa[0];
+          K[(11 + k) * nacc + 13] = -pa[1 + k];
+          K[(11 + k) * nacc + 13 + 1 + k] = pa[0];
         }
     }
   }
@@ -468,8 +471,10 @@ __device__ __forceinline__ int ff_event(const FFTables& T, const float* k, const
         ff_acc(acc[8], ipt);
         ff_acc(acc[9], it_);
         ff_acc_mul(acc[10], it_, t);
+        // the angle factor (1 + a1 c + a2 c^2)/I needs only sum c/p_c and
+        // sum c^2/p_c: its sum of 1/p_c times 1/I equals the event count
+        // less the rest, so slot 13 carries the count (set per part)
         const ff iac = ff_mul_u(ipa, c);
-        ff_acc(acc[13], ipa);
         ff_acc(acc[14], iac);
         ff_acc_mul(acc[15], iac, c);
       }
