@@ -259,6 +259,15 @@ typedef struct {
 rf_status rf_fit(const rf_model* m, const rf_data* d, const double* theta0, const rf_fit_opts* opts,
                  double* theta_hat, double* nll_min, double* cov, int32_t* n_evals, int32_t* fit_status);
 
+/* rf_fit for the sets sets[0..n) of d only (distinct indices in
+ * [0, n_sets)), fitted together as one batch: theta0 (HOST n x n_free, or
+ * NULL for the defaults) and the outputs are per listed set, in the list's
+ * order.  The other sets are not evaluated.  For refitting a few toys of a
+ * batch without moving their events. */
+rf_status rf_fit_sets(const rf_model* m, const rf_data* d, const int32_t* sets, int32_t n, const double* theta0,
+                      const rf_fit_opts* opts, double* theta_hat, double* nll_min, double* cov, int32_t* n_evals,
+                      int32_t* fit_status);
+
 /* ------------------------------------------------------------------- toys */
 
 /* Generate n_sets toy datasets on the device (Sec. 1: toy Monte Carlo).

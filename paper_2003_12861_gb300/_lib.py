@@ -63,6 +63,7 @@ SIGNATURES = {
     "rf_autotune": (C.c_int, [_vp, _vp, C.c_int32, _ip, _ip, _dp]),
     "rf_autotune_scan": (C.c_int, [_vp, _vp, C.c_int32, C.c_int32, _ip, _dp, _ip]),
     "rf_fit": (C.c_int, [_vp, _vp, _dp, C.POINTER(rf_fit_opts), _dp, _dp, _dp, _ip, _ip]),
+    "rf_fit_sets": (C.c_int, [_vp, _vp, _ip, C.c_int32, _dp, C.POINTER(rf_fit_opts), _dp, _dp, _dp, _ip, _ip]),
     "rf_generate_toys": (C.c_int, [_vp, _dp, C.c_int32, C.c_uint64, C.c_int32, _dp, C.c_int32, _ip, C.POINTER(_vp)]),
     "rf_hist64": (C.c_int, [_vp, _vp, C.c_int32, _vp, _vp]),
     "rf_data_refill": (C.c_int, [_vp, C.POINTER(_vp), _vp]),

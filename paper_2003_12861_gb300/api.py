@@ -330,6 +330,29 @@ def fit(model: Model, data: Data, theta0=None, tol_edm: float = 1e-7, max_evals:
                 status=fs)
 
 
+def fit_sets(model: Model, data: Data, sets, theta0=None, tol_edm: float = 1e-7, max_evals: int = 1000,
+             want_cov=False):
+    """rf_fit_sets: fit only the listed sets of a batch (results in the
+    list's order), the events staying where they are."""
+    idx = np.ascontiguousarray(sets, dtype=np.int32)
+    n, P = len(idx), model.n_free
+    th0 = None if theta0 is None else np.ascontiguousarray(theta0, dtype=np.float64).reshape(-1)
+    if th0 is not None and th0.size != n * P:
+        raise ValueError("theta0 must hold len(sets) x n_free values")
+    opts = L.rf_fit_opts(tol_edm, max_evals, 1 if want_cov else 0, 0, 0)
+    th = np.zeros(max(1, n * P))
+    nl = np.zeros(max(1, n))
+    cov = np.zeros(max(1, n * P * P)) if want_cov else None
+    ne = np.zeros(max(1, n), dtype=np.int32)
+    fs = np.zeros(max(1, n), dtype=np.int32)
+    ip = C.POINTER(C.c_int32)
+    L.check(L.load().rf_fit_sets(model._h, data._h, idx.ctypes.data_as(ip), n, _dp(th0) if th0 is not None else None,
+                                 C.byref(opts), _dp(th), _dp(nl), _dp(cov) if want_cov else None,
+                                 ne.ctypes.data_as(ip), fs.ctypes.data_as(ip)))
+    return dict(theta=th[: n * P].reshape(n, P), nll=nl[:n],
+                cov=None if cov is None else cov[: n * P * P].reshape(n, P, P), n_evals=ne[:n], status=fs[:n])
+
+
 def generate_toys(model: Model, theta, seed: int, mean_n, poisson: bool = True, f32: Sequence[bool] | None = None):
     mean_n = _f64(np.atleast_1d(mean_n))
     S = len(mean_n)

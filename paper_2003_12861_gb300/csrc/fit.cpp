@@ -768,3 +768,80 @@ extern "C" rf_status rf_fit(const rf_model* m, const rf_data* d, const double* t
                    split.split > 0 ? &split : nullptr,
                    theta_hat, nll_min, want_cov ? cov : nullptr, n_evals, fit_status);
 }
+
+extern "C" rf_status rf_fit_sets(const rf_model* m, const rf_data* d, const int32_t* sets, int32_t n,
+                                 const double* theta0, const rf_fit_opts* opts, double* theta_hat, double* nll_min,
+                                 double* cov, int32_t* n_evals, int32_t* fit_status) {
+  if (!m || !d || n < 0 || (n > 0 && (!sets || !theta_hat || !nll_min || !n_evals || !fit_status))) {
+    set_error("rf_fit_sets: bad argument (NULL)");
+    return RF_E_INVALID;
+  }
+  if (d->n_obs != m->m.prog.n_obs) {
+    set_error("rf_fit_sets: data and model have different observable counts");
+    return RF_E_INVALID;
+  }
+  const int P = m->m.prog.n_free, S = d->n_sets;
+  std::vector<char> seen(S, 0);
+  for (int i = 0; i < n; ++i) {
+    if (sets[i] < 0 || sets[i] >= S || seen[sets[i]]) {
+      set_error("rf_fit_sets: set indices must be distinct and in [0, n_sets)");
+      return RF_E_INVALID;
+    }
+    seen[sets[i]] = 1;
+  }
+  if (n == 0) return RF_OK;
+  if (P == 0) {
+    set_error("rf_fit_sets: the model has no free parameter");
+    return RF_E_INVALID;
+  }
+  const double tol = (opts && opts->tol_edm > 0.0) ? opts->tol_edm : 1e-7;
+  const int max_evals = (opts && opts->max_evals > 0) ? opts->max_evals : 1000;
+  const bool want_cov = opts && opts->want_cov && cov;
+  rf_data* dd = const_cast<rf_data*>(d);
+  if (!ensure_workspace(m, dd)) return RF_E_OOM;
+  // Problem i of the batch is set srt[i], the listed sets in increasing
+  // order (the evaluator's plans take active sets in increasing order);
+  // pos[i] is its place in the caller's list.
+  std::vector<int32_t> pos(n), srt(n);
+  for (int i = 0; i < n; ++i) pos[i] = i;
+  std::sort(pos.begin(), pos.end(), [&](int a, int b) { return sets[a] < sets[b]; });
+  for (int i = 0; i < n; ++i) srt[i] = sets[pos[i]];
+  std::vector<double> start((size_t)n * P);
+  for (int i = 0; i < n; ++i)
+    for (int k = 0; k < P; ++k)
+      start[(size_t)i * P + k] = theta0 ? theta0[(size_t)pos[i] * P + k] : m->m.theta_default[k];
+  Evaluator ev(m, dd, !(opts && opts->no_graph == 1));
+  std::vector<double> th_s((size_t)S * P), nll_s(S), grad_s((size_t)S * P);
+  std::vector<int32_t> act_s;
+  std::vector<double> th_o((size_t)n * P), nll_o(n), cov_o(want_cov ? (size_t)n * P * P : 0);
+  std::vector<int32_t> ne_o(n), st_o(n);
+  const rf_status r = fit_batch(
+      n, P, m->m.lo.data(), m->m.hi.data(), start.data(), tol, max_evals, want_cov,
+      [&](const std::vector<int32_t>& active, std::vector<double>& th, std::vector<double>& nll,
+          std::vector<double>& grad) {
+        act_s.resize(active.size());
+        for (size_t j = 0; j < active.size(); ++j) {
+          const int i = active[j], s = srt[i];
+          act_s[j] = s;
+          for (int k = 0; k < P; ++k) th_s[(size_t)s * P + k] = th[(size_t)i * P + k];
+        }
+        const rf_status st = ev.run(act_s, th_s, nll_s, grad_s);
+        for (size_t j = 0; j < active.size(); ++j) {
+          const int i = active[j], s = srt[i];
+          nll[i] = nll_s[s];
+          for (int k = 0; k < P; ++k) grad[(size_t)i * P + k] = grad_s[(size_t)s * P + k];
+        }
+        return st;
+      },
+      nullptr, th_o.data(), nll_o.data(), want_cov ? cov_o.data() : nullptr, ne_o.data(), st_o.data());
+  for (int i = 0; i < n; ++i) {
+    const int o = pos[i];
+    for (int k = 0; k < P; ++k) theta_hat[(size_t)o * P + k] = th_o[(size_t)i * P + k];
+    nll_min[o] = nll_o[i];
+    n_evals[o] = ne_o[i];
+    fit_status[o] = st_o[i];
+    if (want_cov)
+      for (int k = 0; k < P * P; ++k) cov[(size_t)o * P * P + k] = cov_o[(size_t)i * P * P + k];
+  }
+  return r;
+}

@@ -137,3 +137,29 @@ def test_pipelined_halves_match_sequential_passes():
     assert (a["status"] == L.RF_OK).mean() > 0.9
     for k in ("theta", "nll", "n_evals", "status"):
         assert np.array_equal(a[k], b[k]), k
+
+
+def test_fit_sets_equals_the_batch_fit_of_those_sets():
+    """rf_fit_sets fits only the listed sets of a batch; each set's fit
+    depends on its own events and start alone, so the results equal, bit for
+    bit, the full batch fit's for those sets (the pipelined and direct
+    batch paths give the same trial points, see the test above)."""
+    spec = W.decay_model()
+    m = api.Model.from_spec(spec)
+    S = 64
+    mean = W.toy_mean_sizes(S, 21, 1e3, 2e4)
+    d = api.generate_toys(m, W.toy_thetas(S, 21), W.SEED_BASE + 21, mean, poisson=True)
+    full = api.fit(m, d, tol_edm=1e-9, want_cov=False, graph=False)
+    sets = [40, 3, 17, 41, 63]
+    sub = api.fit_sets(m, d, sets, tol_edm=1e-9)
+    for j, s in enumerate(sets):
+        assert np.array_equal(sub["theta"][j], full["theta"][s]), s
+        assert sub["nll"][j] == full["nll"][s] and sub["n_evals"][j] == full["n_evals"][s], s
+    # starts per listed set; bad lists are rejected
+    sub2 = api.fit_sets(m, d, [5], theta0=full["theta"][5][None, :], tol_edm=1e-9)
+    assert abs(sub2["nll"][0] - full["nll"][5]) <= 1e-6
+    import pytest as _p
+    with _p.raises(L.RFError):
+        api.fit_sets(m, d, [3, 3])
+    with _p.raises(L.RFError):
+        api.fit_sets(m, d, [S])
