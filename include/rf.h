@@ -243,15 +243,23 @@ typedef struct {
   int32_t max_evals;    /* per set (default 1000)                                 */
   int32_t want_cov;     /* 1: covariance from the Hessian at the minimum          */
   int32_t no_graph;     /* 1: launch each evaluation directly instead of replaying
-                           the captured CUDA graph of the evaluation step        */
-  int32_t reserved;
+                           the captured CUDA graph of the evaluation step; every
+                           quasi-Newton step then runs on the host               */
+  int32_t host_steps;   /* 1: every quasi-Newton step on the host.  0 (default):
+                           in a fit of two or more sets, once fewer than 2^23
+                           of their events are still being fitted, the rounds
+                           run on the device, the step included, 8 per graph
+                           launch; the trial points, and so the results, are
+                           bitwise those of host steps                           */
 } rf_fit_opts;
 
 /* Maximum-likelihood fit of every set (Sec. 1: fits).  Quasi-Newton (BFGS)
- * on the host over internal coordinates (bounded parameters through
+ * over internal coordinates (bounded parameters through
  * theta = lo + (hi-lo)(sin phi + 1)/2), strong-Wolfe line search; every
  * evaluation of all still-active sets is one device pass (n_sets > 1: the
- * batched toy fit).  theta0: HOST n_sets x n_free or NULL (the PARAM
+ * batched toy fit).  The steps run on the host while many events are being
+ * fitted, then on the device (see rf_fit_opts.host_steps), with the same
+ * results.  theta0: HOST n_sets x n_free or NULL (the PARAM
  * defaults).  Outputs (HOST): theta_hat (n_sets x n_free), nll_min (n_sets),
  * cov (n_sets x n_free^2, or NULL), n_evals (n_sets), fit_status (n_sets:
  * rf_status per set).  Returns RF_OK when the call ran, even if some sets did

@@ -35,7 +35,7 @@ class rf_expr(C.Structure):
 
 class rf_fit_opts(C.Structure):
     _fields_ = [("tol_edm", C.c_double), ("max_evals", C.c_int32), ("want_cov", C.c_int32),
-                ("no_graph", C.c_int32), ("reserved", C.c_int32)]
+                ("no_graph", C.c_int32), ("host_steps", C.c_int32)]
 
 
 # Every exported symbol of include/rf.h with (restype, argtypes).

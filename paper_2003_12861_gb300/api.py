@@ -314,10 +314,13 @@ def nll_chunks(model: Model, data: Data, theta, set_index: int = 0, max_chunks: 
 
 
 def fit(model: Model, data: Data, theta0=None, tol_edm: float = 1e-7, max_evals: int = 1000, want_cov=True,
-        graph: bool = True):
+        graph: bool = True, device_steps: bool = True):
+    """rf_fit.  graph=False launches every evaluation directly (and steps on
+    the host); device_steps=False keeps every quasi-Newton step on the host
+    (the results are bitwise the same either way)."""
     S, P = data.n_sets, model.n_free
     th0 = None if theta0 is None else _theta(model, data, theta0)
-    opts = L.rf_fit_opts(tol_edm, max_evals, 1 if want_cov else 0, 0 if graph else 1, 0)
+    opts = L.rf_fit_opts(tol_edm, max_evals, 1 if want_cov else 0, 0 if graph else 1, 0 if device_steps else 1)
     th = np.zeros(S * P)
     nl = np.zeros(S)
     cov = np.zeros(S * P * P) if want_cov else None
@@ -331,7 +334,7 @@ def fit(model: Model, data: Data, theta0=None, tol_edm: float = 1e-7, max_evals:
 
 
 def fit_sets(model: Model, data: Data, sets, theta0=None, tol_edm: float = 1e-7, max_evals: int = 1000,
-             want_cov=False):
+             want_cov=False, device_steps: bool = True):
     """rf_fit_sets: fit only the listed sets of a batch (results in the
     list's order), the events staying where they are."""
     idx = np.ascontiguousarray(sets, dtype=np.int32)
@@ -339,7 +342,7 @@ def fit_sets(model: Model, data: Data, sets, theta0=None, tol_edm: float = 1e-7,
     th0 = None if theta0 is None else np.ascontiguousarray(theta0, dtype=np.float64).reshape(-1)
     if th0 is not None and th0.size != n * P:
         raise ValueError("theta0 must hold len(sets) x n_free values")
-    opts = L.rf_fit_opts(tol_edm, max_evals, 1 if want_cov else 0, 0, 0)
+    opts = L.rf_fit_opts(tol_edm, max_evals, 1 if want_cov else 0, 0, 0 if device_steps else 1)
     th = np.zeros(max(1, n * P))
     nl = np.zeros(max(1, n))
     cov = np.zeros(max(1, n * P * P)) if want_cov else None

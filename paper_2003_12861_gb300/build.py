@@ -20,7 +20,13 @@ LIB = os.path.join(HERE, "librfgpu.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
+# Host code is compiled without floating-point contraction (the same results
+# on x86-64 and aarch64 hosts); the device step of the fits (fit_dev.cu)
+# also without FMA contraction on the device, so that it rounds every
+# operation of the shared quasi-Newton code (fit_step.h) as the host does.
+COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
+          "-I", INCLUDE, "-I", CSRC]
+PER_FILE = {"fit_dev.cu": ["--fmad=false"]}
 
 
 def nvcc() -> str:
@@ -39,7 +45,7 @@ def _digest() -> str:
             h.update(f.encode() + fh.read())
     with open(os.path.join(INCLUDE, "rf.h"), "rb") as fh:
         h.update(fh.read())
-    h.update(" ".join(ARCH + COMMON).encode())
+    h.update(" ".join(ARCH + COMMON + [f"{k}:{' '.join(v)}" for k, v in sorted(PER_FILE.items())]).encode())
     return h.hexdigest()
 
 
@@ -53,7 +59,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     def compile_one(src):
         obj = os.path.join(BUILD, src + ".o")
-        cmd = [nvcc()] + ARCH + COMMON + ["-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [nvcc()] + ARCH + COMMON + PER_FILE.get(src, []) + ["-c", os.path.join(CSRC, src), "-o", obj]
         if src.endswith(".cu"):
             cmd += ["-Xptxas", "-warn-spills"]
         r = subprocess.run(cmd, capture_output=True, text=True)

@@ -204,8 +204,9 @@ Columns make_columns(const rf_data* d) {
 }
 
 bool launch_pass(const rf_model* m, rf_data* d, const Plan& plan, const double* d_theta, double* d_out,
-                 int32_t* d_flags, bool grad, cudaStream_t st, int slot) {
+                 int32_t* d_flags, bool grad, cudaStream_t st, int slot, const int32_t* dyn) {
   Pass pass = make_pass(m, d, plan, d_theta, d_out, d_flags, grad);
+  pass.dyn = dyn;
   if (slot >= 0 && slot < kPassSlots) {
     pass.counter = (int32_t*)d->ws.slot_counter.p + slot;
     pass.slow = (unsigned long long*)d->ws.slot_slow.p + slot;

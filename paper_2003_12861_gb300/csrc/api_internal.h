@@ -91,9 +91,43 @@ struct SplitEval {
 // Below this many active events a pass is short enough that the launch
 // latency of two half passes costs more than the host work they hide.
 constexpr int64_t kPipelineMinEvents = int64_t(1) << 21;
+// Device-resident rounds for the end of a fit (fit.cpp): the evaluator of
+// the fit's dataset and, for a fit of some sets only, problem -> set.
+struct DeviceSteps;
 rf_status fit_batch(int S, int P, const double* lo, const double* hi, const double* start, double tol, int max_evals,
                     bool want_cov, const BatchEval& eval, const SplitEval* split, double* theta_hat,
-                    double* nll_min, double* cov, int32_t* n_evals, int32_t* fit_status);
+                    double* nll_min, double* cov, int32_t* n_evals, int32_t* fit_status,
+                    DeviceSteps* dev = nullptr);
+
+// One quasi-Newton step per listed set on the device (fit_dev.cu), a warp
+// per set: set i (record i of `state`, of qn::tail_record_words(P) doubles;
+// dataset set set_of[i], with chunks[i] chunks) takes the pass's result
+// out[set] (nll, gradient in theta), advances its state machine and, unless
+// done, writes its next trial point to theta[set]; phase[i] gets its phase.
+// The last block to finish then compacts the plan of the next pass: the
+// sets still going (increasing) into plan_sets, their (set, chunk) items
+// into plan_items (item_off: n ints of scratch), the counts into dyn =
+// {sets, items}.  Skipped when dyn reads no active set.  ticket: a counter
+// at zero, left at zero.
+struct FitStepArgs {
+  double* state;
+  const int32_t* set_of;
+  const int32_t* chunks;
+  int32_t n, P;
+  const double* out;
+  double* theta;
+  const double *lo, *hi;
+  const char* bounded;
+  double tol;
+  int32_t max_evals;
+  int32_t* phase;
+  int32_t* plan_sets;
+  int2* plan_items;
+  int32_t* item_off;  // n: scratch of the compaction
+  int32_t* dyn;
+  int32_t* ticket;
+};
+void launch_fit_step(const FitStepArgs& a, cudaStream_t st);
 int sm_count();
 // Counts n kernel launches on st for rf_launch_count (not while st is being
 // captured into a graph).
@@ -130,8 +164,11 @@ bool ensure_workspace(const rf_model* m, rf_data* d);
 // kPassSlots) gives the pass its own work and slow-event counters, for
 // passes over disjoint sets that run at the same time on different streams.
 constexpr int kPassSlots = 4;
+// dyn: null, or device counts {active sets, work items} that replace the
+// plan's (whose sets and items buffers then hold the device-compacted plan
+// of a device-resident fit); no active set skips the pass.
 bool launch_pass(const rf_model* m, rf_data* d, const Plan& plan, const double* d_theta, double* d_out,
-                 int32_t* d_flags, bool grad, cudaStream_t st, int slot = -1);
+                 int32_t* d_flags, bool grad, cudaStream_t st, int slot = -1, const int32_t* dyn = nullptr);
 rf_status eval_host(const rf_model* m, rf_data* d, const Plan& plan, const double* theta, double* nll,
                     double* grad, cudaStream_t st);
 }  // namespace rf

@@ -1,19 +1,19 @@
 // Maximum-likelihood fits (paper Sec. 1: "compute likelihoods and perform
 // fits to data"; Sec. 3: fits converge faster when the likelihood is faster).
 //
-// The paper does not describe its minimiser.  This is BFGS (Nocedal & Wright,
-// Numerical Optimization, 2nd ed., Alg. 6.1) with the strong-Wolfe line search
-// of their Alg. 3.5 / 3.6 (cubic interpolation in the zoom, eq. 3.59), over
-// internal coordinates: a bounded parameter is theta = lo + (hi-lo)(sin phi +
-// 1)/2 (the transform MINUIT documents), an unbounded one is used as is.  A fit
-// stops when EDM = g^T H g / 2 < tol_edm.  The covariance is the inverse of the
-// NLL's Hessian in theta, by central differences of the analytic gradient
-// (an NLL has "up" = 1/2, so cov = Hessian^-1).
+// The paper does not describe its minimiser.  Each set is fitted by BFGS
+// with a strong-Wolfe line search over internal coordinates (the state
+// machine in fit_step.h, shared with the device step); a fit stops when
+// EDM = g^T H g / 2 < tol_edm.  The covariance is the inverse of the NLL's
+// Hessian in theta, by central differences of the analytic gradient (an NLL
+// has "up" = 1/2, so cov = Hessian^-1).
 //
 // Every set of a dataset is fitted by its own state machine; each round asks
 // every active set for one trial point and evaluates all of them in a single
 // device pass (the batched toy fit), so a round costs one pass whatever the
-// number of sets.
+// number of sets.  Once few events remain active, the rounds run on the
+// device: the pass and every set's step (fit_step_kernel) are replayed as one
+// CUDA graph of several rounds, without a host round trip between them.
 #include <algorithm>
 #include <atomic>
 #include <cmath>
@@ -26,29 +26,27 @@
 #include <vector>
 
 #include "api_internal.h"
+#include "fit_step.h"
 
 namespace rf {
 
 namespace {
 
-constexpr double kC1 = 1e-4, kC2 = 0.9;
-// Near a minimum the decrease a step can make falls below the precision of
-// the NLL itself (float-float event sums: ~1e-14 of sum |log p|), and the
-// sufficient-decrease test turns into noise.  A step is then also accepted
-// under the approximate Wolfe conditions of Hager & Zhang (SIAM J. Optim.
-// 16, 2005): the curvature condition on the directional derivative, and a
-// value no more than kEpsF |f| above the start.
-constexpr double kEpsF = 1e-12;
-constexpr int kMaxLineTrials = 25;
 const double kInf = std::numeric_limits<double>::infinity();
+// Rounds per graph launch of the device-resident rounds: a host round trip
+// per kDeviceRounds rounds, and at most kDeviceRounds - 1 skipped rounds
+// (a launch and a flag read each) after the last set is done.
+constexpr int kDeviceRounds = 8;
+// A batched fit hands its rounds to the device once fewer than this many
+// events are still being fitted (the pipelined halves stop there).
+constexpr int64_t kDeviceRoundEvents = int64_t(1) << 23;
 
 struct Coords {
   int P;
   std::vector<double> lo, hi;
   std::vector<char> bounded;
   void to_theta(const double* x, double* th) const {
-    for (int k = 0; k < P; ++k)
-      th[k] = bounded[k] ? lo[k] + (hi[k] - lo[k]) * (std::sin(x[k]) + 1.0) * 0.5 : x[k];
+    qn::to_theta_jac(P, lo.data(), hi.data(), bounded.data(), x, th, nullptr);
   }
   void to_internal(const double* th, double* x) const {
     for (int k = 0; k < P; ++k) {
@@ -61,20 +59,15 @@ struct Coords {
     }
   }
   // d theta / d x
-  double jac(int k, double xk) const { return bounded[k] ? (hi[k] - lo[k]) * 0.5 * std::cos(xk) : 1.0; }
-  // theta and d theta / d x at x, one sine and cosine per bounded parameter
+  double jac(int k, double xk) const {
+    if (!bounded[k]) return 1.0;
+    double sn, cs;
+    qn::sin_cos(xk, &sn, &cs);
+    return (hi[k] - lo[k]) * 0.5 * cs;
+  }
+  // theta and d theta / d x at x
   void to_theta_jac(const double* x, double* th, double* jc) const {
-    for (int k = 0; k < P; ++k) {
-      if (!bounded[k]) {
-        th[k] = x[k];
-        jc[k] = 1.0;
-        continue;
-      }
-      double sn, cs;
-      sincos(x[k], &sn, &cs);
-      th[k] = lo[k] + (hi[k] - lo[k]) * (sn + 1.0) * 0.5;
-      jc[k] = (hi[k] - lo[k]) * 0.5 * cs;
-    }
+    qn::to_theta_jac(P, lo.data(), hi.data(), bounded.data(), x, th, jc);
   }
 };
 
@@ -168,218 +161,26 @@ double dot(const double* a, const double* b, int n) {
   return s;
 }
 
-// Minimiser of the cubic through (a, fa, da), (b, fb, db) (N&W eq. 3.59),
-// kept inside the middle 80 % of [a, b]; bisection when the data are unusable.
-double cubic_step(double a, double fa, double da, double b, double fb, double db) {
-  const double lo = std::min(a, b), hi = std::max(a, b), w = hi - lo;
-  const double mid = 0.5 * (a + b);
-  if (!std::isfinite(fa) || !std::isfinite(fb) || !std::isfinite(da) || !std::isfinite(db)) return mid;
-  const double d1 = da + db - 3.0 * (fa - fb) / (a - b);
-  const double disc = d1 * d1 - da * db;
-  if (disc < 0.0) return mid;
-  const double d2 = std::copysign(std::sqrt(disc), b - a);
-  const double den = db - da + 2.0 * d2;
-  if (den == 0.0) return mid;
-  double t = b - (b - a) * (db + d2 - d1) / den;
-  if (!std::isfinite(t)) return mid;
-  return std::min(hi - 0.1 * w, std::max(lo + 0.1 * w, t));
-}
-
-enum Phase { INIT, BRACKET, ZOOM, DONE };
-
+// One set's fit: the shared state machine and its vectors.
 struct SetFit {
   int P = 0;
-  Phase phase = INIT;
-  int evals = 0, status = RF_E_NOT_CONVERGED;
-  bool first_step = true, reset_once = false;
-  std::vector<double> x, g, H, p;  // accepted point, its gradient, inverse Hessian, direction
-  double f = kInf, d0 = 0.0;       // f(x), g.p
-  // line search
-  double a_prev = 0.0, f_prev = 0.0, d_prev = 0.0, a_cur = 0.0;
-  double a_lo = 0.0, f_lo = 0.0, d_lo = 0.0, a_hi = 0.0, f_hi = 0.0, d_hi = 0.0;
-  std::vector<double> g_lo;
-  int trials = 0;
-  std::vector<double> trial;  // point to evaluate next (internal)
-  std::vector<double> w_s, w_y, w_hy, w_ga;  // scratch of the update and the round (P each)
-
-  void set_trial(double a) {
-    a_cur = a;
-    for (int k = 0; k < P; ++k) trial[k] = x[k] + a * p[k];
+  qn::State c = qn::initial_state();
+  std::vector<double> x, g, H, p, g_lo, trial, w_s, w_y, w_hy, w_r, w_ga;
+  void init(int n) {
+    P = n;
+    for (std::vector<double>* v : {&x, &g, &p, &g_lo, &trial, &w_s, &w_y, &w_hy, &w_r, &w_ga}) v->assign(n, 0.0);
+    H.assign((size_t)n * n, 0.0);
+    for (int k = 0; k < n; ++k) H[(size_t)k * n + k] = 1.0;
+    c = qn::initial_state();
   }
-
-  // New search direction from H; resets H when it is not a descent direction.
-  void new_direction() {
-    for (int i = 0; i < P; ++i) {
-      double s = 0.0;
-      for (int j = 0; j < P; ++j) s -= H[i * P + j] * g[j];
-      p[i] = s;
-    }
-    d0 = dot(g.data(), p.data(), P);
-    if (!(d0 < 0.0)) {
-      std::fill(H.begin(), H.end(), 0.0);
-      for (int k = 0; k < P; ++k) {
-        H[k * P + k] = 1.0;
-        p[k] = -g[k];
-      }
-      first_step = true;
-      d0 = dot(g.data(), p.data(), P);
-    }
-    double a1 = 1.0;
-    if (first_step) {  // keep the first step of a fresh H within 0.2 (internal units)
-      double pm = 0.0;
-      for (int k = 0; k < P; ++k) pm = std::max(pm, std::fabs(p[k]));
-      if (pm > 0.0) a1 = std::min(1.0, 0.2 / pm);
-    }
-    a_prev = 0.0;
-    f_prev = f;
-    d_prev = d0;
-    trials = 0;
-    phase = BRACKET;
-    set_trial(a1);
+  qn::Vecs vecs() {
+    return {x.data(), g.data(), H.data(), p.data(), g_lo.data(), trial.data(),
+            w_s.data(), w_y.data(), w_hy.data(), w_r.data()};
   }
-
-  double edm() const {
-    double e = 0.0;
-    for (int i = 0; i < P; ++i)
-      for (int j = 0; j < P; ++j) e += 0.5 * g[i] * H[i * P + j] * g[j];
-    return e;
-  }
-
-  // Accept the step to alpha with value fa and gradient ga.
-  void accept(double a, double fa, const double* ga, double tol, int max_evals) {
-    double* s = w_s.data();
-    double* y = w_y.data();
-    for (int k = 0; k < P; ++k) {
-      s[k] = a * p[k];
-      y[k] = ga[k] - g[k];
-    }
-    const double sy = dot(s, y, P);
-    if (first_step && sy > 0.0) {  // N&W eq. 6.20
-      const double sc = sy / dot(y, y, P);
-      for (double& h : H) h *= sc;
-    }
-    first_step = false;
-    if (sy > 1e-300) {
-      const double rho = 1.0 / sy;
-      double* Hy = w_hy.data();
-      std::fill(w_hy.begin(), w_hy.end(), 0.0);
-      for (int i = 0; i < P; ++i)
-        for (int j = 0; j < P; ++j) Hy[i] += H[i * P + j] * y[j];
-      const double yHy = dot(y, Hy, P);
-      for (int i = 0; i < P; ++i)
-        for (int j = 0; j < P; ++j)
-          H[i * P + j] += -rho * (Hy[i] * s[j] + s[i] * Hy[j]) + (rho * rho * yHy + rho) * s[i] * s[j];
-    }
-    for (int k = 0; k < P; ++k) x[k] += s[k];
-    f = fa;
-    std::copy(ga, ga + P, g.begin());
-    if (edm() < tol) {
-      status = RF_OK;
-      phase = DONE;
-      return;
-    }
-    if (evals >= max_evals) {
-      phase = DONE;
-      return;
-    }
-    new_direction();
-  }
-
-  void line_failed(double tol, int max_evals) {
-    if (!reset_once && evals < max_evals) {  // one restart from steepest descent
-      reset_once = true;
-      std::fill(H.begin(), H.end(), 0.0);
-      for (int k = 0; k < P; ++k) H[k * P + k] = 1.0;
-      first_step = true;
-      new_direction();
-      return;
-    }
-    (void)tol;
-    phase = DONE;
-  }
-
-  // Deliver f, gradient (internal) at the last trial point.
+  bool done() const { return c.phase == qn::DONE; }
+  // Deliver f and the gradient (internal) at the last trial point.
   void deliver(double fa, const double* ga, double tol, int max_evals) {
-    ++evals;
-    if (phase == INIT) {
-      x = trial;
-      if (!std::isfinite(fa)) {
-        status = RF_E_DOMAIN;
-        phase = DONE;
-        return;
-      }
-      f = fa;
-      std::copy(ga, ga + P, g.begin());
-      if (edm_identity_small(tol)) return;
-      new_direction();
-      return;
-    }
-    const double a = a_cur;
-    const double da = std::isfinite(fa) ? dot(ga, p.data(), P) : std::numeric_limits<double>::quiet_NaN();
-    ++trials;
-    const bool too_many = trials >= kMaxLineTrials || evals >= max_evals;
-    if (approx_wolfe(fa, da)) {
-      accept(a, fa, ga, tol, max_evals);
-      return;
-    }
-    if (phase == BRACKET) {
-      if (!(fa <= f + kC1 * a * d0) || (trials > 1 && fa >= f_prev)) {
-        a_lo = a_prev; f_lo = f_prev; d_lo = d_prev;
-        if (a_prev == 0.0) g_lo = g;
-        a_hi = a; f_hi = fa; d_hi = da;
-        phase = ZOOM;
-      } else if (std::fabs(da) <= -kC2 * d0) {
-        accept(a, fa, ga, tol, max_evals);
-        return;
-      } else if (da >= 0.0) {
-        a_lo = a; f_lo = fa; d_lo = da; std::copy(ga, ga + P, g_lo.begin());
-        a_hi = a_prev; f_hi = f_prev; d_hi = d_prev;
-        phase = ZOOM;
-      } else {
-        a_prev = a; f_prev = fa; d_prev = da; std::copy(ga, ga + P, g_lo.begin());
-        if (too_many) {
-          accept(a, fa, ga, tol, max_evals);  // sufficient decrease holds here
-          return;
-        }
-        set_trial(2.0 * a);  // expand the bracket
-        return;
-      }
-    } else {  // ZOOM
-      if (!(fa <= f + kC1 * a * d0) || fa >= f_lo) {
-        a_hi = a; f_hi = fa; d_hi = da;
-      } else {
-        if (std::fabs(da) <= -kC2 * d0) {
-          accept(a, fa, ga, tol, max_evals);
-          return;
-        }
-        if (da * (a_hi - a_lo) >= 0.0) {
-          a_hi = a_lo; f_hi = f_lo; d_hi = d_lo;
-        }
-        a_lo = a; f_lo = fa; d_lo = da; std::copy(ga, ga + P, g_lo.begin());
-      }
-    }
-    if (too_many) {
-      if (a_lo > 0.0) accept(a_lo, f_lo, g_lo.data(), tol, max_evals);
-      else line_failed(tol, max_evals);
-      return;
-    }
-    set_trial(std::isfinite(f_hi) ? cubic_step(a_lo, f_lo, d_lo, a_hi, f_hi, d_hi) : 0.5 * (a_lo + a_hi));
-  }
-
-  // Hager-Zhang's approximate Wolfe conditions at a trial point (d0 < 0).
-  bool approx_wolfe(double fa, double da) const {
-    return std::isfinite(fa) && std::isfinite(da) && fa <= f + kEpsF * std::fabs(f) && da >= kC2 * d0 &&
-           da <= (2.0 * kC1 - 1.0) * d0;
-  }
-
-  bool edm_identity_small(double tol) {
-    // With H = I the EDM is |g|^2/2: a start at the minimum is already done.
-    if (0.5 * dot(g.data(), g.data(), P) < tol * 1e-6) {
-      status = RF_OK;
-      phase = DONE;
-      return true;
-    }
-    return false;
+    qn::deliver<qn::SeqLoop>(P, c, vecs(), fa, ga, tol, max_evals);
   }
 };
 
@@ -444,7 +245,16 @@ struct Evaluator {
   rf_data* d;
   cudaStream_t st[2] = {nullptr, nullptr};
   bool use_graph = true;
-  Group grp[3];
+  Group grp[4];  // 0, 1: the halves; 2: whole-batch passes; 3: device-resident rounds
+  // device-resident rounds: the sets' records, their dataset sets, chunk
+  // counts and phases, the plan counts {sets, items} and the step's ticket,
+  // the bounds (lo, hi, bounded), the plan the step compacts, the graph and
+  // the plan size it was captured for
+  DevBuf r_state, r_sets, r_chunks, r_phase, r_dyn, r_bounds, r_off;
+  HostBuf h_phase;
+  Plan r_plan;
+  cudaGraphExec_t r_exec = nullptr;
+  int32_t r_cap_sets = 0, r_cap_items = 0;
 
   Evaluator(const rf_model* mm, rf_data* dd, bool graph) : m(mm), d(dd), use_graph(graph) {}
   ~Evaluator() {
@@ -454,6 +264,7 @@ struct Evaluator {
       if (G.exec) cudaGraphExecDestroy(G.exec);
       if (G.done) cudaEventDestroy(G.done);
     }
+    if (r_exec) cudaGraphExecDestroy(r_exec);
     for (cudaStream_t s : st)
       if (s) cudaStreamDestroy(s);
   }
@@ -549,6 +360,57 @@ struct Evaluator {
     return RF_OK;
   }
 
+  // Captures kDeviceRounds rounds of the n sets whose records are in
+  // r_state: the pass over the plan the previous step compacted (r_plan,
+  // counts in r_dyn), then the step.  The launch shapes are those of
+  // n_sets sets and n_items items (at least the counts the rounds see);
+  // ends with the phases' download.
+  rf_status capture_rounds(int n, int32_t n_sets, int32_t n_items, double tol, int max_evals) {
+    cudaStream_t st = this->st[0];
+    if (r_exec) {
+      cudaGraphExecDestroy(r_exec);
+      r_exec = nullptr;
+    }
+    Workspace& w = d->ws;
+    const int P = m->m.prog.n_free;
+    int32_t* dyn = (int32_t*)r_dyn.p;
+    const double* bounds = (const double*)r_bounds.p;
+    r_plan.n_active = n_sets;
+    r_plan.n_items = n_items;
+    r_cap_sets = n_sets;
+    r_cap_items = n_items;
+    FitStepArgs a;
+    a.state = (double*)r_state.p;
+    a.set_of = (const int32_t*)r_sets.p;
+    a.chunks = (const int32_t*)r_chunks.p;
+    a.n = n;
+    a.P = P;
+    a.out = (const double*)w.out.p;
+    a.theta = (double*)w.theta.p;
+    a.lo = bounds;
+    a.hi = bounds + P;
+    a.bounded = (const char*)(bounds + 2 * P);
+    a.tol = tol;
+    a.max_evals = max_evals;
+    a.phase = (int32_t*)r_phase.p;
+    a.plan_sets = (int32_t*)r_plan.sets.p;
+    a.plan_items = (int2*)r_plan.items.p;
+    a.item_off = (int32_t*)r_off.p;
+    a.dyn = dyn;
+    a.ticket = dyn + 2;
+    cudaGraph_t graph = nullptr;
+    if (!cuda_ok(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "graph capture")) return RF_E_CUDA;
+    for (int r = 0; r < kDeviceRounds; ++r) {
+      launch_pass(m, d, r_plan, (const double*)w.theta.p, (double*)w.out.p, (int32_t*)w.flags.p, true, st, 3, dyn);
+      launch_fit_step(a, st);
+    }
+    cudaMemcpyAsync(h_phase.p, r_phase.p, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, st);
+    if (!cuda_ok(cudaStreamEndCapture(st, &graph), "graph capture")) return RF_E_CUDA;
+    const bool ok = cuda_ok(cudaGraphInstantiate(&r_exec, graph, 0), "graph instantiate");
+    cudaGraphDestroy(graph);
+    return ok ? RF_OK : RF_E_CUDA;
+  }
+
   // One synchronous whole-batch pass.
   rf_status run(const std::vector<int32_t>& active, const std::vector<double>& theta, std::vector<double>& nll,
                 std::vector<double>& grad) {
@@ -563,6 +425,115 @@ struct Evaluator {
   }
 };
 
+struct DeviceSteps {
+  Evaluator* ev;
+  const int32_t* set_of;  // problem -> dataset set; null: the identity
+};
+
+namespace {
+
+// Runs the rounds of the still-active problems `active` (increasing) on the
+// device until all are done or max_evals rounds have run.  Their states go
+// to the device as records; each graph launch runs kDeviceRounds rounds of
+// parameter point, event pass and step, the step compacting the next
+// pass's plan to the sets still going; between launches the host only
+// reads the phases (and captures the rounds again, with smaller launch
+// shapes, once the sets fit the block-per-set parameter point or the items
+// have shrunk 4-fold).  The states come back at the end (th and jc
+// refreshed for any problem not done).  Every problem takes the same trial
+// points as in host rounds: the step is the same code, rounding the same
+// way (fit_step.h), and a set's pass result does not depend on the plan.
+rf_status device_rounds(DeviceSteps& dv, const std::vector<int32_t>& active, std::vector<SetFit>& fits,
+                        const Coords& co, double tol, int max_evals, std::vector<double>& th, std::vector<double>& jc) {
+  Evaluator& ev = *dv.ev;
+  rf_data* d = ev.d;
+  Workspace& w = d->ws;
+  const int P = co.P, n = (int)active.size(), W = qn::tail_record_words(P);
+  cudaStream_t& st = ev.st[0];
+  if (!st && !cuda_ok(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking), "stream")) return RF_E_CUDA;
+  std::vector<int32_t> sets(n), chunks(n), phase(n);
+  for (int i = 0; i < n; ++i) {
+    sets[i] = dv.set_of ? dv.set_of[active[i]] : active[i];
+    chunks[i] = (int32_t)d->chunks[sets[i]];
+  }
+  std::vector<double> rec((size_t)n * W);
+  for (int i = 0; i < n; ++i) {
+    const SetFit& F = fits[active[i]];
+    double* r = rec.data() + (size_t)i * W;
+    std::memcpy(r, &F.c, sizeof(qn::State));
+    double* v = r + qn::kStateWords;
+    const std::vector<double>* parts[5] = {&F.x, &F.g, &F.p, &F.g_lo, &F.trial};
+    for (int j = 0; j < 5; ++j) std::copy(parts[j]->begin(), parts[j]->end(), v + (size_t)j * P);
+    std::copy(jc.begin() + (size_t)active[i] * P, jc.begin() + (size_t)(active[i] + 1) * P, v + (size_t)5 * P);
+    std::copy(F.H.begin(), F.H.end(), v + (size_t)6 * P);
+    phase[i] = F.c.phase;
+  }
+  std::vector<char> bounds(sizeof(double) * 2 * P + P);
+  std::memcpy(bounds.data(), co.lo.data(), sizeof(double) * P);
+  std::memcpy(bounds.data() + sizeof(double) * P, co.hi.data(), sizeof(double) * P);
+  std::memcpy(bounds.data() + sizeof(double) * 2 * P, co.bounded.data(), P);
+  // the first plan: every set of the list
+  if (!build_plan(d, sets, &ev.r_plan)) return RF_E_OOM;
+  const int32_t dyn0[3] = {ev.r_plan.n_active, ev.r_plan.n_items, 0};
+  if (!ev.r_state.ensure(sizeof(double) * rec.size()) || !ev.r_sets.ensure(sizeof(int32_t) * n) ||
+      !ev.r_chunks.ensure(sizeof(int32_t) * n) || !ev.r_phase.ensure(sizeof(int32_t) * n) ||
+      !ev.r_off.ensure(sizeof(int32_t) * n) ||
+      !ev.r_dyn.ensure(sizeof(dyn0)) || !ev.r_bounds.ensure(bounds.size()) ||
+      !ev.h_phase.ensure(sizeof(int32_t) * n))
+    return RF_E_OOM;
+  double* h_th = (double*)w.h_theta.p;
+  for (int i = 0; i < n; ++i)
+    std::copy(th.begin() + (size_t)active[i] * P, th.begin() + (size_t)(active[i] + 1) * P, h_th + (size_t)sets[i] * P);
+  const size_t s0 = sets.front(), ns = (size_t)sets.back() + 1 - s0;
+  auto up = [&](void* dst, const void* src, size_t bytes) {
+    return cuda_ok(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st), "upload");
+  };
+  if (!up(ev.r_state.p, rec.data(), sizeof(double) * rec.size()) || !up(ev.r_sets.p, sets.data(), sizeof(int32_t) * n) ||
+      !up(ev.r_chunks.p, chunks.data(), sizeof(int32_t) * n) || !up(ev.r_phase.p, phase.data(), sizeof(int32_t) * n) ||
+      !up(ev.r_dyn.p, dyn0, sizeof(dyn0)) || !up(ev.r_bounds.p, bounds.data(), bounds.size()) ||
+      !up((double*)w.theta.p + s0 * P, h_th + s0 * P, sizeof(double) * ns * P) ||
+      !cuda_ok(cudaStreamSynchronize(st), "upload"))
+    return RF_E_CUDA;
+  std::vector<int32_t> going(n);
+  for (int i = 0; i < n; ++i) going[i] = i;
+  const int32_t* ph = (const int32_t*)ev.h_phase.p;
+  const int max_launches = max_evals / kDeviceRounds + 2;
+  for (int it = 0; it < max_launches && !going.empty(); ++it) {
+    int32_t items = 0;
+    for (int i : going) items += chunks[i];
+    const bool block_k1 = (int)going.size() <= kBlockK1MaxSets;
+    const bool captured_block = ev.r_cap_sets <= kBlockK1MaxSets;
+    if (!ev.r_exec || (block_k1 && !captured_block) || 4 * items < ev.r_cap_items) {
+      const rf_status s = ev.capture_rounds(n, (int32_t)going.size(), items, tol, max_evals);
+      if (s != RF_OK) return s;
+    }
+    if (!cuda_ok(cudaGraphLaunch(ev.r_exec, st), "graph launch") || !cuda_ok(cudaStreamSynchronize(st), "graph sync"))
+      return RF_E_CUDA;
+    note_launches(3 * kDeviceRounds, st);
+    going.clear();
+    for (int i = 0; i < n; ++i)
+      if (ph[i] != qn::DONE) going.push_back(i);
+  }
+  if (!cuda_ok(cudaMemcpyAsync(rec.data(), ev.r_state.p, sizeof(double) * rec.size(), cudaMemcpyDeviceToHost, st),
+               "download") ||
+      !cuda_ok(cudaStreamSynchronize(st), "download"))
+    return RF_E_CUDA;
+  for (int i = 0; i < n; ++i) {
+    const int pr = active[i];
+    SetFit& F = fits[pr];
+    const double* r = rec.data() + (size_t)i * W;
+    std::memcpy(&F.c, r, sizeof(qn::State));
+    const double* v = r + qn::kStateWords;
+    std::vector<double>* parts[5] = {&F.x, &F.g, &F.p, &F.g_lo, &F.trial};
+    for (int j = 0; j < 5; ++j) std::copy(v + (size_t)j * P, v + (size_t)(j + 1) * P, parts[j]->begin());
+    std::copy(v + (size_t)6 * P, v + (size_t)6 * P + (size_t)P * P, F.H.begin());
+    if (!F.done()) co.to_theta_jac(F.trial.data(), &th[(size_t)pr * P], &jc[(size_t)pr * P]);
+  }
+  return RF_OK;
+}
+
+}  // namespace
+
 // The batched fit driver: S independent problems of P parameters with
 // bounds lo/hi (lo >= hi: unbounded), started at `start` (S x P).  Each
 // round asks every active problem for one trial point and evaluates all of
@@ -570,7 +541,7 @@ struct Evaluator {
 // gradient S x P out, indexed by set).  cov (S x P x P) may be null.
 rf_status fit_batch(int S, int P, const double* lo, const double* hi, const double* start, double tol, int max_evals,
                     bool want_cov, const BatchEval& eval, const SplitEval* split, double* theta_hat,
-                    double* nll_min, double* cov, int32_t* n_evals, int32_t* fit_status) {
+                    double* nll_min, double* cov, int32_t* n_evals, int32_t* fit_status, DeviceSteps* dev) {
   (void)want_cov;
   Coords co;
   co.P = P;
@@ -583,21 +554,8 @@ rf_status fit_batch(int S, int P, const double* lo, const double* hi, const doub
   std::vector<SetFit> fits(S);
   std::vector<double> th((size_t)S * P), nll(S), grad((size_t)S * P);
   for (int s = 0; s < S; ++s) {
-    SetFit& F = fits[s];
-    F.P = P;
-    F.x.assign(P, 0.0);
-    F.g.assign(P, 0.0);
-    F.p.assign(P, 0.0);
-    F.trial.assign(P, 0.0);
-    F.g_lo.assign(P, 0.0);
-    F.w_s.assign(P, 0.0);
-    F.w_y.assign(P, 0.0);
-    F.w_hy.assign(P, 0.0);
-    F.w_ga.assign(P, 0.0);
-    F.H.assign(P * P, 0.0);
-    for (int k = 0; k < P; ++k) F.H[k * P + k] = 1.0;
-    co.to_internal(start + (size_t)s * P, F.trial.data());
-    F.phase = INIT;
+    fits[s].init(P);
+    co.to_internal(start + (size_t)s * P, fits[s].trial.data());
   }
   // The per-set update is O(P^2): with many parameters even a few sets are
   // worth spreading over threads.
@@ -615,7 +573,7 @@ rf_status fit_batch(int S, int P, const double* lo, const double* hi, const doub
       double* ga = fits[s].w_ga.data();
       for (int k = 0; k < P; ++k) ga[k] = grad[(size_t)s * P + k] * jc[(size_t)s * P + k];
       fits[s].deliver(nll[s], ga, tol, max_evals);
-      if (fits[s].phase != DONE) co.to_theta_jac(fits[s].trial.data(), &th[(size_t)s * P], &jc[(size_t)s * P]);
+      if (!fits[s].done()) co.to_theta_jac(fits[s].trial.data(), &th[(size_t)s * P], &jc[(size_t)s * P]);
     }, min_n);
   };
   if (split && split->split > 0 && split->split < S) {
@@ -629,7 +587,7 @@ rf_status fit_batch(int S, int P, const double* lo, const double* hi, const doub
       act[g].clear();
       const int a = g ? (int)split->split : 0, b = g ? S : (int)split->split;
       for (int s = a; s < b; ++s)
-        if (fits[s].phase != DONE) act[g].push_back(s);
+        if (!fits[s].done()) act[g].push_back(s);
     };
     auto drain = [&](rf_status st) {
       for (int g = 0; g < 2; ++g)
@@ -655,20 +613,29 @@ rf_status fit_batch(int S, int P, const double* lo, const double* hi, const doub
       }
     }
   }
+  bool dev_used = false;
   while (true) {
     active.clear();
     for (int s = 0; s < S; ++s)
-      if (fits[s].phase != DONE) active.push_back(s);
+      if (!fits[s].done()) active.push_back(s);
     if (active.empty()) break;
+    if (dev && !dev_used && P <= qn::kTailMaxP) {
+      // the remaining rounds on the device; a set it leaves unfinished (it
+      // stops after max_evals rounds) goes on here
+      dev_used = true;
+      const rf_status st = device_rounds(*dev, active, fits, co, tol, max_evals, th, jc);
+      if (st != RF_OK) return st;
+      continue;
+    }
     const rf_status st = eval(active, th, nll, grad);
     if (st != RF_OK) return st;
     deliver(active);
   }
   for (int s = 0; s < S; ++s) {
     co.to_theta(fits[s].x.data(), theta_hat + (size_t)s * P);
-    nll_min[s] = fits[s].status == RF_E_DOMAIN ? kInf : fits[s].f;
-    n_evals[s] = fits[s].evals;
-    fit_status[s] = fits[s].status;
+    nll_min[s] = fits[s].c.status == RF_E_DOMAIN ? kInf : fits[s].c.f;
+    n_evals[s] = fits[s].c.evals;
+    fit_status[s] = fits[s].c.status;
   }
   if (cov) {
     // Central differences of the analytic gradient, all sets per pass; the
@@ -676,7 +643,7 @@ rf_status fit_batch(int S, int P, const double* lo, const double* hi, const doub
     std::vector<double> Hs((size_t)S * P * P, 0.0), h((size_t)S * P);
     std::vector<int32_t> ok_sets;
     for (int s = 0; s < S; ++s) {
-      if (fits[s].status == RF_E_DOMAIN) continue;
+      if (fits[s].c.status == RF_E_DOMAIN) continue;
       ok_sets.push_back(s);
       for (int k = 0; k < P; ++k) {
         const double jk = co.jac(k, fits[s].x[k]);
@@ -707,7 +674,7 @@ rf_status fit_batch(int S, int P, const double* lo, const double* hi, const doub
       std::vector<double> A(Hs.begin() + (size_t)s * P * P, Hs.begin() + (size_t)(s + 1) * P * P);
       for (int i = 0; i < P; ++i)
         for (int j = 0; j < i; ++j) A[i * P + j] = A[j * P + i] = 0.5 * (A[i * P + j] + A[j * P + i]);
-      if (fits[s].status == RF_E_DOMAIN || !invert(A, P, c))
+      if (fits[s].c.status == RF_E_DOMAIN || !invert(A, P, c))
         std::fill(c, c + P * P, std::numeric_limits<double>::quiet_NaN());
     }
   }
@@ -758,7 +725,12 @@ extern "C" rf_status rf_fit(const rf_model* m, const rf_data* d, const double* t
     while (s < S - 1 && 2 * (d->offsets[s] - d->offsets[0]) < total) ++s;
     split.split = s;
   }
-  split.min_events = kPipelineMinEvents;
+  // device rounds for a batch (one set's rounds are faster with host steps:
+  // its pass dominates and the step's serial chain on one warp costs more
+  // than the host's round trip)
+  DeviceSteps dsteps{&ev, nullptr};
+  const bool device = ev.use_graph && !(opts && opts->host_steps == 1) && S >= 2;
+  split.min_events = device ? std::max(kPipelineMinEvents, kDeviceRoundEvents) : kPipelineMinEvents;
   split.launch = [&](int g, const std::vector<int32_t>& a, const std::vector<double>& th) { return ev.launch(g, a, th); };
   split.wait = [&](int g, std::vector<double>& nll, std::vector<double>& grad) { return ev.wait(g, nll, grad); };
   split.events = [&](const std::vector<int32_t>& a) { return ev.events_of(a); };
@@ -766,7 +738,7 @@ extern "C" rf_status rf_fit(const rf_model* m, const rf_data* d, const double* t
                    [&](const std::vector<int32_t>& active, std::vector<double>& th, std::vector<double>& nll,
                        std::vector<double>& grad) { return ev.run(active, th, nll, grad); },
                    split.split > 0 ? &split : nullptr,
-                   theta_hat, nll_min, want_cov ? cov : nullptr, n_evals, fit_status);
+                   theta_hat, nll_min, want_cov ? cov : nullptr, n_evals, fit_status, device ? &dsteps : nullptr);
 }
 
 extern "C" rf_status rf_fit_sets(const rf_model* m, const rf_data* d, const int32_t* sets, int32_t n,
@@ -811,6 +783,8 @@ extern "C" rf_status rf_fit_sets(const rf_model* m, const rf_data* d, const int3
     for (int k = 0; k < P; ++k)
       start[(size_t)i * P + k] = theta0 ? theta0[(size_t)pos[i] * P + k] : m->m.theta_default[k];
   Evaluator ev(m, dd, !(opts && opts->no_graph == 1));
+  DeviceSteps dsteps{&ev, srt.data()};
+  const bool device = ev.use_graph && !(opts && opts->host_steps == 1) && n >= 2;
   std::vector<double> th_s((size_t)S * P), nll_s(S), grad_s((size_t)S * P);
   std::vector<int32_t> act_s;
   std::vector<double> th_o((size_t)n * P), nll_o(n), cov_o(want_cov ? (size_t)n * P * P : 0);
@@ -833,7 +807,8 @@ extern "C" rf_status rf_fit_sets(const rf_model* m, const rf_data* d, const int3
         }
         return st;
       },
-      nullptr, th_o.data(), nll_o.data(), want_cov ? cov_o.data() : nullptr, ne_o.data(), st_o.data());
+      nullptr, th_o.data(), nll_o.data(), want_cov ? cov_o.data() : nullptr, ne_o.data(), st_o.data(),
+      device ? &dsteps : nullptr);
   for (int i = 0; i < n; ++i) {
     const int o = pos[i];
     for (int k = 0; k < P; ++k) theta_hat[(size_t)o * P + k] = th_o[(size_t)i * P + k];

@@ -31,9 +31,6 @@ constexpr double kTwoInvSqrtPi = 1.12837916709551257390;
 // to better than 1e-22 relative and its derivative term is below 1e-21 of
 // the exponential's, so the event takes the one-exponential fast path.
 constexpr double kSlowZ = -7.0;
-// Up to this many active sets K1 runs one block per set (latency), beyond
-// one thread per set (throughput).
-constexpr int kBlockK1MaxSets = 256;
 
 // Programmatic dependent launch: K1 lets the event kernel be scheduled at
 // once; the event kernel stages its tables, then waits for K1's completion
@@ -324,6 +321,8 @@ __device__ bool decay_set_ff(const FFTables& T, const Program& P, const double* 
 // event kernel's work counter.
 __global__ void param_point_kernel(const __grid_constant__ Program P, Pass pass) {
   __shared__ FFTables T;
+  const int n_active = pass.dyn ? pass.dyn[0] : pass.n_active;
+  if (n_active == 0) return;
   pdl_launch_dependents();
   const int a = blockIdx.x * blockDim.x + threadIdx.x;
   if (a == 0) {
@@ -335,7 +334,7 @@ __global__ void param_point_kernel(const __grid_constant__ Program P, Pass pass)
     ff_load_tables(T);
     __syncthreads();
   }
-  if (a >= pass.n_active) return;
+  if (a >= n_active) return;
   const int s = pass.sets[a];
   const double* th = pass.theta + (size_t)s * P.n_free;
   double* C = pass.consts + (size_t)s * P.n_const;
@@ -369,6 +368,7 @@ __global__ void __launch_bounds__(kK1Warps * 32) param_point_block_kernel(const 
   __shared__ ff geff[8];
   __shared__ int ffok;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if ((int)blockIdx.x >= (pass.dyn ? pass.dyn[0] : pass.n_active)) return;
   if (blockIdx.x == 0 && tid == 0) {
     for (int i = 0; i < (pass.n_counters > 1 ? pass.n_counters : 1); ++i) pass.counter[i] = 0;
     if (pass.slow) *pass.slow = 0ull;
@@ -906,12 +906,14 @@ __global__ void __launch_bounds__(kLanes) events_generic(const __grid_constant__
   __shared__ Smem sm;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int Q = kGrad ? 1 + P.n_slots : 1;
+  const int n_items = pass.dyn ? pass.dyn[1] : pass.n_items;
+  if (n_items == 0) return;
   pdl_wait();
   while (true) {
     if (tid == 0) sm.item = atomicAdd(pass.counter, 1);
     __syncthreads();
     const int it = sm.item;
-    if (it >= pass.n_items) break;
+    if (it >= n_items) break;
     const int set = pass.items[it].x, chunk = pass.items[it].y;
     const int64_t s_begin = pass.offsets[set], s_end = pass.offsets[set + 1];
     const int64_t base = s_begin + (int64_t)chunk * kChunk;
@@ -1026,6 +1028,8 @@ __global__ void __launch_bounds__(kLanes, ff_min_blocks(kShape)) events_ff(const
   __shared__ unsigned fbmask_f[kShape == SHAPE_PROD3 ? kLanes : 1];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int Q = pass.Q;
+  const int n_items = pass.dyn ? pass.dyn[1] : pass.n_items;
+  if (n_items == 0) return;
   ff_load_tables(T);
   int col[3];
   if (kShape == SHAPE_PROD3) {
@@ -1033,7 +1037,7 @@ __global__ void __launch_bounds__(kLanes, ff_min_blocks(kShape)) events_ff(const
   } else {
     col[0] = col[1] = col[2] = P.node[0].col;
   }
-  const int n_units = pass.n_items * parts;
+  const int n_units = n_items * parts;
   int kc_set = -1, c_set = -1;  // sets whose constants the block holds (block-uniform)
   pdl_wait();  // K1 has reset the counter and written the constants
   // One unit of lookahead: thread 0 claims the next unit while the block

@@ -46,6 +46,11 @@ struct Pass {
   // pairs of (sum log p, d/dtheta_k sum log p), not negated, for a later
   // ordered combine across shards; out is not written.
   double* pairs;
+  // Null, or device counts {active sets, work items} that replace n_active
+  // and n_items: the rounds of a device-resident fit compact their plan on
+  // the device (sets and items then hold at least that many entries).  No
+  // active set: the pass is skipped.
+  const int32_t* dyn;
 };
 
 // Resident blocks per SM the float-float kernels are compiled for (their

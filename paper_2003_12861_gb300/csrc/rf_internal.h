@@ -20,6 +20,9 @@ constexpr int kMaxPar = 7;       // parameters of one leaf
 // Deterministic reduction geometry: a chunk is 4096 events split over 128
 // lanes (lane l takes events l, l+128, ..., in order); chunks are combined by
 // a radix-32 tree.
+// Up to this many active sets K1 runs one block per set (latency), beyond
+// one thread per set (throughput).
+constexpr int kBlockK1MaxSets = 256;
 constexpr int kChunk = 4096;
 constexpr int kLanes = 128;
 constexpr int kPerLane = kChunk / kLanes;  // 32

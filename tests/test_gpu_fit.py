@@ -134,9 +134,79 @@ def test_pipelined_halves_match_sequential_passes():
     assert d.n_events > 4_000_000
     a = api.fit(m, d, tol_edm=1e-7, want_cov=False, graph=True)
     b = api.fit(m, d, tol_edm=1e-7, want_cov=False, graph=False)
+    # pipelined halves, then whole-batch rounds with every step on the host
+    c = api.fit(m, d, tol_edm=1e-7, want_cov=False, graph=True, device_steps=False)
     assert (a["status"] == L.RF_OK).mean() > 0.9
     for k in ("theta", "nll", "n_evals", "status"):
         assert np.array_equal(a[k], b[k]), k
+        assert np.array_equal(c[k], b[k]), k
+
+
+def test_device_rounds_give_the_host_steps_results():
+    """Once few events of a batch are still being fitted the rounds run on
+    the device (parameter point, event pass and the quasi-Newton step of
+    every set, 8 rounds per graph launch).  The step is the host's code
+    rounding the same way, so each set takes the same trial points: theta,
+    NLL, evaluation counts and statuses equal those of host steps bit for
+    bit, for two large sets (almost their whole fits on the device), for a
+    ragged batch, for a fit that stops at max_evals, and with the covariance
+    computed after the rounds."""
+    spec = W.decay_model()
+    m = api.Model.from_spec(spec)
+    one = api.generate_toys(m, W.DECAY_TRUE, W.SEED_BASE + 31, [400_000.0, 250_000.0], poisson=False)
+    S = 96
+    many = api.generate_toys(m, W.toy_thetas(S, 33), W.SEED_BASE + 33, W.toy_mean_sizes(S, 33, 1e3, 3e4),
+                             poisson=True)
+    for d, kw in ((one, dict(tol_edm=1e-9, want_cov=True)), (many, dict(tol_edm=1e-9, want_cov=False)),
+                  (many, dict(tol_edm=1e-12, max_evals=17, want_cov=False))):
+        dev = api.fit(m, d, device_steps=True, **kw)
+        host = api.fit(m, d, device_steps=False, **kw)
+        for k in ("theta", "nll", "n_evals", "status"):
+            assert np.array_equal(dev[k], host[k]), (k, d.n_sets, kw)
+        if kw.get("want_cov"):
+            assert np.array_equal(dev["cov"], host["cov"])
+        if kw.get("max_evals"):
+            assert np.all(dev["n_evals"] <= 17) and np.any(dev["status"] == L.RF_E_NOT_CONVERGED)
+        else:
+            assert (dev["status"] == L.RF_OK).mean() > 0.9
+
+
+def test_parameter_point_variants_agree_bitwise():
+    """K1 takes a thread per set when a pass covers more than 256 sets and a
+    block per set otherwise; both compute the same constants, so a set's
+    NLL and gradient, and its fit, do not depend on how many sets a pass
+    covers.  Two evaluations per set (max_evals=1): all 300 sets in each
+    pass (direct launches, thread K1) against three of them alone (block
+    K1)."""
+    cases = ((W.decay_model(), W.DECAY_TRUE, None), (W.gauss_poly1_model(), TRUE["gauss_poly1_model"], None),
+             (W.prod3_model(), W.PROD3_TRUE, [True] * 3))
+    for i, (spec, theta, f32) in enumerate(cases):
+        m = api.Model.from_spec(spec)
+        S = 300
+        d = api.generate_toys(m, theta, W.SEED_BASE + 37 + i, [2000.0] * S, poisson=True, f32=f32)
+        k = np.arange(len(theta))
+        th0 = np.array([theta * (1 + 0.02 * np.sin(s + k)) for s in range(S)])
+        allsets = api.fit(m, d, theta0=th0, max_evals=1, want_cov=False, graph=False)
+        pick = [3, 150, 299]
+        sub = api.fit_sets(m, d, pick, theta0=th0[pick], max_evals=1)
+        for j, s in enumerate(pick):
+            assert sub["nll"][j] == allsets["nll"][s], (i, s)
+            assert np.array_equal(sub["theta"][j], allsets["theta"][s]), (i, s)
+            assert sub["n_evals"][j] == allsets["n_evals"][s] == 2, (i, s)
+
+
+def test_device_rounds_product_model_fp32():
+    # 12 free parameters, three FP32 columns: the device rounds of the
+    # product model's fits equal host steps bit for bit
+    spec = W.prod3_model()
+    m = api.Model.from_spec(spec)
+    d = api.generate_toys(m, W.PROD3_TRUE, W.SEED_BASE + 35, [200_000.0, 120_000.0], poisson=False,
+                          f32=[True] * 3)
+    dev = api.fit(m, d, tol_edm=1e-8, want_cov=False, device_steps=True)
+    host = api.fit(m, d, tol_edm=1e-8, want_cov=False, device_steps=False)
+    assert np.all(dev["status"] == L.RF_OK)
+    for k in ("theta", "nll", "n_evals", "status"):
+        assert np.array_equal(dev[k], host[k]), k
 
 
 def test_fit_sets_equals_the_batch_fit_of_those_sets():
