@@ -338,8 +338,11 @@ rf_status rf_mlp_train(rf_mlp* n, const float* d_x, const float* d_t, int32_t ro
  * 64-bin histogram of observable col (rf_hist64), the network's forward
  * pass (with the output de-standardisation of rf_mlp_train), and the
  * prediction in theta0 (HOST, n_sets x n_free doubles, the model's free
- * parameters in order; a start for rf_fit).  The network must map 64 inputs
- * to the model's n_free outputs (RF_E_INVALID otherwise).  Synchronous. */
+ * parameters in order; a start for rf_fit).  A bounded parameter's
+ * prediction is kept 5 % of its range inside the bounds (at a bound the
+ * fit's bound transform is stationary and the parameter barely moves).
+ * The network must map 64 inputs to the model's n_free outputs
+ * (RF_E_INVALID otherwise).  Synchronous. */
 rf_status rf_mlp_predict(rf_mlp* n, const rf_model* m, const rf_data* d, int32_t col, double* theta0);
 rf_status rf_mlp_save(const rf_mlp* n, const char* path);
 rf_status rf_mlp_load(const char* path, rf_mlp** out);

@@ -27,6 +27,11 @@
 #include "api_internal.h"
 
 namespace rf {
+
+// Learned starts of bounded parameters stay this fraction of the range
+// inside the bounds (rf_mlp_predict).
+constexpr double kStartMargin = 0.05;
+
 namespace {
 
 constexpr int BM = 64, BN = 64, BK = 32, PAD = 8;
@@ -603,6 +608,19 @@ extern "C" rf_status rf_mlp_predict(rf_mlp* n, const rf_model* m, const rf_data*
   std::vector<float> y((size_t)S * no);
   if (!cuda_ok(cudaMemcpy(y.data(), n->pred_y.p, sizeof(float) * y.size(), cudaMemcpyDeviceToHost), "rf_mlp_predict"))
     return RF_E_CUDA;
-  for (size_t i = 0; i < y.size(); ++i) theta0[i] = (double)y[i];
+  // A start on (or beyond) a bound sits where the fit's bound transform is
+  // stationary (d theta / d phi = 0): that parameter barely moves.  Bounded
+  // predictions are kept kStartMargin of the range inside the bounds.
+  const std::vector<double>& lo = m->m.lo;
+  const std::vector<double>& hi = m->m.hi;
+  for (int s = 0; s < S; ++s)
+    for (int k = 0; k < no; ++k) {
+      double t = (double)y[(size_t)s * no + k];
+      if (lo[k] < hi[k] && std::isfinite(lo[k]) && std::isfinite(hi[k])) {
+        const double a = lo[k] + kStartMargin * (hi[k] - lo[k]), b = hi[k] - kStartMargin * (hi[k] - lo[k]);
+        t = t < a ? a : (t > b ? b : t);
+      }
+      theta0[(size_t)s * no + k] = t;
+    }
   return RF_OK;
 }

@@ -11,7 +11,9 @@ and from its generating parameters, and its label is the fitted point
 (theta-hat) of the lower of the two minima: small toys of this model have
 several local minima (a resolution parameter or the signal fraction on a
 bound against an interior minimum), and the network should point at the
-deeper one.  The plain fit from the default start is also the fallback and
+deeper one.  Its predictions start the fits at least 5 % of each bounded
+parameter's range inside the bounds (rf_mlp_predict: at a bound the fit's
+bound transform is stationary).  The plain fit from the default start is also the fallback and
 the yardstick: a learned start that fails (outside the domain, or no
 convergence) is refitted from the default start, and a learned fit that ends
 in a different minimum (|delta NLL| >= 1e-6) is counted and reported, higher
