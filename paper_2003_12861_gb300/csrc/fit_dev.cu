@@ -26,12 +26,15 @@ constexpr int kStepThreads = kStepWarps * 32;
 // Shared doubles per warp: the set's record, then ga, w_s, w_y, w_hy, w_r.
 __host__ __device__ inline int step_smem_words(int P) { return qn::tail_record_words(P) + 5 * P; }
 
+// kP: the parameter count when known at compile time (the loops over
+// elements then have constant trip counts), 0 for any count.
+template <int kP>
 __global__ void __launch_bounds__(kStepThreads) fit_step_kernel(FitStepArgs a) {
   extern __shared__ double smem[];
   __shared__ int last;
   __shared__ int scan_a[kStepThreads], scan_i[kStepThreads];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int P = a.P, W = qn::tail_record_words(P);
+  const int P = kP ? kP : a.P, W = qn::tail_record_words(P);
   if (a.dyn[0] == 0) return;  // every set is done: nothing to step or plan
   const int i = blockIdx.x * kStepWarps + warp;
   if (i < a.n) {
@@ -115,7 +118,12 @@ void launch_fit_step(const FitStepArgs& a, cudaStream_t st) {
   if (a.n <= 0) return;
   const int blocks = (a.n + kStepWarps - 1) / kStepWarps;
   const size_t smem = sizeof(double) * kStepWarps * step_smem_words(a.P);
-  fit_step_kernel<<<blocks, kStepThreads, smem, st>>>(a);
+  switch (a.P) {
+    case 4: fit_step_kernel<4><<<blocks, kStepThreads, smem, st>>>(a); break;
+    case 6: fit_step_kernel<6><<<blocks, kStepThreads, smem, st>>>(a); break;
+    case 12: fit_step_kernel<12><<<blocks, kStepThreads, smem, st>>>(a); break;
+    default: fit_step_kernel<0><<<blocks, kStepThreads, smem, st>>>(a);
+  }
 }
 
 }  // namespace rf
