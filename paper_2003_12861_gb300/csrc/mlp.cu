@@ -3,10 +3,11 @@
 // this is the learned-start configuration: 64 -> 128 -> 128 -> 128 -> 6 with
 // GELU, BF16 operands, FP32 accumulation, trained on the GPU).
 //
-// Kernels: a tensor-core GEMM (mma.sync m16n8k16, BF16 x BF16 -> FP32; the
-// operands are rounded to BF16, nearest even, as they are staged into shared
-// memory) with a fused bias / GELU / pre-activation epilogue, used for the
-// forward pass and both backward products; GELU backward; bias gradients
+// Kernels: a tensor-core GEMM on the fifth-generation tensor cores (tcgen05:
+// BF16 x BF16 -> FP32 accumulated in tensor memory; the operands are rounded
+// to BF16, nearest even, as they are staged into shared memory) with a fused
+// bias / GELU / pre-activation epilogue, used for the forward pass and both
+// backward products; GELU backward; bias gradients
 // (column sums in fixed order); MSE loss and its gradient; Adam (Kingma & Ba
 // 2015) on FP32 master weights; a row gather for shuffled mini-batches; and
 // target standardisation.  Every reduction has a fixed order, so training is
@@ -34,8 +35,6 @@ constexpr double kStartMargin = 0.05;
 
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 32, PAD = 8;
-
 struct GemmArgs {
   const float* A;  // M x K (or K x M when transA)
   const float* B;  // K x N (or N x K when transB)
@@ -44,6 +43,11 @@ struct GemmArgs {
   float* Z;        // pre-activation out (M x N) or null
   int M, N, K, lda, ldb, ldc;
   int transA, transB, gelu;
+  // split K: block z takes K rows [z kc, (z + 1) kc) and writes its raw
+  // partial tile to part + z M N (row-major) instead of the epilogue; null
+  // for one block over all of K
+  float* part;
+  int kc;
 };
 
 __device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
@@ -51,87 +55,169 @@ __device__ __forceinline__ float gelu_grad_f(float z) {
   return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * __expf(-0.5f * z * z) * 0.3989422804014327f;
 }
 
-__device__ __forceinline__ uint32_t pack2(const __nv_bfloat16* p) { return *reinterpret_cast<const uint32_t*>(p); }
+// Set when a GEMM's wait for its tensor-core work gave up (checked by the
+// synchronous entry points).
+__device__ int g_gemm_timeout;
 
-__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+// The GEMM's tile: 128 rows (the MMA's M, one TMEM lane per row) x 32
+// columns (N; 32 FP32 accumulator columns of TMEM, the smallest allocation),
+// K staged 64 at a time.  (64 columns measured 4-25 % slower on the
+// network's shapes: half as many blocks for these small GEMMs.)
+constexpr int TM = 128, TN = 32, TK = 64;
+constexpr int kSmemA = TM * TK * 2, kSmemB = TN * TK * 2;
+// Dynamic shared memory per block: the two operand tiles and the barrier;
+// 40 KB also keeps at most 5 blocks (160 TMEM columns of 512) on an SM.
+constexpr int kGemmSmem = 40 * 1024;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// A K-major operand tile without swizzle is stored as core matrices of 8
+// rows x 8 BF16 (16 bytes per row, 128 contiguous bytes); rows 8g.., k
+// 8j.. at byte (g * TK / 8 + j) * 128.  Its shared-memory descriptor: start
+// address, the leading byte offset (next core matrix along K: 128), the
+// stride byte offset (next 8 rows: TK / 8 * 128), descriptor version 1, no
+// swizzle.
+__device__ __forceinline__ int core_off(int r, int k) {
+  return ((r >> 3) * (TK / 8) + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7);
+}
+__device__ __forceinline__ uint64_t operand_desc(uint32_t saddr) {
+  const uint64_t lbo = 128, sbo = (TK / 8) * 128;
+  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((lbo >> 4) & 0x3FFF) << 16 | ((sbo >> 4) & 0x3FFF) << 32 |
+         (uint64_t)1 << 46;
+}
+// The instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B,
+// both K-major, N >> 3 and M >> 4.
+__host__ __device__ constexpr uint32_t mma_idesc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-// C = act(op(A) op(B) + bias).  Block tile 64 x 64, 4 warps of 32 x 32, K in
-// steps of 32; out-of-range elements are zero-filled and not stored.
-__global__ void __launch_bounds__(128) gemm_bf16_kernel(GemmArgs g) {
-  __shared__ __align__(16) __nv_bfloat16 As[BM][BK + PAD];
-  __shared__ __align__(16) __nv_bfloat16 Bs[BN][BK + PAD];  // [n][k]
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int wm = warp >> 1, wn = warp & 1;
-  const int gq = lane >> 2, tq = lane & 3;
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-  float acc[2][4][4];
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int c = 0; c < 4; ++c) acc[i][j][c] = 0.f;
-  for (int k0 = 0; k0 < g.K; k0 += BK) {
-    for (int idx = tid; idx < BM * BK; idx += 128) {
-      const int r = idx / BK, k = idx % BK;
-      const int m = m0 + r, kk = k0 + k;
-      float v = 0.f;
-      if (m < g.M && kk < g.K) v = g.transA ? g.A[(size_t)kk * g.lda + m] : g.A[(size_t)m * g.lda + kk];
-      As[r][k] = __float2bfloat16_rn(v);
-    }
-    for (int idx = tid; idx < BN * BK; idx += 128) {
-      const int c = idx / BK, k = idx % BK;
-      const int n = n0 + c, kk = k0 + k;
-      float v = 0.f;
-      if (n < g.N && kk < g.K) v = g.transB ? g.B[(size_t)n * g.ldb + kk] : g.B[(size_t)kk * g.ldb + n];
-      Bs[c][k] = __float2bfloat16_rn(v);
-    }
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < BK; kk += 16) {
-      uint32_t a[2][4], b[4][2];
-#pragma unroll
-      for (int mi = 0; mi < 2; ++mi) {
-        const int r = wm * 32 + mi * 16;
-        a[mi][0] = pack2(&As[r + gq][kk + 2 * tq]);
-        a[mi][1] = pack2(&As[r + gq + 8][kk + 2 * tq]);
-        a[mi][2] = pack2(&As[r + gq][kk + 2 * tq + 8]);
-        a[mi][3] = pack2(&As[r + gq + 8][kk + 2 * tq + 8]);
-      }
-#pragma unroll
-      for (int ni = 0; ni < 4; ++ni) {
-        const int c = wn * 32 + ni * 8;
-        b[ni][0] = pack2(&Bs[c + gq][kk + 2 * tq]);
-        b[ni][1] = pack2(&Bs[c + gq][kk + 2 * tq + 8]);
-      }
-#pragma unroll
-      for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-        for (int ni = 0; ni < 4; ++ni) mma_bf16(acc[mi][ni], a[mi], b[ni]);
-    }
-    __syncthreads();
+// Waits for phase `parity` of the barrier; gives up (false) after 2^22 tries.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (int it = 0; it < (1 << 22); ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
   }
+  return false;
+}
+
+// C = act(op(A) op(B) + bias), a 128 x 32 tile per block of 4 warps.  Per K
+// stage the block converts its A and B tiles to BF16 into shared memory (out
+// of range: zero), one thread issues four 128 x 32 x 16 MMAs accumulating in
+// tensor memory and commits them to a barrier that every thread waits on;
+// then each warp reads its 32 rows of the accumulator (tcgen05.ld) for the
+// epilogue.  Warp 0 allocates and frees the 32 TMEM columns.
+__global__ void __launch_bounds__(128) gemm_bf16_kernel(GemmArgs g) {
+  extern __shared__ __align__(128) unsigned char gsm[];
+  __nv_bfloat16* As = reinterpret_cast<__nv_bfloat16*>(gsm);
+  __nv_bfloat16* Bs = reinterpret_cast<__nv_bfloat16*>(gsm + kSmemA);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(gsm + kSmemA + kSmemB);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(gsm + kSmemA + kSmemB + 8);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
+  const int kb = g.part ? blockIdx.z * g.kc : 0, ke = g.part ? min(g.K, kb + g.kc) : g.K;
+  const uint32_t bar_a = smem_u32(bar);
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)), "r"(TN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar_a) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = *tslot;
+  uint32_t parity = 0;
+  bool ok = true;
+  for (int k0 = kb; k0 < ke && ok; k0 += TK) {
+    for (int idx = tid; idx < TM * TK; idx += 128) {
+      const int r = idx / TK, k = idx % TK, m = m0 + r, kk = k0 + k;
+      float v = 0.f;
+      if (m < g.M && kk < ke) v = g.transA ? g.A[(size_t)kk * g.lda + m] : g.A[(size_t)m * g.lda + kk];
+      As[core_off(r, k)] = __float2bfloat16_rn(v);
+    }
+    for (int idx = tid; idx < TN * TK; idx += 128) {
+      const int c = idx / TK, k = idx % TK, n = n0 + c, kk = k0 + k;
+      float v = 0.f;
+      if (n < g.N && kk < ke) v = g.transB ? g.B[(size_t)n * g.ldb + kk] : g.B[(size_t)kk * g.ldb + n];
+      Bs[core_off(c, k)] = __float2bfloat16_rn(v);
+    }
+    // the tiles were written through the generic proxy; the MMAs read them
+    // through the async proxy
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const uint32_t sa = smem_u32(As), sb = smem_u32(Bs);
+      for (int s = 0; s < TK / 16; ++s) {
+        const uint64_t da = operand_desc(sa + s * 256), db = operand_desc(sb + s * 256);
+        const uint32_t accumulate = (k0 > kb || s > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+            "l"(da), "l"(db), "r"(mma_idesc(TM, TN)), "r"(accumulate)
+            : "memory");
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar_a)
+                   : "memory");
+    }
+    ok = mbar_wait(bar_a, parity);
+    parity ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    ok = __syncthreads_and(ok) != 0;  // block-uniform: every warp takes the same path
+  }
+  if (!ok) {
+    if (tid == 0) atomicExch(&g_gemm_timeout, 1);
+    mbar_wait(bar_a, parity ^ 1u);  // once more (bounded) for MMAs still in flight
+  } else {
+    for (int c0 = 0; c0 < TN; c0 += 8) {
+      uint32_t r[8];
+      const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+      asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+                   : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                   : "r"(ta)
+                   : "memory");
+      asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+      const int row = m0 + warp * 32 + lane;
 #pragma unroll
-  for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-    for (int ni = 0; ni < 4; ++ni)
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const int row = m0 + wm * 32 + mi * 16 + gq + (c >= 2 ? 8 : 0);
-        const int col = n0 + wn * 32 + ni * 8 + 2 * tq + (c & 1);
-        if (row < g.M && col < g.N) {
-          float v = acc[mi][ni][c] + (g.bias ? g.bias[col] : 0.f);
+      for (int j = 0; j < 8; ++j) {
+        const int col = n0 + c0 + j;
+        if (row < g.M && col < g.N && g.part) {
+          g.part[((size_t)blockIdx.z * g.M + row) * g.N + col] = __uint_as_float(r[j]);
+        } else if (row < g.M && col < g.N) {
+          float v = __uint_as_float(r[j]) + (g.bias ? g.bias[col] : 0.f);
           if (g.Z) g.Z[(size_t)row * g.ldc + col] = v;
           if (g.gelu) v = gelu_f(v);
           g.C[(size_t)row * g.ldc + col] = v;
         }
       }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TN) : "memory");
+}
+
+// The epilogue of a split-K GEMM: per element the splits' partial sums in
+// split order, then bias, pre-activation and activation as in the GEMM.
+__global__ void splitk_reduce_kernel(GemmArgs g, int splits) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)g.M * g.N) return;
+  const int row = (int)(e / g.N), col = (int)(e % g.N);
+  float v = 0.f;
+  for (int z = 0; z < splits; ++z) v += g.part[((size_t)z * g.M + row) * g.N + col];
+  v += g.bias ? g.bias[col] : 0.f;
+  if (g.Z) g.Z[(size_t)row * g.ldc + col] = v;
+  if (g.gelu) v = gelu_f(v);
+  g.C[(size_t)row * g.ldc + col] = v;
 }
 
 // dA *= GELU'(Z), elementwise.
@@ -222,12 +308,48 @@ unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
 
+// A GEMM whose output tiles are few and whose K is long (the weight
+// gradients: K = the batch) splits K over up to kMaxSplits blocks per tile,
+// each at least two stages long, into `ws` (splits x M x N floats), and sums
+// the splits in order in a second kernel.
+constexpr int kMaxSplits = 16;
+int gemm_splits(int M, int N, int K) {
+  const int tiles = ((N + TN - 1) / TN) * ((M + TM - 1) / TM);
+  if (tiles >= 32 || K < 4 * TK) return 1;
+  return std::max(1, std::min(kMaxSplits, K / (2 * TK)));
+}
+size_t gemm_ws_floats(int M, int N, int K) {
+  const int s = gemm_splits(M, N, K);
+  return s > 1 ? (size_t)s * M * N : 0;
+}
 void gemm_bf16(const float* A, int lda, bool tA, const float* B, int ldb, bool tB, float* C, int ldc, int M, int N,
-               int K, const float* bias, float* Z, bool gelu, cudaStream_t st) {
-  GemmArgs g{A, B, C, bias, Z, M, N, K, lda, ldb, ldc, tA ? 1 : 0, tB ? 1 : 0, gelu ? 1 : 0};
-  dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
+               int K, const float* bias, float* Z, bool gelu, float* ws, size_t ws_floats, cudaStream_t st) {
+  GemmArgs g{A, B, C, bias, Z, M, N, K, lda, ldb, ldc, tA ? 1 : 0, tB ? 1 : 0, gelu ? 1 : 0, nullptr, K};
+  const int splits = (ws && gemm_ws_floats(M, N, K) <= ws_floats) ? gemm_splits(M, N, K) : 1;
+  if (splits > 1) {
+    g.kc = ((K + splits - 1) / splits + TK - 1) / TK * TK;
+    g.part = ws;
+  }
+  const int used = splits > 1 ? (K + g.kc - 1) / g.kc : 1;
+  dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM, used);
   note_launches(1, st);
-  gemm_bf16_kernel<<<grid, 128, 0, st>>>(g);
+  gemm_bf16_kernel<<<grid, 128, kGemmSmem, st>>>(g);
+  if (used > 1) {
+    note_launches(1, st);
+    splitk_reduce_kernel<<<blocks_for((int64_t)M * N, 256), 256, 0, st>>>(g, used);
+  }
+}
+
+// After a synchronisation: RF_E_TIMEOUT (and the flag cleared) if a GEMM gave
+// up waiting for its tensor-core work since the last check.
+rf_status gemm_status(const char* what) {
+  int flag = 0;
+  if (!cuda_ok(cudaMemcpyFromSymbol(&flag, g_gemm_timeout, sizeof(int)), what)) return RF_E_CUDA;
+  if (!flag) return RF_OK;
+  const int zero = 0;
+  cudaMemcpyToSymbol(g_gemm_timeout, &zero, sizeof(int));
+  set_error(std::string(what) + ": a GEMM's wait for its tensor-core work gave up");
+  return RF_E_TIMEOUT;
 }
 
 }  // namespace rf
@@ -241,6 +363,7 @@ struct rf_mlp {
   DevBuf params, grads, m, v;
   DevBuf acts, zs, dbuf, dbuf2, y, t_std, loss, idx, xb, tb, mean, sd, scale, shift;
   DevBuf pred_h, pred_y;  // rf_mlp_predict: histograms and outputs of the sets
+  DevBuf splitk;          // partial tiles of the split-K GEMMs
   int cap = 0;  // batch capacity of the activation buffers
   int64_t step = 0;
   bool has_affine = false;
@@ -258,6 +381,12 @@ bool mlp_reserve(rf_mlp* n, int batch) {
   }
   int wmax = *std::max_element(n->dims.begin(), n->dims.end());
   const int nout = n->dims.back();
+  size_t ws = 0;  // the split-K GEMMs' partial tiles: forward, weight gradient, input gradient
+  for (size_t l = 0; l + 1 < n->dims.size(); ++l) {
+    const int ni = n->dims[l], no = n->dims[l + 1];
+    ws = std::max({ws, gemm_ws_floats(batch, no, ni), gemm_ws_floats(ni, no, batch), gemm_ws_floats(batch, ni, no)});
+  }
+  if (ws && !n->splitk.ensure(sizeof(float) * ws)) return false;
   bool ok = n->acts.ensure(sizeof(float) * act) && n->zs.ensure(sizeof(float) * z) &&
             n->dbuf.ensure(sizeof(float) * (size_t)batch * wmax) && n->dbuf2.ensure(sizeof(float) * (size_t)batch * wmax) &&
             n->y.ensure(sizeof(float) * (size_t)batch * nout) && n->t_std.ensure(sizeof(float) * (size_t)batch * nout) &&
@@ -282,7 +411,7 @@ void mlp_forward(rf_mlp* n, const float* x, int batch, cudaStream_t st) {
     float* a_in = acts + ao;
     float* out = (l == L - 1) ? (float*)n->y.p : acts + ao + (int64_t)batch * ni;
     gemm_bf16(a_in, ni, false, P + n->w_off[l], no, false, out, no, batch, no, ni, P + n->b_off[l], zs + zo,
-              l < L - 1, st);
+              l < L - 1, (float*)n->splitk.p, n->splitk.bytes / sizeof(float), st);
     ao += (int64_t)batch * ni;
     zo += (int64_t)batch * no;
   }
@@ -313,12 +442,14 @@ void mlp_backward(rf_mlp* n, int batch, cudaStream_t st) {
       gelu_backward_kernel<<<blocks_for(cnt, 256), 256, 0, st>>>(d, zs + zo[l], cnt);
     }
     // dW = a_in^T dZ  (ni x no), db = column sums of dZ
-    gemm_bf16(acts + ao[l], ni, true, d, no, false, G + n->w_off[l], no, ni, no, batch, nullptr, nullptr, false, st);
+    gemm_bf16(acts + ao[l], ni, true, d, no, false, G + n->w_off[l], no, ni, no, batch, nullptr, nullptr, false,
+              (float*)n->splitk.p, n->splitk.bytes / sizeof(float), st);
     note_launches(1, st);
     colsum_kernel<<<blocks_for(no, 128), 128, 0, st>>>(d, batch, no, G + n->b_off[l]);
     if (l > 0) {
       // dA_in = dZ W^T  (batch x ni)
-      gemm_bf16(d, no, false, P + n->w_off[l], no, true, d2, ni, batch, ni, no, nullptr, nullptr, false, st);
+      gemm_bf16(d, no, false, P + n->w_off[l], no, true, d2, ni, batch, ni, no, nullptr, nullptr, false,
+                (float*)n->splitk.p, n->splitk.bytes / sizeof(float), st);
       std::swap(d, d2);
     }
   }
@@ -441,6 +572,7 @@ rf_status rf_mlp_grad(rf_mlp* n, const float* d_x, const float* d_t, int32_t bat
     if (!cuda_ok(cudaMemcpyAsync(loss, n->loss.p, sizeof(float), cudaMemcpyDeviceToHost, st), "loss") ||
         !cuda_ok(cudaStreamSynchronize(st), "loss"))
       return RF_E_CUDA;
+    return gemm_status("rf_mlp_grad");
   }
   return RF_OK;
 }
@@ -503,6 +635,8 @@ rf_status rf_mlp_train(rf_mlp* n, const float* d_x, const float* d_t, int32_t ro
       cudaMemcpyAsync(&losses[s], n->loss.p, sizeof(float), cudaMemcpyDeviceToHost, 0);
     }
     if (!cuda_ok(cudaDeviceSynchronize(), "rf_mlp_train")) return RF_E_CUDA;
+    const rf_status gs = gemm_status("rf_mlp_train");
+    if (gs != RF_OK) return gs;
     for (float l : losses) sum += l;
     last_epoch = steps_per_epoch > 0 ? sum / steps_per_epoch : 0.0;
   }
@@ -608,6 +742,8 @@ extern "C" rf_status rf_mlp_predict(rf_mlp* n, const rf_model* m, const rf_data*
   std::vector<float> y((size_t)S * no);
   if (!cuda_ok(cudaMemcpy(y.data(), n->pred_y.p, sizeof(float) * y.size(), cudaMemcpyDeviceToHost), "rf_mlp_predict"))
     return RF_E_CUDA;
+  st = gemm_status("rf_mlp_predict");
+  if (st != RF_OK) return st;
   // A start on (or beyond) a bound sits where the fit's bound transform is
   // stationary (d theta / d phi = 0): that parameter barely moves.  Bounded
   // predictions are kept kStartMargin of the range inside the bounds.
