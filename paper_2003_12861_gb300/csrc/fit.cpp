@@ -438,8 +438,7 @@ namespace {
 // parameter point, event pass and step, the step compacting the next
 // pass's plan to the sets still going; between launches the host only
 // reads the phases (and captures the rounds again, with smaller launch
-// shapes, once the sets fit the block-per-set parameter point or the items
-// have shrunk 4-fold).  The states come back at the end (th and jc
+// shapes, once the items have shrunk 4-fold).  The states come back at the end (th and jc
 // refreshed for any problem not done).  Every problem takes the same trial
 // points as in host rounds: the step is the same code, rounding the same
 // way (fit_step.h), and a set's pass result does not depend on the plan.
@@ -501,9 +500,7 @@ rf_status device_rounds(DeviceSteps& dv, const std::vector<int32_t>& active, std
   for (int it = 0; it < max_launches && !going.empty(); ++it) {
     int32_t items = 0;
     for (int i : going) items += chunks[i];
-    const bool block_k1 = (int)going.size() <= kBlockK1MaxSets;
-    const bool captured_block = ev.r_cap_sets <= kBlockK1MaxSets;
-    if (!ev.r_exec || (block_k1 && !captured_block) || 4 * items < ev.r_cap_items) {
+    if (!ev.r_exec || 4 * items < ev.r_cap_items) {
       const rf_status s = ev.capture_rounds(n, (int32_t)going.size(), items, tol, max_evals);
       if (s != RF_OK) return s;
     }

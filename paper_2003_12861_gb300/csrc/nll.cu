@@ -1229,7 +1229,9 @@ void launch_param_point(const Program& P, const Pass& pass, cudaStream_t st) {
     param_point_block_kernel<true><<<pass.n_active, kK1Warps * 32, 0, st>>>(P, pass);
     return;
   }
-  if (pass.n_active > 0 && pass.n_active <= kBlockK1MaxSets) {
+  // In the rounds of a device-resident fit (dyn counts) nothing runs beside
+  // K1, and a block per set finishes sooner for any number of sets.
+  if (pass.n_active > 0 && (pass.n_active <= kBlockK1MaxSets || pass.dyn)) {
     param_point_block_kernel<false><<<pass.n_active, kK1Warps * 32, 0, st>>>(P, pass);
     return;
   }
