@@ -7,11 +7,12 @@
 // 16, 2005) near a minimum.
 //
 // Both sides must produce the same trial points bit for bit: the code below
-// uses only IEEE-rounded operations (+ - * / sqrt, comparisons, rint) and
-// its own sine and cosine, and both translation units that include it are
-// compiled without floating-point contraction (host -ffp-contract=off,
-// device --fmad=false), so every expression rounds the same way on the CPU
-// and on the GPU.
+// uses only correctly rounded operations (+ - * / sqrt, fma, comparisons,
+// rint) and its own sine and cosine, and both translation units that
+// include it are compiled without floating-point contraction (host
+// -ffp-contract=off, device --fmad=false), so every expression rounds the
+// same way on the CPU and on the GPU; the fused multiply-adds are written
+// out (fma), which halves the FP64 instructions of the sums on the device.
 #pragma once
 
 #include <math.h>
@@ -88,7 +89,7 @@ struct SeqLoop {
 
 RF_HD double dot(const double* a, const double* b, int n) {
   double s = 0.0;
-  for (int i = 0; i < n; ++i) s += a[i] * b[i];
+  for (int i = 0; i < n; ++i) s = fma(a[i], b[i], s);
   return s;
 }
 
@@ -98,7 +99,7 @@ RF_HD void mat_vec(const double* M, const double* v, double* r, int n) {
   L::sync();
   for (int i = L::first(); i < n; i += L::step()) {
     double s = 0.0;
-    for (int j = 0; j < n; ++j) s += M[i * n + j] * v[j];
+    for (int j = 0; j < n; ++j) s = fma(M[i * n + j], v[j], s);
     r[i] = s;
   }
   L::sync();
@@ -125,25 +126,25 @@ RF_HD void sin_cos(double x, double* s_out, double* c_out) {
   // 1/n! (correctly rounded) for the sine (odd n from 3) and cosine (even n
   // from 4)
   double ps = 0x1.2f49b46814157p-57;  // 1/19!
-  ps = ps * r2 - 0x1.952c77030ad4ap-49;  // 1/17!
-  ps = ps * r2 + 0x1.ae7f3e733b81fp-41;  // 1/15!
-  ps = ps * r2 - 0x1.6124613a86d09p-33;  // 1/13!
-  ps = ps * r2 + 0x1.ae64567f544e4p-26;  // 1/11!
-  ps = ps * r2 - 0x1.71de3a556c734p-19;  // 1/9!
-  ps = ps * r2 + 0x1.a01a01a01a01ap-13;  // 1/7!
-  ps = ps * r2 - 0x1.1111111111111p-7;  // 1/5!
-  ps = ps * r2 + 0x1.5555555555555p-3;  // 1/3!
-  const double sn = r - (r * r2) * ps;
+  ps = fma(ps, r2, -0x1.952c77030ad4ap-49);  // 1/17!
+  ps = fma(ps, r2, 0x1.ae7f3e733b81fp-41);  // 1/15!
+  ps = fma(ps, r2, -0x1.6124613a86d09p-33);  // 1/13!
+  ps = fma(ps, r2, 0x1.ae64567f544e4p-26);  // 1/11!
+  ps = fma(ps, r2, -0x1.71de3a556c734p-19);  // 1/9!
+  ps = fma(ps, r2, 0x1.a01a01a01a01ap-13);  // 1/7!
+  ps = fma(ps, r2, -0x1.1111111111111p-7);  // 1/5!
+  ps = fma(ps, r2, 0x1.5555555555555p-3);  // 1/3!
+  const double sn = fma(-(r * r2), ps, r);
   double pc = 0x1.e542ba4020225p-62;  // 1/20!
-  pc = pc * r2 - 0x1.6827863b97d97p-53;  // 1/18!
-  pc = pc * r2 + 0x1.ae7f3e733b81fp-45;  // 1/16!
-  pc = pc * r2 - 0x1.93974a8c07c9dp-37;  // 1/14!
-  pc = pc * r2 + 0x1.1eed8eff8d898p-29;  // 1/12!
-  pc = pc * r2 - 0x1.27e4fb7789f5cp-22;  // 1/10!
-  pc = pc * r2 + 0x1.a01a01a01a01ap-16;  // 1/8!
-  pc = pc * r2 - 0x1.6c16c16c16c17p-10;  // 1/6!
-  pc = pc * r2 + 0x1.5555555555555p-5;  // 1/4!
-  const double cs = (1.0 - 0.5 * r2) + (r2 * r2) * pc;
+  pc = fma(pc, r2, -0x1.6827863b97d97p-53);  // 1/18!
+  pc = fma(pc, r2, 0x1.ae7f3e733b81fp-45);  // 1/16!
+  pc = fma(pc, r2, -0x1.93974a8c07c9dp-37);  // 1/14!
+  pc = fma(pc, r2, 0x1.1eed8eff8d898p-29);  // 1/12!
+  pc = fma(pc, r2, -0x1.27e4fb7789f5cp-22);  // 1/10!
+  pc = fma(pc, r2, 0x1.a01a01a01a01ap-16);  // 1/8!
+  pc = fma(pc, r2, -0x1.6c16c16c16c17p-10);  // 1/6!
+  pc = fma(pc, r2, 0x1.5555555555555p-5);  // 1/4!
+  const double cs = fma(r2 * r2, pc, fma(-0.5, r2, 1.0));
   const int q = (int)(long long)k & 3;
   double s = sn, c = cs;
   if (q == 1) {
@@ -209,7 +210,7 @@ template <class L>
 RF_HD void set_trial(int P, State& c, const Vecs& v, double a) {
   c.a_cur = a;
   L::sync();
-  for (int k = L::first(); k < P; k += L::step()) v.trial[k] = v.x[k] + a * v.p[k];
+  for (int k = L::first(); k < P; k += L::step()) v.trial[k] = fma(a, v.p[k], v.x[k]);
   L::sync();
 }
 
@@ -255,7 +256,7 @@ template <class L>
 RF_HD double edm(int P, const Vecs& v) {
   mat_vec<L>(v.H, v.g, v.w_r, P);
   double e = 0.0;
-  for (int i = 0; i < P; ++i) e += 0.5 * v.g[i] * v.w_r[i];
+  for (int i = 0; i < P; ++i) e = fma(0.5 * v.g[i], v.w_r[i], e);
   return e;
 }
 
@@ -288,7 +289,8 @@ RF_HD void accept(int P, State& c, const Vecs& v, double a, double fa, const dou
     L::sync();
     for (int e = L::first(); e < P * P; e += L::step()) {
       const int i = e / P, j = e % P;
-      v.H[e] += -rho * (Hy[i] * s[j] + s[i] * Hy[j]) + b * s[i] * s[j];
+      const double u = fma(Hy[i], s[j], s[i] * Hy[j]);
+      v.H[e] = fma(b * s[i], s[j], fma(-rho, u, v.H[e]));
     }
     L::sync();
   }
