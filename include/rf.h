@@ -305,8 +305,12 @@ rf_status rf_hist64(const rf_model* m, const rf_data* d, int32_t col, float* d_o
  * component; this is the learned-start configuration: n_in inputs,
  * n_hidden_layers hidden layers of n_hidden GELU (erf form) units, n_out
  * linear outputs.  GEMM operands are rounded to BF16 (nearest even) and
- * multiplied on the tensor cores with FP32 accumulation; master weights are
- * FP32.  Weights start Uniform(+-1/sqrt(fan_in)) from `seed`, biases 0.
+ * multiplied on the fifth-generation tensor cores (tcgen05) with FP32
+ * accumulation in tensor memory; master weights are FP32.  A GEMM whose
+ * wait for its tensor-core work gives up (bounded) makes the next
+ * synchronous call (rf_mlp_grad with a loss, rf_mlp_train, rf_mlp_predict)
+ * return RF_E_TIMEOUT.  Weights start Uniform(+-1/sqrt(fan_in)) from
+ * `seed`, biases 0.
  * Parameters (flat FP32): per layer W[n_in x n_out] row-major, then b[n_out]. */
 rf_status rf_mlp_create(int32_t n_in, int32_t n_hidden, int32_t n_hidden_layers, int32_t n_out, uint64_t seed,
                         rf_mlp** out);
