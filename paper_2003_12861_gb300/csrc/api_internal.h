@@ -106,8 +106,7 @@ rf_status fit_batch(int S, int P, const double* lo, const double* hi, const doub
 // done, writes its next trial point to theta[set]; phase[i] gets its phase.
 // The last block to finish then compacts the plan of the next pass: the
 // sets still going (increasing) into plan_sets, their (set, chunk) items
-// into plan_items (item_off: n ints of scratch), the counts into dyn =
-// {sets, items}.  Skipped when dyn reads no active set.  ticket: a counter
+// into plan_items, the counts into dyn = {sets, items}.  Skipped when dyn reads no active set.  ticket: a counter
 // at zero, left at zero.
 struct FitStepArgs {
   double* state;
@@ -123,7 +122,6 @@ struct FitStepArgs {
   int32_t* phase;
   int32_t* plan_sets;
   int2* plan_items;
-  int32_t* item_off;  // n: scratch of the compaction
   int32_t* dyn;
   int32_t* ticket;
 };

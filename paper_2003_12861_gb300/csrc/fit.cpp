@@ -250,7 +250,7 @@ struct Evaluator {
   // counts and phases, the plan counts {sets, items} and the step's ticket,
   // the bounds (lo, hi, bounded), the plan the step compacts, the graph and
   // the plan size it was captured for
-  DevBuf r_state, r_sets, r_chunks, r_phase, r_dyn, r_bounds, r_off;
+  DevBuf r_state, r_sets, r_chunks, r_phase, r_dyn, r_bounds;
   HostBuf h_phase;
   Plan r_plan;
   cudaGraphExec_t r_exec = nullptr;
@@ -395,7 +395,6 @@ struct Evaluator {
     a.phase = (int32_t*)r_phase.p;
     a.plan_sets = (int32_t*)r_plan.sets.p;
     a.plan_items = (int2*)r_plan.items.p;
-    a.item_off = (int32_t*)r_off.p;
     a.dyn = dyn;
     a.ticket = dyn + 2;
     cudaGraph_t graph = nullptr;
@@ -476,7 +475,6 @@ rf_status device_rounds(DeviceSteps& dv, const std::vector<int32_t>& active, std
   const int32_t dyn0[3] = {ev.r_plan.n_active, ev.r_plan.n_items, 0};
   if (!ev.r_state.ensure(sizeof(double) * rec.size()) || !ev.r_sets.ensure(sizeof(int32_t) * n) ||
       !ev.r_chunks.ensure(sizeof(int32_t) * n) || !ev.r_phase.ensure(sizeof(int32_t) * n) ||
-      !ev.r_off.ensure(sizeof(int32_t) * n) ||
       !ev.r_dyn.ensure(sizeof(dyn0)) || !ev.r_bounds.ensure(bounds.size()) ||
       !ev.h_phase.ensure(sizeof(int32_t) * n))
     return RF_E_OOM;

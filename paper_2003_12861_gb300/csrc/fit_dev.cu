@@ -22,6 +22,8 @@ struct WarpLoop {
 
 constexpr int kStepWarps = 4;
 constexpr int kStepThreads = kStepWarps * 32;
+constexpr int kBigSets = 256;
+constexpr int kStageSets = 2048;
 
 // Shared doubles per warp: the set's record, then ga, w_s, w_y, w_hy, w_r.
 __host__ __device__ inline int step_smem_words(int P) { return qn::tail_record_words(P) + 5 * P; }
@@ -33,6 +35,9 @@ __global__ void __launch_bounds__(kStepThreads) fit_step_kernel(FitStepArgs a) {
   extern __shared__ double smem[];
   __shared__ int last;
   __shared__ int scan_a[kStepThreads], scan_i[kStepThreads];
+  __shared__ int n_big;
+  __shared__ int2 big[kBigSets];  // (set index, first item) of sets of more than 32 chunks
+  __shared__ int st_phase[kStageSets], st_chunks[kStageSets], st_set[kStageSets];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int P = kP ? kP : a.P, W = qn::tail_record_words(P);
   if (a.dyn[0] == 0) return;  // every set is done: nothing to step or plan
@@ -70,13 +75,24 @@ __global__ void __launch_bounds__(kStepThreads) fit_step_kernel(FitStepArgs a) {
   __syncthreads();
   if (!last) return;
   __threadfence();
+  // the sets' phases, chunk counts and dataset sets, staged in shared
+  // memory by coalesced loads when they fit
+  const bool staged = a.n <= kStageSets;
+  if (staged) {
+    for (int j = threadIdx.x; j < a.n; j += kStepThreads) {
+      st_phase[j] = __ldcg(a.phase + j);
+      st_chunks[j] = a.chunks[j];
+      st_set[j] = a.set_of[j];
+    }
+    __syncthreads();
+  }
   const int per = (a.n + kStepThreads - 1) / kStepThreads;
   const int b0 = min(a.n, (int)threadIdx.x * per), b1 = min(a.n, b0 + per);
   int na = 0, ni = 0;
   for (int j = b0; j < b1; ++j)
-    if (__ldcg(a.phase + j) != qn::DONE) {
+    if ((staged ? st_phase[j] : __ldcg(a.phase + j)) != qn::DONE) {
       ++na;
-      ni += a.chunks[j];
+      ni += staged ? st_chunks[j] : a.chunks[j];
     }
   scan_a[threadIdx.x] = na;
   scan_i[threadIdx.x] = ni;
@@ -89,13 +105,27 @@ __global__ void __launch_bounds__(kStepThreads) fit_step_kernel(FitStepArgs a) {
     scan_i[threadIdx.x] += xi;
     __syncthreads();
   }
+  // each thread writes its sets and the items of its sets of up to 32
+  // chunks; larger sets go to a list whose items the warps write, a set per
+  // warp, its chunks across the lanes
+  if (threadIdx.x == 0) n_big = 0;
+  __syncthreads();
   int pa = scan_a[threadIdx.x] - na, pi = scan_i[threadIdx.x] - ni;
   for (int j = b0; j < b1; ++j) {
-    const bool going = __ldcg(a.phase + j) != qn::DONE;
-    a.item_off[j] = going ? pi : -1;
-    if (!going) continue;
-    a.plan_sets[pa++] = a.set_of[j];
-    pi += a.chunks[j];
+    if ((staged ? st_phase[j] : __ldcg(a.phase + j)) == qn::DONE) continue;
+    const int s = staged ? st_set[j] : a.set_of[j], c = staged ? st_chunks[j] : a.chunks[j];
+    a.plan_sets[pa++] = s;
+    if (c <= 32) {
+      for (int k = 0; k < c; ++k) a.plan_items[pi + k] = make_int2(s, k);
+    } else {
+      const int b = atomicAdd(&n_big, 1);
+      if (b < kBigSets) {
+        big[b] = make_int2(j, pi);
+      } else {
+        for (int k = 0; k < c; ++k) a.plan_items[pi + k] = make_int2(s, k);
+      }
+    }
+    pi += c;
   }
   if (threadIdx.x == kStepThreads - 1) {
     a.dyn[0] = scan_a[threadIdx.x];
@@ -103,11 +133,9 @@ __global__ void __launch_bounds__(kStepThreads) fit_step_kernel(FitStepArgs a) {
     *a.ticket = 0;
   }
   __syncthreads();
-  // the items, a set per warp at a time, its chunks across the lanes
-  for (int j = warp; j < a.n; j += kStepWarps) {
-    const int off = a.item_off[j];
-    if (off < 0) continue;
-    const int s = a.set_of[j];
+  const int nb = n_big < kBigSets ? n_big : kBigSets;
+  for (int b = warp; b < nb; b += kStepWarps) {
+    const int j = big[b].x, off = big[b].y, s = a.set_of[j];
     for (int k = lane; k < a.chunks[j]; k += 32) a.plan_items[off + k] = make_int2(s, k);
   }
 }
