@@ -195,6 +195,22 @@ def test_parameter_point_variants_agree_bitwise():
             assert sub["n_evals"][j] == allsets["n_evals"][s] == 2, (i, s)
 
 
+def test_device_rounds_generic_and_program_models():
+    """The device rounds through the FP64 interpreter (the decay model with
+    its SUM operands swapped) and through a model with a program node (its
+    normalisation by quadrature in K1): bitwise the host steps' fits."""
+    cases = ((W.decay_generic_model(), W.DECAY_GENERIC_TRUE, 41), (W.expr_gauss_poly1_model(), W.GAUSS_POLY1_TRUE, 43))
+    for spec, theta, seed in cases:
+        m = api.Model.from_spec(spec)
+        S = 24
+        d = api.generate_toys(m, theta, W.SEED_BASE + seed, W.toy_mean_sizes(S, seed, 2e3, 2e4), poisson=True)
+        dev = api.fit(m, d, tol_edm=1e-9, want_cov=False, device_steps=True)
+        host = api.fit(m, d, tol_edm=1e-9, want_cov=False, device_steps=False)
+        assert (dev["status"] == L.RF_OK).mean() > 0.9, dev["status"]
+        for k in ("theta", "nll", "n_evals", "status"):
+            assert np.array_equal(dev[k], host[k]), (k, seed)
+
+
 def test_device_rounds_product_model_fp32():
     # 12 free parameters, three FP32 columns: the device rounds of the
     # product model's fits equal host steps bit for bit
