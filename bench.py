@@ -2,7 +2,7 @@
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--workload prod3_1e8_f32|decay_1e7|decay_generic_1e7|decay_toys_4096|...]
-                    [--no-extras] [--no-cpu-baseline]
+                    [--no-extras] [--no-cpu-baseline] [--blocks-per-sm B]
 
 Default workload (the headline: NLL + gradient over 1e8 events): events/s
 of one NLL + gradient pass over the 3-observable product model
@@ -33,6 +33,8 @@ collective on the data path); rank 0 prints one JSON line (no extras).
 (1 + 12) x 2 compensated sums + the rank-ordered exact merge.
 --impl reference times the CPU oracle (single thread, the machine's host cores)
 on a bounded sample of the same workload, with the same metric.
+--blocks-per-sm pins the event kernel's launch shape instead of the
+autotuner's winner (for profiling runs, whose timings the profiler distorts).
 """
 from __future__ import annotations
 
