@@ -1215,14 +1215,14 @@ int orc_fit(const orc_model* h, const double* const* cols, int64_t N, const doub
     }
     // N&W Sec. 3.5 leave the first trial step to the implementation; with a
     // fresh (identity) H the step -g carries the gradient's units, so its
-    // first trial is limited to 0.2 in every internal coordinate (the sin
+    // first trial is limited to 0.5 in every internal coordinate (the sin
     // transform makes a bounded coordinate periodic: a longer step can land
     // anywhere in the parameter's range).  Later steps try 1 first (Alg. 6.1).
     double a1 = 1.0;
     if (first) {
       double pm = 0.0;
       for (int k = 0; k < P; ++k) pm = std::max(pm, std::fabs(p[k]));
-      if (pm > 0.0) a1 = std::min(1.0, 0.2 / pm);
+      if (pm > 0.0) a1 = std::min(1.0, 0.5 / pm);
     }
     double fn;
     std::vector<double> gn(P);

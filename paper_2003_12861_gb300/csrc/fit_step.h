@@ -238,10 +238,10 @@ RF_HD void new_direction(int P, State& c, const Vecs& v) {
     c.d0 = dot(v.g, v.p, P);
   }
   double a1 = 1.0;
-  if (c.first_step) {  // keep the first step of a fresh H within 0.2 (internal units)
+  if (c.first_step) {  // keep the first step of a fresh H within 0.5 (internal units)
     double pm = 0.0;
     for (int k = 0; k < P; ++k) pm = dmax(pm, fabs(v.p[k]));
-    if (pm > 0.0) a1 = dmin(1.0, 0.2 / pm);
+    if (pm > 0.0) a1 = dmin(1.0, 0.5 / pm);
   }
   c.a_prev = 0.0;
   c.f_prev = c.f;
