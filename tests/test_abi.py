@@ -214,3 +214,17 @@ def test_launch_shape_is_128_threads_with_tunable_blocks_per_sm():
             m.set_launch(t, 4)
     with pytest.raises(L.RFError):
         m.set_launch(128, 33)
+
+
+def test_fit_options_layout_matches_the_header():
+    """rf_fit_opts as include/rf.h lays it out: tol_edm, max_evals,
+    want_cov, no_graph, host_steps (the binding's ctypes struct is what the
+    library reads)."""
+    src = open(os.path.join(ROOT, "include", "rf.h")).read()
+    body = src[src.index("typedef struct {", src.index("/* ------------------------------------------------------------------- fits */")):]
+    body = body[: body.index("} rf_fit_opts;")]
+    fields = [ln.split(";")[0].split()[-1] for ln in body.splitlines() if ";" in ln and ln.strip().split()[0] in ("double", "int32_t")]
+    assert fields == ["tol_edm", "max_evals", "want_cov", "no_graph", "host_steps"], fields
+    assert [f[0] for f in L.rf_fit_opts._fields_] == fields
+    assert C.sizeof(L.rf_fit_opts) == 24
+    assert L.rf_fit_opts.host_steps.offset == 20
