@@ -126,6 +126,16 @@ __device__ __forceinline__ ff ff_fma(ff a, ff b, ff c) {
   lo = __fadd_rn(lo, __fadd_rn(c.lo, s.lo));
   return fast_two_sum(s.hi, lo);
 }
+// ff_fma without the final renormalisation, for an argument of the
+// exponential only: its reduction adds the low word by an exact two-sum, so
+// a low word that cancellation has left as large as the high word costs
+// nothing.  (A product would see that low word rounded to a float.)
+__device__ __forceinline__ ff ff_fma_u(ff a, ff b, ff c) {
+  const ff p = two_prod(a.hi, b.hi);
+  const ff s = two_sum(p.hi, c.hi);
+  const float lo = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, p.lo));
+  return {s.hi, __fadd_rn(lo, __fadd_rn(c.lo, s.lo))};
+}
 __device__ __forceinline__ ff ff_sqr(ff a) {
   ff p = two_prod(a.hi, a.hi);
   p.lo = __fmaf_rn(__fmul_rn(2.0f, a.hi), a.lo, p.lo);
@@ -176,6 +186,13 @@ __device__ __forceinline__ ff ff_fma(ff a, float b, ff c) {
   return fast_two_sum(s.hi, lo);
 }
 __device__ __forceinline__ ff ff_fma(float a, ff b, ff c) { return ff_fma(b, a, c); }
+__device__ __forceinline__ ff ff_fma_u(ff a, float b, ff c) {
+  const ff p = two_prod(a.hi, b);
+  const ff s = two_sum(p.hi, c.hi);
+  const float lo = __fmaf_rn(a.lo, b, p.lo);
+  return {s.hi, __fadd_rn(lo, __fadd_rn(c.lo, s.lo))};
+}
+__device__ __forceinline__ ff ff_fma_u(float a, ff b, ff c) { return ff_fma_u(b, a, c); }
 __device__ __forceinline__ void ff_acc_mul(ff& acc, ff a, float b) {
   const ff p = two_prod(a.hi, b);
   const ff s = two_sum(acc.hi, p.hi);

@@ -271,7 +271,7 @@ __device__ __forceinline__ ff ff_exp0(const FFTables& T, ff x, bool& ok, bool& d
 template <bool kSlow, class OT>
 __device__ __forceinline__ ff decay_shape(const FFTables& T, const float* k, OT t, ff* R, ff* uo, bool& ok,
                                           bool& dropped) {
-  const ff logv = ff_fma(ff_neg(t), ldc(k, 2), ldc(k, 0));
+  const ff logv = ff_fma_u(ff_neg(t), ldc(k, 2), ldc(k, 0));
   if (!kSlow) {
     *R = {0.0f, 0.0f};
     return ff_exp0(T, logv, ok, dropped);
@@ -282,7 +282,7 @@ __device__ __forceinline__ ff decay_shape(const FFTables& T, const float* k, OT 
   const bool neg = z.hi < 0.0f;
   const ff y = neg ? ff_neg(z) : z;
   const ff ex = ff_erfcx(T, y, ok);
-  const ff G = ff_exp0(T, ff_fma(ff_scale(u, -0.5f), u, ldc(k, 20)), ok, dropped);
+  const ff G = ff_exp0(T, ff_fma_u(ff_scale(u, -0.5f), u, ldc(k, 20)), ok, dropped);
   const ff half_g_ex = ff_scale(ff_mul_u(G, ex), 0.5f);
   const ff two_over_sqrtpi = {kTwoInvSqrtPi_hi, kTwoInvSqrtPi_lo};
   if (!neg) {
@@ -402,7 +402,7 @@ __device__ __forceinline__ int ff_event(const FFTables& T, const float* k, const
   } else if constexpr (kShape == SHAPE_SUM_GAUSS_POLY1) {
     const auto x = obs_value<kF32>(in.x[0]);
     const ff u = ff_mul(ff_sub(x, ldc(k, 0)), ldc(k, 2));
-    const ff g = ff_exp0(T, ff_fma(ff_scale(u, -0.5f), u, ldc(k, 14)), ok, dropped);
+    const ff g = ff_exp0(T, ff_fma_u(ff_scale(u, -0.5f), u, ldc(k, 14)), ok, dropped);
     const ff p = ff_fma(ldc(k, 4), g, ff_fma(ldc(k, 8), x, ldc(k, 6)));
     ok = ok && p.hi > 7.9e-31f && p.hi < 1.2e30f;
     if (!ok || (dropped && p.hi < 1e-14f)) return 2;
@@ -435,7 +435,7 @@ __device__ __forceinline__ int ff_event(const FFTables& T, const float* k, const
       const auto c = obs_value<kF32>(in.x[2]);
       const ff um = ff_mul(ff_sub(m, ldc(k, 0)), ldc(k, 2));
       bool dm = false;
-      const ff g = ff_exp0(T, ff_fma(ff_scale(um, -0.5f), um, ldc(k, 14)), ok, dm);
+      const ff g = ff_exp0(T, ff_fma_u(ff_scale(um, -0.5f), um, ldc(k, 14)), ok, dm);
       const ff ym = ff_fma(m, ldc(k, 10), ff_neg(ldc(k, 12)));
       const ff pm = ff_fma(ldc(k, 4), g, ff_fma(ldc(k, 8), ym, ldc(k, 6)));
       const ff pa = ff_fma(ff_fma(ldc(k, 42), c, ldc(k, 40)), c, ldc(k, 38));
@@ -448,7 +448,7 @@ __device__ __forceinline__ int ff_event(const FFTables& T, const float* k, const
       const ff vs = slow ? ff{0.0f, 0.0f} : vsf;
       const ff pt = slow ? ff{1.0f, 0.0f} : ptf;
       okd = slow || (okd && !(dropped && pt.hi < 1e-14f));
-      const ff p = ff_mul(ff_mul(pm, pt), pa);
+      const ff p = ff_mul_u(ff_mul_u(pm, pt), pa);  // logprod_mul takes it unnormalised
       ok = ok && okd && p.hi > 7.9e-31f && p.hi < 1.2e30f && pm.hi > 7.9e-31f && pa.hi > 7.9e-31f &&
            pm.hi < 1.2e30f && pa.hi < 1.2e30f && pt.hi < 1.2e30f;
       if (!ok || (dm && pm.hi < 1e-14f)) return 2;
