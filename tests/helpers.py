@@ -1,6 +1,4 @@
 """Shared test helpers: datasets from the oracle's generator, tolerance checks."""
-import numpy as np
-
 from paper_2003_12861_gb300 import workloads as W
 
 TRUE = {"gauss_poly1_model": W.GAUSS_POLY1_TRUE, "decay_model": W.DECAY_TRUE, "prod3_model": W.PROD3_TRUE}

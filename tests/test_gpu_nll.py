@@ -7,7 +7,7 @@ import pytest
 from paper_2003_12861_gb300 import _lib as L
 from paper_2003_12861_gb300 import api
 from paper_2003_12861_gb300 import workloads as W
-from paper_2003_12861_gb300.workloads import Node, ModelSpec
+from paper_2003_12861_gb300.workloads import Node
 
 from helpers import TRUE, check_nll, oracle_data
 

@@ -2,7 +2,6 @@
 against torch's exact GELU, the backward formulas against central finite
 differences (roundings off), Adam against torch.optim.Adam."""
 import numpy as np
-import pytest
 import torch
 
 from oracle import mlp as M
