@@ -243,7 +243,7 @@ struct Evaluator {
   };
   const rf_model* m;
   rf_data* d;
-  cudaStream_t st[2] = {nullptr, nullptr};
+  cudaStream_t streams[2] = {nullptr, nullptr};
   bool use_graph = true;
   Group grp[4];  // 0, 1: the halves; 2: whole-batch passes; 3: device-resident rounds
   // device-resident rounds: the sets' records, their dataset sets, chunk
@@ -258,14 +258,14 @@ struct Evaluator {
 
   Evaluator(const rf_model* mm, rf_data* dd, bool graph) : m(mm), d(dd), use_graph(graph) {}
   ~Evaluator() {
-    for (cudaStream_t s : st)
+    for (cudaStream_t s : streams)
       if (s) cudaStreamSynchronize(s);
     for (Group& G : grp) {
       if (G.exec) cudaGraphExecDestroy(G.exec);
       if (G.done) cudaEventDestroy(G.done);
     }
     if (r_exec) cudaGraphExecDestroy(r_exec);
-    for (cudaStream_t s : st)
+    for (cudaStream_t s : streams)
       if (s) cudaStreamDestroy(s);
   }
 
@@ -302,7 +302,7 @@ struct Evaluator {
 
   rf_status capture(int g) {
     Group& G = grp[g];
-    cudaStream_t st = this->st[stream_of(g)];
+    cudaStream_t st = streams[stream_of(g)];
     if (G.exec) {
       cudaGraphExecDestroy(G.exec);
       G.exec = nullptr;
@@ -330,7 +330,7 @@ struct Evaluator {
     Group& G = grp[g];
     bool rebuilt = false;
     if (!replan(G, active, &rebuilt)) return RF_E_OOM;
-    cudaStream_t& st = this->st[stream_of(g)];
+    cudaStream_t& st = streams[stream_of(g)];
     if (!st && !cuda_ok(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking), "stream")) return RF_E_CUDA;
     if (!G.done && !cuda_ok(cudaEventCreateWithFlags(&G.done, cudaEventDisableTiming), "event")) return RF_E_CUDA;
     if (rebuilt || !G.exec) {
@@ -366,7 +366,7 @@ struct Evaluator {
   // n_sets sets and n_items items (at least the counts the rounds see);
   // ends with the phases' download.
   rf_status capture_rounds(int n, int32_t n_sets, int32_t n_items, double tol, int max_evals) {
-    cudaStream_t st = this->st[0];
+    cudaStream_t st = streams[0];
     if (r_exec) {
       cudaGraphExecDestroy(r_exec);
       r_exec = nullptr;
@@ -447,7 +447,7 @@ rf_status device_rounds(DeviceSteps& dv, const std::vector<int32_t>& active, std
   rf_data* d = ev.d;
   Workspace& w = d->ws;
   const int P = co.P, n = (int)active.size(), W = qn::tail_record_words(P);
-  cudaStream_t& st = ev.st[0];
+  cudaStream_t& st = ev.streams[0];
   if (!st && !cuda_ok(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking), "stream")) return RF_E_CUDA;
   std::vector<int32_t> sets(n), chunks(n), phase(n);
   for (int i = 0; i < n; ++i) {
