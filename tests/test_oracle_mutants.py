@@ -12,17 +12,22 @@ from pathlib import Path
 
 import pytest
 
+from paper_2003_12861_gb300 import workloads as W
+import test_oracle_binned as PB
+import test_oracle_expr as PE
+import test_oracle_extended as PX
+import test_oracle_mlp as PM
 import test_oracle_pins as P
 
 ORACLE = Path(__file__).resolve().parent.parent / "oracle"
 
 
-def load_mutant(tmp_path, old, new):
+def load_mutant(tmp_path, old, new, file="oracle.cpp"):
     d = tmp_path / "oracle_mutant"
     shutil.copytree(ORACLE, d, ignore=shutil.ignore_patterns("*.so", "*.tmp", "__pycache__"))
-    src = (d / "oracle.cpp").read_text()
+    src = (d / file).read_text()
     assert src.count(old) == 1, f"mutation site not unique: {old}"
-    (d / "oracle.cpp").write_text(src.replace(old, new))
+    (d / file).write_text(src.replace(old, new))
     name = f"oracle_mutant_{uuid.uuid4().hex}"
     spec = importlib.util.spec_from_file_location(name, d / "__init__.py", submodule_search_locations=[str(d)])
     mod = importlib.util.module_from_spec(spec)
@@ -100,12 +105,93 @@ MUTANTS = {
         "if (y < factor_density(m, nm, theta, fac[j], xv, val)) {",
         "if (y > factor_density(m, nm, theta, fac[j], xv, val)) {",
         lambda: [lambda m: P.test_generator_matches_pdf_histogram(m, "gauss_poly1_model")]),
+    # EXPR: the quotient rule with the sign of the divisor's term flipped
+    "expr_quotient_rule_sign": (
+        "for (int k = 0; k < np; ++k) a.d[k] = (a.d[k] - v * b.d[k]) / b.v;",
+        "for (int k = 0; k < np; ++k) a.d[k] = (a.d[k] + v * b.d[k]) / b.v;",
+        lambda: [lambda m: PE.test_expr_gaussian_equals_the_builtin_gaussian(m, W.GAUSS_POLY1_TRUE)]),
+    # EXPR: the power's derivative without its factor a^b
+    "expr_pow_derivative_factor": (
+        "a.d[k] = v * (b.d[k] * la + b.v * a.d[k] / a.v);", "a.d[k] = (b.d[k] * la + b.v * a.d[k] / a.v);",
+        lambda: [lambda m, a=a: PE.test_expr_normalisation_closed_form(m, a) for a in (0.7, 2.3)]),
+    # POISSON: the derivative of its mass with lambda's sign flipped
+    "poisson_norm_derivative_sign": (
+        "ds.add(pk * (k / lam - 1.0));", "ds.add(pk * (k / lam + 1.0));",
+        lambda: [PX.test_poisson_gradient_and_mle]),
+    # EXTEND: the extended term's log with the wrong sign
+    "extended_term_sign": (
+        "ext = nu - (double)N * std::log(nu);", "ext = nu + (double)N * std::log(nu);",
+        lambda: [PX.test_extended_term_and_closed_form_mle]),
+    # EXTEND: the yield's derivative with N / nu added instead of subtracted
+    "extended_derivative_sign": (
+        "sg[fi].add(-(1.0 - (double)N / nu));", "sg[fi].add(-(1.0 + (double)N / nu));",
+        lambda: [PX.test_extended_term_and_closed_form_mle]),
     # fitter: the bound transform mapping onto half of the range
     "fit_bound_transform_scale": (
         "th[k] = bounded[k] ? lo[k] + (hi[k] - lo[k]) * (std::sin(x[k]) + 1.0) * 0.5 : x[k];",
         "th[k] = bounded[k] ? lo[k] + (hi[k] - lo[k]) * (std::sin(x[k]) + 1.0) * 0.25 : x[k];",
         lambda: [P.test_fraction_only_fit_matches_bounded_scalar_minimiser, P.test_gaussian_mle_closed_form]),
 }
+
+
+# Slips in the Python oracles (binned likelihood, MLP): the pins' modules
+# import those oracles by name, so the case points that name at the copy.
+PY_MUTANTS = {
+    # binned: linear extrapolation of g beyond one sigma shifted by 2
+    "binned_extrapolation_offset": (
+        "binned.py", "return 2.0 * abs(alpha) - 1.0, 2.0 if alpha > 0 else -2.0",
+        "return 2.0 * abs(alpha) + 1.0, 2.0 if alpha > 0 else -2.0", PB, "B",
+        lambda: [PB.test_nominal_and_extrapolation] +
+        [lambda a=a: PB.test_interpolation_is_continuously_differentiable(a) for a in (-1.0, 1.0)]),
+    # binned: the normsys quadratic coefficient from the difference of the logs
+    "binned_normsys_coefficient": (
+        "binned.py", "b = 0.5 * (np.log(m.k_hi) + np.log(m.k_lo))", "b = 0.5 * (np.log(m.k_hi) - np.log(m.k_lo))",
+        PB, "B", lambda: [lambda a=a: PB.test_interpolation_reaches_the_variations_at_one_sigma(a) for a in (1.0, -1.0)]),
+    # binned: the histosys quadratic coefficient without the nominal subtracted
+    "binned_histosys_coefficient": (
+        "binned.py", "b = 0.5 * (np.asarray(m.h_hi) + np.asarray(m.h_lo)) - h",
+        "b = 0.5 * (np.asarray(m.h_hi) + np.asarray(m.h_lo))",
+        PB, "B", lambda: [lambda a=a: PB.test_interpolation_reaches_the_variations_at_one_sigma(a) for a in (1.0, -1.0)]),
+    # binned: the Poisson term's derivative weight with n / nu added
+    "binned_poisson_weight_sign": (
+        "binned.py", "w = 1.0 - n / nu", "w = 1.0 + n / nu", PB, "B",
+        lambda: [lambda th=th: PB.test_gradient_richardson(th) for th in ([1.3, 0.4, -0.7],)]),
+    # binned: the constraint without its factor 1/2 in the NLL
+    "binned_constraint_half": (
+        "binned.py", "nll = terms.sum() + 0.5 * np.sum(theta[cons] ** 2)", "nll = terms.sum() + np.sum(theta[cons] ** 2)",
+        PB, "B", lambda: [lambda th=th: PB.test_gradient_richardson(th) for th in ([1.3, 0.4, -0.7],)]),
+    # MLP: GELU with sqrt(2) replaced by 2
+    "mlp_gelu_scale": (
+        "mlp.py", "return 0.5 * z * (1.0 + erf(z / math.sqrt(2.0)))", "return 0.5 * z * (1.0 + erf(z / 2.0))",
+        PM, "M", lambda: [PM.test_gelu_matches_torch]),
+    # MLP: the backward pass through the weights with its columns reversed (a mis-indexed weight)
+    "mlp_backward_transpose": (
+        "mlp.py", "d = _r(dz, rounding) @ _r(W, rounding).T", "d = (_r(dz, rounding) @ _r(W, rounding).T)[:, ::-1]",
+        PM, "M", lambda: [PM.test_backward_matches_finite_differences]),
+    # MLP: Adam's first-moment bias correction with beta2
+    "mlp_adam_bias_correction": (
+        "mlp.py", "mh = m / (1 - b1 ** t)", "mh = m / (1 - b2 ** t)", PM, "M", lambda: [PM.test_adam_matches_torch]),
+    # MLP: bfloat16 rounding that always rounds half up
+    "mlp_bf16_ties": (
+        "mlp.py", "r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16", "r = ((u + 0x8000) >> 16) << 16",
+        PM, "M", lambda: [PM.test_bf16_rounding_matches_torch]),
+}
+
+
+@pytest.mark.parametrize("name", sorted(PY_MUTANTS))
+def test_pins_catch_a_planted_mistake_in_the_python_oracles(tmp_path, monkeypatch, name):
+    file, old, new, test_mod, attr, pins = PY_MUTANTS[name]
+    mod = load_mutant(tmp_path, old, new, file=file)
+    sub = importlib.import_module(f"{mod.__name__}.{file[:-3]}")
+    monkeypatch.setattr(test_mod, attr, sub)
+    failed = []
+    for pin in pins():
+        try:
+            pin()
+        except (AssertionError, RuntimeError, ValueError) as e:
+            failed.append(type(e).__name__)
+            break
+    assert failed, f"no pin noticed the planted mistake '{name}'"
 
 
 @pytest.mark.parametrize("name", sorted(MUTANTS))
@@ -129,3 +215,11 @@ def test_an_unplanted_copy_passes_the_same_pins(tmp_path):
     for name, (_, _, pins) in sorted(MUTANTS.items()):
         for pin in pins():
             pin(mod)
+
+
+def test_unplanted_python_oracles_pass_the_same_pins(tmp_path, monkeypatch):
+    mod = load_mutant(tmp_path, "TEST INFRASTRUCTURE ONLY.", "TEST INFRASTRUCTURE ONLY.")
+    for name, (file, _, _, test_mod, attr, pins) in sorted(PY_MUTANTS.items()):
+        monkeypatch.setattr(test_mod, attr, importlib.import_module(f"{mod.__name__}.{file[:-3]}"))
+        for pin in pins():
+            pin()
