@@ -16,6 +16,7 @@ from paper_2003_12861_gb300 import workloads as W
 import test_oracle_binned as PB
 import test_oracle_expr as PE
 import test_oracle_extended as PX
+import test_oracle_fit_pins as PF
 import test_oracle_mlp as PM
 import test_oracle_pins as P
 
@@ -126,6 +127,14 @@ MUTANTS = {
     "extended_derivative_sign": (
         "sg[fi].add(-(1.0 - (double)N / nu));", "sg[fi].add(-(1.0 + (double)N / nu));",
         lambda: [PX.test_extended_term_and_closed_form_mle]),
+    # covariance: the central difference of the gradient without its 2
+    "covariance_difference_step": (
+        "Hs[j * P + k] = (gp[j] - gm[j]) / (2.0 * hstep);", "Hs[j * P + k] = (gp[j] - gm[j]) / hstep;",
+        lambda: [PF.test_decay_fit_minimum_and_covariance]),
+    # generation: an accept-reject bound below the density's maximum
+    "generation_bound_too_low": (
+        "bounds[j] = 1.2 * mx;", "bounds[j] = 0.6 * mx;",
+        lambda: [lambda m: P.test_generator_matches_pdf_histogram(m, "decay_model")]),
     # fitter: the bound transform mapping onto half of the range
     "fit_bound_transform_scale": (
         "th[k] = bounded[k] ? lo[k] + (hi[k] - lo[k]) * (std::sin(x[k]) + 1.0) * 0.5 : x[k];",
