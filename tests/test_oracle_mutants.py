@@ -68,6 +68,20 @@ MUTANTS = {
         "  const double z = (s - u) / kSqrt2;\n  const double g = std::exp(-0.5 * u * u);",
         "  const double z = (u - s) / kSqrt2;\n  const double g = std::exp(-0.5 * u * u);",
         lambda: [lambda m, a=a: P.test_gaussexp_shape_is_the_convolution(m, *a) for a in CONV_PARAMS]),
+    # erfcx: the continued fraction's partial numerators one index off
+    "erfcx_continued_fraction_index": (
+        "for (int k = 400; k >= 1; --k) t = z + (0.5 * k) / t;",
+        "for (int k = 400; k >= 1; --k) t = z + (0.5 * (k + 1)) / t;",
+        lambda: [lambda m, a=a: P.test_gaussexp_shape_is_the_convolution(m, *a)
+                 for a in (([1.0, 0.5, 0.1], -0.4), ([1.0, 0.5, 0.05], -0.2))]),
+    # EXP: the series of the truncated exponential's mean with 1/6 for 1/12
+    "exp_mean_series_coefficient": (
+        "return 0.5 + y / 12.0 - y * y * y / 720.0;", "return 0.5 + y / 6.0 - y * y * y / 720.0;",
+        lambda: dnorm_pins("exp")),
+    # EXPR quadrature: Gauss-Legendre weights without their factor 2
+    "gauss_legendre_weights": (
+        "w[i] = 2.0 / ((1.0 - z * z) * dp * dp);", "w[i] = 1.0 / ((1.0 - z * z) * dp * dp);",
+        lambda: [lambda m, a=a: PE.test_expr_normalisation_closed_form(m, a) for a in (0.0, 0.7)]),
     # CHEB: the integral of T_k with 1 + k^2 for 1 - k^2
     "cheb_integral_sign": (
         "2.0 / (1.0 - (double)k * k)", "2.0 / (1.0 + (double)k * k)",
