@@ -5,7 +5,9 @@ A model is a computation graph of observables, parameters and PDFs
 event of a dataset in one fused pass on the GPU, fits by BFGS, generates
 toys and fits thousands of them at once.  Everything runs in the CUDA
 library ``librfgpu.so`` behind the C ABI of ``include/rf.h``; ``api`` only
-marshals arguments.  Build it first: ``python -m paper_2003_12861_gb300.build``.
+marshals arguments.  Build it first, from the repository root (the
+package is used in place, with the root on ``sys.path``):
+``python -m paper_2003_12861_gb300.build``.
 
 Example: f * Gauss(x; mu, sigma) + (1 - f) * (1 + a1 x) on x in [0, 10];
 the free parameters, in node order, are theta = (mu, sigma, a1, f)::
